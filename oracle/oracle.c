@@ -1,0 +1,717 @@
+/*
+ * Reference oracle for the ternary (and binary) flip-graph random walk.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes
+ * or calls this file; only the test-suite, the smoke check and the CPU
+ * baseline of the benchmark load it.  It shares no code, header, table or
+ * helper with the CUDA path.
+ *
+ * Representation: every factor vector is a plain array of int8 coefficients
+ * (the "straightforward approach" of Section 3.5, deliberately the slow one),
+ * every step is written out in the order of Algorithm 1 with the operators of
+ * Section 3.3, and no step is blocked, fused or reordered.
+ *
+ * Layout of a scheme (also the layout of the C ABI): term l occupies one row of
+ * LT = mn + np + pm int8 entries: u[i*n+k] (coefficient of a_ik), then
+ * v[k*p+j] (b_kj), then w[j*m+i] (c_ij, the C^T convention of Section 3.1).
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random
+ * Numbers: As Easy as 1, 2, 3", SC'11), written from that description.
+ *
+ * Pins (tests/test_oracle_*.py): Philox known-answer vectors of the Random123
+ * distribution; Brent validity of the paper's (2,2,3:11) example (Section
+ * 3.1.1), of the naive scheme and of a textbook Strassen scheme; the paper's
+ * sign-normalisation example (Section 3.6) reproduced exactly; the tensor
+ * invariant after every single step; brute-force candidate enumeration;
+ * closed-form ranks of the meta operators (Section 3.3.2).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+#define ORC_MODE_ZT 0
+#define ORC_MODE_Z2 1
+
+#define ORC_NOCAND 0
+#define ORC_REJECT 1
+#define ORC_ACCEPT 2
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, from the SC'11 paper: 10 rounds of two 32x32->64 multiplies */
+/* with the Weyl key schedule.                                                */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                       uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;   /* golden ratio */
+            k1 += 0xBB67AE85u;   /* sqrt(3) - 1 */
+        }
+        uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Range reduction of a 32-bit draw onto [0, n): multiply-shift. */
+static uint32_t mulhi_range(uint32_t x, uint32_t n)
+{
+    return (uint32_t)(((uint64_t)x * (uint64_t)n) >> 32);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Format                                                                     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int m, n, p, mode;
+    int len[3];   /* lengths of u, v, w */
+    int off[3];   /* offsets of u, v, w inside a term row */
+    int LT;       /* entries per term */
+} orc_fmt;
+
+static orc_fmt make_fmt(int m, int n, int p, int mode)
+{
+    orc_fmt f;
+    f.m = m; f.n = n; f.p = p; f.mode = mode;
+    f.len[0] = m * n; f.len[1] = n * p; f.len[2] = p * m;
+    f.off[0] = 0; f.off[1] = f.len[0]; f.off[2] = f.len[0] + f.len[1];
+    f.LT = f.len[0] + f.len[1] + f.len[2];
+    return f;
+}
+
+static int8_t *factor(const orc_fmt *f, int8_t *scheme, int term, int which)
+{
+    return scheme + (size_t)term * f->LT + f->off[which];
+}
+
+static int coeff_in_set(int c, int mode)
+{
+    if (mode == ORC_MODE_Z2) return c == 0 || c == 1;
+    return c >= -1 && c <= 1;
+}
+
+/* out = a + s*b, reduced mod 2 in Z_2; returns 1 when every entry stays in the
+ * coefficient set (Section 3.5.2: the validity flag of addition/subtraction). */
+static int vec_add(int8_t *out, const int8_t *a, const int8_t *b, int s, int L, int mode)
+{
+    int ok = 1;
+    for (int e = 0; e < L; ++e) {
+        int c = (int)a[e] + s * (int)b[e];
+        if (mode == ORC_MODE_Z2) c = ((c % 2) + 2) % 2;
+        if (!coeff_in_set(c, mode)) ok = 0;
+        out[e] = (int8_t)c;
+    }
+    return ok;
+}
+
+/* 1 when a == s*b entry-wise (Z_2: s is always +1). */
+static int vec_equal(const int8_t *a, const int8_t *b, int s, int L)
+{
+    for (int e = 0; e < L; ++e)
+        if ((int)a[e] != s * (int)b[e]) return 0;
+    return 1;
+}
+
+static int vec_is_zero(const int8_t *a, int L)
+{
+    for (int e = 0; e < L; ++e)
+        if (a[e] != 0) return 0;
+    return 1;
+}
+
+static void vec_negate(int8_t *a, int L)
+{
+    for (int e = 0; e < L; ++e) a[e] = (int8_t)(-a[e]);
+}
+
+static int first_nonzero(const int8_t *a, int L)
+{
+    for (int e = 0; e < L; ++e)
+        if (a[e] != 0) return a[e];
+    return 0;
+}
+
+/* Sign-symmetry breaking (Section 3.6), applied per term: the first non-zero
+ * coefficient of u and of v is made +1; w absorbs both signs.  This is the
+ * reading under which the paper's example (U,V,W) -> (U',V',W') holds. */
+static void canonicalize_term(const orc_fmt *f, int8_t *scheme, int t)
+{
+    if (f->mode != ORC_MODE_ZT) return;
+    int8_t *u = factor(f, scheme, t, 0), *v = factor(f, scheme, t, 1), *w = factor(f, scheme, t, 2);
+    if (first_nonzero(u, f->len[0]) < 0) { vec_negate(u, f->len[0]); vec_negate(w, f->len[2]); }
+    if (first_nonzero(v, f->len[1]) < 0) { vec_negate(v, f->len[1]); vec_negate(w, f->len[2]); }
+}
+
+void orc_canonicalize(int m, int n, int p, int mode, int r, int8_t *scheme)
+{
+    orc_fmt f = make_fmt(m, n, p, mode);
+    for (int t = 0; t < r; ++t) canonicalize_term(&f, scheme, t);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Brent equations, Eq. (1), in the C^T convention: the reconstructed tensor   */
+/* sum_l u_l (x) v_l (x) w_l must equal T with T[i*n+k][k*p+j][j*m+i] = 1.     */
+/* Exact integer arithmetic (mod 2 for Z_2).  Returns 1 when valid.            */
+/* ------------------------------------------------------------------------ */
+int orc_brent_valid(int m, int n, int p, int mode, int r, const int8_t *scheme)
+{
+    orc_fmt f = make_fmt(m, n, p, mode);
+    for (int i1 = 0; i1 < m; ++i1)
+    for (int i2 = 0; i2 < n; ++i2)
+    for (int j1 = 0; j1 < n; ++j1)
+    for (int j2 = 0; j2 < p; ++j2)
+    for (int k2 = 0; k2 < p; ++k2)
+    for (int k1 = 0; k1 < m; ++k1) {
+        long long sum = 0;
+        for (int l = 0; l < r; ++l) {
+            const int8_t *row = scheme + (size_t)l * f.LT;
+            sum += (long long)row[f.off[0] + i1 * n + i2]
+                 * (long long)row[f.off[1] + j1 * p + j2]
+                 * (long long)row[f.off[2] + k2 * m + k1];
+        }
+        long long rhs = (i2 == j1 && i1 == k1 && j2 == k2) ? 1 : 0;
+        if (mode == ORC_MODE_Z2) {
+            if ((((sum - rhs) % 2) + 2) % 2 != 0) return 0;
+        } else if (sum != rhs) {
+            return 0;
+        }
+    }
+    return 1;
+}
+
+/* Naive additive complexity (Section 4.5): nnz(U)+nnz(V)+nnz(W) - 2r - m*p. */
+long long orc_additive_complexity(int m, int n, int p, int r, const int8_t *scheme)
+{
+    orc_fmt f = make_fmt(m, n, p, ORC_MODE_ZT);
+    long long nnz = 0;
+    for (size_t e = 0; e < (size_t)r * f.LT; ++e) nnz += scheme[e] != 0;
+    return nnz - 2LL * r - (long long)m * p;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Walker state                                                               */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t plateau_len;     /* L: plateau length that triggers a plus transition */
+    uint32_t refresh_thresh; /* equal-rank best refresh when x2 < this (0.01 * 2^32) */
+    int32_t plus_attempts;   /* Philox sub-streams 1..plus_attempts */
+    int32_t plus_enabled;
+    int32_t debug_checks;    /* re-verify the invariants after every step */
+} orc_params;
+
+typedef struct {
+    int32_t r, best_r, r_max, pad;
+    int64_t t, plateau, best_t;
+    uint64_t digest;
+    int64_t accepted, rejected, nocand, drops, merges, plus, reductions;
+    int64_t debug_failures;
+} orc_info;
+
+typedef struct {
+    const orc_fmt *f;
+    const orc_params *prm;
+    int8_t *slots;           /* [r_max][LT] */
+    int8_t *best;            /* [r_max][LT] */
+    orc_info *info;
+    uint32_t walker_id;
+    uint32_t key[2];
+} walker;
+
+/* Digest: a 64-bit multiply-xorshift mix of one packed record per event. */
+static uint64_t digest_mix(uint64_t h, uint64_t v)
+{
+    h ^= v;
+    h *= 0x9E3779B97F4A7C15ull;
+    h ^= h >> 29;
+    return h;
+}
+
+uint64_t orc_digest_init(uint32_t walker_id)
+{
+    return 0xCBF29CE484222325ull ^ (uint64_t)walker_id;
+}
+
+/* Queue of modified terms awaiting reduction checks (at most three entries). */
+typedef struct { int item[8]; int len; } queue_t;
+
+static void q_push(queue_t *q, int v) { q->item[q->len++] = v; }
+static int q_pop_front(queue_t *q)
+{
+    int v = q->item[0];
+    for (int a = 1; a < q->len; ++a) q->item[a - 1] = q->item[a];
+    q->len--;
+    return v;
+}
+static void q_remove(queue_t *q, int v)
+{
+    int o = 0;
+    for (int a = 0; a < q->len; ++a)
+        if (q->item[a] != v) q->item[o++] = q->item[a];
+    q->len = o;
+}
+static void q_rename(queue_t *q, int from, int to)
+{
+    for (int a = 0; a < q->len; ++a)
+        if (q->item[a] == from) q->item[a] = to;
+}
+
+/* Remove the term in slot h: the last live term moves into the hole. */
+static void drop_slot(walker *wk, int h, queue_t *q)
+{
+    const orc_fmt *f = wk->f;
+    int last = wk->info->r - 1;
+    q_remove(q, h);
+    if (h != last) {
+        memcpy(wk->slots + (size_t)h * f->LT, wk->slots + (size_t)last * f->LT, (size_t)f->LT);
+        q_rename(q, last, h);
+    }
+    wk->info->r -= 1;
+}
+
+/* Reduction (Section 3.3.1) applied to "any permutation" of (u, v, w): terms t
+ * and k that share the factor pair P up to signs merge into one term whose
+ * third factor is F_t + sigma*F_k.  Pairs are tried in the order (u,v), (u,w),
+ * (v,w); within a pair the lowest slot k != t whose merged third factor stays
+ * in the coefficient set is taken.  Returns 1 when a merge happened. */
+static const int PAIR_A[3] = {0, 0, 1};
+static const int PAIR_B[3] = {1, 2, 2};
+static const int PAIR_F[3] = {2, 1, 0};
+
+static int try_reduce_term(walker *wk, int t, queue_t *q)
+{
+    const orc_fmt *f = wk->f;
+    int r = wk->info->r;
+    int8_t tmp[64];
+    int sgn[2] = {1, -1};
+    int nsg = (f->mode == ORC_MODE_Z2) ? 1 : 2;
+    for (int P = 0; P < 3; ++P) {
+        int A = PAIR_A[P], B = PAIR_B[P], F = PAIR_F[P];
+        for (int k = 0; k < r; ++k) {
+            if (k == t) continue;
+            for (int ia = 0; ia < nsg; ++ia)
+            for (int ib = 0; ib < nsg; ++ib) {
+                int a = sgn[ia], b = sgn[ib];
+                if (!vec_equal(factor(f, wk->slots, k, A), factor(f, wk->slots, t, A), a, f->len[A])) continue;
+                if (!vec_equal(factor(f, wk->slots, k, B), factor(f, wk->slots, t, B), b, f->len[B])) continue;
+                int sigma = a * b;
+                if (!vec_add(tmp, factor(f, wk->slots, t, F), factor(f, wk->slots, k, F), sigma,
+                             f->len[F], f->mode))
+                    continue;
+                /* merge: (A_t, B_t, F_t + sigma F_k) goes to slot min(t,k) */
+                int lo = t < k ? t : k, hi = t < k ? k : t;
+                if (lo != t)
+                    memcpy(wk->slots + (size_t)lo * f->LT, wk->slots + (size_t)t * f->LT, (size_t)f->LT);
+                memcpy(factor(f, wk->slots, lo, F), tmp, (size_t)f->len[F]);
+                q_remove(q, t);
+                q_remove(q, k);
+                drop_slot(wk, hi, q);
+                wk->info->merges += 1;
+                if (vec_is_zero(factor(f, wk->slots, lo, F), f->len[F])) {
+                    drop_slot(wk, lo, q);
+                    wk->info->drops += 1;
+                } else {
+                    canonicalize_term(f, wk->slots, lo);
+                    q_push(q, lo);
+                }
+                return 1;
+            }
+        }
+    }
+    return 0;
+}
+
+/* "Flip with reduction edge checking" (Section 3.4.1): every modified term is
+ * checked against every other term until no reduction applies. */
+static void reduction_cascade(walker *wk, queue_t *q)
+{
+    while (q->len > 0) {
+        int t = q_pop_front(q);
+        try_reduce_term(wk, t, q);
+    }
+}
+
+/* Candidate list of try_flip for the sampled term i: every j != i and factor X
+ * with X_j = s * X_i, each giving two flips (rho = 0, 1). */
+typedef struct { int X, j, s, rho; } cand_t;
+
+static int enumerate_candidates(const walker *wk, int i, cand_t *out)
+{
+    const orc_fmt *f = wk->f;
+    int r = wk->info->r, K = 0;
+    int nsg = (f->mode == ORC_MODE_Z2) ? 1 : 2;
+    int sgn[2] = {1, -1};
+    for (int X = 0; X < 3; ++X)
+        for (int j = 0; j < r; ++j) {
+            if (j == i) continue;
+            for (int is = 0; is < nsg; ++is) {
+                int s = sgn[is];
+                if (vec_equal(factor(f, wk->slots, j, X), factor(f, wk->slots, i, X), s, f->len[X])) {
+                    cand_t c0 = {X, j, s, 0}, c1 = {X, j, s, 1};
+                    out[K++] = c0;
+                    out[K++] = c1;
+                    break;
+                }
+            }
+        }
+    return K;
+}
+
+int orc_enumerate_candidates(int m, int n, int p, int mode, int r, const int8_t *scheme, int i,
+                             int32_t *out4 /* [K][4]: X, j, s, rho */)
+{
+    orc_fmt f = make_fmt(m, n, p, mode);
+    orc_info info; memset(&info, 0, sizeof info); info.r = r;
+    walker wk; memset(&wk, 0, sizeof wk);
+    wk.f = &f; wk.slots = (int8_t *)scheme; wk.info = &info;
+    cand_t *c = (cand_t *)malloc(sizeof(cand_t) * (size_t)(6 * r + 6));
+    int K = enumerate_candidates(&wk, i, c);
+    for (int a = 0; a < K; ++a) {
+        out4[4 * a + 0] = c[a].X; out4[4 * a + 1] = c[a].j;
+        out4[4 * a + 2] = c[a].s; out4[4 * a + 3] = c[a].rho;
+    }
+    free(c);
+    return K;
+}
+
+static void take_best(walker *wk)
+{
+    memcpy(wk->best, wk->slots, (size_t)wk->info->r * wk->f->LT);
+}
+
+/* ---- invariants for debug mode ---------------------------------------- */
+static int all_canonical(const walker *wk)
+{
+    const orc_fmt *f = wk->f;
+    if (f->mode != ORC_MODE_ZT) return 1;
+    for (int t = 0; t < wk->info->r; ++t) {
+        if (first_nonzero(factor(f, wk->slots, t, 0), f->len[0]) <= 0) return 0;
+        if (first_nonzero(factor(f, wk->slots, t, 1), f->len[1]) <= 0) return 0;
+    }
+    return 1;
+}
+
+static int no_zero_factor(const walker *wk)
+{
+    for (int t = 0; t < wk->info->r; ++t)
+        for (int X = 0; X < 3; ++X)
+            if (vec_is_zero(factor(wk->f, wk->slots, t, X), wk->f->len[X])) return 0;
+    return 1;
+}
+
+static int no_reducible_pair(walker *wk)
+{
+    const orc_fmt *f = wk->f;
+    int r = wk->info->r;
+    int8_t tmp[64];
+    int nsg = (f->mode == ORC_MODE_Z2) ? 1 : 2;
+    int sgn[2] = {1, -1};
+    for (int t = 0; t < r; ++t)
+        for (int k = t + 1; k < r; ++k)
+            for (int P = 0; P < 3; ++P)
+                for (int ia = 0; ia < nsg; ++ia)
+                    for (int ib = 0; ib < nsg; ++ib) {
+                        int A = PAIR_A[P], B = PAIR_B[P], F = PAIR_F[P];
+                        if (!vec_equal(factor(f, wk->slots, k, A), factor(f, wk->slots, t, A), sgn[ia], f->len[A])) continue;
+                        if (!vec_equal(factor(f, wk->slots, k, B), factor(f, wk->slots, t, B), sgn[ib], f->len[B])) continue;
+                        if (vec_add(tmp, factor(f, wk->slots, t, F), factor(f, wk->slots, k, F), sgn[ia] * sgn[ib], f->len[F], f->mode))
+                            return 0;
+                    }
+    return 1;
+}
+
+static void debug_check(walker *wk)
+{
+    const orc_fmt *f = wk->f;
+    if (!orc_brent_valid(f->m, f->n, f->p, f->mode, wk->info->r, wk->slots) ||
+        !all_canonical(wk) || !no_zero_factor(wk) || !no_reducible_pair(wk))
+        wk->info->debug_failures += 1;
+}
+
+/* Plus transition (Section 3.3.1) on a plateau: roles (A,B,C) are a
+ * permutation of (u,v,w); the pair (i, j) becomes three terms
+ *   A_i (x) (B_i + B_j) (x) C_i  +  A_i (x) B_j (x) (C_j - C_i)  +  (A_j - A_i) (x) B_j (x) C_j.
+ * Each of the three new factors must be non-zero and stay in the coefficient
+ * set.  Returns the attempt index (1-based) that succeeded, or 0. */
+static const int PERM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+static int try_plus(walker *wk, uint64_t t, int *pi_out, int *pj_out, int *perm_out)
+{
+    const orc_fmt *f = wk->f;
+    int r = wk->info->r;
+    if (r < 2) return 0;
+    for (int a = 1; a <= wk->prm->plus_attempts; ++a) {
+        uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(t >> 32), wk->walker_id, (uint32_t)a}, y[4];
+        orc_philox4x32_10(ctr, wk->key, y);
+        int i = (int)mulhi_range(y[0], (uint32_t)r);
+        int j = (int)((i + 1 + (int)mulhi_range(y[1], (uint32_t)(r - 1))) % r);
+        int pi = (int)mulhi_range(y[2], 6u);
+        int A = PERM[pi][0], B = PERM[pi][1], C = PERM[pi][2];
+        int8_t nb[64], nc[64], na[64];
+        int ok = vec_add(nb, factor(f, wk->slots, i, B), factor(f, wk->slots, j, B), +1, f->len[B], f->mode);
+        ok &= vec_add(nc, factor(f, wk->slots, j, C), factor(f, wk->slots, i, C), -1, f->len[C], f->mode);
+        ok &= vec_add(na, factor(f, wk->slots, j, A), factor(f, wk->slots, i, A), -1, f->len[A], f->mode);
+        if (!ok || vec_is_zero(nb, f->len[B]) || vec_is_zero(nc, f->len[C]) || vec_is_zero(na, f->len[A]))
+            continue;
+        int nt = r;
+        /* new term r: (A_j - A_i, B_j, C_j) */
+        memcpy(factor(f, wk->slots, nt, A), na, (size_t)f->len[A]);
+        memcpy(factor(f, wk->slots, nt, B), factor(f, wk->slots, j, B), (size_t)f->len[B]);
+        memcpy(factor(f, wk->slots, nt, C), factor(f, wk->slots, j, C), (size_t)f->len[C]);
+        /* term j: (A_i, B_j, C_j - C_i) */
+        memcpy(factor(f, wk->slots, j, A), factor(f, wk->slots, i, A), (size_t)f->len[A]);
+        memcpy(factor(f, wk->slots, j, C), nc, (size_t)f->len[C]);
+        /* term i: (A_i, B_i + B_j, C_i) */
+        memcpy(factor(f, wk->slots, i, B), nb, (size_t)f->len[B]);
+        wk->info->r = r + 1;
+        canonicalize_term(f, wk->slots, i);
+        canonicalize_term(f, wk->slots, j);
+        canonicalize_term(f, wk->slots, nt);
+        *pi_out = i; *pj_out = j; *perm_out = pi;
+        return a;
+    }
+    return 0;
+}
+
+/* Flip (Section 3.3.1) of candidate c on sampled term i, followed by the
+ * removal of zero terms, sign normalisation of the modified terms and the
+ * reduction cascade.  Returns ORC_ACCEPT, or ORC_REJECT when a new factor
+ * leaves the coefficient set (state unchanged). */
+static int apply_flip(walker *wk, int i, cand_t c)
+{
+    const orc_fmt *f = wk->f;
+    orc_info *in = wk->info;
+    int X = c.X, j = c.j, s = c.s;
+    /* (Y, Z) = the two other factors in cyclic order after X; rho swaps them */
+    int Y = (X + 1) % 3, Z = (X + 2) % 3;
+    if (c.rho) { int tmpf = Y; Y = Z; Z = tmpf; }
+    int8_t ny[64], nz[64];
+    int ok = vec_add(ny, factor(f, wk->slots, i, Y), factor(f, wk->slots, j, Y), +1, f->len[Y], f->mode);
+    ok &= vec_add(nz, factor(f, wk->slots, j, Z), factor(f, wk->slots, i, Z), -s, f->len[Z], f->mode);
+    if (!ok) {
+        in->rejected += 1;
+        return ORC_REJECT;
+    }
+    in->accepted += 1;
+    memcpy(factor(f, wk->slots, i, Y), ny, (size_t)f->len[Y]);
+    memcpy(factor(f, wk->slots, j, Z), nz, (size_t)f->len[Z]);
+    queue_t q; q.len = 0;
+    q_push(&q, i);
+    q_push(&q, j);
+    int zi = vec_is_zero(ny, f->len[Y]);
+    int zj = vec_is_zero(nz, f->len[Z]);
+    /* zero terms are removed, the higher slot first */
+    int hi = i > j ? i : j, lo = i > j ? j : i;
+    int zhi = (hi == i) ? zi : zj, zlo = (lo == i) ? zi : zj;
+    if (zhi) { drop_slot(wk, hi, &q); in->drops += 1; }
+    if (zlo) { drop_slot(wk, lo, &q); in->drops += 1; }
+    for (int a = 0; a < q.len; ++a) canonicalize_term(f, wk->slots, q.item[a]);
+    reduction_cascade(wk, &q);
+    return ORC_ACCEPT;
+}
+
+/* Test hook: apply one flip candidate (X, j, s, rho) on term i of a scheme of
+ * rank r held in a buffer of capacity >= r terms; returns the action, and the
+ * new rank through *r_out. */
+int orc_apply_flip(int m, int n, int p, int mode, int r, int8_t *scheme, int i,
+                   int X, int j, int s, int rho, int *r_out)
+{
+    orc_fmt f = make_fmt(m, n, p, mode);
+    orc_info info; memset(&info, 0, sizeof info); info.r = r;
+    walker wk; memset(&wk, 0, sizeof wk);
+    wk.f = &f; wk.slots = scheme; wk.info = &info;
+    cand_t c; c.X = X; c.j = j; c.s = s; c.rho = rho;
+    int action = apply_flip(&wk, i, c);
+    *r_out = info.r;
+    return action;
+}
+
+/* One step of the walk (Algorithm 1 with the plateau-triggered plus policy). */
+static void walk_step(walker *wk, cand_t *cbuf)
+{
+    orc_info *in = wk->info;
+    uint64_t t = (uint64_t)in->t;
+    uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(t >> 32), wk->walker_id, 0u}, x[4];
+    orc_philox4x32_10(ctr, wk->key, x);
+
+    int r_before = in->r;
+    int i = (int)mulhi_range(x[0], (uint32_t)in->r);
+    int K = enumerate_candidates(wk, i, cbuf);
+    int action = ORC_NOCAND, X = 0, j = 0, s = 1, rho = 0;
+    if (K > 0) {
+        cand_t c = cbuf[mulhi_range(x[1], (uint32_t)K)];
+        X = c.X; j = c.j; s = c.s; rho = c.rho;
+        action = apply_flip(wk, i, c);
+    } else {
+        in->nocand += 1;
+    }
+    if (in->r < r_before) in->reductions += 1;
+
+    uint64_t rec = (uint64_t)action | ((uint64_t)X << 4) | ((uint64_t)rho << 6) |
+                   ((uint64_t)(s < 0) << 7) | ((uint64_t)(uint32_t)i << 8) |
+                   ((uint64_t)(uint32_t)j << 24) | ((uint64_t)(uint32_t)in->r << 40);
+    in->digest = digest_mix(in->digest, rec);
+
+    /* best scheme: strictly better always, equal rank with probability 0.01 */
+    if (in->r < in->best_r) {
+        take_best(wk);
+        in->best_r = in->r;
+        in->best_t = (int64_t)t;
+        in->plateau = 0;
+    } else {
+        if (in->r == in->best_r && x[2] < wk->prm->refresh_thresh) take_best(wk);
+        in->plateau += 1;
+    }
+
+    /* plus transition after a plateau, restricted to rank <= best + 2 */
+    if (wk->prm->plus_enabled && in->plateau >= wk->prm->plateau_len &&
+        in->r <= in->best_r + 2 && in->r < in->r_max) {
+        int pi = 0, pj = 0, perm = 0;
+        int a = try_plus(wk, t, &pi, &pj, &perm);
+        if (a > 0) {
+            in->plus += 1;
+            in->plateau = 0;
+            queue_t q; q.len = 0;
+            q_push(&q, pi);
+            q_push(&q, pj);
+            q_push(&q, in->r - 1);
+            reduction_cascade(wk, &q);
+            uint64_t rec2 = 0xFull | ((uint64_t)a << 4) | ((uint64_t)perm << 9) |
+                            ((uint64_t)(uint32_t)pi << 12) | ((uint64_t)(uint32_t)pj << 28) |
+                            ((uint64_t)(uint32_t)in->r << 44);
+            in->digest = digest_mix(in->digest, rec2);
+        }
+    }
+    in->t += 1;
+    if (wk->prm->debug_checks) debug_check(wk);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Start preparation: canonicalise every term, remove terms with a zero        */
+/* factor, then run the reduction cascade over all terms in slot order.        */
+/* Returns the new rank (scheme rewritten in place).                           */
+/* ------------------------------------------------------------------------ */
+int orc_prepare_start(int m, int n, int p, int mode, int r, int8_t *scheme)
+{
+    orc_fmt f = make_fmt(m, n, p, mode);
+    orc_info info; memset(&info, 0, sizeof info);
+    info.r = r;
+    walker wk; memset(&wk, 0, sizeof wk);
+    wk.f = &f; wk.slots = scheme; wk.info = &info;
+    queue_t dummy; dummy.len = 0;
+    for (int t = r - 1; t >= 0; --t) {
+        int zero = 0;
+        for (int X = 0; X < 3; ++X) zero |= vec_is_zero(factor(&f, scheme, t, X), f.len[X]);
+        if (zero) drop_slot(&wk, t, &dummy);
+    }
+    for (int t = 0; t < info.r; ++t) canonicalize_term(&f, scheme, t);
+    /* full reduction passes: every slot in order enters the cascade, repeated
+     * until a whole pass merges nothing */
+    int64_t before;
+    do {
+        before = info.merges;
+        for (int t = 0; t < info.r; ++t) {
+            queue_t q; q.len = 0;
+            q_push(&q, t);
+            reduction_cascade(&wk, &q);
+        }
+    } while (info.merges != before);
+    return info.r;
+}
+
+/* Initialise walker records from a prepared start scheme of rank r0. */
+void orc_init_walkers(int m, int n, int p, int mode, int r0, const int8_t *start, int r_max,
+                      int n_walkers, const uint32_t *walker_ids,
+                      int8_t *slots, int8_t *best, orc_info *info)
+{
+    orc_fmt f = make_fmt(m, n, p, mode);
+    size_t per = (size_t)r_max * f.LT;
+    for (int w = 0; w < n_walkers; ++w) {
+        memset(slots + per * w, 0, per);
+        memset(best + per * w, 0, per);
+        memcpy(slots + per * w, start, (size_t)r0 * f.LT);
+        memcpy(best + per * w, start, (size_t)r0 * f.LT);
+        orc_info *in = info + w;
+        memset(in, 0, sizeof *in);
+        in->r = r0; in->best_r = r0; in->r_max = r_max;
+        in->digest = orc_digest_init(walker_ids[w]);
+    }
+}
+
+typedef struct {
+    const orc_fmt *f;
+    const orc_params *prm;
+    int r_max;
+    uint64_t seed;
+    int64_t steps;
+    int n_walkers;
+    const uint32_t *walker_ids;
+    int8_t *slots, *best;
+    orc_info *info;
+    int next;               /* shared work counter */
+    pthread_mutex_t lock;
+} job_t;
+
+static void run_walker(job_t *job, int w)
+{
+    const orc_fmt *f = job->f;
+    size_t per = (size_t)job->r_max * f->LT;
+    walker wk;
+    wk.f = f; wk.prm = job->prm;
+    wk.slots = job->slots + per * w;
+    wk.best = job->best + per * w;
+    wk.info = job->info + w;
+    wk.walker_id = job->walker_ids[w];
+    wk.key[0] = (uint32_t)job->seed;
+    wk.key[1] = (uint32_t)(job->seed >> 32);
+    cand_t *cbuf = (cand_t *)malloc(sizeof(cand_t) * (size_t)(6 * job->r_max + 6));
+    for (int64_t s = 0; s < job->steps; ++s) walk_step(&wk, cbuf);
+    free(cbuf);
+}
+
+static void *worker_main(void *arg)
+{
+    job_t *job = (job_t *)arg;
+    for (;;) {
+        pthread_mutex_lock(&job->lock);
+        int w = job->next++;
+        pthread_mutex_unlock(&job->lock);
+        if (w >= job->n_walkers) break;
+        run_walker(job, w);
+    }
+    return NULL;
+}
+
+/* Advance n_walkers walkers by `steps` steps each, one walker per thread at a
+ * time over n_threads threads.  State arrays are updated in place. */
+void orc_walk(int m, int n, int p, int mode, const orc_params *prm, int r_max, uint64_t seed,
+              int n_walkers, const uint32_t *walker_ids, int64_t steps, int n_threads,
+              int8_t *slots, int8_t *best, orc_info *info)
+{
+    orc_fmt f = make_fmt(m, n, p, mode);
+    job_t job;
+    job.f = &f; job.prm = prm; job.r_max = r_max; job.seed = seed; job.steps = steps;
+    job.n_walkers = n_walkers; job.walker_ids = walker_ids;
+    job.slots = slots; job.best = best; job.info = info; job.next = 0;
+    pthread_mutex_init(&job.lock, NULL);
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > n_walkers) n_threads = n_walkers > 0 ? n_walkers : 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    for (int a = 0; a < n_threads; ++a) pthread_create(&th[a], NULL, worker_main, &job);
+    for (int a = 0; a < n_threads; ++a) pthread_join(th[a], NULL);
+    free(th);
+    pthread_mutex_destroy(&job.lock);
+}
+
+int orc_info_size(void) { return (int)sizeof(orc_info); }
+int orc_params_size(void) { return (int)sizeof(orc_params); }
