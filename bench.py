@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark of the flip-graph walkers on GB300.
+
+Workload (default): the (3,3,3) populations from the naive rank-27 scheme,
+Z_T and Z_2, 65536 walkers each, plateau 5e4, uniform proposal.  One bench
+step = every walker advances `--chunk` steps (default 50,000; 20 bench steps
+make the full 1e6-step budget), then every walker's best scheme is checked
+against Eq. (1) on the device and the best scheme of each population is
+collected, re-verified on the host and copied out.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on
+the host cores on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "verified flips/sec and reductions per 1e9 flips at 1 GB300, learned vs uniform proposal"
+KERNEL_SRC = os.path.join(ROOT, "paper_2511_20317_gb300", "csrc", "walk_kernel.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "walk_kernel_333_dram_traffic.txt")
+
+# Algorithmic integer work per walker-step (word operations on 32-bit words):
+# candidate search 8 word tests per other slot in Z_T (u, v exact: 2 words each;
+# w exact or negated: 4), 3 in Z_2; the two new factors of a flip 2 x 9
+# (validity 3 + result 6) in Z_T, 2 XOR in Z_2; the reduction check of an
+# accepted flip re-tests both modified terms against every other slot; one
+# Philox4x32-10 draw of 10 rounds x 10 integer operations.
+C_SEARCH = {0: 8, 1: 3}
+C_FLIP = {0: 18, 1: 2}
+C_PHILOX = 100
+
+
+def algorithmic_ops(mode, steps, accepted, rejected, mean_r, word_mult=1):
+    cs = C_SEARCH[mode] * (mean_r - 1)
+    return word_mult * (steps * (cs + C_PHILOX) + (accepted + rejected) * C_FLIP[mode] + accepted * 2 * cs)
+
+
+def kernel_hash() -> str:
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def recorded_traffic():
+    """DRAM bytes per walk-kernel launch from the committed ncu summary, when it
+    was taken on the current kernel source (else None)."""
+    try:
+        kv = {}
+        for line in open(TRAFFIC_FILE):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_sha256_16") != kernel_hash():
+            return None
+        return float(kv["dram_bytes_per_launch_full_workload"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def populations(args):
+    from paper_2511_20317_gb300 import workloads as wl
+    if args.workload == "333":
+        return [((3, 3, 3), 0, wl.naive_start(3, 3, 3), args.walkers),
+                ((3, 3, 3), 1, wl.naive_start(3, 3, 3), args.walkers)], 50_000
+    if args.workload == "222":
+        return [((2, 2, 2), 0, wl.naive_start(2, 2, 2), 1024)], 10_000
+    if args.workload == "mixed":
+        w = wl.workload_mixed()
+        return [(p.fmt, 0, p.start_scheme(), p.walkers) for p in w.populations], 50_000
+    raise SystemExit(f"unknown workload {args.workload}")
+
+
+def dist_setup(args):
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2511_20317_gb300 import tfg
+    rank, world, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    pops, plateau = populations(args)
+    per_rank = sum(p[3] for p in pops)
+    params = tfg.tfg_default_params(plateau_len=plateau, walker_id_base=rank * per_rank)
+    if args.mapping:
+        params.mapping = args.mapping
+    W = tfg.Walkers(pops, seed=args.seed, params=params)
+    stream = W.stream
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+    fails = torch.zeros(1, dtype=torch.int64, device="cuda")
+    L = tfg.lib()
+    import ctypes
+
+    def step():
+        W.walk(args.chunk)
+        tfg._check(L.tfg_verify_all_async(W.ctx, ctypes.c_void_p(fails.data_ptr())))
+
+    def collect():
+        out = []
+        for f in range(W.n_formats):
+            out.append(W.collect_best(f)[1])
+        return out
+
+    for _ in range(args.warmup):
+        step()
+        collect()
+    st0, _ = W.stats()
+    st0_f = [W.stats(f)[0] for f in range(W.n_formats)]
+    W.sync()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    t_wall = time.perf_counter()
+    verify_failures = 0
+    best_ranks = None
+    for k in range(args.steps):
+        flush.zero_()                                # L2 flush between timed steps (untimed)
+        with torch.cuda.stream(stream):
+            ev[k][0].record(stream)
+            W.walk(args.chunk)
+            ev[k][1].record(stream)
+            tfg._check(L.tfg_verify_all_async(W.ctx, ctypes.c_void_p(fails.data_ptr())))
+        best_ranks = collect()                       # argmin + device and host verification + D2H
+        with torch.cuda.stream(stream):
+            ev[k][2].record(stream)
+        verify_failures += int(fails.item())
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    walk_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    t_total = sum(step_ms) / 1e3
+    st1, hist = W.stats()
+    walker_steps = st1["steps"] - st0["steps"]
+    assert walker_steps == per_rank * args.chunk * args.steps
+    # max over ranks
+    t_max = t_total
+    if world > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    total_steps = walker_steps * world
+    value = total_steps / t_max
+
+    # roofline of the walk kernel: algorithmic integer ops per launch / launch time
+    ops = 0.0
+    per_mode = {}
+    for f, (fmt, mode, _, nw) in enumerate(pops):
+        a0, a1 = st0_f[f], W.stats(f)[0]
+        info, _, _ = W.read_walkers(W.pop[f]["first"], min(nw, 4096), slots=False, best=False)
+        mean_r = float(info["r"].mean())
+        steps_f = a1["steps"] - a0["steps"]
+        acc, rej = a1["accepted"] - a0["accepted"], a1["rejected"] - a0["rejected"]
+        ops += algorithmic_ops(mode, steps_f, acc, rej, mean_r)
+        per_mode["ZT" if mode == 0 else "Z2"] = {
+            "lowest_rank": a1["min_best_r"], "mean_live_rank": round(mean_r, 2),
+            "rank_hist": {int(k): int(v) for k, v in enumerate(W.stats(f)[1]) if v},
+            "accepted_frac": round(acc / max(steps_f, 1), 4),
+            "reductions_per_1e9_flips": round((a1["reductions"] - a0["reductions"]) / max(steps_f, 1) * 1e9, 1),
+            "mapping": f"G={W.pop[f]['lanes']} S={W.pop[f]['slots_per_lane']}"}
+    walk_s = sum(walk_ms) / 1e3
+    achieved = ops / walk_s / 1e12          # Tops/s
+    alu_peak = 152 * 4 * 32 * 2.07e9 / 1e12  # one 32-lane integer warp instruction per SMSP per clock
+    traffic = recorded_traffic()
+
+    # end to end through the public API with host buffers, per step:
+    # init from the host start schemes, walk, verify, collect best to the host
+    e2e_steps = max(1, min(args.steps, 3))
+    h2d = sum(np.asarray(p[2]).nbytes for p in pops)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        E = tfg.Walkers(pops, seed=args.seed + 1, params=params)
+        E.walk(args.chunk)
+        E.verify_all()
+        for f in range(E.n_formats):
+            sch, r, w = E.collect_best(f)
+            d2h += sch.nbytes + 8
+        E.close()
+        del E
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    e2e_val = total_steps / args.steps * e2e_steps / e2e_t
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "flips/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic: naive rank-27 starts (catalogue starts unavailable)",
+        "config": {"workload": f"3x3x3 naive27 Z_T+Z_2, {args.walkers} walkers each, {args.chunk} steps "
+                               f"per walker per bench step (1e6 = full budget), plateau {plateau}",
+                   "walkers_per_gpu": per_rank, "steps_per_walker_per_step": args.chunk,
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"walker shards x{world}"},
+        "accepted_flips_per_s": None,
+        "modes": per_mode,
+        "verified": {"device_checked_best_schemes": per_rank * args.steps, "failures": verify_failures,
+                     "collected_best_ranks": best_ranks},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                     "frac": achieved / alu_peak, "traffic": traffic,
+                     "kernel": "walk_kernel", "walk_ms_per_step": sum(walk_ms) / len(walk_ms)},
+        "e2e": {"value": e2e_val, "unit": "flips/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h // e2e_steps},
+        "gpu_launches": (2 * W.n_formats + 2 * W.n_formats) * args.steps,
+        "clocks": clk,
+        "wall_s": wall,
+    }
+    sacc = sum(W.stats(f)[0]["accepted"] - st0_f[f]["accepted"] for f in range(W.n_formats))
+    line["accepted_flips_per_s"] = value * sacc / max(walker_steps, 1)
+    if rank == 0 and args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, pops, plateau, budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(args, pops, plateau, budget_s=15.0):
+    """The oracle as it stands, on the host cores, on a bounded sample of the
+    workload: walkers 0, 256, 512, ... of each population, `n` steps each."""
+    import oracle
+    threads = len(os.sched_getaffinity(0))
+    total_steps, total_t = 0, 0.0
+    n_w = max(threads, 16)
+    steps = 2000
+    for fmt, mode, start, nw in pops:
+        ids = np.arange(0, nw, max(1, nw // n_w))[:n_w]
+        W = oracle.Walkers(fmt, start, ids, seed=args.seed, mode=mode, plateau_len=plateau)
+        t0 = time.perf_counter()
+        W.walk(steps, threads)
+        dt = time.perf_counter() - t0
+        # scale the sample so that the timed CPU work is roughly budget_s per population
+        reps = max(1, int(budget_s / len(pops) / max(dt, 1e-3)) - 1)
+        t1 = time.perf_counter()
+        W.walk(steps * reps, threads)
+        dt += time.perf_counter() - t1
+        total_steps += ids.size * steps * (reps + 1)
+        total_t += dt
+    return {"value": total_steps / total_t, "unit": "flips/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n_w} walkers per population, the first steps of their trajectories, "
+                      f"{total_steps} walker-steps in {total_t:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_setup(args)
+    if rank != 0:
+        return
+    pops, plateau = populations(args)
+    cb = cpu_baseline(args, pops, plateau, budget_s=max(5.0, 40.0 / max(1, args.steps + args.warmup)))
+    # steps: each bench step re-times the bounded sample
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        vals.append(cpu_baseline(args, pops, plateau, budget_s=max(3.0, 60.0 / (args.steps + args.warmup)))["value"])
+    value = float(np.median(vals[args.warmup:])) if args.steps else cb["value"]
+    cb["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "flips/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i8", "data": "synthetic",
+            "config": {"workload": "3x3x3 naive27 Z_T+Z_2 (bounded sample on host cores)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "flips/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="333")
+    ap.add_argument("--walkers", type=int, default=65536)
+    ap.add_argument("--chunk", type=int, default=50_000)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--mapping", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * tfg.h - C ABI of the ternary flip-graph walker library (libtfg.so).
+ *
+ * The library runs many independent random walks over matrix-multiplication
+ * schemes (m,n,p:r) with coefficients in Z_T = {-1,0,1} (or Z_2) on one GPU
+ * (sm_103a): flips with ternary-safety rejection, zero-term and merge
+ * reductions, sign-symmetry normalisation, best-scheme tracking and
+ * plateau-triggered plus transitions (Sections 3.3-3.6, Algorithm 1 of
+ * "Fast Matrix Multiplication via Ternary Meta Flip Graphs").  The meta
+ * operators of Section 3.3.2 run on the host.
+ *
+ * Scheme layout (every int8_t* scheme argument): rank r rows of
+ * LT = m*n + n*p + p*m int8 coefficients; row l is u_l[i*n+k] (coefficient of
+ * a_ik), then v_l[k*p+j] (b_kj), then w_l[j*m+i] (c_ij): the C^T convention of
+ * Section 3.1, in which Eq. (1) reads
+ *     sum_l u_l[i*n+k] v_l[k'*p+j] w_l[j'*m+i'] = [k=k'][j=j'][i=i'].
+ * In Z_T mode coefficients are -1, 0, 1; in Z_2 mode 0, 1.  Every size
+ * m*n, n*p, p*m must be <= 64 (one machine word per factor, Section 4.1).
+ *
+ * Errors: every int-returning call returns TFG_OK (0) or a negative TFG_E*
+ * code; tfg_last_error() gives a message for the calling thread.  No call
+ * falls back to a CPU implementation of the walk: without a usable CUDA
+ * device the device calls fail with TFG_ECUDA.
+ *
+ * Memory: the library allocates no device memory.  The caller provides one
+ * device workspace per context (size from tfg_workspace_size), keeps it alive
+ * until tfg_destroy, and owns it.  Host buffers passed in are read or written
+ * during the call only, except where a call says otherwise.
+ */
+#ifndef TFG_H
+#define TFG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---------------------------------------------------------- */
+#define TFG_OK          0
+#define TFG_EINVAL     -1   /* bad argument: sizes, pointers, mode, capacity */
+#define TFG_ESCHEME    -2   /* coefficient outside the set, or Eq. (1) fails */
+#define TFG_ENOSPC     -3   /* caller buffer too small */
+#define TFG_ENOMEM     -4   /* host allocation failed / workspace too small */
+#define TFG_ECUDA      -5   /* CUDA runtime error (message in tfg_last_error) */
+#define TFG_ETIMEOUT   -6   /* a bounded device wait gave up */
+#define TFG_EINTERNAL  -7   /* an emitted scheme failed verification */
+
+#define TFG_MODE_ZT 0       /* coefficients in {-1, 0, 1} (Section 3.2) */
+#define TFG_MODE_Z2 1       /* binary field (Section 3.5, XOR arithmetic) */
+
+/* Format of one population: sizes of A (m x n) and B (n x p), and the mode. */
+typedef struct {
+    int32_t m, n, p;
+    int32_t mode;           /* TFG_MODE_ZT or TFG_MODE_Z2 */
+} tfg_format;
+
+/* Walk parameters.  tfg_default_params fills the defaults. */
+typedef struct {
+    int64_t plateau_len;      /* L: steps without a new best rank before a plus transition (default 10000) */
+    uint32_t refresh_thresh;  /* equal-rank best refresh when draw x2 < this; default 42949672 = 0.01 * 2^32
+                                 (the 1% acceptance of Algorithm 1); 0 disables */
+    int32_t plus_attempts;    /* plus transition tries per plateau event, Philox sub-streams 1.. (default 16) */
+    int32_t plus_enabled;     /* 1: plus transitions on plateaus (default), 0: never */
+    int32_t r_slack;          /* slots per walker = prepared start rank + r_slack (default 3, >= 1) */
+    int32_t mapping;          /* lanes per walker G in {4,8,16,32}; 0 = autotune (default) */
+    int32_t block_threads;    /* CUDA block size, multiple of 32, at most 256 (default 256) */
+    uint32_t walker_id_base;  /* global id of this context's first walker (sharding across GPUs) */
+    int32_t reserved[5];
+} tfg_params;
+
+/* Per-walker record.  t is the number of steps taken, digest a rolling hash of
+ * every step's action (sampled term, candidate, sign, rank), best_t the step at
+ * which best_r last fell.  Counters are cumulative. */
+typedef struct {
+    int32_t r, best_r, r_max, format;
+    int64_t t, plateau, best_t;
+    uint64_t digest;
+    int64_t accepted, rejected, nocand, drops, merges, plus, reductions;
+    uint32_t walker_id, pad;
+} tfg_walker_info;
+
+/* Aggregate counters over all walkers of a context (or of one format). */
+typedef struct {
+    int64_t walkers, steps, accepted, rejected, nocand, drops, merges, plus, reductions;
+    int32_t min_best_r, max_best_r;
+} tfg_stats;
+
+typedef struct tfg_ctx tfg_ctx;
+
+void tfg_default_params(tfg_params *out);
+const char *tfg_last_error(void);
+
+/* ---- host-only scheme functions ------------------------------------------ */
+
+/* Eq. (1), Section 3.1: exact integer reconstruction of sum_l u_l (x) v_l (x) w_l
+ * against the matrix-multiplication tensor (mod 2 in Z_2 mode).
+ * Returns TFG_OK when valid, TFG_ESCHEME when not, TFG_EINVAL on bad sizes. */
+int tfg_verify(const tfg_format *fmt, int32_t rank, const int8_t *scheme);
+
+/* Section 4.5: naive additive complexity nnz(U)+nnz(V)+nnz(W) - 2r - m*p. */
+int tfg_additive_complexity(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int64_t *out);
+
+/* Section 3.6: per term, make the first non-zero of u and of v equal +1, w
+ * absorbing the signs (in place; Z_T only, Z_2 unchanged). */
+int tfg_canonicalize(const tfg_format *fmt, int32_t rank, int8_t *scheme);
+
+/* Start preparation used by tfg_init: canonicalise, remove terms with a zero
+ * factor, then apply every reduction (Section 3.3.1, terms sharing two
+ * factors up to sign) until none applies.  out has room for `cap` terms;
+ * *out_rank receives the new rank.  Input must pass tfg_verify. */
+int tfg_prepare(const tfg_format *fmt, int32_t rank, const int8_t *scheme,
+                int8_t *out, int32_t cap, int32_t *out_rank);
+
+/* Meta operators, Section 3.3.2.  All are pure host functions writing into a
+ * caller buffer of `cap` terms (TFG_ENOSPC when too small); *out_fmt and
+ * *out_rank receive the result format and rank.  Outputs are sign-normalised
+ * (Z_T) and verified with Eq. (1) before returning (TFG_EINTERNAL if not).
+ * axis: 0 = m (rows of A and C), 1 = n (columns of A, rows of B),
+ *       2 = p (columns of B and C). */
+
+/* project: remove index `index` along `axis`, then remove terms with a zero factor. */
+int tfg_project(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int32_t axis, int32_t index,
+                tfg_format *out_fmt, int8_t *out, int32_t cap, int32_t *out_rank);
+/* extend: add one to a size by merging with the naive scheme of the new block
+ * ((m,n,p:r) -> (m,n,p+1:r+mn) for axis 2). */
+int tfg_extend(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int32_t axis,
+               tfg_format *out_fmt, int8_t *out, int32_t cap, int32_t *out_rank);
+/* merge: (m,n,p1:r1) + (m,n,p2:r2) -> (m,n,p1+p2:r1+r2) for axis 2, likewise for 0, 1.
+ * Scheme a's terms come first. */
+int tfg_merge(const tfg_format *fmt_a, int32_t rank_a, const int8_t *scheme_a,
+              const tfg_format *fmt_b, int32_t rank_b, const int8_t *scheme_b, int32_t axis,
+              tfg_format *out_fmt, int8_t *out, int32_t cap, int32_t *out_rank);
+/* double: merge a scheme with itself along `axis`. */
+int tfg_double(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int32_t axis,
+               tfg_format *out_fmt, int8_t *out, int32_t cap, int32_t *out_rank);
+/* product: tensor product (m1 m2, n1 n2, p1 p2 : r1 r2); term l1*r2 + l2, row index
+ * i1*m2 + i2 and likewise for the other indices. */
+int tfg_product(const tfg_format *fmt_a, int32_t rank_a, const int8_t *scheme_a,
+                const tfg_format *fmt_b, int32_t rank_b, const int8_t *scheme_b,
+                tfg_format *out_fmt, int8_t *out, int32_t cap, int32_t *out_rank);
+/* swap sizes: perm 0..5 gives the result order of (m,n,p):
+ * 0 (m,n,p), 1 (m,p,n) [the paper's swap], 2 (n,m,p), 3 (n,p,m), 4 (p,m,n), 5 (p,n,m). */
+int tfg_swap_sizes(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int32_t perm,
+                   tfg_format *out_fmt, int8_t *out, int32_t cap, int32_t *out_rank);
+
+/* ---- walker contexts (GPU) ------------------------------------------------ */
+
+/* Device workspace bytes for a context of n_formats populations.  ranks are
+ * the ranks of the prepared starts (tfg_prepare), walkers the population sizes. */
+int tfg_workspace_size(int32_t n_formats, const tfg_format *fmts, const int32_t *ranks,
+                       const int64_t *walkers, const tfg_params *params, size_t *bytes);
+
+/* Create a context of n_formats walker populations (mixed formats run in one
+ * call of tfg_walk).  schemes[f] is the start of population f (rank ranks[f],
+ * host memory, copied); it must pass tfg_verify; it is prepared with
+ * tfg_prepare, so workspace sizes must be computed from the prepared ranks.
+ * Walker ids are global: params->walker_id_base + position, populations
+ * contiguous in list order.  Walker w of population f draws its randomness
+ * from Philox4x32-10 with key (seed_lo, seed_hi) and counter (t_lo, t_hi, id,
+ * sub), so a trajectory depends only on (seed, id, step).
+ * d_workspace: caller-owned device memory of >= tfg_workspace_size bytes,
+ * 256-byte aligned.  cuda_stream: a cudaStream_t (NULL = legacy default
+ * stream); all device work of the context is ordered on it.  The call copies
+ * the starts to the device and returns after enqueueing (asynchronous). */
+int tfg_init(int32_t n_formats, const tfg_format *fmts, const int32_t *ranks,
+             const int8_t *const *schemes, const int64_t *walkers, uint64_t seed,
+             const tfg_params *params, void *d_workspace, size_t workspace_bytes,
+             void *cuda_stream, tfg_ctx **out);
+
+/* Advance every walker by `steps` steps (Algorithm 1 with the plateau policy:
+ * draw, try_flip, ternary check, zero-term removal, sign normalisation,
+ * reduction cascade, best update, plus transition).  Asynchronous on the
+ * context stream; errors of the launch are returned, errors of execution at
+ * the next tfg_sync. */
+int tfg_walk(tfg_ctx *ctx, int64_t steps);
+
+/* Wait for the context stream; returns the first CUDA error seen, if any. */
+int tfg_sync(tfg_ctx *ctx);
+
+/* Best scheme of population `format_idx`: the walker with the lowest best rank
+ * (ties: lowest walker id).  Copies it to `out` (cap terms), verifies it on
+ * the device and on the host (Eq. (1); TFG_EINTERNAL on failure) and reports
+ * its rank and global walker id.  Synchronous. */
+int tfg_collect_best(tfg_ctx *ctx, int32_t format_idx, int8_t *out, int32_t cap,
+                     int32_t *rank_out, int64_t *walker_out);
+
+/* Verify every walker's best scheme on the device (Eq. (1), exact integers).
+ * Asynchronous; *d_failures (device pointer, int64) receives the number of
+ * walkers whose best scheme fails (it is zeroed first). */
+int tfg_verify_all_async(tfg_ctx *ctx, int64_t *d_failures);
+
+/* Aggregate counters of population `format_idx` (-1 = all) and, when
+ * rank_hist != NULL, a histogram of best ranks: rank_hist[k] = walkers with
+ * best_r == k for k < hist_len.  Synchronous. */
+int tfg_stats_get(tfg_ctx *ctx, int32_t format_idx, tfg_stats *out, int64_t *rank_hist, int32_t hist_len);
+
+/* Copy walkers [first, first+count) (context-global positions) to the host:
+ * info[count]; slots and best (either may be NULL) as int8 schemes of
+ * [count][r_max][LT] of that walker's population (all walkers of the range
+ * must belong to one population).  Synchronous.  For parity checks and export. */
+int tfg_read_walkers(tfg_ctx *ctx, int64_t first, int64_t count, tfg_walker_info *info,
+                     int8_t *slots, int8_t *best, int32_t r_max_cap);
+
+/* Shape of population f: its format, prepared start rank, r_max, walker count
+ * and position of its first walker. */
+int tfg_population(tfg_ctx *ctx, int32_t f, tfg_format *fmt, int32_t *r0, int32_t *r_max,
+                   int64_t *walkers, int64_t *first);
+
+/* Checkpoint: copy the whole device state (all walkers) into a host buffer of
+ * cap bytes (*used receives the size; call with buf = NULL to query).  Restore
+ * writes it back into a context created with the same arguments; a restored
+ * walk continues bit-identically.  Synchronous. */
+int tfg_checkpoint(tfg_ctx *ctx, void *buf, size_t cap, size_t *used);
+int tfg_restore(tfg_ctx *ctx, const void *buf, size_t size);
+
+/* Mapping chosen for population f (lanes per walker G and slots per lane S). */
+int tfg_mapping(tfg_ctx *ctx, int32_t f, int32_t *lanes, int32_t *slots_per_lane);
+
+/* Release the context (host memory only; the workspace stays the caller's). */
+void tfg_destroy(tfg_ctx *ctx);
+
+/* Philox4x32-10 of the device path, for tests: d_out[4k..4k+3] = Philox(d_ctr[4k..4k+3],
+ * key), n counters; d_ctr and d_out are caller-owned device arrays of 4n words.
+ * Synchronous on cuda_stream. */
+int tfg_philox_device(const uint32_t *d_ctr, int32_t n, uint32_t key_lo, uint32_t key_hi, uint32_t *d_out,
+                      void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TFG_H */

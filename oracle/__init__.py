@@ -268,9 +268,10 @@ def naive_scheme(fmt) -> np.ndarray:
     return join_factors(U, V, W)
 
 
-def merge(fmt_a, scheme_a, fmt_b, scheme_b, axis):
+def merge(fmt_a, scheme_a, fmt_b, scheme_b, axis, mode=MODE_ZT):
     """Block concatenation along `axis` (0: m, 1: n, 2: p): two schemes that agree
-    on the other two sizes compute the two blocks; ranks add."""
+    on the other two sizes compute the two blocks; ranks add.  Section 3.6 keeps
+    every scheme sign-normalised after each transformation (Z_T)."""
     Ua, Va, Wa = split_factors(fmt_a, scheme_a)
     Ub, Vb, Wb = split_factors(fmt_b, scheme_b)
     ma, na, pa = fmt_a
@@ -296,23 +297,26 @@ def merge(fmt_a, scheme_a, fmt_b, scheme_b, axis):
     U[ra:, oi:oi + mb, ok:ok + nb] = Ub
     V[ra:, ok:ok + nb, oj:oj + pb] = Vb
     W[ra:, oj:oj + pb, oi:oi + mb] = Wb
-    return (m, n, p), join_factors(U, V, W)
+    out = join_factors(U, V, W)
+    if mode == MODE_ZT:
+        out = canonicalize((m, n, p), out, mode)
+    return (m, n, p), out
 
 
-def extend(fmt, scheme, axis):
+def extend(fmt, scheme, axis, mode=MODE_ZT):
     """Add one to a size by merging with the naive scheme of the missing block:
     (m,n,p:r) -> (m,n,p+1 : r+mn) along p, and likewise along m and n."""
     m, n, p = fmt
     block = [(1, n, p), (m, 1, p), (m, n, 1)][axis]
-    return merge(fmt, scheme, block, naive_scheme(block), axis)
+    return merge(fmt, scheme, block, naive_scheme(block), axis, mode)
 
 
-def double(fmt, scheme, axis):
+def double(fmt, scheme, axis, mode=MODE_ZT):
     """Merge a scheme with itself along `axis`."""
-    return merge(fmt, scheme, fmt, scheme, axis)
+    return merge(fmt, scheme, fmt, scheme, axis, mode)
 
 
-def product(fmt_a, scheme_a, fmt_b, scheme_b):
+def product(fmt_a, scheme_a, fmt_b, scheme_b, mode=MODE_ZT):
     """Tensor (Kronecker) product: (m1 m2, n1 n2, p1 p2 : r1 r2); term (l1, l2) is
     number l1*r2 + l2; row index i = i1*m2 + i2, and so on for k and j."""
     Ua, Va, Wa = split_factors(fmt_a, scheme_a)
@@ -342,7 +346,10 @@ def product(fmt_a, scheme_a, fmt_b, scheme_b):
                     for i1 in range(m1):
                         for i2 in range(m2):
                             W[l, j1 * p2 + j2, i1 * m2 + i2] = Wa[l1, j1, i1] * Wb[l2, j2, i2]
-    return (m, n, p), join_factors(U, V, W)
+    out = join_factors(U, V, W)
+    if mode == MODE_ZT:
+        out = canonicalize((m, n, p), out, mode)
+    return (m, n, p), out
 
 
 def transpose(fmt, scheme):

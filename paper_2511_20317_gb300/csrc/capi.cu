@@ -1,0 +1,561 @@
+// C ABI of libtfg: walker contexts on one GPU plus the host scheme functions.
+// Device memory is the caller's workspace; the library allocates none.
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "host_scheme.h"
+#include "tfg_internal.h"
+
+using tfg::host::HTerm;
+using tfg::host::set_error;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kHistCap = 1024;
+constexpr int kMaxSlots = 1023;   // per-lane match counts are packed in 10-bit fields
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Results of the small reduction kernels, at the start of the workspace.
+struct Aux {
+    unsigned long long argmin_key;
+    int64_t sums[9];
+    int32_t minmax[2];
+    int64_t verify_failures;
+    int64_t hist[kHistCap];
+};
+constexpr size_t kAuxBytes = (sizeof(Aux) + kAlign - 1) / kAlign * kAlign;
+
+struct Segment {
+    tfg_format fmt{};
+    int r0 = 0, R = 0, word_bits = 32, nwt = 6;
+    int64_t n = 0, first = 0;
+    size_t off_hdr = 0, off_slots = 0, off_best = 0, off_start = 0;
+    const tfg::WalkVariant *var = nullptr;
+    std::vector<int8_t> start_rows;
+};
+
+int nwt_of(const tfg_format &f) { return f.mode == TFG_MODE_ZT ? 6 : 3; }
+int word_bits_of(const tfg_format &f) {
+    return (f.m * f.n <= 32 && f.n * f.p <= 32 && f.p * f.m <= 32) ? 32 : 64;
+}
+
+// Lay out one segment at offset `off`; returns the offset past it.
+size_t layout_segment(Segment &s, size_t off) {
+    const size_t wb = (size_t)s.word_bits / 8;
+    const size_t per = (size_t)s.R * s.nwt * wb;
+    s.off_hdr = off;
+    off = align_up(off + (size_t)s.n * sizeof(tfg_walker_info));
+    s.off_slots = off;
+    off = align_up(off + (size_t)s.n * per);
+    s.off_best = off;
+    off = align_up(off + (size_t)s.n * per);
+    s.off_start = off;
+    off = align_up(off + per);
+    return off;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return TFG_ECUDA;
+}
+
+const tfg::WalkVariant *pick_variant(int mode, int bits, int G, int R) {
+    int cnt = 0;
+    const tfg::WalkVariant *v = tfg::walk_variants(&cnt);
+    const tfg::WalkVariant *best = nullptr;
+    for (int a = 0; a < cnt; ++a) {
+        if (v[a].mode != mode || v[a].word_bits != bits || v[a].G != G) continue;
+        if (v[a].G * v[a].S < R) continue;
+        if (!best || v[a].S < best->S) best = &v[a];
+    }
+    return best;
+}
+
+// Default mapping: the fewest lanes per walker that keep at most 4 slots per lane.
+const tfg::WalkVariant *default_variant(int mode, int bits, int R) {
+    static const int order[4] = {4, 8, 16, 32};
+    for (int G : order) {
+        const tfg::WalkVariant *v = pick_variant(mode, bits, G, R);
+        if (v && v->S <= 4) return v;
+    }
+    return pick_variant(mode, bits, 32, R);
+}
+
+}  // namespace
+
+struct tfg_ctx {
+    std::vector<Segment> segs;
+    tfg_params prm{};
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    char *ws = nullptr;
+    size_t ws_bytes = 0, ws_used = 0;
+    int64_t total = 0;
+    int device = 0;
+
+    tfg::SegDesc desc(const Segment &s) const {
+        tfg::SegDesc d{};
+        d.slots = ws + s.off_slots;
+        d.best = ws + s.off_best;
+        d.hdr = reinterpret_cast<tfg_walker_info *>(ws + s.off_hdr);
+        d.n_walkers = s.n;
+        d.R = s.R;
+        d.m = s.fmt.m; d.n = s.fmt.n; d.p = s.fmt.p;
+        d.key0 = (uint32_t)seed;
+        d.key1 = (uint32_t)(seed >> 32);
+        d.plateau_len = prm.plateau_len;
+        d.refresh_thresh = prm.refresh_thresh;
+        d.plus_attempts = prm.plus_attempts;
+        d.plus_enabled = prm.plus_enabled;
+        return d;
+    }
+    Aux *aux() const { return reinterpret_cast<Aux *>(ws); }
+};
+
+extern "C" {
+
+void tfg_default_params(tfg_params *out) {
+    if (!out) return;
+    std::memset(out, 0, sizeof *out);
+    out->plateau_len = 10000;
+    out->refresh_thresh = 42949672u;
+    out->plus_attempts = 16;
+    out->plus_enabled = 1;
+    out->r_slack = 3;
+    out->mapping = 0;
+    out->block_threads = 256;
+    out->walker_id_base = 0;
+}
+
+const char *tfg_last_error(void) { return tfg::host::last_error(); }
+
+int tfg_verify(const tfg_format *fmt, int32_t rank, const int8_t *scheme) {
+    return tfg::host::check_input(fmt, rank, scheme);
+}
+
+int tfg_additive_complexity(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int64_t *out) {
+    if (!tfg::host::format_ok(fmt) || !out || rank < 0 || (rank > 0 && !scheme)) {
+        set_error("bad arguments");
+        return TFG_EINVAL;
+    }
+    const int LT = tfg::host::term_len(*fmt);
+    int64_t nnz = 0;
+    for (int64_t e = 0; e < (int64_t)rank * LT; ++e) nnz += scheme[e] != 0;
+    *out = nnz - 2LL * rank - (int64_t)fmt->m * fmt->p;
+    return TFG_OK;
+}
+
+int tfg_canonicalize(const tfg_format *fmt, int32_t rank, int8_t *scheme) {
+    if (!tfg::host::format_ok(fmt)) { set_error("bad format"); return TFG_EINVAL; }
+    std::vector<HTerm> t;
+    int rc = tfg::host::parse(*fmt, rank, scheme, t);
+    if (rc) return rc;
+    for (HTerm &h : t) tfg::host::canon_term(*fmt, h);
+    tfg::host::emit(*fmt, t, scheme);
+    return TFG_OK;
+}
+
+int tfg_prepare(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int8_t *out, int32_t cap,
+                int32_t *out_rank) {
+    int rc = tfg::host::check_input(fmt, rank, scheme);
+    if (rc) return rc;
+    std::vector<HTerm> t;
+    tfg::host::parse(*fmt, rank, scheme, t);
+    tfg::host::prepare(*fmt, t);
+    if (out_rank) *out_rank = (int32_t)t.size();
+    if ((int)t.size() > cap) { set_error("output buffer too small"); return TFG_ENOSPC; }
+    if (!t.empty() && !out) { set_error("null output"); return TFG_EINVAL; }
+    tfg::host::emit(*fmt, t, out);
+    return TFG_OK;
+}
+
+int tfg_project(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int32_t axis, int32_t index,
+                tfg_format *out_fmt, int8_t *out, int32_t cap, int32_t *out_rank) {
+    return tfg::host::project(fmt, rank, scheme, axis, index, out_fmt, out, cap, out_rank);
+}
+int tfg_extend(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int32_t axis, tfg_format *out_fmt,
+               int8_t *out, int32_t cap, int32_t *out_rank) {
+    return tfg::host::extend(fmt, rank, scheme, axis, out_fmt, out, cap, out_rank);
+}
+int tfg_merge(const tfg_format *fa, int32_t ra, const int8_t *sa, const tfg_format *fb, int32_t rb,
+              const int8_t *sb, int32_t axis, tfg_format *out_fmt, int8_t *out, int32_t cap, int32_t *out_rank) {
+    return tfg::host::merge(fa, ra, sa, fb, rb, sb, axis, out_fmt, out, cap, out_rank);
+}
+int tfg_double(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int32_t axis, tfg_format *out_fmt,
+               int8_t *out, int32_t cap, int32_t *out_rank) {
+    return tfg::host::merge(fmt, rank, scheme, fmt, rank, scheme, axis, out_fmt, out, cap, out_rank);
+}
+int tfg_product(const tfg_format *fa, int32_t ra, const int8_t *sa, const tfg_format *fb, int32_t rb,
+                const int8_t *sb, tfg_format *out_fmt, int8_t *out, int32_t cap, int32_t *out_rank) {
+    return tfg::host::product(fa, ra, sa, fb, rb, sb, out_fmt, out, cap, out_rank);
+}
+int tfg_swap_sizes(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int32_t perm, tfg_format *out_fmt,
+                   int8_t *out, int32_t cap, int32_t *out_rank) {
+    return tfg::host::swap_sizes(fmt, rank, scheme, perm, out_fmt, out, cap, out_rank);
+}
+
+static int check_params(const tfg_params &p) {
+    if (p.plateau_len < 1 || p.plus_attempts < 0 || p.r_slack < 1 || p.block_threads < 32 ||
+        p.block_threads % 32 != 0 || p.block_threads > 256) {
+        set_error("bad parameters (plateau_len >= 1, r_slack >= 1, block_threads a multiple of 32 <= 256)");
+        return TFG_EINVAL;
+    }
+    if (p.mapping != 0 && p.mapping != 4 && p.mapping != 8 && p.mapping != 16 && p.mapping != 32) {
+        set_error("mapping must be 0 (auto), 4, 8, 16 or 32");
+        return TFG_EINVAL;
+    }
+    return TFG_OK;
+}
+
+static int plan_segments(int32_t n_formats, const tfg_format *fmts, const int32_t *ranks, const int64_t *walkers,
+                         const tfg_params &prm, std::vector<Segment> &segs, size_t *bytes) {
+    if (n_formats < 1 || !fmts || !ranks || !walkers) { set_error("need at least one population"); return TFG_EINVAL; }
+    segs.assign((size_t)n_formats, Segment{});
+    size_t off = kAuxBytes;
+    int64_t first = 0;
+    for (int f = 0; f < n_formats; ++f) {
+        Segment &s = segs[f];
+        if (!tfg::host::format_ok(&fmts[f])) { set_error("bad format " + std::to_string(f)); return TFG_EINVAL; }
+        if (ranks[f] < 1 || walkers[f] < 0) { set_error("bad rank or walker count"); return TFG_EINVAL; }
+        s.fmt = fmts[f];
+        s.r0 = ranks[f];
+        s.R = ranks[f] + prm.r_slack;
+        if (s.R > kMaxSlots) { set_error("rank + slack exceeds the supported 1023 slots"); return TFG_EINVAL; }
+        s.word_bits = word_bits_of(s.fmt);
+        s.nwt = nwt_of(s.fmt);
+        s.n = walkers[f];
+        s.first = first;
+        first += s.n;
+        if (first > (int64_t)UINT32_MAX) { set_error("more than 2^32 walkers"); return TFG_EINVAL; }
+        off = layout_segment(s, off);
+        s.var = prm.mapping ? pick_variant(s.fmt.mode, s.word_bits, prm.mapping, s.R)
+                            : default_variant(s.fmt.mode, s.word_bits, s.R);
+        if (!s.var) { set_error("no compiled kernel variant for this format/rank/mapping"); return TFG_EINVAL; }
+    }
+    *bytes = off;
+    return TFG_OK;
+}
+
+int tfg_workspace_size(int32_t n_formats, const tfg_format *fmts, const int32_t *ranks, const int64_t *walkers,
+                       const tfg_params *params, size_t *bytes) {
+    tfg_params prm;
+    if (params) prm = *params; else tfg_default_params(&prm);
+    int rc = check_params(prm);
+    if (rc) return rc;
+    if (!bytes) { set_error("null bytes"); return TFG_EINVAL; }
+    std::vector<Segment> segs;
+    return plan_segments(n_formats, fmts, ranks, walkers, prm, segs, bytes);
+}
+
+static void pack_terms(const Segment &s, const std::vector<HTerm> &t, std::vector<uint8_t> &buf) {
+    const size_t wb = (size_t)s.word_bits / 8;
+    buf.assign((size_t)s.R * s.nwt * wb, 0);
+    for (size_t l = 0; l < t.size(); ++l)
+        for (int x = 0; x < 3; ++x) {
+            uint64_t words[2] = {t[l].p[x], t[l].n[x]};
+            const int nw = s.nwt == 6 ? 2 : 1;
+            for (int q = 0; q < nw; ++q) {
+                const size_t idx = l * s.nwt + (size_t)x * nw + q;
+                if (wb == 4) {
+                    const uint32_t v = (uint32_t)words[q];
+                    std::memcpy(&buf[idx * 4], &v, 4);
+                } else {
+                    std::memcpy(&buf[idx * 8], &words[q], 8);
+                }
+            }
+        }
+}
+
+static void unpack_terms(const Segment &s, const uint8_t *words, int r, int8_t *rows) {
+    const size_t wb = (size_t)s.word_bits / 8;
+    std::vector<HTerm> t((size_t)r);
+    const int nw = s.nwt == 6 ? 2 : 1;
+    for (int l = 0; l < r; ++l)
+        for (int x = 0; x < 3; ++x)
+            for (int q = 0; q < nw; ++q) {
+                const size_t idx = (size_t)l * s.nwt + (size_t)x * nw + q;
+                uint64_t v = 0;
+                if (wb == 4) { uint32_t v32; std::memcpy(&v32, words + idx * 4, 4); v = v32; }
+                else std::memcpy(&v, words + idx * 8, 8);
+                (q == 0 ? t[l].p[x] : t[l].n[x]) = v;
+            }
+    tfg::host::emit(s.fmt, t, rows);
+}
+
+int tfg_init(int32_t n_formats, const tfg_format *fmts, const int32_t *ranks, const int8_t *const *schemes,
+             const int64_t *walkers, uint64_t seed, const tfg_params *params, void *d_workspace,
+             size_t workspace_bytes, void *cuda_stream, tfg_ctx **out) {
+    if (!out) { set_error("null out"); return TFG_EINVAL; }
+    *out = nullptr;
+    tfg_params prm;
+    if (params) prm = *params; else tfg_default_params(&prm);
+    int rc = check_params(prm);
+    if (rc) return rc;
+    if (n_formats < 1 || !fmts || !ranks || !schemes || !walkers) { set_error("null arguments"); return TFG_EINVAL; }
+    if (!d_workspace || ((uintptr_t)d_workspace % kAlign) != 0) { set_error("workspace must be 256-byte aligned device memory"); return TFG_EINVAL; }
+
+    // validate and prepare every start on the host
+    std::vector<std::vector<HTerm>> starts((size_t)n_formats);
+    std::vector<int32_t> r0((size_t)n_formats);
+    for (int f = 0; f < n_formats; ++f) {
+        rc = tfg::host::check_input(&fmts[f], ranks[f], schemes[f]);
+        if (rc) return rc;
+        tfg::host::parse(fmts[f], ranks[f], schemes[f], starts[f]);
+        tfg::host::prepare(fmts[f], starts[f]);
+        r0[f] = (int32_t)starts[f].size();
+        if (r0[f] < 1) { set_error("prepared start is empty"); return TFG_ESCHEME; }
+    }
+    auto *ctx = new tfg_ctx();
+    ctx->prm = prm;
+    ctx->seed = seed;
+    ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    ctx->ws = reinterpret_cast<char *>(d_workspace);
+    ctx->ws_bytes = workspace_bytes;
+    rc = plan_segments(n_formats, fmts, r0.data(), walkers, prm, ctx->segs, &ctx->ws_used);
+    if (rc) { delete ctx; return rc; }
+    if (ctx->ws_used > workspace_bytes) {
+        set_error("workspace holds " + std::to_string(workspace_bytes) + " bytes, need " + std::to_string(ctx->ws_used));
+        delete ctx;
+        return TFG_ENOMEM;
+    }
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "cudaGetDevice"); }
+    for (int f = 0; f < n_formats; ++f) {
+        Segment &s = ctx->segs[f];
+        s.first = (f == 0) ? 0 : ctx->segs[f - 1].first + ctx->segs[f - 1].n;
+        s.start_rows.resize((size_t)r0[f] * tfg::host::term_len(s.fmt));
+        tfg::host::emit(s.fmt, starts[f], s.start_rows.data());
+        std::vector<uint8_t> buf;
+        pack_terms(s, starts[f], buf);
+        e = cudaMemcpyAsync(ctx->ws + s.off_start, buf.data(), buf.size(), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "copy start"); }
+        tfg::launch_replicate(ctx->desc(s), ctx->ws + s.off_start, s.r0, prm.walker_id_base + (uint32_t)s.first, f,
+                              s.word_bits, s.nwt, ctx->stream);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "replicate launch"); }
+    }
+    ctx->total = ctx->segs.back().first + ctx->segs.back().n;
+    *out = ctx;
+    return TFG_OK;
+}
+
+int tfg_walk(tfg_ctx *ctx, int64_t steps) {
+    if (!ctx || steps < 0) { set_error("bad arguments"); return TFG_EINVAL; }
+    const int block = ctx->prm.block_threads;
+    while (steps > 0) {
+        const int32_t chunk = (int32_t)std::min<int64_t>(steps, 1 << 30);
+        for (const Segment &s : ctx->segs) {
+            if (s.n == 0) continue;
+            const int64_t threads = s.n * s.var->G;
+            const int64_t grid = (threads + block - 1) / block;
+            s.var->launch(ctx->desc(s), chunk, (int)grid, block, ctx->stream);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "walk launch");
+        steps -= chunk;
+    }
+    return TFG_OK;
+}
+
+int tfg_sync(tfg_ctx *ctx) {
+    if (!ctx) { set_error("null ctx"); return TFG_EINVAL; }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "device error");
+    return TFG_OK;
+}
+
+int tfg_population(tfg_ctx *ctx, int32_t f, tfg_format *fmt, int32_t *r0, int32_t *r_max, int64_t *walkers,
+                   int64_t *first) {
+    if (!ctx || f < 0 || f >= (int)ctx->segs.size()) { set_error("bad population index"); return TFG_EINVAL; }
+    const Segment &s = ctx->segs[f];
+    if (fmt) *fmt = s.fmt;
+    if (r0) *r0 = s.r0;
+    if (r_max) *r_max = s.R;
+    if (walkers) *walkers = s.n;
+    if (first) *first = s.first;
+    return TFG_OK;
+}
+
+int tfg_mapping(tfg_ctx *ctx, int32_t f, int32_t *lanes, int32_t *slots_per_lane) {
+    if (!ctx || f < 0 || f >= (int)ctx->segs.size()) { set_error("bad population index"); return TFG_EINVAL; }
+    if (lanes) *lanes = ctx->segs[f].var->G;
+    if (slots_per_lane) *slots_per_lane = ctx->segs[f].var->S;
+    return TFG_OK;
+}
+
+int tfg_verify_all_async(tfg_ctx *ctx, int64_t *d_failures) {
+    if (!ctx || !d_failures) { set_error("bad arguments"); return TFG_EINVAL; }
+    cudaError_t e = cudaMemsetAsync(d_failures, 0, sizeof(int64_t), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    for (const Segment &s : ctx->segs)
+        tfg::launch_verify_best(ctx->desc(s), 0, s.n, s.word_bits, s.fmt.mode, d_failures, ctx->stream);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "verify launch");
+    return TFG_OK;
+}
+
+int tfg_collect_best(tfg_ctx *ctx, int32_t format_idx, int8_t *out, int32_t cap, int32_t *rank_out,
+                     int64_t *walker_out) {
+    if (!ctx || format_idx < 0 || format_idx >= (int)ctx->segs.size()) { set_error("bad population index"); return TFG_EINVAL; }
+    const Segment &s = ctx->segs[format_idx];
+    if (s.n == 0) { set_error("empty population"); return TFG_EINVAL; }
+    Aux *aux = ctx->aux();
+    cudaError_t e = cudaMemsetAsync(&aux->argmin_key, 0xff, sizeof(aux->argmin_key), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    const tfg::SegDesc d = ctx->desc(s);
+    tfg::launch_argmin_best(d, &aux->argmin_key, ctx->stream);
+    unsigned long long key = 0;
+    e = cudaMemcpyAsync(&key, &aux->argmin_key, sizeof key, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy key");
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "argmin");
+    const int64_t w = (int64_t)(key & 0xffffffffull);
+    const int r = (int)(key >> 32);
+    // device check of the chosen walker's best scheme
+    e = cudaMemsetAsync(&aux->verify_failures, 0, sizeof(int64_t), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    tfg::launch_verify_best(d, w, 1, s.word_bits, s.fmt.mode, &aux->verify_failures, ctx->stream);
+    const size_t per = (size_t)s.R * s.nwt * (s.word_bits / 8);
+    std::vector<uint8_t> words(per);
+    int64_t dev_fail = 0;
+    e = cudaMemcpyAsync(words.data(), ctx->ws + s.off_best + per * w, per, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&dev_fail, &aux->verify_failures, sizeof dev_fail, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "collect best");
+    std::vector<int8_t> rows((size_t)r * tfg::host::term_len(s.fmt));
+    unpack_terms(s, words.data(), r, rows.data());
+    std::vector<HTerm> t;
+    const bool host_ok = tfg::host::parse(s.fmt, r, rows.data(), t) == TFG_OK && tfg::host::brent_ok(s.fmt, t);
+    if (rank_out) *rank_out = r;
+    if (walker_out) *walker_out = (int64_t)ctx->prm.walker_id_base + s.first + w;
+    if (!host_ok || dev_fail != 0) {
+        set_error("best scheme failed verification (host " + std::string(host_ok ? "ok" : "FAIL") + ", device " +
+                  std::string(dev_fail ? "FAIL" : "ok") + ")");
+        return TFG_EINTERNAL;
+    }
+    if (r > cap) { set_error("output buffer too small"); return TFG_ENOSPC; }
+    if (out) std::memcpy(out, rows.data(), rows.size());
+    return TFG_OK;
+}
+
+int tfg_stats_get(tfg_ctx *ctx, int32_t format_idx, tfg_stats *out, int64_t *rank_hist, int32_t hist_len) {
+    if (!ctx || !out || format_idx < -1 || format_idx >= (int)ctx->segs.size()) { set_error("bad arguments"); return TFG_EINVAL; }
+    if (rank_hist && (hist_len < 1 || hist_len > kHistCap)) { set_error("hist_len must be 1..1024"); return TFG_EINVAL; }
+    Aux *aux = ctx->aux();
+    cudaError_t e = cudaMemsetAsync(aux->sums, 0, sizeof(aux->sums), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&aux->minmax[0], 0x7f, sizeof(int32_t), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&aux->minmax[1], 0x80, sizeof(int32_t), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(aux->hist, 0, sizeof(aux->hist), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    for (int f = 0; f < (int)ctx->segs.size(); ++f) {
+        if (format_idx >= 0 && f != format_idx) continue;
+        tfg::launch_stats(ctx->desc(ctx->segs[f]), aux->sums, aux->minmax, aux->hist, kHistCap, ctx->stream);
+    }
+    Aux host;
+    e = cudaMemcpyAsync(&host, aux, sizeof(Aux), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stats");
+    out->walkers = host.sums[0];
+    out->steps = host.sums[1];
+    out->accepted = host.sums[2];
+    out->rejected = host.sums[3];
+    out->nocand = host.sums[4];
+    out->drops = host.sums[5];
+    out->merges = host.sums[6];
+    out->plus = host.sums[7];
+    out->reductions = host.sums[8];
+    out->min_best_r = host.minmax[0];
+    out->max_best_r = host.minmax[1];
+    if (rank_hist) std::memcpy(rank_hist, host.hist, sizeof(int64_t) * hist_len);
+    return TFG_OK;
+}
+
+int tfg_read_walkers(tfg_ctx *ctx, int64_t first, int64_t count, tfg_walker_info *info, int8_t *slots, int8_t *best,
+                     int32_t r_max_cap) {
+    if (!ctx || first < 0 || count < 0 || first + count > ctx->total) { set_error("walker range out of bounds"); return TFG_EINVAL; }
+    if (count == 0) return TFG_OK;
+    const Segment *sp = nullptr;
+    for (const Segment &s : ctx->segs)
+        if (first >= s.first && first + count <= s.first + s.n) sp = &s;
+    if (!sp) { set_error("walker range spans several populations"); return TFG_EINVAL; }
+    const Segment &s = *sp;
+    if ((slots || best) && r_max_cap < s.R) { set_error("r_max_cap smaller than the population's r_max"); return TFG_ENOSPC; }
+    const int64_t lo = first - s.first;
+    const size_t per = (size_t)s.R * s.nwt * (s.word_bits / 8);
+    const int LT = tfg::host::term_len(s.fmt);
+    std::vector<tfg_walker_info> hdr((size_t)count);
+    cudaError_t e = cudaMemcpyAsync(hdr.data(), ctx->ws + s.off_hdr + sizeof(tfg_walker_info) * lo,
+                                    sizeof(tfg_walker_info) * count, cudaMemcpyDeviceToHost, ctx->stream);
+    std::vector<uint8_t> ws, wb;
+    if (e == cudaSuccess && slots) {
+        ws.resize(per * count);
+        e = cudaMemcpyAsync(ws.data(), ctx->ws + s.off_slots + per * lo, per * count, cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (e == cudaSuccess && best) {
+        wb.resize(per * count);
+        e = cudaMemcpyAsync(wb.data(), ctx->ws + s.off_best + per * lo, per * count, cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "read walkers");
+    if (info) std::memcpy(info, hdr.data(), sizeof(tfg_walker_info) * count);
+    for (int64_t a = 0; a < count; ++a) {
+        if (slots) {
+            int8_t *dst = slots + (size_t)a * r_max_cap * LT;
+            std::memset(dst, 0, (size_t)r_max_cap * LT);
+            unpack_terms(s, ws.data() + per * a, std::min(hdr[a].r, s.R), dst);
+        }
+        if (best) {
+            int8_t *dst = best + (size_t)a * r_max_cap * LT;
+            std::memset(dst, 0, (size_t)r_max_cap * LT);
+            unpack_terms(s, wb.data() + per * a, std::min(hdr[a].best_r, s.R), dst);
+        }
+    }
+    return TFG_OK;
+}
+
+int tfg_checkpoint(tfg_ctx *ctx, void *buf, size_t cap, size_t *used) {
+    if (!ctx || !used) { set_error("bad arguments"); return TFG_EINVAL; }
+    const size_t n = ctx->ws_used - kAuxBytes;
+    *used = n;
+    if (!buf) return TFG_OK;
+    if (cap < n) { set_error("checkpoint buffer too small"); return TFG_ENOSPC; }
+    cudaError_t e = cudaMemcpyAsync(buf, ctx->ws + kAuxBytes, n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "checkpoint");
+    return TFG_OK;
+}
+
+int tfg_restore(tfg_ctx *ctx, const void *buf, size_t size) {
+    if (!ctx || !buf) { set_error("bad arguments"); return TFG_EINVAL; }
+    if (size != ctx->ws_used - kAuxBytes) { set_error("checkpoint size does not match this context"); return TFG_EINVAL; }
+    cudaError_t e = cudaMemcpyAsync(ctx->ws + kAuxBytes, buf, size, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "restore");
+    return TFG_OK;
+}
+
+void tfg_destroy(tfg_ctx *ctx) { delete ctx; }
+
+int tfg_philox_device(const uint32_t *d_ctr, int32_t n, uint32_t key_lo, uint32_t key_hi, uint32_t *d_out,
+                      void *cuda_stream) {
+    if (n < 0 || (n > 0 && (!d_ctr || !d_out))) { set_error("bad arguments"); return TFG_EINVAL; }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    tfg::launch_philox(d_ctr, n, key_lo, key_hi, d_out, st);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "philox");
+    return TFG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,43 @@
+// Host-side scheme representation used by the C ABI implementation.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tfg.h"
+
+namespace tfg {
+namespace host {
+
+// One term: positive and negative coefficient masks of u, v, w (Z_2: p only).
+struct HTerm {
+    uint64_t p[3] = {0, 0, 0};
+    uint64_t n[3] = {0, 0, 0};
+};
+
+void set_error(const std::string &s);
+const char *last_error();
+
+bool format_ok(const tfg_format *f);
+int factor_len(const tfg_format &f, int x);
+int term_len(const tfg_format &f);
+int parse(const tfg_format &f, int rank, const int8_t *rows, std::vector<HTerm> &out);
+void emit(const tfg_format &f, const std::vector<HTerm> &t, int8_t *rows);
+bool brent_ok(const tfg_format &f, const std::vector<HTerm> &t);
+void canon_term(const tfg_format &f, HTerm &h);
+void prepare(const tfg_format &f, std::vector<HTerm> &t);
+int check_input(const tfg_format *f, int rank, const int8_t *rows);
+
+int project(const tfg_format *f, int r, const int8_t *rows, int axis, int index, tfg_format *of, int8_t *out,
+            int cap, int *orank);
+int merge(const tfg_format *fa, int ra, const int8_t *sa, const tfg_format *fb, int rb, const int8_t *sb, int axis,
+          tfg_format *of, int8_t *out, int cap, int *orank);
+int extend(const tfg_format *f, int r, const int8_t *rows, int axis, tfg_format *of, int8_t *out, int cap,
+           int *orank);
+int product(const tfg_format *fa, int ra, const int8_t *sa, const tfg_format *fb, int rb, const int8_t *sb,
+            tfg_format *of, int8_t *out, int cap, int *orank);
+int swap_sizes(const tfg_format *f, int r, const int8_t *rows, int perm, tfg_format *of, int8_t *out, int cap,
+               int *orank);
+
+}  // namespace host
+}  // namespace tfg

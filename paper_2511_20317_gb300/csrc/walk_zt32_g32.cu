@@ -1,0 +1,15 @@
+// Walk kernel variants: mode ZT, 32-bit words, 32 lanes per walker.
+#include "walk_kernel.cuh"
+
+namespace tfg {
+const WalkVariant *walk_variants_zt32_g32(int *n) {
+    static const WalkVariant v[] = {
+        TFG_WALK_VARIANT(TFG_MODE_ZT, uint32_t, 32, 32, 1),
+        TFG_WALK_VARIANT(TFG_MODE_ZT, uint32_t, 32, 32, 2),
+        TFG_WALK_VARIANT(TFG_MODE_ZT, uint32_t, 32, 32, 3),
+        TFG_WALK_VARIANT(TFG_MODE_ZT, uint32_t, 32, 32, 4),
+    };
+    *n = (int)(sizeof(v) / sizeof(v[0]));
+    return v;
+}
+}  // namespace tfg

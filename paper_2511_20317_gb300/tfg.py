@@ -1,0 +1,371 @@
+"""Python binding of libtfg (include/tfg.h): argument marshalling only.
+
+Every function named ``tfg_*`` here calls the C function of the same name.
+PyTorch provides the device workspace and the CUDA stream; every step of the
+walk runs in the library's CUDA kernels.  There is no CPU fallback: if
+libtfg.so is missing or CUDA is unavailable, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtfg.so")
+
+TFG_OK, TFG_EINVAL, TFG_ESCHEME, TFG_ENOSPC, TFG_ENOMEM, TFG_ECUDA, TFG_ETIMEOUT, TFG_EINTERNAL = 0, -1, -2, -3, -4, -5, -6, -7
+TFG_MODE_ZT, TFG_MODE_Z2 = 0, 1
+ERROR_NAMES = {0: "TFG_OK", -1: "TFG_EINVAL", -2: "TFG_ESCHEME", -3: "TFG_ENOSPC", -4: "TFG_ENOMEM",
+               -5: "TFG_ECUDA", -6: "TFG_ETIMEOUT", -7: "TFG_EINTERNAL"}
+
+
+class TfgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class tfg_format(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("n", ctypes.c_int32), ("p", ctypes.c_int32), ("mode", ctypes.c_int32)]
+
+
+class tfg_params(ctypes.Structure):
+    _fields_ = [("plateau_len", ctypes.c_int64), ("refresh_thresh", ctypes.c_uint32),
+                ("plus_attempts", ctypes.c_int32), ("plus_enabled", ctypes.c_int32),
+                ("r_slack", ctypes.c_int32), ("mapping", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("walker_id_base", ctypes.c_uint32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class tfg_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("walkers", "steps", "accepted", "rejected", "nocand", "drops",
+                                              "merges", "plus", "reductions")] + \
+               [("min_best_r", ctypes.c_int32), ("max_best_r", ctypes.c_int32)]
+
+
+WALKER_INFO_DTYPE = np.dtype([("r", np.int32), ("best_r", np.int32), ("r_max", np.int32), ("format", np.int32),
+                              ("t", np.int64), ("plateau", np.int64), ("best_t", np.int64),
+                              ("digest", np.uint64),
+                              ("accepted", np.int64), ("rejected", np.int64), ("nocand", np.int64),
+                              ("drops", np.int64), ("merges", np.int64), ("plus", np.int64),
+                              ("reductions", np.int64), ("walker_id", np.uint32), ("pad", np.uint32)])
+
+# every symbol include/tfg.h declares
+EXPORTED = ["tfg_default_params", "tfg_last_error", "tfg_verify", "tfg_additive_complexity", "tfg_canonicalize",
+            "tfg_prepare", "tfg_project", "tfg_extend", "tfg_merge", "tfg_double", "tfg_product",
+            "tfg_swap_sizes", "tfg_workspace_size", "tfg_init", "tfg_walk", "tfg_sync", "tfg_collect_best",
+            "tfg_verify_all_async", "tfg_stats_get", "tfg_read_walkers", "tfg_population", "tfg_checkpoint",
+            "tfg_restore", "tfg_mapping", "tfg_destroy", "tfg_philox_device"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib() -> ctypes.CDLL:
+    """Load libtfg.so (built by __graft_entry__.build() or paper_2511_20317_gb300._build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libtfg.so not built ({LIB_PATH}); run paper_2511_20317_gb300._build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            P, i32, i64, u32, u64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                         ctypes.c_uint64, ctypes.c_size_t)
+            F = ctypes.POINTER(tfg_format)
+            sig = {
+                "tfg_default_params": (None, [ctypes.POINTER(tfg_params)]),
+                "tfg_last_error": (ctypes.c_char_p, []),
+                "tfg_verify": (i32, [F, i32, P]),
+                "tfg_additive_complexity": (i32, [F, i32, P, ctypes.POINTER(ctypes.c_int64)]),
+                "tfg_canonicalize": (i32, [F, i32, P]),
+                "tfg_prepare": (i32, [F, i32, P, P, i32, ctypes.POINTER(ctypes.c_int32)]),
+                "tfg_project": (i32, [F, i32, P, i32, i32, F, P, i32, ctypes.POINTER(ctypes.c_int32)]),
+                "tfg_extend": (i32, [F, i32, P, i32, F, P, i32, ctypes.POINTER(ctypes.c_int32)]),
+                "tfg_merge": (i32, [F, i32, P, F, i32, P, i32, F, P, i32, ctypes.POINTER(ctypes.c_int32)]),
+                "tfg_double": (i32, [F, i32, P, i32, F, P, i32, ctypes.POINTER(ctypes.c_int32)]),
+                "tfg_product": (i32, [F, i32, P, F, i32, P, F, P, i32, ctypes.POINTER(ctypes.c_int32)]),
+                "tfg_swap_sizes": (i32, [F, i32, P, i32, F, P, i32, ctypes.POINTER(ctypes.c_int32)]),
+                "tfg_workspace_size": (i32, [i32, F, P, P, ctypes.POINTER(tfg_params), ctypes.POINTER(sz)]),
+                "tfg_init": (i32, [i32, F, P, P, P, u64, ctypes.POINTER(tfg_params), P, sz, P,
+                                   ctypes.POINTER(P)]),
+                "tfg_walk": (i32, [P, i64]),
+                "tfg_sync": (i32, [P]),
+                "tfg_collect_best": (i32, [P, i32, P, i32, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int64)]),
+                "tfg_verify_all_async": (i32, [P, P]),
+                "tfg_stats_get": (i32, [P, i32, ctypes.POINTER(tfg_stats), P, i32]),
+                "tfg_read_walkers": (i32, [P, i64, i64, P, P, P, i32]),
+                "tfg_population": (i32, [P, i32, F, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+                "tfg_checkpoint": (i32, [P, P, sz, ctypes.POINTER(sz)]),
+                "tfg_restore": (i32, [P, P, sz]),
+                "tfg_mapping": (i32, [P, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+                "tfg_destroy": (None, [P]),
+                "tfg_philox_device": (i32, [P, i32, u32, u32, P, P]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != TFG_OK:
+        raise TfgError(rc, lib().tfg_last_error().decode(errors="replace"))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _fmt(fmt, mode=TFG_MODE_ZT) -> tfg_format:
+    if isinstance(fmt, tfg_format):
+        return fmt
+    m, n, p = fmt[:3]
+    return tfg_format(int(m), int(n), int(p), int(fmt[3] if len(fmt) > 3 else mode))
+
+
+def term_len(fmt) -> int:
+    m, n, p = fmt[:3]
+    return m * n + n * p + p * m
+
+
+def _rows(fmt, scheme) -> np.ndarray:
+    return np.ascontiguousarray(scheme, dtype=np.int8).reshape(-1, term_len(fmt))
+
+
+# ---------------------------------------------------------------------------------------------
+# host functions
+# ---------------------------------------------------------------------------------------------
+def tfg_default_params(**overrides) -> tfg_params:
+    p = tfg_params()
+    lib().tfg_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def tfg_verify(fmt, scheme, mode=TFG_MODE_ZT) -> bool:
+    s = _rows(fmt, scheme)
+    rc = lib().tfg_verify(ctypes.byref(_fmt(fmt, mode)), s.shape[0], _ptr(s))
+    if rc in (TFG_OK, TFG_ESCHEME):
+        return rc == TFG_OK
+    _check(rc)
+
+
+def tfg_additive_complexity(fmt, scheme) -> int:
+    s = _rows(fmt, scheme)
+    out = ctypes.c_int64()
+    _check(lib().tfg_additive_complexity(ctypes.byref(_fmt(fmt)), s.shape[0], _ptr(s), ctypes.byref(out)))
+    return out.value
+
+
+def tfg_canonicalize(fmt, scheme, mode=TFG_MODE_ZT) -> np.ndarray:
+    s = _rows(fmt, scheme).copy()
+    _check(lib().tfg_canonicalize(ctypes.byref(_fmt(fmt, mode)), s.shape[0], _ptr(s)))
+    return s
+
+
+def tfg_prepare(fmt, scheme, mode=TFG_MODE_ZT) -> np.ndarray:
+    s = _rows(fmt, scheme)
+    out = np.zeros_like(s)
+    r = ctypes.c_int32()
+    _check(lib().tfg_prepare(ctypes.byref(_fmt(fmt, mode)), s.shape[0], _ptr(s), _ptr(out), s.shape[0],
+                             ctypes.byref(r)))
+    return out[: r.value].copy()
+
+
+def _meta_call(name, args, cap_terms, out_lt_max=192):
+    out_fmt = tfg_format()
+    out = np.zeros((max(cap_terms, 1), out_lt_max), dtype=np.int8)
+    r = ctypes.c_int32()
+    _check(getattr(lib(), name)(*args, ctypes.byref(out_fmt), _ptr(out), max(cap_terms, 1), ctypes.byref(r)))
+    f = (out_fmt.m, out_fmt.n, out_fmt.p)
+    LT = term_len(f)
+    # the library wrote rows of LT entries contiguously
+    flat = out.reshape(-1)[: r.value * LT].reshape(r.value, LT).copy()
+    return f, flat
+
+
+def tfg_project(fmt, scheme, axis, index, mode=TFG_MODE_ZT):
+    s = _rows(fmt, scheme)
+    return _meta_call("tfg_project", [ctypes.byref(_fmt(fmt, mode)), s.shape[0], _ptr(s), axis, index], s.shape[0])
+
+
+def tfg_extend(fmt, scheme, axis, mode=TFG_MODE_ZT):
+    s = _rows(fmt, scheme)
+    m, n, p = fmt[:3]
+    cap = s.shape[0] + [n * p, m * p, m * n][axis]
+    return _meta_call("tfg_extend", [ctypes.byref(_fmt(fmt, mode)), s.shape[0], _ptr(s), axis], cap)
+
+
+def tfg_merge(fmt_a, scheme_a, fmt_b, scheme_b, axis, mode=TFG_MODE_ZT):
+    a, b = _rows(fmt_a, scheme_a), _rows(fmt_b, scheme_b)
+    return _meta_call("tfg_merge", [ctypes.byref(_fmt(fmt_a, mode)), a.shape[0], _ptr(a),
+                                    ctypes.byref(_fmt(fmt_b, mode)), b.shape[0], _ptr(b), axis],
+                      a.shape[0] + b.shape[0])
+
+
+def tfg_double(fmt, scheme, axis, mode=TFG_MODE_ZT):
+    s = _rows(fmt, scheme)
+    return _meta_call("tfg_double", [ctypes.byref(_fmt(fmt, mode)), s.shape[0], _ptr(s), axis], 2 * s.shape[0])
+
+
+def tfg_product(fmt_a, scheme_a, fmt_b, scheme_b, mode=TFG_MODE_ZT):
+    a, b = _rows(fmt_a, scheme_a), _rows(fmt_b, scheme_b)
+    return _meta_call("tfg_product", [ctypes.byref(_fmt(fmt_a, mode)), a.shape[0], _ptr(a),
+                                      ctypes.byref(_fmt(fmt_b, mode)), b.shape[0], _ptr(b)],
+                      a.shape[0] * b.shape[0])
+
+
+def tfg_swap_sizes(fmt, scheme, perm, mode=TFG_MODE_ZT):
+    s = _rows(fmt, scheme)
+    return _meta_call("tfg_swap_sizes", [ctypes.byref(_fmt(fmt, mode)), s.shape[0], _ptr(s), perm], s.shape[0])
+
+
+def tfg_philox_device(ctr: np.ndarray, key_lo: int, key_hi: int) -> np.ndarray:
+    import torch
+    c = torch.from_numpy(np.ascontiguousarray(ctr, dtype=np.uint32).view(np.int32)).cuda()
+    out = torch.empty_like(c)
+    _check(lib().tfg_philox_device(ctypes.c_void_p(c.data_ptr()), c.numel() // 4, key_lo, key_hi,
+                                   ctypes.c_void_p(out.data_ptr()),
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return out.cpu().numpy().view(np.uint32)
+
+
+# ---------------------------------------------------------------------------------------------
+# walker contexts
+# ---------------------------------------------------------------------------------------------
+class Walkers:
+    """A context of walker populations on the current CUDA device.
+
+    populations: list of (fmt (m,n,p), mode, start scheme int8 [r, LT], n_walkers).
+    The device workspace is a torch uint8 tensor owned by this object; all work
+    is ordered on `stream` (default: torch's current stream)."""
+
+    def __init__(self, populations, seed: int, params: tfg_params | None = None, stream=None):
+        import torch
+        self.torch = torch
+        L = lib()
+        self.params = params if params is not None else tfg_default_params()
+        nf = len(populations)
+        self.fmts = (tfg_format * nf)()
+        prepared, ranks, walkers = [], (ctypes.c_int32 * nf)(), (ctypes.c_int64 * nf)()
+        for a, (fmt, mode, start, nw) in enumerate(populations):
+            self.fmts[a] = _fmt(fmt, mode)
+            st = tfg_prepare(fmt, start, mode)  # validates and reports the prepared rank
+            prepared.append(_rows(fmt, start))
+            ranks[a] = st.shape[0]
+            walkers[a] = int(nw)
+        self._starts = prepared
+        in_ranks = (ctypes.c_int32 * nf)(*[s.shape[0] for s in prepared])
+        bytes_ = ctypes.c_size_t()
+        _check(L.tfg_workspace_size(nf, self.fmts, ctypes.cast(ranks, ctypes.c_void_p),
+                                    ctypes.cast(walkers, ctypes.c_void_p), ctypes.byref(self.params),
+                                    ctypes.byref(bytes_)))
+        self.workspace_bytes = bytes_.value
+        self.workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ptrs = (ctypes.c_void_p * nf)(*[s.ctypes.data for s in prepared])
+        ctx = ctypes.c_void_p()
+        _check(L.tfg_init(nf, self.fmts, ctypes.cast(in_ranks, ctypes.c_void_p), ctypes.cast(ptrs, ctypes.c_void_p),
+                          ctypes.cast(walkers, ctypes.c_void_p), ctypes.c_uint64(seed), ctypes.byref(self.params),
+                          ctypes.c_void_p(self.workspace.data_ptr()), self.workspace_bytes,
+                          ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx)))
+        self.ctx = ctx
+        self.n_formats = nf
+        self.pop = [self.population(a) for a in range(nf)]
+        self.total = sum(p["walkers"] for p in self.pop)
+
+    # -- plain calls ----------------------------------------------------------
+    def tfg_walk(self, steps: int):
+        _check(lib().tfg_walk(self.ctx, int(steps)))
+        return self
+
+    walk = tfg_walk
+
+    def tfg_sync(self):
+        _check(lib().tfg_sync(self.ctx))
+        return self
+
+    sync = tfg_sync
+
+    def population(self, f: int) -> dict:
+        fmt, r0, rmax, nw, first = tfg_format(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().tfg_population(self.ctx, f, ctypes.byref(fmt), ctypes.byref(r0), ctypes.byref(rmax),
+                                    ctypes.byref(nw), ctypes.byref(first)))
+        G, S = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().tfg_mapping(self.ctx, f, ctypes.byref(G), ctypes.byref(S)))
+        return {"fmt": (fmt.m, fmt.n, fmt.p), "mode": fmt.mode, "r0": r0.value, "r_max": rmax.value,
+                "walkers": nw.value, "first": first.value, "lanes": G.value, "slots_per_lane": S.value}
+
+    def tfg_collect_best(self, f: int):
+        p = self.pop[f]
+        out = np.zeros((p["r_max"], term_len(p["fmt"])), dtype=np.int8)
+        r, w = ctypes.c_int32(), ctypes.c_int64()
+        _check(lib().tfg_collect_best(self.ctx, f, _ptr(out), p["r_max"], ctypes.byref(r), ctypes.byref(w)))
+        return out[: r.value].copy(), r.value, w.value
+
+    collect_best = tfg_collect_best
+
+    def tfg_verify_all(self) -> int:
+        fails = self.torch.zeros(1, dtype=self.torch.int64, device="cuda")
+        _check(lib().tfg_verify_all_async(self.ctx, ctypes.c_void_p(fails.data_ptr())))
+        self.sync()
+        return int(fails.item())
+
+    verify_all = tfg_verify_all
+
+    def tfg_stats_get(self, f: int = -1, hist_len: int = 1024):
+        st = tfg_stats()
+        hist = np.zeros(hist_len, dtype=np.int64)
+        _check(lib().tfg_stats_get(self.ctx, f, ctypes.byref(st), _ptr(hist), hist_len))
+        d = {k: getattr(st, k) for k, _ in tfg_stats._fields_}
+        return d, hist
+
+    stats = tfg_stats_get
+
+    def tfg_read_walkers(self, first: int, count: int, slots: bool = True, best: bool = True):
+        """Returns (info structured array, slots int8 [count, r_max, LT] | None, best | None)."""
+        f = next(a for a, p in enumerate(self.pop) if p["first"] <= first < p["first"] + p["walkers"])
+        p = self.pop[f]
+        LT = term_len(p["fmt"])
+        info = np.zeros(count, dtype=WALKER_INFO_DTYPE)
+        s = np.zeros((count, p["r_max"], LT), dtype=np.int8) if slots else None
+        b = np.zeros((count, p["r_max"], LT), dtype=np.int8) if best else None
+        _check(lib().tfg_read_walkers(self.ctx, first, count, _ptr(info),
+                                      _ptr(s) if slots else None, _ptr(b) if best else None, p["r_max"]))
+        return info, s, b
+
+    read_walkers = tfg_read_walkers
+
+    def tfg_checkpoint(self) -> bytes:
+        used = ctypes.c_size_t()
+        _check(lib().tfg_checkpoint(self.ctx, None, 0, ctypes.byref(used)))
+        buf = np.zeros(used.value, dtype=np.uint8)
+        _check(lib().tfg_checkpoint(self.ctx, _ptr(buf), used.value, ctypes.byref(used)))
+        return buf.tobytes()
+
+    checkpoint = tfg_checkpoint
+
+    def tfg_restore(self, data: bytes):
+        buf = np.frombuffer(data, dtype=np.uint8).copy()
+        _check(lib().tfg_restore(self.ctx, _ptr(buf), buf.size))
+
+    restore = tfg_restore
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().tfg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

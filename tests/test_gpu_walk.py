@@ -1,0 +1,183 @@
+"""GPU parity: the CUDA walkers (through the C ABI) against the CPU oracle,
+bit-exact on every compared walker's slots, best scheme, counters and
+trajectory digest."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_20317_gb300 import tfg
+from paper_2511_20317_gb300.workloads import golden_dir, naive_start, read_scheme, workload_mixed
+
+pytestmark = pytest.mark.gpu
+
+THREADS = len(os.sched_getaffinity(0))
+FIELDS = ["r", "best_r", "t", "plateau", "best_t", "digest", "accepted", "rejected", "nocand", "drops",
+          "merges", "plus", "reductions"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2511_20317_gb300 import _build
+    _build.build()
+    tfg.lib()
+    torch.cuda.set_device(0)
+
+
+def gpu_walkers(fmt, mode, start, nw, seed, steps, chunks=1, **params):
+    p = tfg.tfg_default_params(**params)
+    W = tfg.Walkers([(fmt, mode, start, nw)], seed=seed, params=p)
+    for _ in range(chunks):
+        W.walk(steps // chunks)
+    W.sync()
+    return W
+
+
+def assert_parity(info, slots, best, ref, ref_rows, label=""):
+    """info/slots/best: GPU rows; ref: oracle.Walkers; ref_rows: oracle indices."""
+    for a, w in enumerate(ref_rows):
+        oi = ref.info[w]
+        for f in FIELDS:
+            assert info[f][a] == oi[f], f"{label} walker row {a}: {f} gpu={info[f][a]} oracle={oi[f]}"
+        r, br = oi["r"], oi["best_r"]
+        assert np.array_equal(slots[a, :r], ref.slots[w, :r]), f"{label} walker row {a}: slots differ"
+        assert np.array_equal(best[a, :br], ref.best[w, :br]), f"{label} walker row {a}: best differs"
+
+
+def test_philox_device_matches_oracle():
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2**32, size=(257, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    key = (0xA4093822, 0x299F31D0)
+    got = tfg.tfg_philox_device(ctr.reshape(-1), *key).reshape(-1, 4)
+    for k in range(ctr.shape[0]):
+        assert list(got[k]) == list(oracle.philox4x32_10(ctr[k], key))
+    kat = tfg.tfg_philox_device(np.array([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], np.uint32),
+                                0xA4093822, 0x299F31D0)
+    assert list(kat) == [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]
+
+
+@pytest.mark.parametrize("mode", [tfg.TFG_MODE_ZT, tfg.TFG_MODE_Z2])
+@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+@pytest.mark.parametrize("fmt,L,steps,nw", [((2, 2, 2), 200, 6000, 300), ((3, 3, 3), 600, 4000, 200),
+                                            ((2, 3, 4), 400, 3000, 130)])
+def test_parity_small_all_mappings(fmt, L, steps, nw, lanes, mode):
+    seed = 17
+    start = naive_start(*fmt)
+    W = gpu_walkers(fmt, mode, start, nw, seed, steps, chunks=3, plateau_len=L, mapping=lanes)
+    assert W.pop[0]["lanes"] == lanes
+    info, slots, best = W.read_walkers(0, nw)
+    ref = oracle.Walkers(fmt, start, np.arange(nw), seed=seed, mode=mode, plateau_len=L).walk(steps, THREADS)
+    assert (ref.info["plus"] > 0).any() and (ref.info["merges"] > 0).any()
+    assert_parity(info, slots, best, ref, range(nw), f"{fmt} G={lanes} mode={mode}")
+    assert W.verify_all() == 0
+    W.close()
+
+
+def test_parity_222_full_workload_all_walkers():
+    """(2,2,2) Z_T from the naive rank-8 scheme: 1024 walkers x 1e5 steps,
+    plateau 1e4; every walker replayed by the oracle."""
+    fmt, nw, steps, L = (2, 2, 2), 1024, 100_000, 10_000
+    start = naive_start(*fmt)
+    W = gpu_walkers(fmt, tfg.TFG_MODE_ZT, start, nw, 0, steps, plateau_len=L)
+    info, slots, best = W.read_walkers(0, nw)
+    ref = oracle.Walkers(fmt, start, np.arange(nw), seed=0, plateau_len=L).walk(steps, THREADS)
+    assert_parity(info, slots, best, ref, range(nw), "222-full")
+    assert W.verify_all() == 0
+    scheme, rank, walker = W.collect_best(0)
+    assert rank == info["best_r"].min() and walker == int(np.argmin(info["best_r"]))
+    assert tfg.tfg_verify(fmt, scheme) and oracle.brent_valid(fmt, scheme)
+    W.close()
+
+
+@pytest.mark.parametrize("mode,seed", [(tfg.TFG_MODE_ZT, 0), (tfg.TFG_MODE_Z2, 1)])
+def test_parity_333_full_population_sampled(mode, seed):
+    """(3,3,3) from the naive rank-27 scheme, 65536 walkers, plateau 5e4; the
+    GPU runs the whole population, the oracle replays walkers 256*k."""
+    fmt, nw, steps, L = (3, 3, 3), 65536, 200_000, 50_000
+    start = naive_start(*fmt)
+    W = gpu_walkers(fmt, mode, start, nw, seed, steps, chunks=2, plateau_len=L)
+    sample = np.arange(0, nw, 256)
+    infos, slots, bests = [], [], []
+    for w in sample:
+        i, s, b = W.read_walkers(int(w), 1)
+        infos.append(i); slots.append(s); bests.append(b)
+    info = np.concatenate(infos)
+    ref = oracle.Walkers(fmt, start, sample, seed=seed, mode=mode, plateau_len=L).walk(steps, THREADS)
+    assert_parity(info, np.concatenate(slots), np.concatenate(bests), ref, range(sample.size), f"333 mode={mode}")
+    assert W.verify_all() == 0
+    W.close()
+
+
+def test_chunking_and_checkpoint_resume():
+    fmt, nw, L = (3, 3, 3), 512, 700
+    start = naive_start(*fmt)
+    p = tfg.tfg_default_params(plateau_len=L)
+    A = tfg.Walkers([(fmt, 0, start, nw)], seed=3, params=p)
+    A.walk(2500).sync()
+    ck = A.checkpoint()
+    A.walk(2501).sync()
+    ia, sa, ba = A.read_walkers(0, nw)
+    B = tfg.Walkers([(fmt, 0, start, nw)], seed=3, params=p)
+    B.restore(ck)
+    B.walk(1000).walk(1501).sync()
+    ib, sb, bb = B.read_walkers(0, nw)
+    assert np.array_equal(ia, ib) and np.array_equal(sa, sb) and np.array_equal(ba, bb)
+    C = tfg.Walkers([(fmt, 0, start, nw)], seed=3, params=p)
+    C.walk(5001).sync()
+    ic, sc, bc = C.read_walkers(0, nw)
+    assert np.array_equal(ia, ic) and np.array_equal(sa, sc)
+
+
+def test_shards_equal_single_run():
+    """Walker ids are global (walker_id_base): two half populations reproduce one
+    whole population, as a two-GPU split would."""
+    fmt, nw, L, steps = (2, 3, 4), 600, 500, 3000
+    start = naive_start(*fmt)
+    whole = gpu_walkers(fmt, 0, start, nw, 8, steps, plateau_len=L)
+    iw, sw, bw = whole.read_walkers(0, nw)
+    lo = gpu_walkers(fmt, 0, start, 250, 8, steps, plateau_len=L, walker_id_base=0)
+    hi = gpu_walkers(fmt, 0, start, 350, 8, steps, plateau_len=L, walker_id_base=250)
+    i1, s1, b1 = lo.read_walkers(0, 250)
+    i2, s2, b2 = hi.read_walkers(0, 350)
+    assert np.array_equal(np.concatenate([i1, i2]), iw)
+    assert np.array_equal(np.concatenate([s1, s2]), sw) and np.array_equal(np.concatenate([b1, b2]), bw)
+
+
+def test_mixed_formats_one_context():
+    """Five formats of the mixed workload (naive starts) in one context; each
+    population checked against the oracle with its global walker ids."""
+    wl = workload_mixed(total=1040)
+    pops = [(p.fmt, 0, p.start_scheme(), p.walkers) for p in wl.populations]
+    L, steps, seed = 800, 2000, 0
+    W = tfg.Walkers(pops, seed=seed, params=tfg.tfg_default_params(plateau_len=L))
+    W.walk(steps).sync()
+    for f, pop in enumerate(W.pop):
+        take = np.linspace(0, pop["walkers"] - 1, 12).astype(int)
+        rows = [W.read_walkers(pop["first"] + int(w), 1) for w in take]
+        info = np.concatenate([x[0] for x in rows])
+        ids = pop["first"] + take
+        assert (info["walker_id"] == ids).all()
+        ref = oracle.Walkers(pop["fmt"], wl.populations[f].start_scheme(), ids, seed=seed,
+                             plateau_len=L).walk(steps, THREADS)
+        assert_parity(info, np.concatenate([x[1] for x in rows]), np.concatenate([x[2] for x in rows]), ref,
+                      range(len(take)), f"mixed {pop['fmt']}")
+    assert W.verify_all() == 0
+
+
+def test_start_from_paper_scheme_and_edge_formats():
+    """Start from the (2,2,3:11) example of Section 3.1.1; and the degenerate
+    formats (1,1,1) (rank 1: no candidate ever) and (1,2,1)."""
+    fmt, s = read_scheme(os.path.join(golden_dir(), "paper_2x2x3_r11.txt"))
+    for (f, st, nw) in [(fmt, s, 96), ((1, 1, 1), naive_start(1, 1, 1), 40), ((1, 2, 1), naive_start(1, 2, 1), 40),
+                        ((1, 1, 5), naive_start(1, 1, 5), 33)]:
+        W = gpu_walkers(f, 0, st, nw, 2, 2000, plateau_len=100)
+        info, slots, best = W.read_walkers(0, nw)
+        ref = oracle.Walkers(f, st, np.arange(nw), seed=2, plateau_len=100).walk(2000, THREADS)
+        assert_parity(info, slots, best, ref, range(nw), f"edge {f}")
+        if f == (1, 1, 1):
+            assert (info["nocand"] == 2000).all()
+        assert W.verify_all() == 0
