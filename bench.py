@@ -27,7 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "verified flips/sec and reductions per 1e9 flips at 1 GB300, learned vs uniform proposal"
-KERNEL_SRC = os.path.join(ROOT, "paper_2511_20317_gb300", "csrc", "walk_kernel.cuh")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2511_20317_gb300", "csrc", f) for f in ("walk_solo.cuh", "walk_group.cuh", "pterm.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "walk_kernel_333_dram_traffic.txt")
 
 # Algorithmic integer work per walker-step (word operations on 32-bit words):
@@ -47,7 +47,10 @@ def algorithmic_ops(mode, steps, accepted, rejected, mean_r, word_mult=1):
 
 
 def kernel_hash() -> str:
-    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in KERNEL_SRCS:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():
@@ -233,7 +236,9 @@ def run_ours(args):
             "mapping": f"G={W.pop[f]['lanes']} S={W.pop[f]['slots_per_lane']}"}
     walk_s = sum(walk_ms) / 1e3
     achieved = ops / walk_s / 1e12          # Tops/s
-    alu_peak = 152 * 4 * 32 * 2.07e9 / 1e12  # one 32-lane integer warp instruction per SMSP per clock
+    # integer ALU pipe: one warp instruction per 2 cycles per SM sub-partition (16 lanes/clk),
+    # 4 sub-partitions x 152 SMs at the 2070 MHz maximum SM clock
+    alu_peak = 152 * 4 * 16 * 2.07e9 / 1e12
     traffic = recorded_traffic()
 
     # end to end through the public API with host buffers, per step:
@@ -279,7 +284,7 @@ def run_ours(args):
                      "collected_best_ranks": best_ranks},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
-                     "kernel": "walk_kernel", "walk_ms_per_step": sum(walk_ms) / len(walk_ms)},
+                     "kernel": "walk_solo_kernel / walk_group_kernel", "walk_ms_per_step": sum(walk_ms) / len(walk_ms)},
         "e2e": {"value": e2e_val, "unit": "flips/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h // e2e_steps},
         "gpu_launches": (2 * W.n_formats + 2 * W.n_formats) * args.steps,

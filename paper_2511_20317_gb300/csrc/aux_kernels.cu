@@ -3,7 +3,7 @@
 #include <cstdint>
 
 #include "tfg_internal.h"
-#include "walk_kernel.cuh"
+#include "pterm.cuh"
 
 namespace tfg {
 namespace {
@@ -11,14 +11,14 @@ namespace {
 // ---- population set-up: every walker starts from the prepared start scheme
 template <class Wd>
 __global__ void replicate_kernel(const SegDesc d, const Wd *__restrict__ start, int32_t r0,
-                                 uint32_t id_base, int32_t fidx, int nwt) {
+                                 uint32_t id_base, int32_t fidx) {
     const int64_t w = blockIdx.x;
     if (w >= d.n_walkers) return;
-    const size_t per = (size_t)d.R * nwt;
+    const size_t per = (size_t)d.R * d.nws;
     Wd *s = reinterpret_cast<Wd *>(d.slots) + per * w;
     Wd *b = reinterpret_cast<Wd *>(d.best) + per * w;
     for (size_t e = threadIdx.x; e < per; e += blockDim.x) {
-        const Wd v = (e < (size_t)r0 * nwt) ? start[e] : Wd(0);
+        const Wd v = (e < (size_t)r0 * d.nws) ? start[e] : Wd(0);
         s[e] = v;
         b[e] = v;
     }
@@ -37,7 +37,7 @@ __global__ void replicate_kernel(const SegDesc d, const Wd *__restrict__ start, 
 // ---- Eq. (1) on one walker's best scheme per block.  Coefficients are
 // unpacked into shared memory; every tensor entry (a, b, c) sums r products.
 template <class Wd>
-__global__ void verify_best_kernel(const SegDesc d, int64_t first, int mode, int nwt,
+__global__ void verify_best_kernel(const SegDesc d, int64_t first, int mode,
                                    unsigned long long *failures) {
     extern __shared__ int8_t coef[];   // [r][LT]
     __shared__ int bad;
@@ -46,19 +46,14 @@ __global__ void verify_best_kernel(const SegDesc d, int64_t first, int mode, int
     const int m = d.m, n = d.n, p = d.p;
     const int LU = m * n, LV = n * p, LW = p * m, LT = LU + LV + LW;
     const int r = d.hdr[w].best_r;
-    const Wd *b = reinterpret_cast<const Wd *>(d.best) + (size_t)d.R * nwt * w;
+    const int WB = (int)sizeof(Wd) * 8;
+    const Wd *b = reinterpret_cast<const Wd *>(d.best) + (size_t)d.R * d.nws * w;
     if (threadIdx.x == 0) bad = 0;
     for (int e = threadIdx.x; e < r * LT; e += blockDim.x) {
-        const int l = e / LT, c = e - l * LT;
-        const int f = c < LU ? 0 : (c < LU + LV ? 1 : 2);
-        const int bit = c - (f == 0 ? 0 : (f == 1 ? LU : LU + LV));
-        int v;
-        if (mode == TFG_MODE_ZT) {
-            const Wd pw = b[(size_t)l * nwt + 2 * f], nw = b[(size_t)l * nwt + 2 * f + 1];
-            v = (int)((pw >> bit) & 1) - (int)((nw >> bit) & 1);
-        } else {
-            v = (int)((b[(size_t)l * nwt + f] >> bit) & 1);
-        }
+        const int l = e / LT, bit = e - l * LT;
+        const int q = bit / WB, o = bit - q * WB;
+        int v = (int)((b[(size_t)l * d.nws + q] >> o) & 1);
+        if (mode == TFG_MODE_ZT) v -= (int)((b[(size_t)l * d.nws + d.tw + q] >> o) & 1);
         coef[e] = (int8_t)v;
     }
     __syncthreads();
@@ -128,29 +123,27 @@ __global__ void philox_kernel(const uint32_t *ctr, int n, uint32_t k0, uint32_t 
 }  // namespace
 
 void launch_replicate(const SegDesc &d, const void *start_words, int32_t r0, uint32_t id_base,
-                      int32_t format_idx, int word_bits, int nwt, cudaStream_t st) {
+                      int32_t format_idx, cudaStream_t st) {
     if (d.n_walkers <= 0) return;
-    if (word_bits == 32)
+    if (d.word_bits == 32)
         replicate_kernel<uint32_t><<<(unsigned)d.n_walkers, 128, 0, st>>>(
-            d, reinterpret_cast<const uint32_t *>(start_words), r0, id_base, format_idx, nwt);
+            d, reinterpret_cast<const uint32_t *>(start_words), r0, id_base, format_idx);
     else
         replicate_kernel<uint64_t><<<(unsigned)d.n_walkers, 128, 0, st>>>(
-            d, reinterpret_cast<const uint64_t *>(start_words), r0, id_base, format_idx, nwt);
+            d, reinterpret_cast<const uint64_t *>(start_words), r0, id_base, format_idx);
 }
 
-void launch_verify_best(const SegDesc &d, int64_t first, int64_t count, int word_bits, int mode,
-                        int64_t *d_failures, cudaStream_t st) {
+void launch_verify_best(const SegDesc &d, int64_t first, int64_t count, int mode, int64_t *d_failures,
+                        cudaStream_t st) {
     if (count <= 0) return;
-    const int LT = d.m * d.n + d.n * d.p + d.p * d.m;
-    const size_t smem = (size_t)d.R * LT;
-    const int nwt = (mode == TFG_MODE_ZT) ? 6 : 3;
+    const size_t smem = (size_t)d.R * d.lt;
     auto *fail = reinterpret_cast<unsigned long long *>(d_failures);
-    if (word_bits == 32) {
+    if (d.word_bits == 32) {
         cudaFuncSetAttribute(verify_best_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        verify_best_kernel<uint32_t><<<(unsigned)count, 256, smem, st>>>(d, first, mode, nwt, fail);
+        verify_best_kernel<uint32_t><<<(unsigned)count, 256, smem, st>>>(d, first, mode, fail);
     } else {
         cudaFuncSetAttribute(verify_best_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        verify_best_kernel<uint64_t><<<(unsigned)count, 256, smem, st>>>(d, first, mode, nwt, fail);
+        verify_best_kernel<uint64_t><<<(unsigned)count, 256, smem, st>>>(d, first, mode, fail);
     }
 }
 

@@ -34,22 +34,26 @@ constexpr size_t kAuxBytes = (sizeof(Aux) + kAlign - 1) / kAlign * kAlign;
 
 struct Segment {
     tfg_format fmt{};
-    int r0 = 0, R = 0, word_bits = 32, nwt = 6;
+    int r0 = 0, R = 0, word_bits = 32, lt = 0, tw = 1, nws = 2;
     int64_t n = 0, first = 0;
     size_t off_hdr = 0, off_slots = 0, off_best = 0, off_start = 0;
     const tfg::WalkVariant *var = nullptr;
     std::vector<int8_t> start_rows;
 };
 
-int nwt_of(const tfg_format &f) { return f.mode == TFG_MODE_ZT ? 6 : 3; }
-int word_bits_of(const tfg_format &f) {
-    return (f.m * f.n <= 32 && f.n * f.p <= 32 && f.p * f.m <= 32) ? 32 : 64;
+// Packed term geometry: LT coefficient bits per sign in TW words of 32 bits
+// (LT <= 32) or 64 bits; NWS words per slot (both signs in Z_T).
+void set_geometry(Segment &s) {
+    s.lt = s.fmt.m * s.fmt.n + s.fmt.n * s.fmt.p + s.fmt.p * s.fmt.m;
+    s.word_bits = s.lt <= 32 ? 32 : 64;
+    s.tw = (s.lt + s.word_bits - 1) / s.word_bits;
+    s.nws = (s.fmt.mode == TFG_MODE_ZT ? 2 : 1) * s.tw;
 }
 
 // Lay out one segment at offset `off`; returns the offset past it.
 size_t layout_segment(Segment &s, size_t off) {
     const size_t wb = (size_t)s.word_bits / 8;
-    const size_t per = (size_t)s.R * s.nwt * wb;
+    const size_t per = (size_t)s.R * s.nws * wb;
     s.off_hdr = off;
     off = align_up(off + (size_t)s.n * sizeof(tfg_walker_info));
     s.off_slots = off;
@@ -66,26 +70,29 @@ int cuda_fail(cudaError_t e, const char *what) {
     return TFG_ECUDA;
 }
 
-const tfg::WalkVariant *pick_variant(int mode, int bits, int G, int R) {
+const tfg::WalkVariant *pick_variant(int mode, int bits, int tw, int G, int R) {
     int cnt = 0;
     const tfg::WalkVariant *v = tfg::walk_variants(&cnt);
     const tfg::WalkVariant *best = nullptr;
     for (int a = 0; a < cnt; ++a) {
-        if (v[a].mode != mode || v[a].word_bits != bits || v[a].G != G) continue;
-        if (v[a].G * v[a].S < R) continue;
+        if (v[a].mode != mode || v[a].word_bits != bits || v[a].tw != tw || v[a].G != G) continue;
+        if (v[a].capacity() < R) continue;
         if (!best || v[a].S < best->S) best = &v[a];
     }
     return best;
 }
 
-// Default mapping: the fewest lanes per walker that keep at most 4 slots per lane.
-const tfg::WalkVariant *default_variant(int mode, int bits, int R) {
+// Default mapping: one thread per walker (shared-memory slots) when such a
+// variant exists for the rank; otherwise the fewest lanes per walker that keep
+// at most 4 slots per lane; otherwise 32 lanes.
+const tfg::WalkVariant *default_variant(int mode, int bits, int tw, int R) {
+    if (const tfg::WalkVariant *v = pick_variant(mode, bits, tw, 1, R)) return v;
     static const int order[4] = {4, 8, 16, 32};
     for (int G : order) {
-        const tfg::WalkVariant *v = pick_variant(mode, bits, G, R);
+        const tfg::WalkVariant *v = pick_variant(mode, bits, tw, G, R);
         if (v && v->S <= 4) return v;
     }
-    return pick_variant(mode, bits, 32, R);
+    return pick_variant(mode, bits, tw, 32, R);
 }
 
 }  // namespace
@@ -108,6 +115,18 @@ struct tfg_ctx {
         d.n_walkers = s.n;
         d.R = s.R;
         d.m = s.fmt.m; d.n = s.fmt.n; d.p = s.fmt.p;
+        d.lt = s.lt; d.tw = s.tw; d.nws = s.nws; d.word_bits = s.word_bits;
+        const int off[3] = {0, s.fmt.m * s.fmt.n, s.fmt.m * s.fmt.n + s.fmt.n * s.fmt.p};
+        const int len[3] = {s.fmt.m * s.fmt.n, s.fmt.n * s.fmt.p, s.fmt.p * s.fmt.m};
+        for (int f = 0; f < 3; ++f)
+            for (int q = 0; q < 3; ++q) {
+                uint64_t mword = 0;
+                for (int b = 0; b < s.word_bits; ++b) {
+                    const int bit = q * s.word_bits + b;
+                    if (bit >= off[f] && bit < off[f] + len[f]) mword |= 1ull << b;
+                }
+                d.fmask[f][q] = mword;
+            }
         d.key0 = (uint32_t)seed;
         d.key1 = (uint32_t)(seed >> 32);
         d.plateau_len = prm.plateau_len;
@@ -207,8 +226,8 @@ static int check_params(const tfg_params &p) {
         set_error("bad parameters (plateau_len >= 1, r_slack >= 1, block_threads a multiple of 32 <= 256)");
         return TFG_EINVAL;
     }
-    if (p.mapping != 0 && p.mapping != 4 && p.mapping != 8 && p.mapping != 16 && p.mapping != 32) {
-        set_error("mapping must be 0 (auto), 4, 8, 16 or 32");
+    if (p.mapping != 0 && p.mapping != 1 && p.mapping != 4 && p.mapping != 8 && p.mapping != 16 && p.mapping != 32) {
+        set_error("mapping must be 0 (auto), 1 (thread per walker), 4, 8, 16 or 32");
         return TFG_EINVAL;
     }
     return TFG_OK;
@@ -228,15 +247,14 @@ static int plan_segments(int32_t n_formats, const tfg_format *fmts, const int32_
         s.r0 = ranks[f];
         s.R = ranks[f] + prm.r_slack;
         if (s.R > kMaxSlots) { set_error("rank + slack exceeds the supported 1023 slots"); return TFG_EINVAL; }
-        s.word_bits = word_bits_of(s.fmt);
-        s.nwt = nwt_of(s.fmt);
+        set_geometry(s);
         s.n = walkers[f];
         s.first = first;
         first += s.n;
         if (first > (int64_t)UINT32_MAX) { set_error("more than 2^32 walkers"); return TFG_EINVAL; }
         off = layout_segment(s, off);
-        s.var = prm.mapping ? pick_variant(s.fmt.mode, s.word_bits, prm.mapping, s.R)
-                            : default_variant(s.fmt.mode, s.word_bits, s.R);
+        s.var = prm.mapping ? pick_variant(s.fmt.mode, s.word_bits, s.tw, prm.mapping, s.R)
+                            : default_variant(s.fmt.mode, s.word_bits, s.tw, s.R);
         if (!s.var) { set_error("no compiled kernel variant for this format/rank/mapping"); return TFG_EINVAL; }
     }
     *bytes = off;
@@ -254,15 +272,26 @@ int tfg_workspace_size(int32_t n_formats, const tfg_format *fmts, const int32_t 
     return plan_segments(n_formats, fmts, ranks, walkers, prm, segs, bytes);
 }
 
+// Host term (one 64-bit mask per factor and sign) -> packed slot words.
 static void pack_terms(const Segment &s, const std::vector<HTerm> &t, std::vector<uint8_t> &buf) {
     const size_t wb = (size_t)s.word_bits / 8;
-    buf.assign((size_t)s.R * s.nwt * wb, 0);
+    buf.assign((size_t)s.R * s.nws * wb, 0);
+    const int off[3] = {0, s.fmt.m * s.fmt.n, s.fmt.m * s.fmt.n + s.fmt.n * s.fmt.p};
+    const int len[3] = {s.fmt.m * s.fmt.n, s.fmt.n * s.fmt.p, s.fmt.p * s.fmt.m};
+    const int signs = s.fmt.mode == TFG_MODE_ZT ? 2 : 1;
     for (size_t l = 0; l < t.size(); ++l)
-        for (int x = 0; x < 3; ++x) {
-            uint64_t words[2] = {t[l].p[x], t[l].n[x]};
-            const int nw = s.nwt == 6 ? 2 : 1;
-            for (int q = 0; q < nw; ++q) {
-                const size_t idx = l * s.nwt + (size_t)x * nw + q;
+        for (int sg = 0; sg < signs; ++sg) {
+            std::vector<uint64_t> words((size_t)s.tw, 0);
+            for (int x = 0; x < 3; ++x) {
+                const uint64_t m = sg == 0 ? t[l].p[x] : t[l].n[x];
+                for (int e = 0; e < len[x]; ++e)
+                    if ((m >> e) & 1) {
+                        const int bit = off[x] + e;
+                        words[bit / s.word_bits] |= 1ull << (bit % s.word_bits);
+                    }
+            }
+            for (int q = 0; q < s.tw; ++q) {
+                const size_t idx = l * s.nws + (size_t)sg * s.tw + q;
                 if (wb == 4) {
                     const uint32_t v = (uint32_t)words[q];
                     std::memcpy(&buf[idx * 4], &v, 4);
@@ -275,17 +304,27 @@ static void pack_terms(const Segment &s, const std::vector<HTerm> &t, std::vecto
 
 static void unpack_terms(const Segment &s, const uint8_t *words, int r, int8_t *rows) {
     const size_t wb = (size_t)s.word_bits / 8;
+    const int off[3] = {0, s.fmt.m * s.fmt.n, s.fmt.m * s.fmt.n + s.fmt.n * s.fmt.p};
+    const int len[3] = {s.fmt.m * s.fmt.n, s.fmt.n * s.fmt.p, s.fmt.p * s.fmt.m};
+    const int signs = s.fmt.mode == TFG_MODE_ZT ? 2 : 1;
     std::vector<HTerm> t((size_t)r);
-    const int nw = s.nwt == 6 ? 2 : 1;
     for (int l = 0; l < r; ++l)
-        for (int x = 0; x < 3; ++x)
-            for (int q = 0; q < nw; ++q) {
-                const size_t idx = (size_t)l * s.nwt + (size_t)x * nw + q;
-                uint64_t v = 0;
-                if (wb == 4) { uint32_t v32; std::memcpy(&v32, words + idx * 4, 4); v = v32; }
-                else std::memcpy(&v, words + idx * 8, 8);
-                (q == 0 ? t[l].p[x] : t[l].n[x]) = v;
+        for (int sg = 0; sg < signs; ++sg) {
+            std::vector<uint64_t> w((size_t)s.tw, 0);
+            for (int q = 0; q < s.tw; ++q) {
+                const size_t idx = (size_t)l * s.nws + (size_t)sg * s.tw + q;
+                if (wb == 4) { uint32_t v32; std::memcpy(&v32, words + idx * 4, 4); w[q] = v32; }
+                else std::memcpy(&w[q], words + idx * 8, 8);
             }
+            for (int x = 0; x < 3; ++x) {
+                uint64_t m = 0;
+                for (int e = 0; e < len[x]; ++e) {
+                    const int bit = off[x] + e;
+                    if ((w[bit / s.word_bits] >> (bit % s.word_bits)) & 1) m |= 1ull << e;
+                }
+                (sg == 0 ? t[l].p[x] : t[l].n[x]) = m;
+            }
+        }
     tfg::host::emit(s.fmt, t, rows);
 }
 
@@ -338,7 +377,7 @@ int tfg_init(int32_t n_formats, const tfg_format *fmts, const int32_t *ranks, co
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "copy start"); }
         tfg::launch_replicate(ctx->desc(s), ctx->ws + s.off_start, s.r0, prm.walker_id_base + (uint32_t)s.first, f,
-                              s.word_bits, s.nwt, ctx->stream);
+                              ctx->stream);
         e = cudaGetLastError();
         if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "replicate launch"); }
     }
@@ -354,9 +393,10 @@ int tfg_walk(tfg_ctx *ctx, int64_t steps) {
         const int32_t chunk = (int32_t)std::min<int64_t>(steps, 1 << 30);
         for (const Segment &s : ctx->segs) {
             if (s.n == 0) continue;
+            const int b = s.var->block ? s.var->block : block;
             const int64_t threads = s.n * s.var->G;
-            const int64_t grid = (threads + block - 1) / block;
-            s.var->launch(ctx->desc(s), chunk, (int)grid, block, ctx->stream);
+            const int64_t grid = (threads + b - 1) / b;
+            s.var->launch(ctx->desc(s), chunk, (int)grid, b, ctx->stream);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "walk launch");
@@ -398,7 +438,7 @@ int tfg_verify_all_async(tfg_ctx *ctx, int64_t *d_failures) {
     cudaError_t e = cudaMemsetAsync(d_failures, 0, sizeof(int64_t), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
     for (const Segment &s : ctx->segs)
-        tfg::launch_verify_best(ctx->desc(s), 0, s.n, s.word_bits, s.fmt.mode, d_failures, ctx->stream);
+        tfg::launch_verify_best(ctx->desc(s), 0, s.n, s.fmt.mode, d_failures, ctx->stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "verify launch");
     return TFG_OK;
@@ -424,8 +464,8 @@ int tfg_collect_best(tfg_ctx *ctx, int32_t format_idx, int8_t *out, int32_t cap,
     // device check of the chosen walker's best scheme
     e = cudaMemsetAsync(&aux->verify_failures, 0, sizeof(int64_t), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
-    tfg::launch_verify_best(d, w, 1, s.word_bits, s.fmt.mode, &aux->verify_failures, ctx->stream);
-    const size_t per = (size_t)s.R * s.nwt * (s.word_bits / 8);
+    tfg::launch_verify_best(d, w, 1, s.fmt.mode, &aux->verify_failures, ctx->stream);
+    const size_t per = (size_t)s.R * s.nws * (s.word_bits / 8);
     std::vector<uint8_t> words(per);
     int64_t dev_fail = 0;
     e = cudaMemcpyAsync(words.data(), ctx->ws + s.off_best + per * w, per, cudaMemcpyDeviceToHost, ctx->stream);
@@ -492,7 +532,7 @@ int tfg_read_walkers(tfg_ctx *ctx, int64_t first, int64_t count, tfg_walker_info
     const Segment &s = *sp;
     if ((slots || best) && r_max_cap < s.R) { set_error("r_max_cap smaller than the population's r_max"); return TFG_ENOSPC; }
     const int64_t lo = first - s.first;
-    const size_t per = (size_t)s.R * s.nwt * (s.word_bits / 8);
+    const size_t per = (size_t)s.R * s.nws * (s.word_bits / 8);
     const int LT = tfg::host::term_len(s.fmt);
     std::vector<tfg_walker_info> hdr((size_t)count);
     cudaError_t e = cudaMemcpyAsync(hdr.data(), ctx->ws + s.off_hdr + sizeof(tfg_walker_info) * lo,

@@ -10,9 +10,12 @@ namespace tfg {
 
 enum Action : int { kNoCand = 0, kReject = 1, kAccept = 2 };
 
-// Device view of one walker population ("segment").  Walker w's slots are
-// words [w][R][NWT] (NWT = 6 in Z_T: pos/neg masks of u, v, w; 3 in Z_2),
-// its best scheme the same shape in `best`, its record hdr[w].
+// Device view of one walker population ("segment").  A term is packed: its
+// LT = mn + np + pm coefficients (u | v | w concatenated) as TW words of
+// +1 bits followed, in Z_T, by TW words of -1 bits (NWS = 2*TW words per
+// slot; NWS = TW in Z_2).  Walker w's slots are words [w][R][NWS], its best
+// scheme the same shape in `best`, its record hdr[w].  fmask[f][q] selects
+// factor f (u, v, w) in word q.
 struct SegDesc {
     void *slots;
     void *best;
@@ -20,6 +23,8 @@ struct SegDesc {
     int64_t n_walkers;
     int32_t R;            // slots per walker (r_max)
     int32_t m, n, p;      // format
+    int32_t lt, tw, nws, word_bits;
+    uint64_t fmask[3][3];
     uint32_t key0, key1;  // Philox key = seed
     int64_t plateau_len;
     uint32_t refresh_thresh;
@@ -28,14 +33,17 @@ struct SegDesc {
     int32_t pad;
 };
 
-// One (mode, word size, lanes per walker, slots per lane) variant of the walk kernel.
+// One compiled variant of the walk kernel.
 struct WalkVariant {
     int mode;       // TFG_MODE_ZT / TFG_MODE_Z2
     int word_bits;  // 32 or 64
-    int G;          // lanes per walker
-    int S;          // slots per lane
+    int tw;         // words per sign of a packed term
+    int G;          // lanes per walker (1: thread-per-walker kernel)
+    int S;          // slots per lane (lane groups) or slot capacity (G = 1)
+    int block;      // fixed block size (G = 1), 0 = chosen by the caller
     void (*launch)(const SegDesc &d, int32_t steps, int grid, int block, cudaStream_t st);
     const void *kernel;  // for cudaFuncGetAttributes
+    int capacity() const { return G == 1 ? S : G * S; }
 };
 
 // Registry of compiled variants (filled by the instantiation units).
@@ -43,9 +51,9 @@ const WalkVariant *walk_variants(int *count);
 
 // Auxiliary kernels (aux_kernels.cu).
 void launch_replicate(const SegDesc &d, const void *start_words, int32_t r0, uint32_t id_base,
-                      int32_t format_idx, int word_bits, int nwt, cudaStream_t st);
-void launch_verify_best(const SegDesc &d, int64_t first, int64_t count, int word_bits, int mode,
-                        int64_t *d_failures, cudaStream_t st);
+                      int32_t format_idx, cudaStream_t st);
+void launch_verify_best(const SegDesc &d, int64_t first, int64_t count, int mode, int64_t *d_failures,
+                        cudaStream_t st);
 void launch_argmin_best(const SegDesc &d, unsigned long long *d_key, cudaStream_t st);
 void launch_stats(const SegDesc &d, int64_t *d_sums /*[9]*/, int *d_minmax /*[2]*/, int64_t *d_hist,
                   int hist_len, cudaStream_t st);

@@ -1,11 +1,11 @@
-// Flip-graph walk kernel for sm_103a.
+// Lane-group flip-graph walk kernel for sm_103a.
 //
 // One walker = one group of G lanes (G in {4, 8, 16, 32}); lane l of the group
 // holds slots l*S .. l*S+S-1 of the walker's scheme in registers (blocked
-// layout, S compile-time).  A term is NWT words: the positive and negative
-// bit masks of u, v, w in Z_T ("digits"/"signs" of Section 3.5.1, stored as
-// pos = digits & ~signs, neg = digits & signs), or the three masks of Z_2.
-// Word bit e is coefficient e of the factor (u: i*n+k, v: k*p+j, w: j*m+i).
+// layout, S compile-time) as packed terms (pterm.cuh): TW words of positive
+// and TW words of negative coefficient bits over the concatenated u|v|w
+// index.  This mapping serves large ranks and terms longer than 64 bits;
+// small formats use the thread-per-walker kernel (walk_solo.cuh).
 //
 // Every step follows Algorithm 1 with the plateau policy:
 //   draw (Philox4x32-10, counter (t, walker, 0)) -> sample term i ->
@@ -20,36 +20,10 @@
 #pragma once
 #include <cstdint>
 
-#include "tfg_internal.h"
+#include "pterm.cuh"
 
 namespace tfg {
 namespace dev {
-
-// ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon et al., SC'11): 10 rounds, Weyl key schedule.
-// ---------------------------------------------------------------------------
-struct U4 { uint32_t x, y, z, w; };
-
-__device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                       uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int rd = 0; rd < 10; ++rd) {
-        if (rd > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-        const uint32_t n0 = hi1 ^ c1 ^ k0;
-        const uint32_t n2 = hi0 ^ c3 ^ k1;
-        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
-    }
-    return U4{c0, c1, c2, c3};
-}
-
-__device__ __forceinline__ uint64_t digest_mix(uint64_t h, uint64_t v) {
-    h ^= v;
-    h *= 0x9E3779B97F4A7C15ull;
-    h ^= h >> 29;
-    return h;
-}
 
 // ---------------------------------------------------------------------------
 // Lane group of G lanes inside a warp.
@@ -73,93 +47,40 @@ struct Group {
     }
 };
 
-template <class Wd, int NWT>
-struct Term { Wd w[NWT]; };
-
-// ---- factor access (f is group-uniform; selects keep the term in registers)
-template <class Wd, int NWT>
-__device__ __forceinline__ Wd fpos(const Term<Wd, NWT> &t, int f) {
-    constexpr int st = NWT / 3;
-    return f == 0 ? t.w[0] : (f == 1 ? t.w[st] : t.w[2 * st]);
-}
-template <class Wd, int NWT>
-__device__ __forceinline__ Wd fneg(const Term<Wd, NWT> &t, int f) {
-    if constexpr (NWT == 6) return f == 0 ? t.w[1] : (f == 1 ? t.w[3] : t.w[5]);
-    else return Wd(0);
-}
-template <class Wd, int NWT>
-__device__ __forceinline__ void fset(Term<Wd, NWT> &t, int f, Wd p, Wd n) {
-    constexpr int st = NWT / 3;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        if (f == q) {
-            t.w[q * st] = p;
-            if constexpr (NWT == 6) t.w[q * st + 1] = n;
-        }
-    }
-}
-
-// Section 3.6: first non-zero of u, then of v, made +1; w absorbs the sign.
-template <class Wd, int NWT>
-__device__ __forceinline__ void canon(Term<Wd, NWT> &t) {
-    if constexpr (NWT == 6) {
-        {
-            const Wd d = t.w[0] | t.w[1];
-            const Wd low = d & (Wd(0) - d);
-            if (t.w[1] & low) {
-                Wd a = t.w[0]; t.w[0] = t.w[1]; t.w[1] = a;
-                a = t.w[4]; t.w[4] = t.w[5]; t.w[5] = a;
-            }
-        }
-        {
-            const Wd d = t.w[2] | t.w[3];
-            const Wd low = d & (Wd(0) - d);
-            if (t.w[3] & low) {
-                Wd a = t.w[2]; t.w[2] = t.w[3]; t.w[3] = a;
-                a = t.w[4]; t.w[4] = t.w[5]; t.w[5] = a;
-            }
-        }
-    }
-}
-
-// Ternary a + b (Section 3.5.2 validity: no position with both +1 or both -1).
-template <class Wd>
-__device__ __forceinline__ bool tadd(Wd ap, Wd an, Wd bp, Wd bn, Wd &rp, Wd &rn) {
-    const bool bad = ((ap & bp) | (an & bn)) != Wd(0);
-    rp = (ap | bp) & ~(an | bn);
-    rn = (an | bn) & ~(ap | bp);
-    return !bad;
-}
-
 // ---------------------------------------------------------------------------
 // Walker: state in registers plus the group-uniform bookkeeping.
 // ---------------------------------------------------------------------------
-template <int MODE, class Wd, int G, int S>
-struct Walker {
+template <int MODE, class Wd, int TW, int G, int S>
+struct GroupWalker {
     static constexpr bool ZT = (MODE == TFG_MODE_ZT);
-    static constexpr int NWT = ZT ? 6 : 3;
-    using T = Term<Wd, NWT>;
+    static constexpr int NWS = (ZT ? 2 : 1) * TW;   // words per slot in HBM
+    using T = PTerm<Wd, TW, ZT>;
+    using O = Ops<Wd, TW, ZT>;
+    using M = Masks<Wd, TW>;
 
     Group<G> g;
-    Wd st[S][NWT];
+    T st[S];
+    M mk;
     int r, best_r, R;
     int64_t t, plateau, best_t;
     uint64_t dig;
     uint32_t wid, key0, key1;
     uint32_t c_acc, c_rej, c_noc, c_drp, c_mrg, c_pls, c_red;
-
-    // Reduction queue: slots of at most three modified terms awaiting checks.
-    int qlen, q0, q1, q2;
+    int qlen, q0, q1, q2;   // reduction queue (slot indices)
 
     __device__ __forceinline__ T fetch(int k) const {
         const int o = k / S, pos = k - o * S;
         T out;
 #pragma unroll
-        for (int w = 0; w < NWT; ++w) {
-            Wd v = st[0][w];
+        for (int w = 0; w < TW; ++w) {
+            Wd vp = st[0].p[w], vn = st[0].n[w];
 #pragma unroll
-            for (int p = 1; p < S; ++p) v = (pos == p) ? st[p][w] : v;
-            out.w[w] = g.shfl(v, o);
+            for (int p = 1; p < S; ++p) {
+                vp = (pos == p) ? st[p].p[w] : vp;
+                if constexpr (ZT) vn = (pos == p) ? st[p].n[w] : vn;
+            }
+            out.p[w] = g.shfl(vp, o);
+            out.n[w] = ZT ? g.shfl(vn, o) : Wd(0);
         }
         return out;
     }
@@ -168,15 +89,10 @@ struct Walker {
         const int o = k / S, pos = k - o * S;
         const bool me = (g.lane == o);
 #pragma unroll
-        for (int p = 0; p < S; ++p) {
-            if (me && pos == p) {
-#pragma unroll
-                for (int w = 0; w < NWT; ++w) st[p][w] = v.w[w];
-            }
-        }
+        for (int p = 0; p < S; ++p)
+            if (me && pos == p) st[p] = v;
     }
 
-    // ---- queue helpers (registers only)
     __device__ __forceinline__ void q_push(int s) {
         q0 = (qlen == 0) ? s : q0;
         q1 = (qlen == 1) ? s : q1;
@@ -214,27 +130,37 @@ struct Walker {
         r -= 1;
     }
 
-    // Does term v (in slot s) share any factor pair with another live slot?
-    // (superset filter of the reduction test; no validity check)
-    __device__ __forceinline__ bool pair_hit(const T &v, int s) const {
+    // Any other live slot sharing a factor pair with a (slot sa) or b (slot sb)?
+    // (superset filter of the reduction test; validity is not checked)
+    __device__ __forceinline__ bool pair_hit2(const T &a, int sa, const T &b, int sb) const {
         bool hit = false;
 #pragma unroll
         for (int p = 0; p < S; ++p) {
             const int slot = g.lane * S + p;
-            const bool live = slot < r && slot != s;
-            bool eu, ev, ew;
-            if constexpr (ZT) {
-                eu = st[p][0] == v.w[0] && st[p][1] == v.w[1];
-                ev = st[p][2] == v.w[2] && st[p][3] == v.w[3];
-                ew = (st[p][4] == v.w[4] && st[p][5] == v.w[5]) || (st[p][4] == v.w[5] && st[p][5] == v.w[4]);
-            } else {
-                eu = st[p][0] == v.w[0];
-                ev = st[p][1] == v.w[1];
-                ew = st[p][2] == v.w[2];
-            }
-            hit |= live && ((eu && ev) || (eu && ew) || (ev && ew));
+            bool eu, ev, ewp, ewn;
+            O::compare(st[p], a, mk, eu, ev, ewp, ewn);
+            const bool ew = ewp || ewn;
+            const bool ha = (eu && ev) || (eu && ew) || (ev && ew);
+            O::compare(st[p], b, mk, eu, ev, ewp, ewn);
+            const bool ew2 = ewp || ewn;
+            const bool hb = (eu && ev) || (eu && ew2) || (ev && ew2);
+            hit |= (slot < r) && ((ha && slot != sa) || (hb && slot != sb));
         }
         return g.ballot(hit) != 0u;
+    }
+
+    __device__ __forceinline__ bool sum_ok(const T &a, const T &b, int f, bool neg) const {
+        if constexpr (ZT) {
+            Wd bad = 0;
+#pragma unroll
+            for (int w = 0; w < TW; ++w) {
+                const Wd bp = neg ? b.n[w] : b.p[w], bn = neg ? b.p[w] : b.n[w];
+                bad |= ((a.p[w] & bp) | (a.n[w] & bn)) & mk.m[f][w];
+            }
+            return bad == Wd(0);
+        } else {
+            return true;
+        }
     }
 
     // Reduction (Section 3.3.1, any permutation of u, v, w) of the term in slot
@@ -248,68 +174,43 @@ struct Walker {
         for (int p = 0; p < S; ++p) {
             const int slot = g.lane * S + p;
             const bool live = slot < r && slot != s;
-            if constexpr (ZT) {
-                // u and v are sign-normalised, so they match only exactly; w up to sign
-                const bool eu = st[p][0] == v.w[0] && st[p][1] == v.w[1];
-                const bool ev = st[p][2] == v.w[2] && st[p][3] == v.w[3];
-                const bool ewp = st[p][4] == v.w[4] && st[p][5] == v.w[5];
-                const bool ewn = st[p][4] == v.w[5] && st[p][5] == v.w[4];
-                // third-factor validity: w_s + w_k ; v_s + sigma v_k ; u_s + sigma u_k
-                const bool vw = ((v.w[4] & st[p][4]) | (v.w[5] & st[p][5])) == Wd(0);
-                const Wd kvp = ewn ? st[p][3] : st[p][2], kvn = ewn ? st[p][2] : st[p][3];
-                const bool vv = ((v.w[2] & kvp) | (v.w[3] & kvn)) == Wd(0);
-                const Wd kup = ewn ? st[p][1] : st[p][0], kun = ewn ? st[p][0] : st[p][1];
-                const bool vu = ((v.w[0] & kup) | (v.w[1] & kun)) == Wd(0);
-                m0 |= (uint32_t)(live && eu && ev && vw) << p;
-                m1 |= (uint32_t)(live && eu && (ewp || ewn) && vv) << p;
-                m2 |= (uint32_t)(live && ev && (ewp || ewn) && vu) << p;
-                mn |= (uint32_t)ewn << p;
-            } else {
-                const bool eu = st[p][0] == v.w[0], ev = st[p][1] == v.w[1], ew = st[p][2] == v.w[2];
-                m0 |= (uint32_t)(live && eu && ev) << p;
-                m1 |= (uint32_t)(live && eu && ew) << p;
-                m2 |= (uint32_t)(live && ev && ew) << p;
-            }
+            bool eu, ev, ewp, ewn;
+            O::compare(st[p], v, mk, eu, ev, ewp, ewn);
+            const bool ew = ewp || ewn;
+            m0 |= (uint32_t)(live && eu && ev && sum_ok(v, st[p], 2, false)) << p;
+            m1 |= (uint32_t)(live && eu && ew && sum_ok(v, st[p], 1, ewn)) << p;
+            m2 |= (uint32_t)(live && ev && ew && sum_ok(v, st[p], 0, ewn)) << p;
+            mn |= (uint32_t)ewn << p;
         }
         const unsigned b0 = g.ballot(m0 != 0u), b1 = g.ballot(m1 != 0u), b2 = g.ballot(m2 != 0u);
         if ((b0 | b1 | b2) == 0u) return;
         const int P = b0 ? 0 : (b1 ? 1 : 2);
         const unsigned lanes = b0 ? b0 : (b1 ? b1 : b2);
-        const uint32_t mk = P == 0 ? m0 : (P == 1 ? m1 : m2);
+        const uint32_t mkp = P == 0 ? m0 : (P == 1 ? m1 : m2);
         const int ol = __ffs(lanes) - 1;
-        const int pos = mk ? __ffs(mk) - 1 : 0;  // meaningful on the owner lane
+        const int pos = mkp ? __ffs(mkp) - 1 : 0;  // meaningful on the owner lane
         const int kneg_l = (P == 0) ? 0 : (int)((mn >> pos) & 1u);
         const int pk = g.shfl((g.lane * S + pos) | (kneg_l << 16), ol);
         const int k = pk & 0xffff;
         const bool kneg = (pk >> 16) != 0;
         const int F = 2 - P;  // third factor: w, v, u
         const T kv = fetch(k);
-        T mv = v;
-        Wd rp, rn;
-        if constexpr (ZT) {
-            const Wd kp = kneg ? fneg(kv, F) : fpos(kv, F);
-            const Wd kn = kneg ? fpos(kv, F) : fneg(kv, F);
-            tadd(fpos(v, F), fneg(v, F), kp, kn, rp, rn);
-        } else {
-            rp = fpos(v, F) ^ fpos(kv, F);
-            rn = Wd(0);
-        }
-        fset(mv, F, rp, rn);
-        const bool zero = (rp | rn) == Wd(0);
-        canon(mv);
+        T mv;
+        O::add(v, kv, F, kneg, mk, mv);
+        const bool zero = O::zero(mv, F, mk);
+        O::canon(mv, mk);
         const int lo = s < k ? s : k;
         const int hi = s < k ? k : s;
         q_remove(k);
         store(mv, lo);
         c_mrg += 1;
-        // drop hi, then lo as well when the merged term vanished
-#pragma unroll 1
-        for (int d = 0; d < 2; ++d) {
-            if (d == 1 && !zero) break;
-            drop(d == 0 ? hi : lo);
+        drop(hi);
+        if (zero) {
+            drop(lo);
+            c_drp += 1;
+        } else {
+            q_push(lo);
         }
-        if (zero) c_drp += 1;
-        else q_push(lo);
     }
 
     __device__ __forceinline__ void cascade() {
@@ -323,14 +224,16 @@ struct Walker {
             const int slot = g.lane * S + p;
             if (slot < r) {
 #pragma unroll
-                for (int w = 0; w < NWT; ++w) bestp[(size_t)slot * NWT + w] = st[p][w];
+                for (int w = 0; w < TW; ++w) {
+                    bestp[(size_t)slot * NWS + w] = st[p].p[w];
+                    if constexpr (ZT) bestp[(size_t)slot * NWS + TW + w] = st[p].n[w];
+                }
             }
         }
     }
 
-    // Plus transition (Section 3.3.1) with roles (A,B,C) a permutation of
-    // (u,v,w): writes the three new terms and queues them; returns the record
-    // for the digest, or 0 when no attempt passed.
+    // Plus transition (Section 3.3.1): writes the three new terms and queues
+    // them; returns the digest record (0 when no attempt passed).
     __device__ __forceinline__ uint64_t plus_setup(const SegDesc &d) {
 #pragma unroll 1
         for (int a = 1; a <= d.plus_attempts; ++a) {
@@ -338,39 +241,22 @@ struct Walker {
             const int pi = (int)__umulhi(y.x, (uint32_t)r);
             const int pj = (pi + 1 + (int)__umulhi(y.y, (uint32_t)(r - 1))) % r;
             const int perm = (int)__umulhi(y.z, 6u);
-            // PERM = {u,v,w},{u,w,v},{v,u,w},{v,w,u},{w,u,v},{w,v,u}
-            const int A = perm >> 1;
-            const int B = (perm == 0 || perm == 5) ? 1 : ((perm == 1 || perm == 3) ? 2 : 0);
-            const int C = 3 - A - B;
+            int A, B, C;
+            plus_roles(perm, A, B, C);
             const T ti = fetch(pi), tj = fetch(pj);
-            Wd nbp, nbn, ncp, ncn, nap, nan_;
-            bool ok;
-            if constexpr (ZT) {
-                ok = tadd(fpos(ti, B), fneg(ti, B), fpos(tj, B), fneg(tj, B), nbp, nbn);
-                ok &= tadd(fpos(tj, C), fneg(tj, C), fneg(ti, C), fpos(ti, C), ncp, ncn);
-                ok &= tadd(fpos(tj, A), fneg(tj, A), fneg(ti, A), fpos(ti, A), nap, nan_);
-            } else {
-                nbp = fpos(ti, B) ^ fpos(tj, B);
-                ncp = fpos(tj, C) ^ fpos(ti, C);
-                nap = fpos(tj, A) ^ fpos(ti, A);
-                nbn = ncn = nan_ = Wd(0);
-                ok = true;
-            }
-            ok = ok && ((nbp | nbn) != Wd(0)) && ((ncp | ncn) != Wd(0)) && ((nap | nan_) != Wd(0));
+            T nb, nc, na;
+            bool ok = O::add(ti, tj, B, false, mk, nb);      // B_i + B_j
+            ok &= O::add(tj, ti, C, true, mk, nc);           // C_j - C_i
+            ok &= O::add(tj, ti, A, true, mk, na);           // A_j - A_i
+            ok = ok && !O::zero(nb, B, mk) && !O::zero(nc, C, mk) && !O::zero(na, A, mk);
             if (!ok) continue;
-            T tn = tj;
-            fset(tn, A, nap, nan_);  // (A_j - A_i, B_j, C_j)
-            canon(tn);
-            store(tn, r);
-            tn = tj;
-            fset(tn, A, fpos(ti, A), fneg(ti, A));  // (A_i, B_j, C_j - C_i)
-            fset(tn, C, ncp, ncn);
-            canon(tn);
-            store(tn, pj);
-            tn = ti;
-            fset(tn, B, nbp, nbn);  // (A_i, B_i + B_j, C_i)
-            canon(tn);
-            store(tn, pi);
+            O::canon(na, mk);          // (A_j - A_i, B_j, C_j)
+            store(na, r);
+            O::take(nc, ti, A, mk);    // (A_i, B_j, C_j - C_i)
+            O::canon(nc, mk);
+            store(nc, pj);
+            O::canon(nb, mk);          // (A_i, B_i + B_j, C_i)
+            store(nb, pi);
             r += 1;
             plateau = 0;
             c_pls += 1;
@@ -378,8 +264,7 @@ struct Walker {
             q_push(pi);
             q_push(pj);
             q_push(r - 1);
-            return 0xFull | ((uint64_t)a << 4) | ((uint64_t)perm << 9) | ((uint64_t)(uint32_t)pi << 12) |
-                   ((uint64_t)(uint32_t)pj << 28);
+            return plus_record(a, perm, pi, pj);
         }
         return 0;
     }
@@ -390,15 +275,19 @@ struct Walker {
         t = H->t; plateau = H->plateau; best_t = H->best_t;
         dig = H->digest; wid = H->walker_id;
         key0 = d.key0; key1 = d.key1;
+        mk.load(d);
         c_acc = c_rej = c_noc = c_drp = c_mrg = c_pls = c_red = 0;
         qlen = 0; q0 = q1 = q2 = 0;
-        const Wd *src = reinterpret_cast<const Wd *>(d.slots) + (size_t)w * R * NWT;
-        Wd *bestp = reinterpret_cast<Wd *>(d.best) + (size_t)w * R * NWT;
+        const Wd *src = reinterpret_cast<const Wd *>(d.slots) + (size_t)w * R * NWS;
+        Wd *bestp = reinterpret_cast<Wd *>(d.best) + (size_t)w * R * NWS;
 #pragma unroll
         for (int p = 0; p < S; ++p) {
             const int slot = g.lane * S + p;
 #pragma unroll
-            for (int q = 0; q < NWT; ++q) st[p][q] = (slot < R) ? src[(size_t)slot * NWT + q] : Wd(0);
+            for (int q = 0; q < TW; ++q) {
+                st[p].p[q] = (slot < R) ? src[(size_t)slot * NWS + q] : Wd(0);
+                st[p].n[q] = (ZT && slot < R) ? src[(size_t)slot * NWS + TW + q] : Wd(0);
+            }
         }
 
         uint32_t xr0 = 0, xr1 = 0, xr2 = 0;
@@ -419,29 +308,22 @@ struct Walker {
             const int i = (int)__umulhi(x0, (uint32_t)r);
             int action = kNoCand, X = 0, j = 0, rho = 0, sneg = 0;
             {
-                T ti = fetch(i);
+                const T ti = fetch(i);
                 // ---- try_flip: candidates (X, j) with X_j = +-X_i, ordered (X, slot)
                 uint32_t bu = 0, bv = 0, bw = 0, bwn = 0;
 #pragma unroll
                 for (int p = 0; p < S; ++p) {
                     const int slot = g.lane * S + p;
                     const bool live = slot < r && slot != i;
-                    if constexpr (ZT) {
-                        const bool eu = st[p][0] == ti.w[0] && st[p][1] == ti.w[1];
-                        const bool ev = st[p][2] == ti.w[2] && st[p][3] == ti.w[3];
-                        const bool ewp = st[p][4] == ti.w[4] && st[p][5] == ti.w[5];
-                        const bool ewn = st[p][4] == ti.w[5] && st[p][5] == ti.w[4];
-                        bu |= (uint32_t)(live && eu) << p;
-                        bv |= (uint32_t)(live && ev) << p;
-                        bw |= (uint32_t)(live && (ewp || ewn)) << p;
-                        bwn |= (uint32_t)(live && ewn) << p;
-                    } else {
-                        bu |= (uint32_t)(live && st[p][0] == ti.w[0]) << p;
-                        bv |= (uint32_t)(live && st[p][1] == ti.w[1]) << p;
-                        bw |= (uint32_t)(live && st[p][2] == ti.w[2]) << p;
-                    }
+                    bool eu, ev, ewp, ewn;
+                    O::compare(st[p], ti, mk, eu, ev, ewp, ewn);
+                    bu |= (uint32_t)(live && eu) << p;
+                    bv |= (uint32_t)(live && ev) << p;
+                    bw |= (uint32_t)(live && (ewp || ewn)) << p;
+                    bwn |= (uint32_t)(live && ewn) << p;
                 }
-                const uint32_t own = (uint32_t)__popc(bu) | ((uint32_t)__popc(bv) << 10) | ((uint32_t)__popc(bw) << 20);
+                const uint32_t own = (uint32_t)__popc(bu) | ((uint32_t)__popc(bv) << 10) |
+                                     ((uint32_t)__popc(bw) << 20);
                 uint32_t incl = own;
 #pragma unroll
                 for (int dd = 1; dd < G; dd <<= 1) {
@@ -467,12 +349,12 @@ struct Walker {
                     const int mycnt = (int)((own >> sh) & 1023u);
                     const unsigned ob = g.ballot(idx >= myex && idx < myex + mycnt);
                     const int ol = __ffs(ob) - 1;
-                    const uint32_t mk = X == 0 ? bu : (X == 1 ? bv : bw);
+                    const uint32_t mkx = X == 0 ? bu : (X == 1 ? bv : bw);
                     const int nth = idx - myex;
                     int pos = 0, cnt = 0;
 #pragma unroll
                     for (int p = 0; p < S; ++p) {
-                        const int b = (int)((mk >> p) & 1u);
+                        const int b = (int)((mkx >> p) & 1u);
                         if (b && cnt == nth) pos = p;
                         cnt += b;
                     }
@@ -480,39 +362,27 @@ struct Walker {
                     const int pk = g.shfl(packed, ol);
                     j = pk & 0xffff;
                     sneg = pk >> 16;
-                    T tj = fetch(j);
+                    const T tj = fetch(j);
 
                     // flip: (Y, Z) cyclic after X, rho swaps; Y_i += Y_j, Z_j -= s Z_i
                     int Y = X == 0 ? 1 : (X == 1 ? 2 : 0);
                     int Z = X == 0 ? 2 : (X == 1 ? 0 : 1);
                     if (rho) { const int tmp = Y; Y = Z; Z = tmp; }
-                    Wd nyp, nyn, nzp, nzn;
-                    bool ok;
-                    if constexpr (ZT) {
-                        ok = tadd(fpos(ti, Y), fneg(ti, Y), fpos(tj, Y), fneg(tj, Y), nyp, nyn);
-                        const Wd ap = sneg ? fpos(ti, Z) : fneg(ti, Z);
-                        const Wd an = sneg ? fneg(ti, Z) : fpos(ti, Z);
-                        ok &= tadd(fpos(tj, Z), fneg(tj, Z), ap, an, nzp, nzn);
-                    } else {
-                        nyp = fpos(ti, Y) ^ fpos(tj, Y);
-                        nzp = fpos(tj, Z) ^ fpos(ti, Z);
-                        nyn = nzn = Wd(0);
-                        ok = true;
-                    }
+                    T ti2, tj2;
+                    bool ok = O::add(ti, tj, Y, false, mk, ti2);
+                    ok &= O::add(tj, ti, Z, sneg == 0, mk, tj2);
                     if (!ok) {
                         action = kReject;
                         c_rej += 1;
                     } else {
                         action = kAccept;
                         c_acc += 1;
-                        fset(ti, Y, nyp, nyn);
-                        fset(tj, Z, nzp, nzn);
-                        const bool zi = (nyp | nyn) == Wd(0);
-                        const bool zj = (nzp | nzn) == Wd(0);
-                        canon(ti);
-                        canon(tj);
-                        store(ti, i);
-                        store(tj, j);
+                        const bool zi = O::zero(ti2, Y, mk);
+                        const bool zj = O::zero(tj2, Z, mk);
+                        O::canon(ti2, mk);
+                        O::canon(tj2, mk);
+                        store(ti2, i);
+                        store(tj2, j);
                         qlen = 0;
                         if (zi || zj) {
                             q_push(i);
@@ -524,7 +394,7 @@ struct Walker {
                                 const bool z = dd == 0 ? zhi : zlo;
                                 if (z) { drop(dd == 0 ? hi : lo); c_drp += 1; }
                             }
-                        } else if (pair_hit(ti, i) || pair_hit(tj, j)) {
+                        } else if (pair_hit2(ti2, i, tj2, j)) {
                             // the queue is only needed when a term shares a factor pair
                             q_push(i);
                             q_push(j);
@@ -546,10 +416,7 @@ struct Walker {
                     break;
                 }
                 if (r < r_before) c_red += 1;
-                const uint64_t rec = (uint64_t)action | ((uint64_t)X << 4) | ((uint64_t)rho << 6) |
-                                     ((uint64_t)sneg << 7) | ((uint64_t)(uint32_t)i << 8) |
-                                     ((uint64_t)(uint32_t)j << 24) | ((uint64_t)(uint32_t)r << 40);
-                dig = digest_mix(dig, rec);
+                dig = digest_mix(dig, flip_record(action, X, rho, sneg, i, j, r));
                 // best scheme: always when better, with probability 0.01 when equal
                 if (r < best_r) {
                     snapshot(bestp);
@@ -571,13 +438,16 @@ struct Walker {
         }
 
         // ---- write back
-        Wd *dst = reinterpret_cast<Wd *>(d.slots) + (size_t)w * R * NWT;
+        Wd *dst = reinterpret_cast<Wd *>(d.slots) + (size_t)w * R * NWS;
 #pragma unroll
         for (int p = 0; p < S; ++p) {
             const int slot = g.lane * S + p;
             if (slot < R) {
 #pragma unroll
-                for (int q = 0; q < NWT; ++q) dst[(size_t)slot * NWT + q] = st[p][q];
+                for (int q = 0; q < TW; ++q) {
+                    dst[(size_t)slot * NWS + q] = st[p].p[q];
+                    if constexpr (ZT) dst[(size_t)slot * NWS + TW + q] = st[p].n[q];
+                }
             }
         }
         if (g.lane == 0) {
@@ -590,24 +460,24 @@ struct Walker {
     }
 };
 
-template <int MODE, class Wd, int G, int S>
-__global__ void __launch_bounds__(256) walk_kernel(const SegDesc d, const int32_t steps) {
+template <int MODE, class Wd, int TW, int G, int S>
+__global__ void __launch_bounds__(256) walk_group_kernel(const SegDesc d, const int32_t steps) {
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t w = gt / G;
     if (w >= d.n_walkers) return;  // whole groups exit together (G divides 32)
-    Walker<MODE, Wd, G, S> wk;
+    GroupWalker<MODE, Wd, TW, G, S> wk;
     wk.run(d, w, steps);
 }
 
 }  // namespace dev
 
-template <int MODE, class Wd, int G, int S>
-void launch_walk_variant(const SegDesc &d, int32_t steps, int grid, int block, cudaStream_t st) {
-    dev::walk_kernel<MODE, Wd, G, S><<<grid, block, 0, st>>>(d, steps);
+template <int MODE, class Wd, int TW, int G, int S>
+void launch_walk_group(const SegDesc &d, int32_t steps, int grid, int block, cudaStream_t st) {
+    dev::walk_group_kernel<MODE, Wd, TW, G, S><<<grid, block, 0, st>>>(d, steps);
 }
 
-#define TFG_WALK_VARIANT(MODE, WD, BITS, G, S) \
-    WalkVariant{MODE, BITS, G, S, &launch_walk_variant<MODE, WD, G, S>, \
-                reinterpret_cast<const void *>(&dev::walk_kernel<MODE, WD, G, S>)}
+#define TFG_GROUP_VARIANT(MODE, WD, BITS, TW, G, S) \
+    WalkVariant{MODE, BITS, TW, G, S, 0, &launch_walk_group<MODE, WD, TW, G, S>, \
+                reinterpret_cast<const void *>(&dev::walk_group_kernel<MODE, WD, TW, G, S>)}
 
 }  // namespace tfg

@@ -1,0 +1,39 @@
+// Lane-group walk kernel variants (64).
+#include "walk_group.cuh"
+
+namespace tfg {
+const WalkVariant *walk_variants_group_64(int *n) {
+    static const WalkVariant v[] = {
+        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 1, 8, 4),
+        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 1, 8, 8),
+        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 1, 8, 12),
+        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 1, 16, 4),
+        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 1, 16, 6),
+        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 1, 32, 2),
+        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 1, 32, 3),
+        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 1, 32, 4),
+        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 2, 32, 4),
+        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 2, 32, 7),
+        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 2, 32, 8),
+        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 3, 32, 6),
+        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 3, 32, 8),
+        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 3, 32, 12),
+        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 1, 8, 4),
+        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 1, 8, 8),
+        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 1, 8, 12),
+        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 1, 16, 4),
+        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 1, 16, 6),
+        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 1, 32, 2),
+        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 1, 32, 3),
+        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 1, 32, 4),
+        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 2, 32, 4),
+        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 2, 32, 7),
+        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 2, 32, 8),
+        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 3, 32, 6),
+        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 3, 32, 8),
+        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 3, 32, 12),
+    };
+    *n = (int)(sizeof(v) / sizeof(v[0]));
+    return v;
+}
+}  // namespace tfg

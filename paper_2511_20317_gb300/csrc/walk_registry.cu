@@ -4,23 +4,25 @@
 #include "tfg_internal.h"
 
 namespace tfg {
-#define TFG_DECL(name) const WalkVariant *name(int *n);
-TFG_DECL(walk_variants_zt32_g4)
-TFG_DECL(walk_variants_zt32_g8)
-TFG_DECL(walk_variants_zt32_g16)
-TFG_DECL(walk_variants_zt32_g32)
-TFG_DECL(walk_variants_z232_g4)
-TFG_DECL(walk_variants_z232_g8)
-TFG_DECL(walk_variants_z232_g16)
-TFG_DECL(walk_variants_z232_g32)
-#undef TFG_DECL
+const WalkVariant *walk_variants_group_zt32(int *n);
+const WalkVariant *walk_variants_group_z232(int *n);
+const WalkVariant *walk_variants_group_64(int *n);
+const WalkVariant *walk_variants_solo_zt32(int *n);
+const WalkVariant *walk_variants_solo_z232(int *n);
+const WalkVariant *walk_variants_solo_zt64(int *n);
+const WalkVariant *walk_variants_solo_z264(int *n);
 
 const WalkVariant *walk_variants(int *count) {
     static std::vector<WalkVariant> all = [] {
         std::vector<WalkVariant> v;
         const WalkVariant *(*parts[])(int *) = {
-            walk_variants_zt32_g4, walk_variants_zt32_g8, walk_variants_zt32_g16, walk_variants_zt32_g32,
-            walk_variants_z232_g4, walk_variants_z232_g8, walk_variants_z232_g16, walk_variants_z232_g32,
+            walk_variants_group_zt32,
+            walk_variants_group_z232,
+            walk_variants_group_64,
+            walk_variants_solo_zt32,
+            walk_variants_solo_z232,
+            walk_variants_solo_zt64,
+            walk_variants_solo_z264,
         };
         for (auto part : parts) {
             int n = 0;

@@ -1,0 +1,455 @@
+// Thread-per-walker flip-graph walk kernel for sm_103a.
+//
+// Each thread owns one walker.  The walker's live scheme sits in shared
+// memory as packed terms (pterm.cuh) in a [slot][thread] layout, so that a
+// warp reading "slot k" touches one contiguous 8/16-byte-per-thread row
+// (conflict-free vector loads).  Every loop over the slots is unrolled to
+// the compile-time capacity RMAX, which turns every shared-memory address
+// into an immediate offset and every candidate-mask bit into a constant;
+// slots past the live rank are predicated off.  No lane of a warp waits on
+// another: the only cross-thread effects are the shared memory banks.
+//
+// Step order (Algorithm 1 with the plateau policy) and every tie-break are
+// identical to the lane-group kernel and to the CPU reference:
+//   draw -> sample term i -> try_flip candidates ordered (factor, slot, rho)
+//   -> flip + ternary validity -> zero-term removal -> sign normalisation ->
+//   reduction cascade -> best/plateau -> plus transition (+ cascade).
+#pragma once
+#include <cstdint>
+
+#include "pterm.cuh"
+
+namespace tfg {
+namespace dev {
+
+// Bit set over RMAX slots (words of 64 bits, slot index compile-time in loops).
+template <int RMAX>
+struct SlotBits {
+    static constexpr int NW = (RMAX + 63) / 64;
+    uint64_t w[NW];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int a = 0; a < NW; ++a) w[a] = 0;
+    }
+    __device__ __forceinline__ int count() const {
+        int c = 0;
+#pragma unroll
+        for (int a = 0; a < NW; ++a) c += __popcll(w[a]);
+        return c;
+    }
+    __device__ __forceinline__ bool test(int k) const {
+        uint64_t v = w[0];
+#pragma unroll
+        for (int a = 1; a < NW; ++a) v = (k >> 6) == a ? w[a] : v;
+        return (v >> (k & 63)) & 1ull;
+    }
+    // position of the n-th (0-based) set bit; the set must hold more than n bits
+    __device__ __forceinline__ int nth(int n) const {
+        int base = 0;
+        uint64_t x = w[0];
+#pragma unroll
+        for (int a = 1; a < NW; ++a) {
+            const int c = __popcll(x);
+            if (n >= c && base == (a - 1) * 64) { n -= c; base = a * 64; x = w[a]; }
+        }
+        int pos = 0;
+        uint32_t y;
+        int c = __popc((uint32_t)x);
+        if (n >= c) { n -= c; pos = 32; y = (uint32_t)(x >> 32); } else { y = (uint32_t)x; }
+        c = __popc(y & 0xffffu);
+        if (n >= c) { n -= c; pos += 16; y >>= 16; }
+        c = __popc(y & 0xffu);
+        if (n >= c) { n -= c; pos += 8; y >>= 8; }
+        c = __popc(y & 0xfu);
+        if (n >= c) { n -= c; pos += 4; y >>= 4; }
+        c = __popc(y & 0x3u);
+        if (n >= c) { n -= c; pos += 2; y >>= 2; }
+        if (n >= (int)(y & 1u)) pos += 1;
+        return base + pos;
+    }
+};
+
+template <int MODE, class Wd, int RMAX, int BT>
+struct SoloWalker {
+    static constexpr bool ZT = (MODE == TFG_MODE_ZT);
+    static constexpr int NWS = ZT ? 2 : 1;   // words per slot (TW = 1)
+    using T = PTerm<Wd, 1, ZT>;
+    using O = Ops<Wd, 1, ZT>;
+    using M = Masks<Wd, 1>;
+
+    Wd *sm;      // this thread's column: slot k at sm[k * BT * NWS]
+    M mk;
+    int r, best_r, R;
+    int64_t t, plateau, best_t;
+    uint64_t dig;
+    uint32_t wid, key0, key1;
+    uint32_t c_acc, c_rej, c_noc, c_drp, c_mrg, c_pls, c_red;
+    int qlen, q0, q1, q2;
+
+    __device__ __forceinline__ T ld(int k) const {
+        const Wd *a = sm + (size_t)k * BT * NWS;
+        T v;
+        if constexpr (ZT) {
+            if constexpr (sizeof(Wd) == 4) {
+                const uint2 q = *reinterpret_cast<const uint2 *>(a);
+                v.p[0] = q.x; v.n[0] = q.y;
+            } else {
+                const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(a);
+                v.p[0] = q.x; v.n[0] = q.y;
+            }
+        } else {
+            v.p[0] = a[0];
+            v.n[0] = 0;
+        }
+        return v;
+    }
+    __device__ __forceinline__ void st(int k, const T &v) {
+        Wd *a = sm + (size_t)k * BT * NWS;
+        if constexpr (ZT) {
+            if constexpr (sizeof(Wd) == 4) *reinterpret_cast<uint2 *>(a) = make_uint2(v.p[0], v.n[0]);
+            else *reinterpret_cast<ulonglong2 *>(a) = make_ulonglong2(v.p[0], v.n[0]);
+        } else {
+            a[0] = v.p[0];
+        }
+    }
+
+    // ---- reduction queue (slot indices)
+    __device__ __forceinline__ void q_push(int s) {
+        q0 = (qlen == 0) ? s : q0;
+        q1 = (qlen == 1) ? s : q1;
+        q2 = (qlen == 2) ? s : q2;
+        qlen += 1;
+    }
+    __device__ __forceinline__ int q_pop() {
+        const int s = q0;
+        q0 = q1; q1 = q2;
+        qlen -= 1;
+        return s;
+    }
+    __device__ __forceinline__ void q_remove(int s) {
+        const bool k0 = qlen > 0 && q0 != s, k1 = qlen > 1 && q1 != s, k2 = qlen > 2 && q2 != s;
+        const int n0 = k0 ? q0 : (k1 ? q1 : q2);
+        const int n1 = k0 ? (k1 ? q1 : q2) : q2;
+        q0 = n0; q1 = n1;
+        qlen = (int)k0 + (int)k1 + (int)k2;
+    }
+    __device__ __forceinline__ void q_rename(int from, int to) {
+        q0 = (qlen > 0 && q0 == from) ? to : q0;
+        q1 = (qlen > 1 && q1 == from) ? to : q1;
+        q2 = (qlen > 2 && q2 == from) ? to : q2;
+    }
+
+    // Remove slot h: the last live term moves into the hole.
+    __device__ __forceinline__ void drop(int h) {
+        const int last = r - 1;
+        q_remove(h);
+        if (h != last) {
+            st(h, ld(last));
+            q_rename(last, h);
+        }
+        r -= 1;
+    }
+
+    // Any other live slot sharing a factor pair with a (slot sa) or b (slot sb)?
+    __device__ __forceinline__ bool pair_hit2(const T &a, int sa, const T &b, int sb) const {
+        bool hit = false;
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k) {
+            const T c = ld(k);
+            bool eu, ev, ewp, ewn;
+            O::compare(c, a, mk, eu, ev, ewp, ewn);
+            const bool ew = ewp || ewn;
+            const bool ha = (eu && ev) || (eu && ew) || (ev && ew);
+            O::compare(c, b, mk, eu, ev, ewp, ewn);
+            const bool ew2 = ewp || ewn;
+            const bool hb = (eu && ev) || (eu && ew2) || (ev && ew2);
+            hit |= (k < r) && ((ha && k != sa) || (hb && k != sb));
+        }
+        return hit;
+    }
+
+    // validity of a_f + (neg ? -b_f : b_f)
+    __device__ __forceinline__ bool sum_ok(const T &a, const T &b, Wd m, bool neg) const {
+        if constexpr (ZT) {
+            const Wd bp = neg ? b.n[0] : b.p[0], bn = neg ? b.p[0] : b.n[0];
+            return (((a.p[0] & bp) | (a.n[0] & bn)) & m) == Wd(0);
+        } else {
+            return true;
+        }
+    }
+
+    // Reduction of slot s with the lowest partner sharing (u,v), else (u,w),
+    // else (v,w), whose merged third factor stays in the coefficient set.
+    __device__ __forceinline__ void reduce_one(int s) {
+        const T v = ld(s);
+        int k0 = -1, k1 = -1, k2 = -1;
+        bool n1 = false, n2 = false;
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k) {
+            const T c = ld(k);
+            const bool live = k < r && k != s;
+            bool eu, ev, ewp, ewn;
+            O::compare(c, v, mk, eu, ev, ewp, ewn);
+            const bool ew = ewp || ewn;
+            const bool m0 = live && eu && ev && sum_ok(v, c, mk.m[2][0], false);
+            const bool m1 = live && eu && ew && sum_ok(v, c, mk.m[1][0], ewn);
+            const bool m2 = live && ev && ew && sum_ok(v, c, mk.m[0][0], ewn);
+            if (m0 && k0 < 0) k0 = k;
+            if (m1 && k1 < 0) { k1 = k; n1 = ewn; }
+            if (m2 && k2 < 0) { k2 = k; n2 = ewn; }
+        }
+        if (k0 < 0 && k1 < 0 && k2 < 0) return;
+        const int P = k0 >= 0 ? 0 : (k1 >= 0 ? 1 : 2);
+        const int k = P == 0 ? k0 : (P == 1 ? k1 : k2);
+        const bool kneg = P == 1 ? n1 : (P == 2 ? n2 : false);
+        const int F = 2 - P;   // third factor: w, v, u
+        const T kv = ld(k);
+        T mv;
+        O::add(v, kv, F, kneg, mk, mv);
+        const bool zero = O::zero(mv, F, mk);
+        O::canon(mv, mk);
+        const int lo = s < k ? s : k;
+        const int hi = s < k ? k : s;
+        q_remove(k);
+        st(lo, mv);
+        c_mrg += 1;
+        drop(hi);
+        if (zero) {
+            drop(lo);
+            c_drp += 1;
+        } else {
+            q_push(lo);
+        }
+    }
+
+    __device__ __forceinline__ void cascade() {
+#pragma unroll 1
+        while (qlen > 0) reduce_one(q_pop());
+    }
+
+    __device__ __forceinline__ void snapshot(Wd *bestp) const {
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k) {
+            if (k < r) {
+                const T v = ld(k);
+                if constexpr (ZT) {
+                    if constexpr (sizeof(Wd) == 4) reinterpret_cast<uint2 *>(bestp)[k] = make_uint2(v.p[0], v.n[0]);
+                    else reinterpret_cast<ulonglong2 *>(bestp)[k] = make_ulonglong2(v.p[0], v.n[0]);
+                } else {
+                    bestp[k] = v.p[0];
+                }
+            }
+        }
+    }
+
+    // Plus transition (Section 3.3.1): writes the three new terms and queues
+    // them; returns the digest record (0 when no attempt passed).
+    __device__ __forceinline__ uint64_t plus_setup(const SegDesc &d) {
+#pragma unroll 1
+        for (int a = 1; a <= d.plus_attempts; ++a) {
+            const U4 y = philox10((uint32_t)t, (uint32_t)(t >> 32), wid, (uint32_t)a, key0, key1);
+            const int pi = (int)__umulhi(y.x, (uint32_t)r);
+            const int pj = (pi + 1 + (int)__umulhi(y.y, (uint32_t)(r - 1))) % r;
+            const int perm = (int)__umulhi(y.z, 6u);
+            int A, B, C;
+            plus_roles(perm, A, B, C);
+            const T ti = ld(pi), tj = ld(pj);
+            T nb, nc, na;
+            bool ok = O::add(ti, tj, B, false, mk, nb);      // B_i + B_j
+            ok &= O::add(tj, ti, C, true, mk, nc);           // C_j - C_i
+            ok &= O::add(tj, ti, A, true, mk, na);           // A_j - A_i
+            ok = ok && !O::zero(nb, B, mk) && !O::zero(nc, C, mk) && !O::zero(na, A, mk);
+            if (!ok) continue;
+            T tn = na;                 // (A_j - A_i, B_j, C_j)
+            O::canon(tn, mk);
+            st(r, tn);
+            T tj2 = nc;                // (A_i, B_j, C_j - C_i)
+            O::take(tj2, ti, A, mk);
+            O::canon(tj2, mk);
+            st(pj, tj2);
+            T ti2 = nb;                // (A_i, B_i + B_j, C_i)
+            O::canon(ti2, mk);
+            st(pi, ti2);
+            r += 1;
+            plateau = 0;
+            c_pls += 1;
+            qlen = 0;
+            q_push(pi);
+            q_push(pj);
+            q_push(r - 1);
+            return plus_record(a, perm, pi, pj);
+        }
+        return 0;
+    }
+
+    __device__ __forceinline__ void run(const SegDesc &d, int64_t w, int32_t steps) {
+        tfg_walker_info *H = d.hdr + w;
+        r = H->r; best_r = H->best_r; R = d.R;
+        t = H->t; plateau = H->plateau; best_t = H->best_t;
+        dig = H->digest; wid = H->walker_id;
+        key0 = d.key0; key1 = d.key1;
+        mk.load(d);
+        c_acc = c_rej = c_noc = c_drp = c_mrg = c_pls = c_red = 0;
+        qlen = 0; q0 = q1 = q2 = 0;
+        const Wd *src = reinterpret_cast<const Wd *>(d.slots) + (size_t)w * R * NWS;
+        Wd *bestp = reinterpret_cast<Wd *>(d.best) + (size_t)w * R * NWS;
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k) {
+            T v;
+            v.p[0] = (k < R) ? src[(size_t)k * NWS] : Wd(0);
+            v.n[0] = (ZT && k < R) ? src[(size_t)k * NWS + (NWS - 1)] : Wd(0);
+            st(k, v);
+        }
+
+#pragma unroll 1
+        for (int32_t step = 0; step < steps; ++step) {
+            const U4 x = philox10((uint32_t)t, (uint32_t)(t >> 32), wid, 0u, key0, key1);
+            const int r_before = r;
+            const int i = (int)__umulhi(x.x, (uint32_t)r);
+            int action = kNoCand, X = 0, j = 0, rho = 0, sneg = 0;
+            {
+                const T ti = ld(i);
+                // ---- try_flip candidates: X_j = +-X_i, ordered (X, slot, rho)
+                SlotBits<RMAX> mu, mv, mw, mwn;
+                mu.clear(); mv.clear(); mw.clear(); mwn.clear();
+#pragma unroll
+                for (int k = 0; k < RMAX; ++k) {
+                    const T c = ld(k);
+                    const bool live = k < r && k != i;
+                    bool eu, ev, ewp, ewn;
+                    O::compare(c, ti, mk, eu, ev, ewp, ewn);
+                    const uint64_t bit = 1ull << (k & 63);
+                    mu.w[k >> 6] |= (live && eu) ? bit : 0ull;
+                    mv.w[k >> 6] |= (live && ev) ? bit : 0ull;
+                    mw.w[k >> 6] |= (live && (ewp || ewn)) ? bit : 0ull;
+                    if constexpr (ZT) mwn.w[k >> 6] |= (live && ewn) ? bit : 0ull;
+                }
+                const int nU = mu.count(), nV = mv.count(), nW = mw.count();
+                const int K = 2 * (nU + nV + nW);
+                if (K > 0) {
+                    const int c = (int)__umulhi(x.y, (uint32_t)K);
+                    rho = c & 1;
+                    const int mi = c >> 1;
+                    if (mi < nU) { X = 0; j = mu.nth(mi); }
+                    else if (mi < nU + nV) { X = 1; j = mv.nth(mi - nU); }
+                    else { X = 2; j = mw.nth(mi - nU - nV); sneg = ZT ? (int)mwn.test(j) : 0; }
+                    const T tj = ld(j);
+                    // flip: (Y, Z) cyclic after X, rho swaps; Y_i += Y_j, Z_j -= s Z_i
+                    int Y = X == 0 ? 1 : (X == 1 ? 2 : 0);
+                    int Z = X == 0 ? 2 : (X == 1 ? 0 : 1);
+                    if (rho) { const int tmp = Y; Y = Z; Z = tmp; }
+                    T ti2, tj2;
+                    bool ok = O::add(ti, tj, Y, false, mk, ti2);
+                    ok &= O::add(tj, ti, Z, sneg == 0, mk, tj2);
+                    if (!ok) {
+                        action = kReject;
+                        c_rej += 1;
+                    } else {
+                        action = kAccept;
+                        c_acc += 1;
+                        const bool zi = O::zero(ti2, Y, mk);
+                        const bool zj = O::zero(tj2, Z, mk);
+                        O::canon(ti2, mk);
+                        O::canon(tj2, mk);
+                        st(i, ti2);
+                        st(j, tj2);
+                        qlen = 0;
+                        if (zi || zj) {
+                            q_push(i);
+                            q_push(j);
+                            const int hi = i > j ? i : j, lo = i > j ? j : i;
+                            const bool zhi = (hi == i) ? zi : zj, zlo = (lo == i) ? zi : zj;
+                            if (zhi) { drop(hi); c_drp += 1; }
+                            if (zlo) { drop(lo); c_drp += 1; }
+                        } else if (pair_hit2(ti2, i, tj2, j)) {
+                            q_push(i);
+                            q_push(j);
+                        }
+                    }
+                } else {
+                    c_noc += 1;
+                }
+            }
+
+            // ---- reduction cascade (flip), bookkeeping, plus + its cascade
+            bool plus_phase = false;
+            uint64_t rec2 = 0;
+#pragma unroll 1
+            for (;;) {
+                cascade();
+                if (plus_phase) {
+                    dig = digest_mix(dig, rec2 | ((uint64_t)(uint32_t)r << 44));
+                    break;
+                }
+                if (r < r_before) c_red += 1;
+                dig = digest_mix(dig, flip_record(action, X, rho, sneg, i, j, r));
+                if (r < best_r) {
+                    snapshot(bestp);
+                    best_r = r;
+                    best_t = t;
+                    plateau = 0;
+                } else {
+                    if (r == best_r && x.z < d.refresh_thresh) snapshot(bestp);
+                    plateau += 1;
+                }
+                if (d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2) {
+                    rec2 = plus_setup(d);
+                    if (rec2) { plus_phase = true; continue; }
+                }
+                break;
+            }
+            t += 1;
+        }
+
+        Wd *dst = reinterpret_cast<Wd *>(d.slots) + (size_t)w * R * NWS;
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k) {
+            if (k < R) {
+                const T v = ld(k);
+                dst[(size_t)k * NWS] = v.p[0];
+                if constexpr (ZT) dst[(size_t)k * NWS + 1] = v.n[0];
+            }
+        }
+        H->r = r; H->best_r = best_r;
+        H->t = t; H->plateau = plateau; H->best_t = best_t;
+        H->digest = dig;
+        H->accepted += c_acc; H->rejected += c_rej; H->nocand += c_noc;
+        H->drops += c_drp; H->merges += c_mrg; H->plus += c_pls; H->reductions += c_red;
+    }
+};
+
+template <int MODE, class Wd, int RMAX, int BT>
+__global__ void __launch_bounds__(BT) walk_solo_kernel(const SegDesc d, const int32_t steps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t w = (int64_t)blockIdx.x * BT + threadIdx.x;
+    if (w >= d.n_walkers) return;   // no block-wide barrier is used
+    SoloWalker<MODE, Wd, RMAX, BT> wk;
+    constexpr int NWS = (MODE == TFG_MODE_ZT) ? 2 : 1;
+    wk.sm = reinterpret_cast<Wd *>(smem_raw) + (size_t)threadIdx.x * NWS;
+    wk.run(d, w, steps);
+}
+
+}  // namespace dev
+
+template <int MODE, class Wd, int RMAX, int BT>
+constexpr size_t solo_smem_bytes() {
+    return (size_t)RMAX * BT * ((MODE == TFG_MODE_ZT) ? 2 : 1) * sizeof(Wd);
+}
+
+template <int MODE, class Wd, int RMAX, int BT>
+void launch_walk_solo(const SegDesc &d, int32_t steps, int grid, int /*block*/, cudaStream_t st) {
+    constexpr size_t smem = solo_smem_bytes<MODE, Wd, RMAX, BT>();
+    static bool attr = [] {
+        cudaFuncSetAttribute(dev::walk_solo_kernel<MODE, Wd, RMAX, BT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return true;
+    }();
+    (void)attr;
+    dev::walk_solo_kernel<MODE, Wd, RMAX, BT><<<grid, BT, smem, st>>>(d, steps);
+}
+
+#define TFG_SOLO_VARIANT(MODE, WD, BITS, RMAX, BT) \
+    WalkVariant{MODE, BITS, 1, 1, RMAX, BT, &launch_walk_solo<MODE, WD, RMAX, BT>, \
+                reinterpret_cast<const void *>(&dev::walk_solo_kernel<MODE, WD, RMAX, BT>)}
+
+}  // namespace tfg

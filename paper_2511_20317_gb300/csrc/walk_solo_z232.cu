@@ -1,0 +1,15 @@
+// Thread-per-walker walk kernel variants (z232), 128 threads per block.
+#include "walk_solo.cuh"
+
+namespace tfg {
+const WalkVariant *walk_variants_solo_z232(int *n) {
+    static const WalkVariant v[] = {
+        TFG_SOLO_VARIANT(TFG_MODE_Z2, uint32_t, 32, 12, 128),
+        TFG_SOLO_VARIANT(TFG_MODE_Z2, uint32_t, 32, 16, 128),
+        TFG_SOLO_VARIANT(TFG_MODE_Z2, uint32_t, 32, 24, 128),
+        TFG_SOLO_VARIANT(TFG_MODE_Z2, uint32_t, 32, 32, 128),
+    };
+    *n = (int)(sizeof(v) / sizeof(v[0]));
+    return v;
+}
+}  // namespace tfg

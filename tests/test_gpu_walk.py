@@ -30,8 +30,8 @@ def gpu():
 def gpu_walkers(fmt, mode, start, nw, seed, steps, chunks=1, **params):
     p = tfg.tfg_default_params(**params)
     W = tfg.Walkers([(fmt, mode, start, nw)], seed=seed, params=p)
-    for _ in range(chunks):
-        W.walk(steps // chunks)
+    for c in range(chunks):
+        W.walk(steps // chunks + (steps % chunks if c == chunks - 1 else 0))
     W.sync()
     return W
 
@@ -61,7 +61,7 @@ def test_philox_device_matches_oracle():
 
 
 @pytest.mark.parametrize("mode", [tfg.TFG_MODE_ZT, tfg.TFG_MODE_Z2])
-@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+@pytest.mark.parametrize("lanes", [1, 4, 8, 16, 32])
 @pytest.mark.parametrize("fmt,L,steps,nw", [((2, 2, 2), 200, 6000, 300), ((3, 3, 3), 600, 4000, 200),
                                             ((2, 3, 4), 400, 3000, 130)])
 def test_parity_small_all_mappings(fmt, L, steps, nw, lanes, mode):
@@ -181,3 +181,23 @@ def test_start_from_paper_scheme_and_edge_formats():
         if f == (1, 1, 1):
             assert (info["nocand"] == 2000).all()
         assert W.verify_all() == 0
+
+
+@pytest.mark.parametrize("lanes", [0, 32])
+def test_large_formats_from_meta_operator_starts(lanes):
+    """Large formats need two and three 64-bit words per sign: (4,5,12) from
+    product(Strassen, double(extend(Strassen))) extended on n (rank 202), and
+    (6,7,9) from the naive rank-378 scheme."""
+    fmt_s, S = read_scheme(os.path.join(golden_dir(), "strassen_2x2x2_r7.txt"))
+    f1, s1 = tfg.tfg_extend(fmt_s, S, 2)
+    f2, s2 = tfg.tfg_double(f1, s1, 2)
+    f3, s3 = tfg.tfg_product(fmt_s, S, f2, s2)
+    f4, s4 = tfg.tfg_extend(f3, s3, 1)
+    assert f4 == (4, 5, 12) and s4.shape[0] == 202
+    for fmt, start, nw, steps, L in [(f4, s4, 40, 1500, 300), ((6, 7, 9), naive_start(6, 7, 9), 12, 400, 100)]:
+        W = gpu_walkers(fmt, 0, start, nw, 4, steps, plateau_len=L, mapping=lanes)
+        info, slots, best = W.read_walkers(0, nw)
+        ref = oracle.Walkers(fmt, start, np.arange(nw), seed=4, plateau_len=L).walk(steps, THREADS)
+        assert_parity(info, slots, best, ref, range(nw), f"large {fmt} lanes={lanes}")
+        assert W.verify_all() == 0
+        W.close()
