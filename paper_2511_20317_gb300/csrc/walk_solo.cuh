@@ -86,8 +86,26 @@ struct SoloWalker {
     uint32_t c_acc, c_rej, c_noc, c_drp, c_mrg, c_pls, c_red;
     int qlen, q0, q1, q2;
 
+    __device__ __forceinline__ static T ld_from(const Wd *col, int k) {
+        const Wd *a = col + (size_t)k * BT * NWS;
+        T v;
+        if constexpr (ZT) {
+            if constexpr (sizeof(Wd) == 4) {
+                const uint2 q = *reinterpret_cast<const uint2 *>(a);
+                v.p[0] = q.x; v.n[0] = q.y;
+            } else {
+                const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(a);
+                v.p[0] = q.x; v.n[0] = q.y;
+            }
+        } else {
+            v.p[0] = a[0];
+            v.n[0] = 0;
+        }
+        return v;
+    }
     __device__ __forceinline__ T ld(int k) const {
         const Wd *a = sm + (size_t)k * BT * NWS;
+
         T v;
         if constexpr (ZT) {
             if constexpr (sizeof(Wd) == 4) {
@@ -150,24 +168,6 @@ struct SoloWalker {
         r -= 1;
     }
 
-    // Any other live slot sharing a factor pair with a (slot sa) or b (slot sb)?
-    __device__ __forceinline__ bool pair_hit2(const T &a, int sa, const T &b, int sb) const {
-        bool hit = false;
-#pragma unroll
-        for (int k = 0; k < RMAX; ++k) {
-            const T c = ld(k);
-            bool eu, ev, ewp, ewn;
-            O::compare(c, a, mk, eu, ev, ewp, ewn);
-            const bool ew = ewp || ewn;
-            const bool ha = (eu && ev) || (eu && ew) || (ev && ew);
-            O::compare(c, b, mk, eu, ev, ewp, ewn);
-            const bool ew2 = ewp || ewn;
-            const bool hb = (eu && ev) || (eu && ew2) || (ev && ew2);
-            hit |= (k < r) && ((ha && k != sa) || (hb && k != sb));
-        }
-        return hit;
-    }
-
     // validity of a_f + (neg ? -b_f : b_f)
     __device__ __forceinline__ bool sum_ok(const T &a, const T &b, Wd m, bool neg) const {
         if constexpr (ZT) {
@@ -222,21 +222,98 @@ struct SoloWalker {
         }
     }
 
-    __device__ __forceinline__ void cascade() {
+    // Reduction cascade of every thread of the warp: the loop runs while any
+    // thread still has queued terms, so the warp is converged afterwards.
+    __device__ __forceinline__ void cascade_all(unsigned wmask) {
 #pragma unroll 1
-        while (qlen > 0) reduce_one(q_pop());
+        while (__any_sync(wmask, qlen > 0)) {
+            if (qlen > 0) reduce_one(q_pop());
+        }
     }
 
-    __device__ __forceinline__ void snapshot(Wd *bestp) const {
+    // Any other live slot sharing a factor pair with a (slot sa) or b (slot sb)?
+    __device__ __forceinline__ bool pair_hit2(const T &a, int sa, const T &b, int sb) const {
+        bool hit = false;
 #pragma unroll
         for (int k = 0; k < RMAX; ++k) {
-            if (k < r) {
-                const T v = ld(k);
+            const T c = ld(k);
+            bool eu, ev, ewp, ewn;
+            O::compare(c, a, mk, eu, ev, ewp, ewn);
+            const bool ew = ewp || ewn;
+            const bool ha = (eu && ev) || (eu && ew) || (ev && ew);
+            O::compare(c, b, mk, eu, ev, ewp, ewn);
+            const bool ew2 = ewp || ewn;
+            const bool hb = (eu && ev) || (eu && ew2) || (ev && ew2);
+            hit |= (k < r) && ((ha && k != sa) || (hb && k != sb));
+        }
+        return hit;
+    }
+
+    // Reduction filter of the warp's accepted flips (terms ti2 in slot i and
+    // tj2 in slot j share a factor pair with another live slot?).  When few
+    // threads need it, the warp checks one walker at a time, its lanes taking
+    // the walker's slots lane, lane+nl, ... from shared memory; when most
+    // need it, every thread scans its own slots.
+    __device__ __forceinline__ bool coop_pair_hit(unsigned wmask, int lane, int nl, bool need, const T &ti2,
+                                                  int i, const T &tj2, int j) const {
+        unsigned pend = __ballot_sync(wmask, need);
+        if (__popc(pend) * 4 > RMAX * 3) return need && pair_hit2(ti2, i, tj2, j);
+        bool mine = false;
+        const int packed = i | (j << 10) | (r << 20);
+#pragma unroll 1
+        while (pend) {
+            const int a = __ffs(pend) - 1;
+            pend &= pend - 1;
+            T A, B;
+            A.p[0] = __shfl_sync(wmask, ti2.p[0], a);
+            B.p[0] = __shfl_sync(wmask, tj2.p[0], a);
+            if constexpr (ZT) {
+                A.n[0] = __shfl_sync(wmask, ti2.n[0], a);
+                B.n[0] = __shfl_sync(wmask, tj2.n[0], a);
+            } else {
+                A.n[0] = 0; B.n[0] = 0;
+            }
+            const int pa = __shfl_sync(wmask, packed, a);
+            const int ia = pa & 1023, ja = (pa >> 10) & 1023, ra = pa >> 20;
+            const Wd *col = sm + (a - lane) * NWS;   // walker a's column
+            bool hit = false;
+#pragma unroll 1
+            for (int k = lane; k < ra; k += nl) {
+                const T c = ld_from(col, k);
+                bool eu, ev, ewp, ewn;
+                O::compare(c, A, mk, eu, ev, ewp, ewn);
+                bool ew = ewp || ewn;
+                const bool ha = (eu && ev) || (eu && ew) || (ev && ew);
+                O::compare(c, B, mk, eu, ev, ewp, ewn);
+                ew = ewp || ewn;
+                const bool hb = (eu && ev) || (eu && ew) || (ev && ew);
+                hit = hit || (ha && k != ia) || (hb && k != ja);
+            }
+            const unsigned hv = __ballot_sync(wmask, hit);
+            if (lane == a) mine = hv != 0u;
+        }
+        return mine;
+    }
+
+    // Warp-cooperative best snapshot: lanes copy consecutive slots of each
+    // requesting walker's column to its best buffer (coalesced stores).
+    __device__ __forceinline__ void coop_snapshot(unsigned wmask, int lane, int nl, bool want, Wd *bestp) const {
+        unsigned pend = __ballot_sync(wmask, want);
+#pragma unroll 1
+        while (pend) {
+            const int a = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int ra = __shfl_sync(wmask, r, a);
+            Wd *dst = reinterpret_cast<Wd *>(__shfl_sync(wmask, reinterpret_cast<unsigned long long>(bestp), a));
+            const Wd *col = sm + (a - lane) * NWS;
+#pragma unroll 1
+            for (int k = lane; k < ra; k += nl) {
+                const T v = ld_from(col, k);
                 if constexpr (ZT) {
-                    if constexpr (sizeof(Wd) == 4) reinterpret_cast<uint2 *>(bestp)[k] = make_uint2(v.p[0], v.n[0]);
-                    else reinterpret_cast<ulonglong2 *>(bestp)[k] = make_ulonglong2(v.p[0], v.n[0]);
+                    if constexpr (sizeof(Wd) == 4) reinterpret_cast<uint2 *>(dst)[k] = make_uint2(v.p[0], v.n[0]);
+                    else reinterpret_cast<ulonglong2 *>(dst)[k] = make_ulonglong2(v.p[0], v.n[0]);
                 } else {
-                    bestp[k] = v.p[0];
+                    dst[k] = v.p[0];
                 }
             }
         }
@@ -301,12 +378,21 @@ struct SoloWalker {
             st(k, v);
         }
 
+        // threads past the population returned already; the live lanes of a
+        // warp are 0 .. nl-1 (walkers are assigned to consecutive threads)
+        const unsigned wmask = __activemask();
+        const int lane = threadIdx.x & 31;
+        const int nl = __popc(wmask);
 #pragma unroll 1
         for (int32_t step = 0; step < steps; ++step) {
             const U4 x = philox10((uint32_t)t, (uint32_t)(t >> 32), wid, 0u, key0, key1);
             const int r_before = r;
             const int i = (int)__umulhi(x.x, (uint32_t)r);
             int action = kNoCand, X = 0, j = 0, rho = 0, sneg = 0;
+            bool need_check = false;
+            T ti2, tj2;
+            ti2.p[0] = tj2.p[0] = 0;
+            ti2.n[0] = tj2.n[0] = 0;
             {
                 const T ti = ld(i);
                 // ---- try_flip candidates: X_j = +-X_i, ordered (X, slot, rho)
@@ -315,14 +401,21 @@ struct SoloWalker {
 #pragma unroll
                 for (int k = 0; k < RMAX; ++k) {
                     const T c = ld(k);
-                    const bool live = k < r && k != i;
                     bool eu, ev, ewp, ewn;
                     O::compare(c, ti, mk, eu, ev, ewp, ewn);
                     const uint64_t bit = 1ull << (k & 63);
-                    mu.w[k >> 6] |= (live && eu) ? bit : 0ull;
-                    mv.w[k >> 6] |= (live && ev) ? bit : 0ull;
-                    mw.w[k >> 6] |= (live && (ewp || ewn)) ? bit : 0ull;
-                    if constexpr (ZT) mwn.w[k >> 6] |= (live && ewn) ? bit : 0ull;
+                    mu.w[k >> 6] |= eu ? bit : 0ull;
+                    mv.w[k >> 6] |= ev ? bit : 0ull;
+                    mw.w[k >> 6] |= (ewp || ewn) ? bit : 0ull;
+                    if constexpr (ZT) mwn.w[k >> 6] |= ewn ? bit : 0ull;
+                }
+                // keep live slots [0, r) other than i
+#pragma unroll
+                for (int q = 0; q < SlotBits<RMAX>::NW; ++q) {
+                    const int lo = r - 64 * q;
+                    uint64_t lm = lo >= 64 ? ~0ull : (lo > 0 ? ((1ull << lo) - 1ull) : 0ull);
+                    if ((i >> 6) == q) lm &= ~(1ull << (i & 63));
+                    mu.w[q] &= lm; mv.w[q] &= lm; mw.w[q] &= lm; mwn.w[q] &= lm;
                 }
                 const int nU = mu.count(), nV = mv.count(), nW = mw.count();
                 const int K = 2 * (nU + nV + nW);
@@ -338,7 +431,6 @@ struct SoloWalker {
                     int Y = X == 0 ? 1 : (X == 1 ? 2 : 0);
                     int Z = X == 0 ? 2 : (X == 1 ? 0 : 1);
                     if (rho) { const int tmp = Y; Y = Z; Z = tmp; }
-                    T ti2, tj2;
                     bool ok = O::add(ti, tj, Y, false, mk, ti2);
                     ok &= O::add(tj, ti, Z, sneg == 0, mk, tj2);
                     if (!ok) {
@@ -361,42 +453,44 @@ struct SoloWalker {
                             const bool zhi = (hi == i) ? zi : zj, zlo = (lo == i) ? zi : zj;
                             if (zhi) { drop(hi); c_drp += 1; }
                             if (zlo) { drop(lo); c_drp += 1; }
-                        } else if (pair_hit2(ti2, i, tj2, j)) {
-                            q_push(i);
-                            q_push(j);
+                        } else {
+                            need_check = true;
                         }
                     }
                 } else {
                     c_noc += 1;
                 }
             }
+            // ---- reduction filter for the accepted flips of the warp (converged)
+            if (coop_pair_hit(wmask, lane, nl, need_check, ti2, i, tj2, j)) {
+                q_push(i);
+                q_push(j);
+            }
 
-            // ---- reduction cascade (flip), bookkeeping, plus + its cascade
-            bool plus_phase = false;
+            // ---- phase 0: flip cascade, bookkeeping, snapshot, plus; phase 1: plus cascade
             uint64_t rec2 = 0;
 #pragma unroll 1
-            for (;;) {
-                cascade();
-                if (plus_phase) {
+            for (int phase = 0; phase < 2; ++phase) {
+                cascade_all(wmask);
+                if (phase == 0) {
+                    if (r < r_before) c_red += 1;
+                    dig = digest_mix(dig, flip_record(action, X, rho, sneg, i, j, r));
+                    bool want = false;
+                    if (r < best_r) {
+                        want = true;
+                        best_r = r;
+                        best_t = t;
+                        plateau = 0;
+                    } else {
+                        want = (r == best_r && x.z < d.refresh_thresh);
+                        plateau += 1;
+                    }
+                    coop_snapshot(wmask, lane, nl, want, bestp);
+                    if (d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2)
+                        rec2 = plus_setup(d);
+                } else if (rec2) {
                     dig = digest_mix(dig, rec2 | ((uint64_t)(uint32_t)r << 44));
-                    break;
                 }
-                if (r < r_before) c_red += 1;
-                dig = digest_mix(dig, flip_record(action, X, rho, sneg, i, j, r));
-                if (r < best_r) {
-                    snapshot(bestp);
-                    best_r = r;
-                    best_t = t;
-                    plateau = 0;
-                } else {
-                    if (r == best_r && x.z < d.refresh_thresh) snapshot(bestp);
-                    plateau += 1;
-                }
-                if (d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2) {
-                    rec2 = plus_setup(d);
-                    if (rec2) { plus_phase = true; continue; }
-                }
-                break;
             }
             t += 1;
         }
