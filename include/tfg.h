@@ -221,6 +221,46 @@ int tfg_mapping(tfg_ctx *ctx, int32_t f, int32_t *lanes, int32_t *slots_per_lane
 /* Release the context (host memory only; the workspace stays the caller's). */
 void tfg_destroy(tfg_ctx *ctx);
 
+/* ---- learned flip proposal (BASELINE configs[4]; not in the paper) -------- */
+
+/* Scoring MLP 32 -> 128 -> 128 -> 1 with ReLU, BF16 weights and inputs, FP32
+ * accumulation, run on the tensor cores (tcgen05).  Parameter blob layout
+ * (device memory, tfg_mlp_param_bytes() bytes, 16-byte aligned):
+ *   W1  bf16 [32][128]   (row = input feature)
+ *   W2  bf16 [128][128]  (row = first hidden unit)
+ *   b1, b2, w3  f32 [128] each;  b3  f32 (then 12 bytes of padding).
+ * score = w3 . relu(W2^T relu(W1^T x + b1) + b2) + b3, with the first hidden
+ * layer rounded to bf16 before the second product. */
+size_t tfg_mlp_param_bytes(void);
+
+/* Scores n candidate feature rows d_x (bf16 [n][32], device, 16-byte aligned)
+ * into d_out (f32 [n], device).  Asynchronous on cuda_stream; *d_err (device
+ * int32, caller-zeroed) is set to 1 if a tensor-core completion wait gave up. */
+int tfg_mlp_score(const void *d_params, const uint16_t *d_x, int64_t n, float *d_out, int32_t *d_err,
+                  void *cuda_stream);
+
+/* Training of the scoring MLP on the tensor cores.  Samples: features d_x (bf16
+ * [n][32]), labels d_label (f32 0/1 [n]), weights d_weight (f32 [n]); loss =
+ * sum_k weight_k * log(1 + exp(-(2 label_k - 1) score_k)) (weighted logistic).
+ * Parameter vector order of every gradient / state array: W1 [32][128], W2
+ * [128][128], b1, b2, w3 [128] each, b3 (P = 20865 floats).  The first hidden
+ * layer and the hidden-layer gradients enter the products as bf16.
+ *
+ * tfg_mlp_grad: d_grad (device f32 [P + 1], overwritten) receives the gradient
+ * and, at [P], the loss.  Asynchronous; *d_err set to 1 if a tensor-core
+ * completion wait gave up.
+ * tfg_mlp_train_state_bytes / tfg_mlp_train_init: optimizer state (FP32 master
+ * weights, Adam moments, gradient) in caller device memory, initialised from
+ * the parameter blob.
+ * tfg_mlp_train_step: one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step
+ * counted from 1) on the samples; rewrites d_params (bf16 W1, W2, f32 rest). */
+int tfg_mlp_grad(const void *d_params, const uint16_t *d_x, const float *d_label, const float *d_weight, int64_t n,
+                 float *d_grad, int32_t *d_err, void *cuda_stream);
+size_t tfg_mlp_train_state_bytes(void);
+int tfg_mlp_train_init(void *d_state, const void *d_params, void *cuda_stream);
+int tfg_mlp_train_step(void *d_state, void *d_params, const uint16_t *d_x, const float *d_label,
+                       const float *d_weight, int64_t n, float lr, int32_t step, int32_t *d_err, void *cuda_stream);
+
 /* Philox4x32-10 of the device path, for tests: d_out[4k..4k+3] = Philox(d_ctr[4k..4k+3],
  * key), n counters; d_ctr and d_out are caller-owned device arrays of 4n words.
  * Synchronous on cuda_stream. */

@@ -587,6 +587,59 @@ int tfg_restore(tfg_ctx *ctx, const void *buf, size_t size) {
 
 void tfg_destroy(tfg_ctx *ctx) { delete ctx; }
 
+size_t tfg_mlp_param_bytes(void) { return tfg::mlp_param_bytes(); }
+
+int tfg_mlp_score(const void *d_params, const uint16_t *d_x, int64_t n, float *d_out, int32_t *d_err,
+                  void *cuda_stream) {
+    if (n < 0 || (n > 0 && (!d_params || !d_x || !d_out || !d_err))) { set_error("bad arguments"); return TFG_EINVAL; }
+    if (((uintptr_t)d_x % 16) != 0 || ((uintptr_t)d_params % 16) != 0) { set_error("inputs must be 16-byte aligned"); return TFG_EINVAL; }
+    tfg::launch_mlp_score(d_params, d_x, n, d_out, d_err, reinterpret_cast<cudaStream_t>(cuda_stream));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "mlp score launch");
+    return TFG_OK;
+}
+
+size_t tfg_mlp_train_state_bytes(void) { return (size_t)(4 * tfg::mlp_num_params() + 4) * sizeof(float); }
+
+int tfg_mlp_grad(const void *d_params, const uint16_t *d_x, const float *d_label, const float *d_weight, int64_t n,
+                 float *d_grad, int32_t *d_err, void *cuda_stream) {
+    if (n < 0 || !d_params || !d_grad || !d_err || (n > 0 && (!d_x || !d_label || !d_weight))) {
+        set_error("bad arguments");
+        return TFG_EINVAL;
+    }
+    if (((uintptr_t)d_x % 16) != 0) { set_error("features must be 16-byte aligned"); return TFG_EINVAL; }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaMemsetAsync(d_grad, 0, sizeof(float) * (tfg::mlp_num_params() + 1), st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    tfg::launch_mlp_grad(d_params, d_x, d_label, d_weight, n, d_grad, d_err, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "mlp grad launch");
+    return TFG_OK;
+}
+
+int tfg_mlp_train_init(void *d_state, const void *d_params, void *cuda_stream) {
+    if (!d_state || !d_params) { set_error("bad arguments"); return TFG_EINVAL; }
+    const int P = tfg::mlp_num_params();
+    float *s = reinterpret_cast<float *>(d_state);
+    tfg::launch_master_from_blob(d_params, s, s + P, s + 2 * P, reinterpret_cast<cudaStream_t>(cuda_stream));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "train init launch");
+    return TFG_OK;
+}
+
+int tfg_mlp_train_step(void *d_state, void *d_params, const uint16_t *d_x, const float *d_label,
+                       const float *d_weight, int64_t n, float lr, int32_t step, int32_t *d_err, void *cuda_stream) {
+    if (!d_state || !d_params || step < 1) { set_error("bad arguments (step counts from 1)"); return TFG_EINVAL; }
+    const int P = tfg::mlp_num_params();
+    float *s = reinterpret_cast<float *>(d_state);
+    int rc = tfg_mlp_grad(d_params, d_x, d_label, d_weight, n, s + 3 * P, d_err, cuda_stream);
+    if (rc) return rc;
+    tfg::launch_adam(s, s + P, s + 2 * P, s + 3 * P, d_params, lr, step, reinterpret_cast<cudaStream_t>(cuda_stream));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "adam launch");
+    return TFG_OK;
+}
+
 int tfg_philox_device(const uint32_t *d_ctr, int32_t n, uint32_t key_lo, uint32_t key_hi, uint32_t *d_out,
                       void *cuda_stream) {
     if (n < 0 || (n > 0 && (!d_ctr || !d_out))) { set_error("bad arguments"); return TFG_EINVAL; }

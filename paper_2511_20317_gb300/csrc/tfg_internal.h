@@ -57,6 +57,14 @@ void launch_verify_best(const SegDesc &d, int64_t first, int64_t count, int mode
 void launch_argmin_best(const SegDesc &d, unsigned long long *d_key, cudaStream_t st);
 void launch_stats(const SegDesc &d, int64_t *d_sums /*[9]*/, int *d_minmax /*[2]*/, int64_t *d_hist,
                   int hist_len, cudaStream_t st);
+size_t mlp_param_bytes();
+int launch_mlp_score(const void *params, const void *x, int64_t n, float *out, int *err, cudaStream_t st);
+int mlp_num_params();
+void launch_mlp_grad(const void *params, const void *x, const float *label, const float *weight, int64_t n,
+                     float *grad, int *err, cudaStream_t st);
+void launch_adam(float *master, float *m1, float *m2, const float *grad, void *blob, float lr, int step,
+                 cudaStream_t st);
+void launch_master_from_blob(const void *blob, float *master, float *m1, float *m2, cudaStream_t st);
 void launch_philox(const uint32_t *d_ctr, int n, uint32_t k0, uint32_t k1, uint32_t *d_out, cudaStream_t st);
 
 }  // namespace tfg

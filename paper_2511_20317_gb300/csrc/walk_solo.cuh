@@ -77,7 +77,11 @@ struct SoloWalker {
     using O = Ops<Wd, 1, ZT>;
     using M = Masks<Wd, 1>;
 
-    Wd *sm;      // this thread's column: slot k at sm[k * BT * NWS]
+    // Shared-memory rows hold one slot of every thread of the block; a row is
+    // padded by one element so that walking one thread's column across the
+    // lanes of a warp (cooperative filter and snapshot) spreads over the banks.
+    static constexpr int RS = (BT + 1) * NWS;   // words per row
+    Wd *sm;      // this thread's column: slot k at sm[k * RS]
     M mk;
     int r, best_r, R;
     int64_t t, plateau, best_t;
@@ -87,7 +91,7 @@ struct SoloWalker {
     int qlen, q0, q1, q2;
 
     __device__ __forceinline__ static T ld_from(const Wd *col, int k) {
-        const Wd *a = col + (size_t)k * BT * NWS;
+        const Wd *a = col + (size_t)k * RS;
         T v;
         if constexpr (ZT) {
             if constexpr (sizeof(Wd) == 4) {
@@ -104,7 +108,7 @@ struct SoloWalker {
         return v;
     }
     __device__ __forceinline__ T ld(int k) const {
-        const Wd *a = sm + (size_t)k * BT * NWS;
+        const Wd *a = sm + (size_t)k * RS;
 
         T v;
         if constexpr (ZT) {
@@ -122,7 +126,7 @@ struct SoloWalker {
         return v;
     }
     __device__ __forceinline__ void st(int k, const T &v) {
-        Wd *a = sm + (size_t)k * BT * NWS;
+        Wd *a = sm + (size_t)k * RS;
         if constexpr (ZT) {
             if constexpr (sizeof(Wd) == 4) *reinterpret_cast<uint2 *>(a) = make_uint2(v.p[0], v.n[0]);
             else *reinterpret_cast<ulonglong2 *>(a) = make_ulonglong2(v.p[0], v.n[0]);
@@ -527,7 +531,7 @@ __global__ void __launch_bounds__(BT) walk_solo_kernel(const SegDesc d, const in
 
 template <int MODE, class Wd, int RMAX, int BT>
 constexpr size_t solo_smem_bytes() {
-    return (size_t)RMAX * BT * ((MODE == TFG_MODE_ZT) ? 2 : 1) * sizeof(Wd);
+    return (size_t)RMAX * (BT + 1) * ((MODE == TFG_MODE_ZT) ? 2 : 1) * sizeof(Wd);
 }
 
 template <int MODE, class Wd, int RMAX, int BT>

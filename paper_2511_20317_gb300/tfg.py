@@ -58,7 +58,9 @@ EXPORTED = ["tfg_default_params", "tfg_last_error", "tfg_verify", "tfg_additive_
             "tfg_prepare", "tfg_project", "tfg_extend", "tfg_merge", "tfg_double", "tfg_product",
             "tfg_swap_sizes", "tfg_workspace_size", "tfg_init", "tfg_walk", "tfg_sync", "tfg_collect_best",
             "tfg_verify_all_async", "tfg_stats_get", "tfg_read_walkers", "tfg_population", "tfg_checkpoint",
-            "tfg_restore", "tfg_mapping", "tfg_destroy", "tfg_philox_device"]
+            "tfg_restore", "tfg_mapping", "tfg_destroy", "tfg_philox_device", "tfg_mlp_param_bytes",
+            "tfg_mlp_score", "tfg_mlp_grad", "tfg_mlp_train_state_bytes", "tfg_mlp_train_init",
+            "tfg_mlp_train_step"]
 
 _lib = None
 _lock = threading.Lock()
@@ -105,6 +107,12 @@ def lib() -> ctypes.CDLL:
                 "tfg_mapping": (i32, [P, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
                 "tfg_destroy": (None, [P]),
                 "tfg_philox_device": (i32, [P, i32, u32, u32, P, P]),
+                "tfg_mlp_param_bytes": (sz, []),
+                "tfg_mlp_score": (i32, [P, P, i64, P, P, P]),
+                "tfg_mlp_grad": (i32, [P, P, P, P, i64, P, P, P]),
+                "tfg_mlp_train_state_bytes": (sz, []),
+                "tfg_mlp_train_init": (i32, [P, P, P]),
+                "tfg_mlp_train_step": (i32, [P, P, P, P, P, i64, ctypes.c_float, i32, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -236,6 +244,77 @@ def tfg_philox_device(ctr: np.ndarray, key_lo: int, key_hi: int) -> np.ndarray:
                                    ctypes.c_void_p(out.data_ptr()),
                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
     return out.cpu().numpy().view(np.uint32)
+
+
+def tfg_mlp_param_bytes() -> int:
+    return int(lib().tfg_mlp_param_bytes())
+
+
+def tfg_mlp_score(params, x, out=None, err=None, stream=None):
+    """Score candidate rows x (torch bf16 [n, 32] on the device) with the MLP whose
+    parameter blob `params` is a torch uint8 device tensor; returns f32 scores."""
+    import torch
+    n = x.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=x.device)
+    own_err = err is None
+    if own_err:
+        err = torch.zeros(1, dtype=torch.int32, device=x.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().tfg_mlp_score(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(x.data_ptr()), n,
+                               ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(err.data_ptr()),
+                               ctypes.c_void_p(st.cuda_stream)))
+    if own_err:
+        if int(err.item()) != 0:
+            raise TfgError(TFG_ETIMEOUT, "tensor-core completion wait gave up")
+    return out
+
+
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def tfg_mlp_grad(params, x, label, weight, stream=None):
+    """Gradient (float32 [P]) and loss of the weighted logistic loss on (x, label, weight)."""
+    import torch
+    P = (tfg_mlp_train_state_bytes() // 4 - 4) // 4
+    grad = torch.empty(P + 1, dtype=torch.float32, device=x.device)
+    err = torch.zeros(1, dtype=torch.int32, device=x.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().tfg_mlp_grad(_vp(params), _vp(x), _vp(label), _vp(weight), x.shape[0], _vp(grad), _vp(err),
+                              ctypes.c_void_p(st.cuda_stream)))
+    if int(err.item()) != 0:
+        raise TfgError(TFG_ETIMEOUT, "tensor-core completion wait gave up")
+    return grad[:P], float(grad[P].item())
+
+
+def tfg_mlp_train_state_bytes() -> int:
+    return int(lib().tfg_mlp_train_state_bytes())
+
+
+class MlpTrainer:
+    """Adam training of the parameter blob `params` (torch uint8 device tensor, updated in place)."""
+
+    def __init__(self, params, stream=None):
+        import torch
+        self.params = params
+        self.state = torch.zeros(tfg_mlp_train_state_bytes() // 4, dtype=torch.float32, device=params.device)
+        self.err = torch.zeros(1, dtype=torch.int32, device=params.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.step_no = 0
+        _check(lib().tfg_mlp_train_init(_vp(self.state), _vp(params), ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def tfg_mlp_train_step(self, x, label, weight, lr):
+        self.step_no += 1
+        _check(lib().tfg_mlp_train_step(_vp(self.state), _vp(self.params), _vp(x), _vp(label), _vp(weight),
+                                        x.shape[0], ctypes.c_float(lr), self.step_no, _vp(self.err),
+                                        ctypes.c_void_p(self.stream.cuda_stream)))
+
+    step = tfg_mlp_train_step
+
+    def loss(self) -> float:
+        P = self.state.numel() // 4 - 1
+        return float(self.state[3 * P + P].item())
 
 
 # ---------------------------------------------------------------------------------------------
