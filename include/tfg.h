@@ -261,6 +261,42 @@ int tfg_mlp_train_init(void *d_state, const void *d_params, void *cuda_stream);
 int tfg_mlp_train_step(void *d_state, void *d_params, const uint16_t *d_x, const float *d_label,
                        const float *d_weight, int64_t n, float lr, int32_t step, int32_t *d_err, void *cuda_stream);
 
+/* Window-mode walk (the step the learned proposal acts on).  Each step of a
+ * walker considers a window of up to 128 try_flip candidates: starting at term
+ * i0 = mulhi(x0, r), terms i0, i0+1, ... (mod r) append their candidates in
+ * (factor, slot, rho) order until 128 are collected.  Each candidate gets 32
+ * small-integer features (see the design doc of the repository: one-hot factor,
+ * rho, sign, non-zero counts and ternary validity of the two sums, overlaps,
+ * zero-sum flags, candidate count and window position of the term, r - best_r,
+ * r, m, n, p, a constant 1).  policy 0 (uniform): candidate mulhi(x1, K);
+ * policy 1 (learned): with x3 < eps_thresh as policy 0, else the candidate of
+ * highest MLP score (first on ties).  The chosen flip then goes through the
+ * same validity test, reductions and bookkeeping as tfg_walk.
+ * Populations must be Z_T with m*n + n*p + p*m <= 64 and r_max <= 88.
+ * d_scratch: caller device memory of tfg_window_scratch_bytes (window
+ * features, descriptors, scores).  d_choices (optional, device int32
+ * [steps][walkers]) receives the chosen window index of every step (-1: no
+ * candidate).  log (optional): chosen features with label 1 when the step
+ * lowered the rank (always kept) or 0 (kept when a Philox draw of sub-stream
+ * 256 is below neg_thresh), appended at d_count (device int64, caller-zeroed)
+ * up to capacity entries. */
+typedef struct {
+    uint16_t feat[32];  /* bf16 features of the chosen candidate */
+    float label;        /* 1: the step lowered the rank */
+    uint32_t walker_id, step, pad;
+} tfg_log_entry;
+
+typedef struct {
+    tfg_log_entry *d_entries;
+    int64_t capacity;
+    int64_t *d_count;
+    uint32_t neg_thresh;
+} tfg_log_spec;
+
+int tfg_window_scratch_bytes(tfg_ctx *ctx, size_t *bytes);
+int tfg_walk_window(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_mlp_params, uint32_t eps_thresh,
+                    void *d_scratch, size_t scratch_bytes, int32_t *d_choices, const tfg_log_spec *log);
+
 /* Philox4x32-10 of the device path, for tests: d_out[4k..4k+3] = Philox(d_ctr[4k..4k+3],
  * key), n counters; d_ctr and d_out are caller-owned device arrays of 4n words.
  * Synchronous on cuda_stream. */

@@ -86,6 +86,10 @@ def lib():
             L.orc_init_walkers.argtypes = [i32, i32, i32, i32, i32, P, i32, i32, P, P, P, P]
             L.orc_walk.argtypes = [i32, i32, i32, i32, ctypes.POINTER(Params), i32, u64,
                                    i32, P, i64, i32, P, P, P]
+            L.orc_window_features.argtypes = [i32, i32, i32, i32, i32, P, i32, i32, P, P]
+            L.orc_window_features.restype = i32
+            L.orc_walk_window.argtypes = [i32, i32, i32, ctypes.POINTER(Params), i32, u64, i32, P, i64, i32,
+                                          i32, i32, P, P, P, P]
             L.orc_digest_init.argtypes = [u32]
             L.orc_digest_init.restype = u64
             L.orc_info_size.restype = i32
@@ -162,6 +166,20 @@ def apply_flip(fmt, scheme, i, X, j, s, rho, mode=MODE_ZT):
     return int(action), buf[: r_out.value].copy()
 
 
+WINDOW = 128
+
+
+def window_features(fmt, scheme, best_r, i0, W=WINDOW):
+    """Window of a state (rank = rows of `scheme`) for start term i0: returns
+    (features float32 [K, 32], candidates int32 [K, 5] = (i, X, j, s, rho))."""
+    m, n, p = fmt
+    s = np.ascontiguousarray(scheme, dtype=np.int8).reshape(-1, term_len(fmt))
+    feat = np.zeros((W, 32), np.float32)
+    cand = np.zeros((W, 5), np.int32)
+    K = lib().orc_window_features(m, n, p, s.shape[0], int(best_r), _ptr(s), int(i0), W, _ptr(feat), _ptr(cand))
+    return feat[:K].copy(), cand[:K].copy()
+
+
 def digest_init(walker_id: int) -> int:
     return int(lib().orc_digest_init(walker_id))
 
@@ -202,6 +220,23 @@ class Walkers:
         lib().orc_walk(m, n, p, self.mode, ctypes.byref(self.params), self.r_max, self.seed,
                        self.walker_ids.size, _ptr(self.walker_ids), int(steps), int(threads),
                        _ptr(self.slots), _ptr(self.best), _ptr(self.info))
+        return self
+
+    def walk_window(self, steps: int, policy: int = 0, choices=None, window: int = WINDOW,
+                    threads: int | None = None):
+        """Window-mode steps: policy 0 uniform over the window, policy 1 replays
+        choices [n_walkers, steps] (window index per step, -1 = no candidate)."""
+        if threads is None:
+            threads = len(os.sched_getaffinity(0))
+        m, n, p = self.fmt
+        ch = None
+        if policy == 1:
+            ch = np.ascontiguousarray(choices, dtype=np.int32)
+            assert ch.shape == (self.walker_ids.size, steps)
+        lib().orc_walk_window(m, n, p, ctypes.byref(self.params), self.r_max, self.seed, self.walker_ids.size,
+                              _ptr(self.walker_ids), int(steps), int(threads), int(window), int(policy),
+                              _ptr(ch) if ch is not None else None, _ptr(self.slots), _ptr(self.best),
+                              _ptr(self.info))
         return self
 
     def scheme(self, w: int) -> np.ndarray:

@@ -536,25 +536,15 @@ int orc_apply_flip(int m, int n, int p, int mode, int r, int8_t *scheme, int i,
     return action;
 }
 
-/* One step of the walk (Algorithm 1 with the plateau-triggered plus policy). */
-static void walk_step(walker *wk, cand_t *cbuf)
+/* Rest of a step after the flip: rank-reduction count, digest record, best
+ * scheme (strictly better always, equal rank when x2 < 0.01 * 2^32), plateau,
+ * and the plus transition when the plateau is long and the rank is close to
+ * the best (Algorithm 1's expand guard r <= best + 2). */
+static void finish_step(walker *wk, const uint32_t *x, int r_before, int action, int X, int rho, int s, int i,
+                        int j)
 {
     orc_info *in = wk->info;
     uint64_t t = (uint64_t)in->t;
-    uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(t >> 32), wk->walker_id, 0u}, x[4];
-    orc_philox4x32_10(ctr, wk->key, x);
-
-    int r_before = in->r;
-    int i = (int)mulhi_range(x[0], (uint32_t)in->r);
-    int K = enumerate_candidates(wk, i, cbuf);
-    int action = ORC_NOCAND, X = 0, j = 0, s = 1, rho = 0;
-    if (K > 0) {
-        cand_t c = cbuf[mulhi_range(x[1], (uint32_t)K)];
-        X = c.X; j = c.j; s = c.s; rho = c.rho;
-        action = apply_flip(wk, i, c);
-    } else {
-        in->nocand += 1;
-    }
     if (in->r < r_before) in->reductions += 1;
 
     uint64_t rec = (uint64_t)action | ((uint64_t)X << 4) | ((uint64_t)rho << 6) |
@@ -562,7 +552,6 @@ static void walk_step(walker *wk, cand_t *cbuf)
                    ((uint64_t)(uint32_t)j << 24) | ((uint64_t)(uint32_t)in->r << 40);
     in->digest = digest_mix(in->digest, rec);
 
-    /* best scheme: strictly better always, equal rank with probability 0.01 */
     if (in->r < in->best_r) {
         take_best(wk);
         in->best_r = in->r;
@@ -573,7 +562,6 @@ static void walk_step(walker *wk, cand_t *cbuf)
         in->plateau += 1;
     }
 
-    /* plus transition after a plateau, restricted to rank <= best + 2 */
     if (wk->prm->plus_enabled && in->plateau >= wk->prm->plateau_len &&
         in->r <= in->best_r + 2 && in->r < in->r_max) {
         int pi = 0, pj = 0, perm = 0;
@@ -594,6 +582,152 @@ static void walk_step(walker *wk, cand_t *cbuf)
     }
     in->t += 1;
     if (wk->prm->debug_checks) debug_check(wk);
+}
+
+/* One step of the walk (Algorithm 1 with the plateau-triggered plus policy). */
+static void walk_step(walker *wk, cand_t *cbuf)
+{
+    orc_info *in = wk->info;
+    uint64_t t = (uint64_t)in->t;
+    uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(t >> 32), wk->walker_id, 0u}, x[4];
+    orc_philox4x32_10(ctr, wk->key, x);
+
+    int r_before = in->r;
+    int i = (int)mulhi_range(x[0], (uint32_t)in->r);
+    int K = enumerate_candidates(wk, i, cbuf);
+    int action = ORC_NOCAND, X = 0, j = 0, s = 1, rho = 0;
+    if (K > 0) {
+        cand_t c = cbuf[mulhi_range(x[1], (uint32_t)K)];
+        X = c.X; j = c.j; s = c.s; rho = c.rho;
+        action = apply_flip(wk, i, c);
+    } else {
+        in->nocand += 1;
+    }
+    finish_step(wk, x, r_before, action, X, rho, s, i, j);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Window mode (the step the learned proposal acts on): the candidates of     */
+/* terms i0, i0+1, ... (mod r), each term's in walk order, first W of them.   */
+/* ------------------------------------------------------------------------ */
+#define ORC_FEATURES 32
+
+typedef struct { int i, X, j, s, rho, ki, q; } wcand_t;
+
+static int build_window(const walker *wk, int i0, int W, wcand_t *out, cand_t *tmp)
+{
+    int r = wk->info->r, K = 0;
+    for (int q = 0; q < r && K < W; ++q) {
+        int i = (i0 + q) % r;
+        int ki = enumerate_candidates(wk, i, tmp);
+        for (int a = 0; a < ki && K < W; ++a) {
+            wcand_t c = {i, tmp[a].X, tmp[a].j, tmp[a].s, tmp[a].rho, ki, q};
+            out[K++] = c;
+        }
+    }
+    return K;
+}
+
+static int nnz(const int8_t *a, int L)
+{
+    int c = 0;
+    for (int e = 0; e < L; ++e) c += a[e] != 0;
+    return c;
+}
+
+/* Features of one window candidate: one-hot factor X, rho, sign, non-zero
+ * counts of X_i, Y_i, Y_j, of the sum Y_i + Y_j (0 when it leaves Z_T) and
+ * its validity, the same for Z_i, Z_j and Z_j - s Z_i, positions where both
+ * Y (resp. Z) factors are non-zero, whether each sum vanishes, the term's
+ * candidate count and window position (both capped at 64), r - best_r, r, m,
+ * n, p, and a constant 1. */
+static void window_features(const walker *wk, const wcand_t *c, float *f)
+{
+    const orc_fmt *F = wk->f;
+    int Y = (c->X + 1) % 3, Z = (c->X + 2) % 3;
+    if (c->rho) { int t = Y; Y = Z; Z = t; }
+    int8_t sy[64], sz[64];
+    int vy = vec_add(sy, factor(F, wk->slots, c->i, Y), factor(F, wk->slots, c->j, Y), +1, F->len[Y], F->mode);
+    int vz = vec_add(sz, factor(F, wk->slots, c->j, Z), factor(F, wk->slots, c->i, Z), -c->s, F->len[Z], F->mode);
+    int oy = 0, oz = 0;
+    for (int e = 0; e < F->len[Y]; ++e)
+        oy += factor(F, wk->slots, c->i, Y)[e] != 0 && factor(F, wk->slots, c->j, Y)[e] != 0;
+    for (int e = 0; e < F->len[Z]; ++e)
+        oz += factor(F, wk->slots, c->i, Z)[e] != 0 && factor(F, wk->slots, c->j, Z)[e] != 0;
+    for (int k = 0; k < ORC_FEATURES; ++k) f[k] = 0.f;
+    f[c->X] = 1.f;
+    f[3] = (float)c->rho;
+    f[4] = (float)(c->s < 0);
+    f[5] = (float)nnz(factor(F, wk->slots, c->i, c->X), F->len[c->X]);
+    f[6] = (float)nnz(factor(F, wk->slots, c->i, Y), F->len[Y]);
+    f[7] = (float)nnz(factor(F, wk->slots, c->j, Y), F->len[Y]);
+    f[8] = vy ? (float)nnz(sy, F->len[Y]) : 0.f;
+    f[9] = (float)vy;
+    f[10] = (float)nnz(factor(F, wk->slots, c->i, Z), F->len[Z]);
+    f[11] = (float)nnz(factor(F, wk->slots, c->j, Z), F->len[Z]);
+    f[12] = vz ? (float)nnz(sz, F->len[Z]) : 0.f;
+    f[13] = (float)vz;
+    f[14] = (float)oy;
+    f[15] = (float)oz;
+    f[16] = (float)(vy && nnz(sy, F->len[Y]) == 0);
+    f[17] = (float)(vz && nnz(sz, F->len[Z]) == 0);
+    f[18] = (float)(c->ki < 64 ? c->ki : 64);
+    f[19] = (float)(wk->info->r - wk->info->best_r);
+    f[20] = (float)wk->info->r;
+    f[21] = (float)F->m;
+    f[22] = (float)F->n;
+    f[23] = (float)F->p;
+    f[24] = (float)(c->q < 64 ? c->q : 64);
+    f[31] = 1.f;
+}
+
+/* One window-mode step.  policy 0: candidate mulhi(x1, K); otherwise the
+ * candidate index is taken from *choice (a logged decision being replayed,
+ * -1 when there was no candidate). */
+static void walk_step_window(walker *wk, wcand_t *wbuf, cand_t *tmp, int W, int policy, const int32_t *choice)
+{
+    orc_info *in = wk->info;
+    uint64_t t = (uint64_t)in->t;
+    uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(t >> 32), wk->walker_id, 0u}, x[4];
+    orc_philox4x32_10(ctr, wk->key, x);
+    int r_before = in->r;
+    int i0 = (int)mulhi_range(x[0], (uint32_t)in->r);
+    int K = build_window(wk, i0, W, wbuf, tmp);
+    int action = ORC_NOCAND, X = 0, j = 0, s = 1, rho = 0, i = i0;
+    if (K > 0) {
+        int c = (policy == 0) ? (int)mulhi_range(x[1], (uint32_t)K) : *choice;
+        if (c < 0 || c >= K) { in->debug_failures += 1; c = 0; }
+        wcand_t w = wbuf[c];
+        cand_t cc = {w.X, w.j, w.s, w.rho};
+        i = w.i; X = w.X; j = w.j; s = w.s; rho = w.rho;
+        action = apply_flip(wk, i, cc);
+    } else {
+        if (policy != 0 && *choice != -1) in->debug_failures += 1;
+        in->nocand += 1;
+    }
+    finish_step(wk, x, r_before, action, X, rho, s, i, j);
+}
+
+/* Window and features of a given state (rank r, best rank best_r) for i0:
+ * returns K; out_feat [K][32], out_cand [K][5] = (i, X, j, s, rho). */
+int orc_window_features(int m, int n, int p, int r, int best_r, const int8_t *scheme, int i0, int W,
+                        float *out_feat, int32_t *out_cand)
+{
+    orc_fmt f = make_fmt(m, n, p, ORC_MODE_ZT);
+    orc_info info; memset(&info, 0, sizeof info);
+    info.r = r; info.best_r = best_r;
+    walker wk; memset(&wk, 0, sizeof wk);
+    wk.f = &f; wk.slots = (int8_t *)scheme; wk.info = &info;
+    wcand_t *wb = (wcand_t *)malloc(sizeof(wcand_t) * (size_t)(W > 0 ? W : 1));
+    cand_t *tmp = (cand_t *)malloc(sizeof(cand_t) * (size_t)(6 * r + 6));
+    int K = build_window(&wk, i0, W, wb, tmp);
+    for (int k = 0; k < K; ++k) {
+        window_features(&wk, &wb[k], out_feat + (size_t)k * ORC_FEATURES);
+        out_cand[5 * k + 0] = wb[k].i; out_cand[5 * k + 1] = wb[k].X; out_cand[5 * k + 2] = wb[k].j;
+        out_cand[5 * k + 3] = wb[k].s; out_cand[5 * k + 4] = wb[k].rho;
+    }
+    free(wb); free(tmp);
+    return K;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -654,6 +788,9 @@ typedef struct {
     int r_max;
     uint64_t seed;
     int64_t steps;
+    int window;              /* 0: walk_step; > 0: window mode with this capacity */
+    int policy;              /* window mode: 0 uniform, 1 replay choices */
+    const int32_t *choices;  /* replay: [n_walkers][steps] */
     int n_walkers;
     const uint32_t *walker_ids;
     int8_t *slots, *best;
@@ -675,7 +812,15 @@ static void run_walker(job_t *job, int w)
     wk.key[0] = (uint32_t)job->seed;
     wk.key[1] = (uint32_t)(job->seed >> 32);
     cand_t *cbuf = (cand_t *)malloc(sizeof(cand_t) * (size_t)(6 * job->r_max + 6));
-    for (int64_t s = 0; s < job->steps; ++s) walk_step(&wk, cbuf);
+    if (job->window > 0) {
+        wcand_t *wbuf = (wcand_t *)malloc(sizeof(wcand_t) * (size_t)job->window);
+        for (int64_t s = 0; s < job->steps; ++s)
+            walk_step_window(&wk, wbuf, cbuf, job->window, job->policy,
+                             job->choices ? job->choices + (size_t)w * job->steps + s : NULL);
+        free(wbuf);
+    } else {
+        for (int64_t s = 0; s < job->steps; ++s) walk_step(&wk, cbuf);
+    }
     free(cbuf);
 }
 
@@ -703,6 +848,29 @@ void orc_walk(int m, int n, int p, int mode, const orc_params *prm, int r_max, u
     job.f = &f; job.prm = prm; job.r_max = r_max; job.seed = seed; job.steps = steps;
     job.n_walkers = n_walkers; job.walker_ids = walker_ids;
     job.slots = slots; job.best = best; job.info = info; job.next = 0;
+    job.window = 0; job.policy = 0; job.choices = NULL;
+    pthread_mutex_init(&job.lock, NULL);
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > n_walkers) n_threads = n_walkers > 0 ? n_walkers : 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    for (int a = 0; a < n_threads; ++a) pthread_create(&th[a], NULL, worker_main, &job);
+    for (int a = 0; a < n_threads; ++a) pthread_join(th[a], NULL);
+    free(th);
+    pthread_mutex_destroy(&job.lock);
+}
+
+/* Window mode: policy 0 picks uniformly over the window; policy 1 replays
+ * choices [n_walkers][steps] (window index per step, -1 for no candidate). */
+void orc_walk_window(int m, int n, int p, const orc_params *prm, int r_max, uint64_t seed, int n_walkers,
+                     const uint32_t *walker_ids, int64_t steps, int n_threads, int window, int policy,
+                     const int32_t *choices, int8_t *slots, int8_t *best, orc_info *info)
+{
+    orc_fmt f = make_fmt(m, n, p, ORC_MODE_ZT);
+    job_t job;
+    job.f = &f; job.prm = prm; job.r_max = r_max; job.seed = seed; job.steps = steps;
+    job.n_walkers = n_walkers; job.walker_ids = walker_ids;
+    job.slots = slots; job.best = best; job.info = info; job.next = 0;
+    job.window = window; job.policy = policy; job.choices = choices;
     pthread_mutex_init(&job.lock, NULL);
     if (n_threads < 1) n_threads = 1;
     if (n_threads > n_walkers) n_threads = n_walkers > 0 ? n_walkers : 1;

@@ -640,6 +640,59 @@ int tfg_mlp_train_step(void *d_state, void *d_params, const uint16_t *d_x, const
     return TFG_OK;
 }
 
+static size_t window_row_bytes() { return (size_t)tfg::window_cap() * (32 * 2 + 4 + 4); }
+
+int tfg_window_scratch_bytes(tfg_ctx *ctx, size_t *bytes) {
+    if (!ctx || !bytes) { set_error("bad arguments"); return TFG_EINVAL; }
+    *bytes = align_up((size_t)ctx->total * window_row_bytes() + (size_t)ctx->total * 4);
+    return TFG_OK;
+}
+
+int tfg_walk_window(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_mlp_params, uint32_t eps_thresh,
+                    void *d_scratch, size_t scratch_bytes, int32_t *d_choices, const tfg_log_spec *log) {
+    if (!ctx || steps < 0 || (policy != 0 && policy != 1) || (policy == 1 && !d_mlp_params) || !d_scratch) {
+        set_error("bad arguments");
+        return TFG_EINVAL;
+    }
+    size_t need = 0;
+    tfg_window_scratch_bytes(ctx, &need);
+    if (scratch_bytes < need) { set_error("window scratch too small"); return TFG_ENOMEM; }
+    if ((uintptr_t)d_scratch % 16) { set_error("scratch must be 16-byte aligned"); return TFG_EINVAL; }
+    for (const Segment &s : ctx->segs) {
+        if (s.fmt.mode != TFG_MODE_ZT || s.tw != 1 || s.R > 128 ||
+            tfg::window_apply_capacity(s.word_bits, s.R) == 0) {
+            set_error("window mode needs Z_T populations with m*n+n*p+p*m <= 64 and r_max <= 88");
+            return TFG_EINVAL;
+        }
+    }
+    const int W = tfg::window_cap();
+    const int64_t N = ctx->total;
+    char *base = reinterpret_cast<char *>(d_scratch);
+    auto *feat = reinterpret_cast<uint16_t *>(base);
+    auto *desc = reinterpret_cast<uint32_t *>(base + (size_t)N * W * 64);
+    auto *score = reinterpret_cast<float *>(base + (size_t)N * W * 68);
+    auto *kwin = reinterpret_cast<int *>(base + (size_t)N * W * 72);
+    tfg_log_spec lg{};
+    if (log) lg = *log;
+    int32_t *err = reinterpret_cast<int32_t *>(&ctx->aux()->verify_failures);
+    cudaError_t e = cudaSuccess;
+    for (int64_t st = 0; st < steps; ++st) {
+        for (const Segment &s : ctx->segs)
+            tfg::launch_window(ctx->desc(s), feat + (size_t)s.first * W * 32, desc + (size_t)s.first * W,
+                               kwin + s.first, ctx->stream);
+        if (policy == 1) tfg::launch_mlp_score(d_mlp_params, feat, N * W, score, err, ctx->stream);
+        for (const Segment &s : ctx->segs) {
+            int32_t *ch = d_choices ? d_choices + (size_t)st * N + s.first : nullptr;
+            tfg::launch_window_apply(ctx->desc(s), desc + (size_t)s.first * W, kwin + s.first,
+                                     score + (size_t)s.first * W, policy, eps_thresh,
+                                     feat + (size_t)s.first * W * 32, ch, lg, ctx->stream);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "window step launch");
+    }
+    return TFG_OK;
+}
+
 int tfg_philox_device(const uint32_t *d_ctr, int32_t n, uint32_t key_lo, uint32_t key_hi, uint32_t *d_out,
                       void *cuda_stream) {
     if (n < 0 || (n > 0 && (!d_ctr || !d_out))) { set_error("bad arguments"); return TFG_EINVAL; }

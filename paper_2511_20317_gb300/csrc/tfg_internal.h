@@ -57,6 +57,13 @@ void launch_verify_best(const SegDesc &d, int64_t first, int64_t count, int mode
 void launch_argmin_best(const SegDesc &d, unsigned long long *d_key, cudaStream_t st);
 void launch_stats(const SegDesc &d, int64_t *d_sums /*[9]*/, int *d_minmax /*[2]*/, int64_t *d_hist,
                   int hist_len, cudaStream_t st);
+using WindowLog = tfg_log_spec;
+using WindowLogEntry = tfg_log_entry;
+int window_cap();
+int window_apply_capacity(int word_bits, int R);
+void launch_window(const SegDesc &d, void *feat, uint32_t *desc, int *kwin, cudaStream_t st);
+int launch_window_apply(const SegDesc &d, const uint32_t *desc, const int *kwin, const float *score, int policy,
+                        uint32_t eps, const void *feat, int32_t *choices, const WindowLog &log, cudaStream_t st);
 size_t mlp_param_bytes();
 int launch_mlp_score(const void *params, const void *x, int64_t n, float *out, int *err, cudaStream_t st);
 int mlp_num_params();

@@ -363,8 +363,9 @@ struct SoloWalker {
         return 0;
     }
 
-    __device__ __forceinline__ void run(const SegDesc &d, int64_t w, int32_t steps) {
-        tfg_walker_info *H = d.hdr + w;
+    // ---- walker record and slots: HBM -> registers / shared memory
+    __device__ __forceinline__ void load(const SegDesc &d, int64_t w) {
+        const tfg_walker_info *H = d.hdr + w;
         r = H->r; best_r = H->best_r; R = d.R;
         t = H->t; plateau = H->plateau; best_t = H->best_t;
         dig = H->digest; wid = H->walker_id;
@@ -373,7 +374,6 @@ struct SoloWalker {
         c_acc = c_rej = c_noc = c_drp = c_mrg = c_pls = c_red = 0;
         qlen = 0; q0 = q1 = q2 = 0;
         const Wd *src = reinterpret_cast<const Wd *>(d.slots) + (size_t)w * R * NWS;
-        Wd *bestp = reinterpret_cast<Wd *>(d.best) + (size_t)w * R * NWS;
 #pragma unroll
         for (int k = 0; k < RMAX; ++k) {
             T v;
@@ -381,7 +381,103 @@ struct SoloWalker {
             v.n[0] = (ZT && k < R) ? src[(size_t)k * NWS + (NWS - 1)] : Wd(0);
             st(k, v);
         }
+    }
 
+    __device__ __forceinline__ void store(const SegDesc &d, int64_t w) {
+        Wd *dst = reinterpret_cast<Wd *>(d.slots) + (size_t)w * R * NWS;
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k) {
+            if (k < R) {
+                const T v = ld(k);
+                dst[(size_t)k * NWS] = v.p[0];
+                if constexpr (ZT) dst[(size_t)k * NWS + 1] = v.n[0];
+            }
+        }
+        tfg_walker_info *H = d.hdr + w;
+        H->r = r; H->best_r = best_r;
+        H->t = t; H->plateau = plateau; H->best_t = best_t;
+        H->digest = dig;
+        H->accepted += c_acc; H->rejected += c_rej; H->nocand += c_noc;
+        H->drops += c_drp; H->merges += c_mrg; H->plus += c_pls; H->reductions += c_red;
+    }
+
+    // ---- flip of candidate (X, j, sign, rho) on term i (Section 3.3.1) with the
+    // ternary validity test; on acceptance the terms are normalised and stored,
+    // zero terms are removed, and need_check asks for the reduction filter.
+    __device__ __forceinline__ void apply_candidate(const T &ti, int i, int X, int j, int sneg, int rho, int &action,
+                                                    bool &need_check, T &ti2, T &tj2) {
+        const T tj = ld(j);
+        // (Y, Z) cyclic after X, rho swaps; Y_i += Y_j, Z_j -= s Z_i
+        int Y = X == 0 ? 1 : (X == 1 ? 2 : 0);
+        int Z = X == 0 ? 2 : (X == 1 ? 0 : 1);
+        if (rho) { const int tmp = Y; Y = Z; Z = tmp; }
+        bool ok = O::add(ti, tj, Y, false, mk, ti2);
+        ok &= O::add(tj, ti, Z, sneg == 0, mk, tj2);
+        if (!ok) {
+            action = kReject;
+            c_rej += 1;
+            return;
+        }
+        action = kAccept;
+        c_acc += 1;
+        const bool zi = O::zero(ti2, Y, mk);
+        const bool zj = O::zero(tj2, Z, mk);
+        O::canon(ti2, mk);
+        O::canon(tj2, mk);
+        st(i, ti2);
+        st(j, tj2);
+        qlen = 0;
+        if (zi || zj) {
+            q_push(i);
+            q_push(j);
+            const int hi = i > j ? i : j, lo = i > j ? j : i;
+            const bool zhi = (hi == i) ? zi : zj, zlo = (lo == i) ? zi : zj;
+            if (zhi) { drop(hi); c_drp += 1; }
+            if (zlo) { drop(lo); c_drp += 1; }
+        } else {
+            need_check = true;
+        }
+    }
+
+    // ---- rest of a step, warp-converged: reduction filter and cascade, digest,
+    // best / plateau bookkeeping and snapshot, plus transition and its cascade.
+    __device__ __forceinline__ void finish_step(const SegDesc &d, unsigned wmask, int lane, int nl, Wd *bestp,
+                                                uint32_t x2, int r_before, int action, int X, int rho, int sneg,
+                                                int i, int j, bool need_check, const T &ti2, const T &tj2) {
+        if (coop_pair_hit(wmask, lane, nl, need_check, ti2, i, tj2, j)) {
+            q_push(i);
+            q_push(j);
+        }
+        uint64_t rec2 = 0;
+#pragma unroll 1
+        for (int phase = 0; phase < 2; ++phase) {
+            cascade_all(wmask);
+            if (phase == 0) {
+                if (r < r_before) c_red += 1;
+                dig = digest_mix(dig, flip_record(action, X, rho, sneg, i, j, r));
+                bool want = false;
+                if (r < best_r) {
+                    want = true;
+                    best_r = r;
+                    best_t = t;
+                    plateau = 0;
+                } else {
+                    want = (r == best_r && x2 < d.refresh_thresh);
+                    plateau += 1;
+                }
+                coop_snapshot(wmask, lane, nl, want, bestp);
+                if (d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2)
+                    rec2 = plus_setup(d);
+            } else if (rec2) {
+                dig = digest_mix(dig, rec2 | ((uint64_t)(uint32_t)r << 44));
+            }
+        }
+        t += 1;
+    }
+
+    __device__ __forceinline__ void run(const SegDesc &d, int64_t w, int32_t steps) {
+        load(d, w);
+        Wd *bestp = reinterpret_cast<Wd *>(d.best) + (size_t)w * R * NWS;
         // threads past the population returned already; the live lanes of a
         // warp are 0 .. nl-1 (walkers are assigned to consecutive threads)
         const unsigned wmask = __activemask();
@@ -430,89 +526,14 @@ struct SoloWalker {
                     if (mi < nU) { X = 0; j = mu.nth(mi); }
                     else if (mi < nU + nV) { X = 1; j = mv.nth(mi - nU); }
                     else { X = 2; j = mw.nth(mi - nU - nV); sneg = ZT ? (int)mwn.test(j) : 0; }
-                    const T tj = ld(j);
-                    // flip: (Y, Z) cyclic after X, rho swaps; Y_i += Y_j, Z_j -= s Z_i
-                    int Y = X == 0 ? 1 : (X == 1 ? 2 : 0);
-                    int Z = X == 0 ? 2 : (X == 1 ? 0 : 1);
-                    if (rho) { const int tmp = Y; Y = Z; Z = tmp; }
-                    bool ok = O::add(ti, tj, Y, false, mk, ti2);
-                    ok &= O::add(tj, ti, Z, sneg == 0, mk, tj2);
-                    if (!ok) {
-                        action = kReject;
-                        c_rej += 1;
-                    } else {
-                        action = kAccept;
-                        c_acc += 1;
-                        const bool zi = O::zero(ti2, Y, mk);
-                        const bool zj = O::zero(tj2, Z, mk);
-                        O::canon(ti2, mk);
-                        O::canon(tj2, mk);
-                        st(i, ti2);
-                        st(j, tj2);
-                        qlen = 0;
-                        if (zi || zj) {
-                            q_push(i);
-                            q_push(j);
-                            const int hi = i > j ? i : j, lo = i > j ? j : i;
-                            const bool zhi = (hi == i) ? zi : zj, zlo = (lo == i) ? zi : zj;
-                            if (zhi) { drop(hi); c_drp += 1; }
-                            if (zlo) { drop(lo); c_drp += 1; }
-                        } else {
-                            need_check = true;
-                        }
-                    }
+                    apply_candidate(ti, i, X, j, sneg, rho, action, need_check, ti2, tj2);
                 } else {
                     c_noc += 1;
                 }
             }
-            // ---- reduction filter for the accepted flips of the warp (converged)
-            if (coop_pair_hit(wmask, lane, nl, need_check, ti2, i, tj2, j)) {
-                q_push(i);
-                q_push(j);
-            }
-
-            // ---- phase 0: flip cascade, bookkeeping, snapshot, plus; phase 1: plus cascade
-            uint64_t rec2 = 0;
-#pragma unroll 1
-            for (int phase = 0; phase < 2; ++phase) {
-                cascade_all(wmask);
-                if (phase == 0) {
-                    if (r < r_before) c_red += 1;
-                    dig = digest_mix(dig, flip_record(action, X, rho, sneg, i, j, r));
-                    bool want = false;
-                    if (r < best_r) {
-                        want = true;
-                        best_r = r;
-                        best_t = t;
-                        plateau = 0;
-                    } else {
-                        want = (r == best_r && x.z < d.refresh_thresh);
-                        plateau += 1;
-                    }
-                    coop_snapshot(wmask, lane, nl, want, bestp);
-                    if (d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2)
-                        rec2 = plus_setup(d);
-                } else if (rec2) {
-                    dig = digest_mix(dig, rec2 | ((uint64_t)(uint32_t)r << 44));
-                }
-            }
-            t += 1;
+            finish_step(d, wmask, lane, nl, bestp, x.z, r_before, action, X, rho, sneg, i, j, need_check, ti2, tj2);
         }
-
-        Wd *dst = reinterpret_cast<Wd *>(d.slots) + (size_t)w * R * NWS;
-#pragma unroll
-        for (int k = 0; k < RMAX; ++k) {
-            if (k < R) {
-                const T v = ld(k);
-                dst[(size_t)k * NWS] = v.p[0];
-                if constexpr (ZT) dst[(size_t)k * NWS + 1] = v.n[0];
-            }
-        }
-        H->r = r; H->best_r = best_r;
-        H->t = t; H->plateau = plateau; H->best_t = best_t;
-        H->digest = dig;
-        H->accepted += c_acc; H->rejected += c_rej; H->nocand += c_noc;
-        H->drops += c_drp; H->merges += c_mrg; H->plus += c_pls; H->reductions += c_red;
+        store(d, w);
     }
 };
 

@@ -46,6 +46,15 @@ class tfg_stats(ctypes.Structure):
                [("min_best_r", ctypes.c_int32), ("max_best_r", ctypes.c_int32)]
 
 
+class tfg_log_spec(ctypes.Structure):
+    _fields_ = [("d_entries", ctypes.c_void_p), ("capacity", ctypes.c_int64), ("d_count", ctypes.c_void_p),
+                ("neg_thresh", ctypes.c_uint32)]
+
+
+LOG_ENTRY_DTYPE = np.dtype([("feat", np.uint16, 32), ("label", np.float32), ("walker_id", np.uint32),
+                            ("step", np.uint32), ("pad", np.uint32)])
+WINDOW = 128
+
 WALKER_INFO_DTYPE = np.dtype([("r", np.int32), ("best_r", np.int32), ("r_max", np.int32), ("format", np.int32),
                               ("t", np.int64), ("plateau", np.int64), ("best_t", np.int64),
                               ("digest", np.uint64),
@@ -60,7 +69,7 @@ EXPORTED = ["tfg_default_params", "tfg_last_error", "tfg_verify", "tfg_additive_
             "tfg_verify_all_async", "tfg_stats_get", "tfg_read_walkers", "tfg_population", "tfg_checkpoint",
             "tfg_restore", "tfg_mapping", "tfg_destroy", "tfg_philox_device", "tfg_mlp_param_bytes",
             "tfg_mlp_score", "tfg_mlp_grad", "tfg_mlp_train_state_bytes", "tfg_mlp_train_init",
-            "tfg_mlp_train_step"]
+            "tfg_mlp_train_step", "tfg_window_scratch_bytes", "tfg_walk_window"]
 
 _lib = None
 _lock = threading.Lock()
@@ -110,6 +119,8 @@ def lib() -> ctypes.CDLL:
                 "tfg_mlp_param_bytes": (sz, []),
                 "tfg_mlp_score": (i32, [P, P, i64, P, P, P]),
                 "tfg_mlp_grad": (i32, [P, P, P, P, i64, P, P, P]),
+                "tfg_window_scratch_bytes": (i32, [P, ctypes.POINTER(sz)]),
+                "tfg_walk_window": (i32, [P, i64, i32, P, ctypes.c_uint32, P, sz, P, ctypes.POINTER(tfg_log_spec)]),
                 "tfg_mlp_train_state_bytes": (sz, []),
                 "tfg_mlp_train_init": (i32, [P, P, P]),
                 "tfg_mlp_train_step": (i32, [P, P, P, P, P, i64, ctypes.c_float, i32, P, P]),
@@ -292,6 +303,21 @@ def tfg_mlp_train_state_bytes() -> int:
     return int(lib().tfg_mlp_train_state_bytes())
 
 
+class TransitionLog:
+    """Device buffers for window-mode logging (entries, count), read back as numpy."""
+
+    def __init__(self, capacity: int, neg_thresh: int = 0):
+        import torch
+        self.capacity = int(capacity)
+        self.neg_thresh = int(neg_thresh)
+        self.entries = torch.zeros(self.capacity * LOG_ENTRY_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        self.count = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def read(self) -> np.ndarray:
+        n = min(int(self.count.item()), self.capacity)
+        return self.entries[: n * LOG_ENTRY_DTYPE.itemsize].cpu().numpy().view(LOG_ENTRY_DTYPE).copy()
+
+
 class MlpTrainer:
     """Adam training of the parameter blob `params` (torch uint8 device tensor, updated in place)."""
 
@@ -422,6 +448,42 @@ class Walkers:
         return info, s, b
 
     read_walkers = tfg_read_walkers
+
+    def tfg_walk_window(self, steps: int, policy: int = 0, mlp_params=None, eps_thresh: int = 0,
+                        record_choices: bool = False, log=None):
+        """Window-mode steps (policy 0 uniform over the window, 1 learned).  Returns
+        the chosen window indices [steps, walkers] (device tensor) when asked."""
+        torch = self.torch
+        if getattr(self, "_wscratch", None) is None:
+            b = ctypes.c_size_t()
+            _check(lib().tfg_window_scratch_bytes(self.ctx, ctypes.byref(b)))
+            self._wscratch = torch.empty(b.value, dtype=torch.uint8, device="cuda")
+        choices = None
+        if record_choices:
+            choices = torch.full((steps, self.total), -2, dtype=torch.int32, device="cuda")
+        spec = None
+        if log is not None:
+            spec = tfg_log_spec(log.entries.data_ptr(), log.capacity, log.count.data_ptr(), log.neg_thresh)
+        _check(lib().tfg_walk_window(self.ctx, int(steps), int(policy),
+                                     ctypes.c_void_p(mlp_params.data_ptr()) if mlp_params is not None else None,
+                                     ctypes.c_uint32(eps_thresh), ctypes.c_void_p(self._wscratch.data_ptr()),
+                                     self._wscratch.numel(),
+                                     ctypes.c_void_p(choices.data_ptr()) if choices is not None else None,
+                                     ctypes.byref(spec) if spec is not None else None))
+        return choices
+
+    walk_window = tfg_walk_window
+
+    def window_buffers(self):
+        """Views of the last window step's scratch: features (bf16 [N, 128, 32]),
+        descriptors (int32 [N, 128]), scores (float32 [N, 128]), window sizes (int32 [N])."""
+        torch, N, W = self.torch, self.total, WINDOW
+        b = self._wscratch
+        feat = b[: N * W * 64].view(torch.bfloat16).view(N, W, 32)
+        desc = b[N * W * 64: N * W * 68].view(torch.int32).view(N, W)
+        score = b[N * W * 68: N * W * 72].view(torch.float32).view(N, W)
+        kwin = b[N * W * 72: N * W * 72 + N * 4].view(torch.int32)
+        return feat, desc, score, kwin
 
     def tfg_checkpoint(self) -> bytes:
         used = ctypes.c_size_t()

@@ -51,7 +51,7 @@ def test_score_matches_reference(n):
     # ranking of candidates (what the proposal uses) agrees except near ties
     if n >= 128:
         order_gap = np.sort(want)[-1] - np.sort(want)[-2]
-        if order_gap > 1e-2 * scale:
+        if order_gap > 2 * bound.max():
             assert np.argmax(got) == np.argmax(want)
 
 

@@ -1,0 +1,128 @@
+"""Window-mode walks (the learned proposal's step) against the oracle: uniform
+policy bit-exact; learned policy replayed from the logged choices bit-exact;
+window features bit-exact; network scores and greedy choices within the
+tensor-core tolerance."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_2511_20317_gb300 import tfg
+from paper_2511_20317_gb300.workloads import naive_start
+
+pytestmark = pytest.mark.gpu
+THREADS = len(os.sched_getaffinity(0))
+FIELDS = ["r", "best_r", "t", "plateau", "best_t", "digest", "accepted", "rejected", "nocand", "drops",
+          "merges", "plus", "reductions"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2511_20317_gb300 import _build
+    _build.build()
+    tfg.lib()
+
+
+def device_params(p):
+    import torch
+    return torch.from_numpy(np.frombuffer(p.blob(), dtype=np.uint8).copy()).cuda()
+
+
+def assert_parity(W, ref, n, label):
+    info, slots, best = W.read_walkers(0, n)
+    assert (ref.info["debug_failures"] == 0).all(), label
+    for w in range(n):
+        for f in FIELDS:
+            assert info[f][w] == ref.info[f][w], f"{label} walker {w}: {f} gpu={info[f][w]} oracle={ref.info[f][w]}"
+        r, br = ref.info["r"][w], ref.info["best_r"][w]
+        assert np.array_equal(slots[w, :r], ref.slots[w, :r]), f"{label} walker {w} slots"
+        assert np.array_equal(best[w, :br], ref.best[w, :br]), f"{label} walker {w} best"
+
+
+CASES = [((2, 2, 2), 300, 3000, 200), ((3, 3, 3), 160, 1500, 300), ((3, 4, 5), 70, 400, 100),
+         ((4, 4, 4), 70, 400, 100)]
+
+
+@pytest.mark.parametrize("fmt,nw,steps,L", CASES)
+def test_window_uniform_parity(fmt, nw, steps, L):
+    start = naive_start(*fmt)
+    W = tfg.Walkers([(fmt, 0, start, nw)], seed=5, params=tfg.tfg_default_params(plateau_len=L))
+    W.walk_window(steps, policy=0)
+    ref = oracle.Walkers(fmt, start, np.arange(nw), seed=5, plateau_len=L).walk_window(steps, threads=THREADS)
+    assert_parity(W, ref, nw, f"window-uniform {fmt}")
+    assert W.verify_all() == 0
+
+
+@pytest.mark.parametrize("fmt,nw,steps,L", CASES[1:])
+def test_window_learned_replay(fmt, nw, steps, L):
+    """The learned policy's decisions are replayed by the oracle from the
+    logged window indices: every trajectory matches bit for bit."""
+    start = naive_start(*fmt)
+    p = mlp.Params.random(np.random.default_rng(11))
+    W = tfg.Walkers([(fmt, 0, start, nw)], seed=6, params=tfg.tfg_default_params(plateau_len=L))
+    ch = W.walk_window(steps, policy=1, mlp_params=device_params(p), eps_thresh=int(0.2 * 2**32),
+                       record_choices=True).cpu().numpy()
+    assert (ch >= -1).all()
+    ref = oracle.Walkers(fmt, start, np.arange(nw), seed=6, plateau_len=L).walk_window(
+        steps, policy=1, choices=ch.T, threads=THREADS)
+    assert_parity(W, ref, nw, f"window-learned {fmt}")
+
+
+@pytest.mark.parametrize("fmt", [(3, 3, 3), (4, 4, 4)])
+def test_window_features_scores_and_choice(fmt):
+    """One learned step from a walked state: features and candidates equal the
+    oracle's; scores match the float64 network within the bf16 bound; exploit
+    steps pick a candidate whose reference score is the maximum up to that bound;
+    explore steps (x3 < eps) pick mulhi(x1, K)."""
+    nw, eps = 96, int(0.25 * 2**32)
+    start = naive_start(*fmt)
+    W = tfg.Walkers([(fmt, 0, start, nw)], seed=9, params=tfg.tfg_default_params(plateau_len=150))
+    W.walk_window(300, policy=0)
+    info0, slots0, _ = W.read_walkers(0, nw)
+    p = mlp.Params.random(np.random.default_rng(4))
+    ch = W.walk_window(1, policy=1, mlp_params=device_params(p), eps_thresh=eps, record_choices=True)
+    ch = ch.cpu().numpy()[0]
+    feat, desc, score, kwin = (b.cpu() for b in W.window_buffers())
+    feat = feat.float().numpy()
+    desc, score, kwin = desc.numpy().view(np.uint32), score.numpy(), kwin.numpy()
+    for w in range(nw):
+        r, br, t, wid = int(info0["r"][w]), int(info0["best_r"][w]), int(info0["t"][w]), int(info0["walker_id"][w])
+        x = oracle.philox4x32_10([t & 0xFFFFFFFF, t >> 32, wid, 0], [9, 0])
+        i0 = (int(x[0]) * r) >> 32
+        f_ref, c_ref = oracle.window_features(fmt, slots0[w, :r], br, i0)
+        K = f_ref.shape[0]
+        assert kwin[w] == K
+        assert np.array_equal(feat[w, :K], f_ref)
+        d = desc[w, :K]
+        got = np.stack([d & 1023, (d >> 10) & 3, (d >> 12) & 1023, np.where((d >> 22) & 1, -1, 1), (d >> 23) & 1], 1)
+        assert np.array_equal(got, c_ref)
+        y, cache = mlp.forward(p, f_ref)
+        path = np.abs(p.W2) @ np.abs(p.w3)
+        bound = 2 * ((np.abs(cache[2]) * 2.0 ** -8) * path).max(axis=1) + 1e-5 * (1 + np.abs(y))
+        assert (np.abs(score[w, :K] - y) <= bound).all()
+        if K == 0:
+            assert ch[w] == -1
+        elif int(x[3]) < eps:
+            assert ch[w] == (int(x[1]) * K) >> 32
+        else:
+            assert y[ch[w]] >= y.max() - 2 * bound.max()
+
+
+def test_transition_log():
+    """Logging keeps every rank-lowering step (label 1) and samples the rest."""
+    fmt, nw = (3, 3, 3), 512
+    start = naive_start(*fmt)
+    W = tfg.Walkers([(fmt, 0, start, nw)], seed=3, params=tfg.tfg_default_params(plateau_len=200))
+    log = tfg.TransitionLog(200000, neg_thresh=int(0.02 * 2**32))
+    W.walk_window(1500, policy=0, log=log)
+    st, _ = W.stats()
+    e = log.read()
+    assert int((e["label"] == 1).sum()) == st["reductions"]
+    neg = int((e["label"] == 0).sum())
+    expected = 0.02 * (st["steps"] - st["nocand"] - st["reductions"])
+    assert 0.7 * expected < neg < 1.3 * expected
+    assert set(np.unique(e["label"])) <= {0.0, 1.0}
