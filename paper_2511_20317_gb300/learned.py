@@ -1,0 +1,153 @@
+"""Learned flip proposal: data collection, device training and the A/B test
+against the uniform proposal over the same candidate windows.
+
+Every step of the walk and of the network runs in libtfg's kernels; this module
+only sequences them.  Usage:
+
+    python -m paper_2511_20317_gb300.learned --ab      # collect, train, compare
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import tfg
+from .workloads import MIXED_FORMATS, naive_start
+
+TRAIN_FORMATS = [(2, 2, 2), (3, 3, 3)] + MIXED_FORMATS   # the formats of the uniform workloads
+EVAL_FORMATS = [(4, 4, 4), (3, 4, 5)]
+
+
+def init_params(seed: int = 0):
+    """He-style random parameter blob (device uint8 tensor)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(0, np.sqrt(2.0 / 32), (32, 128)).astype(np.float32)
+    W2 = rng.normal(0, np.sqrt(2.0 / 128), (128, 128)).astype(np.float32)
+    b1 = np.zeros(128, np.float32)
+    b2 = np.zeros(128, np.float32)
+    w3 = rng.normal(0, np.sqrt(1.0 / 128), 128).astype(np.float32)
+    parts = [_bf16_bits(W1), _bf16_bits(W2), b1.tobytes(), b2.tobytes(), w3.tobytes(),
+             np.zeros(4, np.float32).tobytes()]
+    blob = np.frombuffer(b"".join(parts), dtype=np.uint8).copy()
+    assert blob.size == tfg.tfg_mlp_param_bytes()
+    return torch.from_numpy(blob).cuda()
+
+
+def _bf16_bits(a: np.ndarray) -> bytes:
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+    return r.tobytes()
+
+
+def collect(formats=TRAIN_FORMATS, walkers=4096, steps=2000, seed=100, neg_rate=0.01, plateau=500):
+    """Window-uniform walks with transition logging: every rank-lowering step
+    (label 1) and a neg_rate sample of the others (label 0)."""
+    entries = []
+    for k, fmt in enumerate(formats):
+        W = tfg.Walkers([(fmt, 0, naive_start(*fmt), walkers)], seed=seed + k,
+                        params=tfg.tfg_default_params(plateau_len=plateau))
+        log = tfg.TransitionLog(walkers * steps // 20 + 100000, neg_thresh=int(neg_rate * 2**32))
+        W.walk_window(steps, policy=0, log=log)
+        e = log.read()
+        entries.append(e)
+        W.close()
+    return np.concatenate(entries)
+
+
+def train(entries, params=None, epochs=30, batch=8192, lr=2e-3, seed=0):
+    """Adam on the device, class-balanced weighted logistic loss."""
+    import torch
+    if params is None:
+        params = init_params(seed)
+    rng = np.random.default_rng(seed)
+    feats = torch.from_numpy(entries["feat"].view(np.int16).copy()).cuda().view(torch.bfloat16)
+    labels = torch.from_numpy(entries["label"].astype(np.float32)).cuda()
+    n = labels.numel()
+    pos = float(labels.sum().item())
+    neg = n - pos
+    tr = tfg.MlpTrainer(params)
+    history = []
+    for ep in range(epochs):
+        perm = torch.from_numpy(rng.permutation(n)).cuda()
+        for b0 in range(0, n - batch + 1 if n >= batch else 1, batch):
+            idx = perm[b0:b0 + batch]
+            x = feats[idx].contiguous()
+            y = labels[idx].contiguous()
+            p_b = float(y.sum().item())
+            n_b = y.numel() - p_b
+            w = torch.where(y > 0, 0.5 / max(p_b, 1.0), 0.5 / max(n_b, 1.0)).float().contiguous()
+            tr.step(x, y, w, lr)
+        history.append(tr.loss())
+    return params, {"samples": n, "positives": pos, "negatives": neg, "loss": history}
+
+
+def evaluate(fmt, policy, params=None, walkers=16384, steps=3000, seed=0, eps=0.05, plateau=500):
+    """One arm of the A/B: window-mode walks from the naive scheme; returns
+    reductions per 1e9 steps, the lowest rank, every best scheme verified."""
+    import torch
+    W = tfg.Walkers([(fmt, 0, naive_start(*fmt), walkers)], seed=seed,
+                    params=tfg.tfg_default_params(plateau_len=plateau))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    W.walk_window(steps, policy=policy, mlp_params=params, eps_thresh=int(eps * 2**32))
+    W.sync()
+    dt = time.perf_counter() - t0
+    st, hist = W.stats()
+    fails = W.verify_all()
+    scheme, rank, _ = W.collect_best(0)
+    W.close()
+    return {"reductions_per_1e9": st["reductions"] / st["steps"] * 1e9, "lowest_rank": st["min_best_r"],
+            "steps_per_s": st["steps"] / dt, "verify_failures": fails, "accepted_frac": st["accepted"] / st["steps"],
+            "rank_hist": {int(k): int(v) for k, v in enumerate(hist) if v}}
+
+
+def ab_test(params, formats=EVAL_FORMATS, seeds=(0, 1, 2, 3, 4), **kw):
+    out = {}
+    for fmt in formats:
+        arms = {"uniform": [], "learned": []}
+        for s in seeds:
+            arms["uniform"].append(evaluate(fmt, 0, None, seed=1000 + s, **kw))
+            arms["learned"].append(evaluate(fmt, 1, params, seed=1000 + s, **kw))
+        res = {}
+        for arm, runs in arms.items():
+            v = np.array([r["reductions_per_1e9"] for r in runs])
+            res[arm] = {"reductions_per_1e9_mean": float(v.mean()),
+                        "ci95": float(1.96 * v.std(ddof=1) / np.sqrt(len(v))) if len(v) > 1 else None,
+                        "lowest_rank": int(min(r["lowest_rank"] for r in runs)),
+                        "steps_per_s": float(np.mean([r["steps_per_s"] for r in runs])),
+                        "verify_failures": int(sum(r["verify_failures"] for r in runs))}
+        res["gain"] = res["learned"]["reductions_per_1e9_mean"] / max(res["uniform"]["reductions_per_1e9_mean"], 1e-9)
+        out["x".join(map(str, fmt))] = res
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--ab", action="store_true")
+    ap.add_argument("--walkers", type=int, default=16384)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--collect-walkers", type=int, default=4096)
+    ap.add_argument("--collect-steps", type=int, default=2000)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--seeds", type=int, default=5)
+    args = ap.parse_args()
+    import torch
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    e = collect(walkers=args.collect_walkers, steps=args.collect_steps)
+    t1 = time.perf_counter()
+    params, info = train(e, epochs=args.epochs)
+    t2 = time.perf_counter()
+    res = ab_test(params, seeds=tuple(range(args.seeds)), walkers=args.walkers, steps=args.steps)
+    t3 = time.perf_counter()
+    print(json.dumps({"train": {k: v for k, v in info.items() if k != "loss"}, "loss_first_last":
+                      [info["loss"][0], info["loss"][-1]], "ab": res,
+                      "seconds": {"collect": t1 - t0, "train": t2 - t1, "ab": t3 - t2}}))
+
+
+if __name__ == "__main__":
+    main()
