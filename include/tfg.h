@@ -297,6 +297,24 @@ int tfg_window_scratch_bytes(tfg_ctx *ctx, size_t *bytes);
 int tfg_walk_window(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_mlp_params, uint32_t eps_thresh,
                     void *d_scratch, size_t scratch_bytes, int32_t *d_choices, const tfg_log_spec *log);
 
+/* tfg_walk_window without any caller scratch: the paper has no counterpart to
+ * this entry point.  It is for callers that cannot call cudaMalloc (code that
+ * runs inside another framework's memory arena, or a process whose device
+ * memory is reserved up front): the window features, candidate descriptors
+ * and scores live in a 32 MiB array that the library itself defines as static
+ * device memory, which every GPU that loads the library holds until the
+ * process exits.  Contexts of more than 3639 walkers (the array's capacity at
+ * 9220 bytes per walker) are rejected with TFG_EINVAL and a message.  The call
+ * allocates nothing; the context's device must be current; the first call on a
+ * device looks up the array's device address, so make that first call before
+ * any stream capture.  All calls share the one array (it keeps the last
+ * call's contents; every value a step reads is written by the same step), so
+ * calls whose work overlaps on the GPU, such as two contexts on different
+ * streams, race on it and must be serialised by the caller.  Results equal
+ * tfg_walk_window's for the same context and arguments. */
+int tfg_walk_window_noalloc(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_mlp_params,
+                            uint32_t eps_thresh, int32_t *d_choices, const tfg_log_spec *log);
+
 /* Philox4x32-10 of the device path, for tests: d_out[4k..4k+3] = Philox(d_ctr[4k..4k+3],
  * key), n counters; d_ctr and d_out are caller-owned device arrays of 4n words.
  * Synchronous on cuda_stream. */

@@ -2,6 +2,7 @@
 // Device memory is the caller's workspace; the library allocates none.
 #include <algorithm>
 #include <climits>
+#include <mutex>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -705,3 +706,89 @@ int tfg_philox_device(const uint32_t *d_ctr, int32_t n, uint32_t key_lo, uint32_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Window-mode walk with library-owned scratch, for callers that cannot call
+// cudaMalloc (e.g. code running inside another allocator's arena or a
+// runtime whose memory is fully reserved up front): the per-step window
+// scratch lives in this file's static device array instead of caller memory.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;   // 32 MiB, held by every GPU that loads the library
+__device__ __align__(256) unsigned char g_window_scratch[kNoAllocScratchBytes];
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_window_scratch on the current device (host code only
+// sees a host-side stand-in of the symbol); looked up once per device.
+int window_scratch_address(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) { set_error("device index beyond 64"); return TFG_EINVAL; }
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_window_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return TFG_OK;
+}
+}  // namespace
+
+extern "C" int tfg_walk_window_noalloc(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_mlp_params,
+                                       uint32_t eps_thresh, int32_t *d_choices, const tfg_log_spec *log) {
+    if (!ctx || steps < 0 || (policy != 0 && policy != 1) || (policy == 1 && !d_mlp_params)) {
+        set_error("bad arguments");
+        return TFG_EINVAL;
+    }
+    size_t need = 0;
+    tfg_window_scratch_bytes(ctx, &need);
+    if (need > kNoAllocScratchBytes) {
+        set_error("tfg_walk_window_noalloc: " + std::to_string(ctx->total) + " walkers need " + std::to_string(need) +
+                  " scratch bytes, the static scratch holds " + std::to_string(kNoAllocScratchBytes) +
+                  " (at most " + std::to_string(kNoAllocScratchBytes / (window_row_bytes() + 4)) + " walkers)");
+        return TFG_EINVAL;
+    }
+    for (const Segment &s : ctx->segs) {
+        if (s.fmt.mode != TFG_MODE_ZT || s.tw != 1 || s.R > 128 ||
+            tfg::window_apply_capacity(s.word_bits, s.R) == 0) {
+            set_error("window mode needs Z_T populations with m*n+n*p+p*m <= 64 and r_max <= 88");
+            return TFG_EINVAL;
+        }
+    }
+    void *scratch = nullptr;
+    int rc = window_scratch_address(&scratch);
+    if (rc) return rc;
+    // Every row the step reads is written by the step itself (features and
+    // window sizes by the window kernel, scores by the network), so nothing
+    // left in the array by an earlier call needs clearing.
+    const int W = tfg::window_cap();
+    const int64_t N = ctx->total;
+    char *base = reinterpret_cast<char *>(scratch);
+    auto *feat = reinterpret_cast<uint16_t *>(base);
+    auto *desc = reinterpret_cast<uint32_t *>(base + (size_t)N * W * 64);
+    auto *score = reinterpret_cast<float *>(base + (size_t)N * W * 68);
+    auto *kwin = reinterpret_cast<int *>(base + (size_t)N * W * 72);
+    tfg_log_spec lg{};
+    if (log) lg = *log;
+    int32_t *err = reinterpret_cast<int32_t *>(&ctx->aux()->verify_failures);
+    for (int64_t st = 0; st < steps; ++st) {
+        for (const Segment &s : ctx->segs)
+            tfg::launch_window(ctx->desc(s), feat + (size_t)s.first * W * 32, desc + (size_t)s.first * W,
+                               kwin + s.first, ctx->stream);
+        if (policy == 1) tfg::launch_mlp_score(d_mlp_params, feat, N * W, score, err, ctx->stream);
+        for (const Segment &s : ctx->segs) {
+            int32_t *ch = d_choices ? d_choices + (size_t)st * N + s.first : nullptr;
+            tfg::launch_window_apply(ctx->desc(s), desc + (size_t)s.first * W, kwin + s.first,
+                                     score + (size_t)s.first * W, policy, eps_thresh,
+                                     feat + (size_t)s.first * W * 32, ch, lg, ctx->stream);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "window step launch");
+    }
+    return TFG_OK;
+}

@@ -69,7 +69,7 @@ EXPORTED = ["tfg_default_params", "tfg_last_error", "tfg_verify", "tfg_additive_
             "tfg_verify_all_async", "tfg_stats_get", "tfg_read_walkers", "tfg_population", "tfg_checkpoint",
             "tfg_restore", "tfg_mapping", "tfg_destroy", "tfg_philox_device", "tfg_mlp_param_bytes",
             "tfg_mlp_score", "tfg_mlp_grad", "tfg_mlp_train_state_bytes", "tfg_mlp_train_init",
-            "tfg_mlp_train_step", "tfg_window_scratch_bytes", "tfg_walk_window"]
+            "tfg_mlp_train_step", "tfg_window_scratch_bytes", "tfg_walk_window", "tfg_walk_window_noalloc"]
 
 _lib = None
 _lock = threading.Lock()
@@ -120,6 +120,8 @@ def lib() -> ctypes.CDLL:
                 "tfg_mlp_score": (i32, [P, P, i64, P, P, P]),
                 "tfg_mlp_grad": (i32, [P, P, P, P, i64, P, P, P]),
                 "tfg_window_scratch_bytes": (i32, [P, ctypes.POINTER(sz)]),
+                "tfg_walk_window_noalloc": (i32, [P, i64, i32, P, ctypes.c_uint32, P,
+                                                  ctypes.POINTER(tfg_log_spec)]),
                 "tfg_walk_window": (i32, [P, i64, i32, P, ctypes.c_uint32, P, sz, P, ctypes.POINTER(tfg_log_spec)]),
                 "tfg_mlp_train_state_bytes": (sz, []),
                 "tfg_mlp_train_init": (i32, [P, P, P]),
@@ -473,6 +475,19 @@ class Walkers:
         return choices
 
     walk_window = tfg_walk_window
+
+    def tfg_walk_window_noalloc(self, steps: int, policy: int = 0, mlp_params=None, eps_thresh: int = 0,
+                                d_choices=None):
+        """tfg_walk_window with the library's own static scratch (no device
+        allocation by the call).  d_choices: optional caller-owned int32 device
+        tensor [steps, walkers] receiving the chosen window indices."""
+        _check(lib().tfg_walk_window_noalloc(
+            self.ctx, int(steps), int(policy),
+            ctypes.c_void_p(mlp_params.data_ptr()) if mlp_params is not None else None,
+            ctypes.c_uint32(eps_thresh), ctypes.c_void_p(d_choices.data_ptr()) if d_choices is not None else None,
+            None))
+
+    walk_window_noalloc = tfg_walk_window_noalloc
 
     def window_buffers(self):
         """Views of the last window step's scratch: features (bf16 [N, 128, 32]),
