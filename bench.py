@@ -155,7 +155,9 @@ def run_ours(args):
     params = tfg.tfg_default_params(plateau_len=plateau, walker_id_base=rank * per_rank)
     if args.mapping:
         params.mapping = args.mapping
+    params.use_graph = args.graph
     W = tfg.Walkers(pops, seed=args.seed, params=params)
+    lanes = W.autotune(trial_steps=300, trial_walkers=65536) if args.autotune else None
     stream = W.stream
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
     fails = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -293,12 +295,33 @@ def run_ours(args):
     }
     sacc = sum(W.stats(f)[0]["accepted"] - st0_f[f]["accepted"] for f in range(W.n_formats))
     line["accepted_flips_per_s"] = value * sacc / max(walker_steps, 1)
+    if lanes is not None:
+        line["config"]["autotuned_lanes_per_walker"] = lanes
+    if rank == 0 and args.learned:
+        line["learned_vs_uniform"] = learned_ab(args)
     if rank == 0 and args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, pops, plateau, budget_s=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def learned_ab(args):
+    """Reductions per 1e9 flips of the learned proposal against uniform choice over
+    the same candidate windows, at equal step budgets: train the network on the
+    device from window-uniform walks on the uniform workloads' formats, then run
+    both arms on the naive (4,4,4) and (3,4,5) schemes with seeds 0..2."""
+    from paper_2511_20317_gb300 import learned
+    t0 = time.perf_counter()
+    entries = learned.collect(walkers=4096, steps=2000)
+    params, info = learned.train(entries, epochs=30)
+    res = learned.ab_test(params, seeds=(0, 1, 2), walkers=args.ab_walkers, steps=args.ab_steps)
+    return {"workload": f"naive (4,4,4) and (3,4,5), Z_T, {args.ab_walkers} walkers x {args.ab_steps} window steps, "
+                        "3 seeds per arm, eps 0.05",
+            "training": {"samples": info["samples"], "positives": info["positives"],
+                         "loss_first": info["loss"][0], "loss_last": info["loss"][-1]},
+            "results": res, "seconds": time.perf_counter() - t0}
 
 
 def cpu_baseline(args, pops, plateau, budget_s=15.0):
@@ -359,8 +382,13 @@ def main():
     ap.add_argument("--chunk", type=int, default=50_000)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--mapping", type=int, default=0)
+    ap.add_argument("--graph", type=int, default=1, help="0 plain launches, 1 chained graph, 2 forked graph")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-learned", dest="learned", action="store_false")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--ab-walkers", type=int, default=8192)
+    ap.add_argument("--ab-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

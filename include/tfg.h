@@ -67,7 +67,10 @@ typedef struct {
     int32_t mapping;          /* lanes per walker G in {4,8,16,32}; 0 = autotune (default) */
     int32_t block_threads;    /* CUDA block size, multiple of 32, at most 256 (default 256) */
     uint32_t walker_id_base;  /* global id of this context's first walker (sharding across GPUs) */
-    int32_t reserved[5];
+    int32_t use_graph;        /* tfg_walk launches one captured CUDA graph of all populations' kernels:
+                                 1 chained (default), 2 forked onto one stream per population
+                                 (concurrent); 0 plain launches on the context stream */
+    int32_t reserved[4];
 } tfg_params;
 
 /* Per-walker record.  t is the number of steps taken, digest a rolling hash of
@@ -214,6 +217,14 @@ int tfg_population(tfg_ctx *ctx, int32_t f, tfg_format *fmt, int32_t *r0, int32_
  * walk continues bit-identically.  Synchronous. */
 int tfg_checkpoint(tfg_ctx *ctx, void *buf, size_t cap, size_t *used);
 int tfg_restore(tfg_ctx *ctx, const void *buf, size_t size);
+
+/* Autotuner: for every population, time each compiled kernel variant that fits
+ * it (one thread per walker; 4, 8, 16 or 32 lanes per walker) for trial_steps
+ * steps on its first min(walkers, trial_walkers) walkers, keep the fastest, and
+ * restore those walkers' state bit for bit (host copies; no device memory is
+ * allocated).  lanes_out[f] (optional) receives the chosen lanes per walker.
+ * Synchronous. */
+int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32_t *lanes_out);
 
 /* Mapping chosen for population f (lanes per walker G and slots per lane S). */
 int tfg_mapping(tfg_ctx *ctx, int32_t f, int32_t *lanes, int32_t *slots_per_lane);

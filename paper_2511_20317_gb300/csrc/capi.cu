@@ -99,6 +99,16 @@ const tfg::WalkVariant *default_variant(int mode, int bits, int tw, int R) {
 }  // namespace
 
 struct tfg_ctx {
+    // one captured graph per launch step count: fork to one stream per population, join
+    struct Graph { int32_t steps; cudaGraphExec_t exec; };
+    std::vector<Graph> graphs;
+    std::vector<cudaStream_t> fork_streams;   // [0] carries the graph, [1 + f] population f
+    std::vector<cudaEvent_t> fork_events;     // [f] join of population f, [P] fork, [P+1] / [P+2] in / out
+    ~tfg_ctx() {
+        for (Graph &g : graphs) cudaGraphExecDestroy(g.exec);
+        for (cudaStream_t s : fork_streams) cudaStreamDestroy(s);
+        for (cudaEvent_t e : fork_events) cudaEventDestroy(e);
+    }
     std::vector<Segment> segs;
     tfg_params prm{};
     uint64_t seed = 0;
@@ -152,6 +162,7 @@ void tfg_default_params(tfg_params *out) {
     out->mapping = 0;
     out->block_threads = 256;
     out->walker_id_base = 0;
+    out->use_graph = 1;
 }
 
 const char *tfg_last_error(void) { return tfg::host::last_error(); }
@@ -225,6 +236,10 @@ static int check_params(const tfg_params &p) {
     if (p.plateau_len < 1 || p.plus_attempts < 0 || p.r_slack < 1 || p.block_threads < 32 ||
         p.block_threads % 32 != 0 || p.block_threads > 256) {
         set_error("bad parameters (plateau_len >= 1, r_slack >= 1, block_threads a multiple of 32 <= 256)");
+        return TFG_EINVAL;
+    }
+    if (p.use_graph < 0 || p.use_graph > 2) {
+        set_error("use_graph must be 0 (plain launches), 1 (chained graph) or 2 (forked graph)");
         return TFG_EINVAL;
     }
     if (p.mapping != 0 && p.mapping != 1 && p.mapping != 4 && p.mapping != 8 && p.mapping != 16 && p.mapping != 32) {
@@ -387,22 +402,147 @@ int tfg_init(int32_t n_formats, const tfg_format *fmts, const int32_t *ranks, co
     return TFG_OK;
 }
 
+static void launch_segment(tfg_ctx *ctx, const Segment &s, int32_t steps, cudaStream_t st) {
+    const int b = s.var->block ? s.var->block : ctx->prm.block_threads;
+    const int64_t threads = s.n * s.var->G;
+    const int64_t grid = (threads + b - 1) / b;
+    s.var->launch(ctx->desc(s), steps, (int)grid, b, st);
+}
+
+// Capture (once per step count) a graph of every population's walk kernel:
+// chained on one stream (use_graph 1), or forked into one stream per
+// population and joined (use_graph 2).
+// The capture origin is a private stream (the caller's stream may be the
+// legacy default stream, which cannot be captured).
+static int walk_graph(tfg_ctx *ctx, int32_t steps, cudaGraphExec_t *out) {
+    for (const tfg_ctx::Graph &g : ctx->graphs)
+        if (g.steps == steps) { *out = g.exec; return TFG_OK; }
+    const size_t P = ctx->segs.size();
+    cudaError_t e = cudaSuccess;
+    while (ctx->fork_streams.size() < P + 1 && e == cudaSuccess) {
+        cudaStream_t s;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) ctx->fork_streams.push_back(s);
+    }
+    while (ctx->fork_events.size() < P + 3 && e == cudaSuccess) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) ctx->fork_events.push_back(ev);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "graph streams");
+    for (const Segment &s : ctx->segs)
+        if (s.var->prepare) s.var->prepare();   // kernel attributes are set outside the capture
+    cudaStream_t origin = ctx->fork_streams[0];
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    if (ctx->prm.use_graph == 2) {
+        // forked: every population on its own branch, all concurrent
+        cudaEventRecord(ctx->fork_events[P], origin);
+        for (size_t f = 0; f < P; ++f) {
+            cudaStream_t sf = ctx->fork_streams[1 + f];
+            cudaStreamWaitEvent(sf, ctx->fork_events[P], 0);
+            if (ctx->segs[f].n > 0) launch_segment(ctx, ctx->segs[f], steps, sf);
+            cudaEventRecord(ctx->fork_events[f], sf);
+            cudaStreamWaitEvent(origin, ctx->fork_events[f], 0);
+        }
+    } else {
+        // chained: the populations one after another inside the one graph
+        for (size_t f = 0; f < P; ++f)
+            if (ctx->segs[f].n > 0) launch_segment(ctx, ctx->segs[f], steps, origin);
+    }
+    e = cudaStreamEndCapture(origin, &graph);
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    ctx->graphs.push_back({steps, exec});
+    *out = exec;
+    return TFG_OK;
+}
+
 int tfg_walk(tfg_ctx *ctx, int64_t steps) {
     if (!ctx || steps < 0) { set_error("bad arguments"); return TFG_EINVAL; }
-    const int block = ctx->prm.block_threads;
     while (steps > 0) {
         const int32_t chunk = (int32_t)std::min<int64_t>(steps, 1 << 30);
-        for (const Segment &s : ctx->segs) {
-            if (s.n == 0) continue;
-            const int b = s.var->block ? s.var->block : block;
-            const int64_t threads = s.n * s.var->G;
-            const int64_t grid = (threads + b - 1) / b;
-            s.var->launch(ctx->desc(s), chunk, (int)grid, b, ctx->stream);
+        if (ctx->prm.use_graph) {
+            cudaGraphExec_t exec = nullptr;
+            int rc = walk_graph(ctx, chunk, &exec);
+            if (rc) return rc;
+            const size_t P = ctx->segs.size();
+            cudaStream_t origin = ctx->fork_streams[0];
+            // order the graph after the context stream's work, and that stream after the graph
+            cudaError_t e = cudaEventRecord(ctx->fork_events[P + 1], ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, ctx->fork_events[P + 1], 0);
+            if (e == cudaSuccess) e = cudaGraphLaunch(exec, origin);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->fork_events[P + 2], origin);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->fork_events[P + 2], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+        } else {
+            for (const Segment &s : ctx->segs)
+                if (s.n > 0) launch_segment(ctx, s, chunk, ctx->stream);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e, "walk launch");
         }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "walk launch");
         steps -= chunk;
     }
+    return TFG_OK;
+}
+
+int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32_t *lanes_out) {
+    if (!ctx || trial_steps < 1 || trial_walkers < 1) { set_error("bad arguments"); return TFG_EINVAL; }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    int cnt = 0;
+    const tfg::WalkVariant *all = tfg::walk_variants(&cnt);
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    for (size_t f = 0; f < ctx->segs.size(); ++f) {
+        Segment &s = ctx->segs[f];
+        if (s.n == 0) continue;
+        const int64_t nt = std::min<int64_t>(s.n, trial_walkers);
+        const size_t per = (size_t)s.R * s.nws * (s.word_bits / 8);
+        // save the trial walkers' records and schemes
+        std::vector<char> hdr(sizeof(tfg_walker_info) * nt), sl(per * nt), be(per * nt);
+        e = cudaMemcpy(hdr.data(), ctx->ws + s.off_hdr, hdr.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(sl.data(), ctx->ws + s.off_slots, sl.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(be.data(), ctx->ws + s.off_best, be.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "autotune save");
+        tfg::SegDesc d = ctx->desc(s);
+        d.n_walkers = nt;
+        const tfg::WalkVariant *best = s.var;
+        float best_ms = 1e30f;
+        static const int lanes[5] = {1, 4, 8, 16, 32};
+        for (int G : lanes) {
+            const tfg::WalkVariant *v = pick_variant(s.fmt.mode, s.word_bits, s.tw, G, s.R);
+            if (!v) continue;
+            (void)all;
+            const int b = v->block ? v->block : ctx->prm.block_threads;
+            const int64_t grid = (nt * v->G + b - 1) / b;
+            v->launch(d, (int32_t)std::min<int64_t>(trial_steps, 64), (int)grid, b, ctx->stream);   // warm-up
+            cudaEventRecord(t0, ctx->stream);
+            v->launch(d, (int32_t)trial_steps, (int)grid, b, ctx->stream);
+            cudaEventRecord(t1, ctx->stream);
+            e = cudaEventSynchronize(t1);
+            if (e != cudaSuccess) return cuda_fail(e, "autotune trial");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, t0, t1);
+            if (ms < best_ms) { best_ms = ms; best = v; }
+        }
+        // restore the trial walkers bit for bit
+        e = cudaMemcpy(ctx->ws + s.off_hdr, hdr.data(), hdr.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(ctx->ws + s.off_slots, sl.data(), sl.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(ctx->ws + s.off_best, be.data(), be.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "autotune restore");
+        s.var = best;
+        if (lanes_out) lanes_out[f] = best->G;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    for (tfg_ctx::Graph &g : ctx->graphs) cudaGraphExecDestroy(g.exec);   // variants changed
+    ctx->graphs.clear();
     return TFG_OK;
 }
 

@@ -43,6 +43,7 @@ struct WalkVariant {
     int block;      // fixed block size (G = 1), 0 = chosen by the caller
     void (*launch)(const SegDesc &d, int32_t steps, int grid, int block, cudaStream_t st);
     const void *kernel;  // for cudaFuncGetAttributes
+    void (*prepare)();   // one-time kernel attribute set-up (may be null)
     int capacity() const { return G == 1 ? S : G * S; }
 };
 

@@ -478,6 +478,6 @@ void launch_walk_group(const SegDesc &d, int32_t steps, int grid, int block, cud
 
 #define TFG_GROUP_VARIANT(MODE, WD, BITS, TW, G, S) \
     WalkVariant{MODE, BITS, TW, G, S, 0, &launch_walk_group<MODE, WD, TW, G, S>, \
-                reinterpret_cast<const void *>(&dev::walk_group_kernel<MODE, WD, TW, G, S>)}
+                reinterpret_cast<const void *>(&dev::walk_group_kernel<MODE, WD, TW, G, S>), nullptr}
 
 }  // namespace tfg

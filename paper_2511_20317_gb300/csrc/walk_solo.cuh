@@ -556,19 +556,24 @@ constexpr size_t solo_smem_bytes() {
 }
 
 template <int MODE, class Wd, int RMAX, int BT>
-void launch_walk_solo(const SegDesc &d, int32_t steps, int grid, int /*block*/, cudaStream_t st) {
-    constexpr size_t smem = solo_smem_bytes<MODE, Wd, RMAX, BT>();
+void prepare_walk_solo() {
     static bool attr = [] {
-        cudaFuncSetAttribute(dev::walk_solo_kernel<MODE, Wd, RMAX, BT>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(dev::walk_solo_kernel<MODE, Wd, RMAX, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)solo_smem_bytes<MODE, Wd, RMAX, BT>());
         return true;
     }();
     (void)attr;
-    dev::walk_solo_kernel<MODE, Wd, RMAX, BT><<<grid, BT, smem, st>>>(d, steps);
+}
+
+template <int MODE, class Wd, int RMAX, int BT>
+void launch_walk_solo(const SegDesc &d, int32_t steps, int grid, int /*block*/, cudaStream_t st) {
+    prepare_walk_solo<MODE, Wd, RMAX, BT>();
+    dev::walk_solo_kernel<MODE, Wd, RMAX, BT><<<grid, BT, solo_smem_bytes<MODE, Wd, RMAX, BT>(), st>>>(d, steps);
 }
 
 #define TFG_SOLO_VARIANT(MODE, WD, BITS, RMAX, BT) \
     WalkVariant{MODE, BITS, 1, 1, RMAX, BT, &launch_walk_solo<MODE, WD, RMAX, BT>, \
-                reinterpret_cast<const void *>(&dev::walk_solo_kernel<MODE, WD, RMAX, BT>)}
+                reinterpret_cast<const void *>(&dev::walk_solo_kernel<MODE, WD, RMAX, BT>), \
+                &prepare_walk_solo<MODE, WD, RMAX, BT>}
 
 }  // namespace tfg

@@ -37,7 +37,7 @@ class tfg_params(ctypes.Structure):
                 ("plus_attempts", ctypes.c_int32), ("plus_enabled", ctypes.c_int32),
                 ("r_slack", ctypes.c_int32), ("mapping", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("walker_id_base", ctypes.c_uint32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class tfg_stats(ctypes.Structure):
@@ -67,7 +67,7 @@ EXPORTED = ["tfg_default_params", "tfg_last_error", "tfg_verify", "tfg_additive_
             "tfg_prepare", "tfg_project", "tfg_extend", "tfg_merge", "tfg_double", "tfg_product",
             "tfg_swap_sizes", "tfg_workspace_size", "tfg_init", "tfg_walk", "tfg_sync", "tfg_collect_best",
             "tfg_verify_all_async", "tfg_stats_get", "tfg_read_walkers", "tfg_population", "tfg_checkpoint",
-            "tfg_restore", "tfg_mapping", "tfg_destroy", "tfg_philox_device", "tfg_mlp_param_bytes",
+            "tfg_restore", "tfg_mapping", "tfg_autotune", "tfg_destroy", "tfg_philox_device", "tfg_mlp_param_bytes",
             "tfg_mlp_score", "tfg_mlp_grad", "tfg_mlp_train_state_bytes", "tfg_mlp_train_init",
             "tfg_mlp_train_step", "tfg_window_scratch_bytes", "tfg_walk_window", "tfg_walk_window_noalloc"]
 
@@ -115,6 +115,7 @@ def lib() -> ctypes.CDLL:
                 "tfg_restore": (i32, [P, P, sz]),
                 "tfg_mapping": (i32, [P, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
                 "tfg_destroy": (None, [P]),
+                "tfg_autotune": (i32, [P, i64, i64, P]),
                 "tfg_philox_device": (i32, [P, i32, u32, u32, P, P]),
                 "tfg_mlp_param_bytes": (sz, []),
                 "tfg_mlp_score": (i32, [P, P, i64, P, P, P]),
@@ -410,6 +411,14 @@ class Walkers:
         _check(lib().tfg_mapping(self.ctx, f, ctypes.byref(G), ctypes.byref(S)))
         return {"fmt": (fmt.m, fmt.n, fmt.p), "mode": fmt.mode, "r0": r0.value, "r_max": rmax.value,
                 "walkers": nw.value, "first": first.value, "lanes": G.value, "slots_per_lane": S.value}
+
+    def tfg_autotune(self, trial_steps: int = 400, trial_walkers: int = 32768):
+        lanes = (ctypes.c_int32 * self.n_formats)()
+        _check(lib().tfg_autotune(self.ctx, int(trial_steps), int(trial_walkers), ctypes.cast(lanes, ctypes.c_void_p)))
+        self.pop = [self.population(a) for a in range(self.n_formats)]
+        return list(lanes)
+
+    autotune = tfg_autotune
 
     def tfg_collect_best(self, f: int):
         p = self.pop[f]

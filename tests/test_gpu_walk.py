@@ -201,3 +201,24 @@ def test_large_formats_from_meta_operator_starts(lanes):
         assert_parity(info, slots, best, ref, range(nw), f"large {fmt} lanes={lanes}")
         assert W.verify_all() == 0
         W.close()
+
+
+def test_graph_launch_equals_stream_launch_and_autotune_restores_state():
+    """The mixed populations run as one captured graph (forked: one concurrent
+    branch per format) or as plain launches on one stream: identical results.  The autotuner's
+    trial runs leave no trace in the walkers' state."""
+    wl = workload_mixed(total=6000)
+    pops = [(p.fmt, 0, p.start_scheme(), p.walkers) for p in wl.populations]
+    A = tfg.Walkers(pops, seed=2, params=tfg.tfg_default_params(plateau_len=300, use_graph=2))
+    B = tfg.Walkers(pops, seed=2, params=tfg.tfg_default_params(plateau_len=300, use_graph=0))
+    A.walk(700)
+    B.walk(700)
+    lanes = A.autotune(trial_steps=150, trial_walkers=900)
+    assert len(lanes) == len(pops) and all(g in (1, 4, 8, 16, 32) for g in lanes)
+    A.walk(800).walk(500)
+    B.walk(1300)
+    for pop in A.pop:
+        ia, sa, ba = A.read_walkers(pop["first"], pop["walkers"])
+        ib, sb, bb = B.read_walkers(pop["first"], pop["walkers"])
+        assert np.array_equal(ia, ib) and np.array_equal(sa, sb) and np.array_equal(ba, bb), pop["fmt"]
+    assert A.verify_all() == 0
