@@ -61,8 +61,8 @@ def measured_peaks():
 
 
 def recorded_traffic():
-    """DRAM bytes per walk-kernel launch from the committed ncu summary, when it
-    was taken on the current kernel source (else None)."""
+    """DRAM bytes of one bench step's walk-kernel launches from the committed ncu
+    summary, when it was taken on the current kernel sources (else None)."""
     try:
         kv = {}
         for line in open(TRAFFIC_FILE):
@@ -71,7 +71,7 @@ def recorded_traffic():
                 kv[k.strip()] = v.strip()
         if kv.get("kernel_sha256_16") != kernel_hash():
             return None
-        return float(kv["dram_bytes_per_launch_full_workload"])
+        return float(kv["dram_bytes_per_step_walk_launches"])
     except Exception:
         return None
 

@@ -1,0 +1,99 @@
+"""Single-launch cases of the hot kernels, sized for profiler captures.
+
+    python -m paper_2511_20317_gb300.profile_cases --case walk_zt333
+    python -m paper_2511_20317_gb300.profile_cases --case all
+
+Each case builds its inputs, runs one warm-up launch of a different size, then
+the profiled launch, and prints its CUDA-event time.
+"""
+from __future__ import annotations
+
+import argparse
+import time
+
+import numpy as np
+
+from . import tfg
+from .workloads import naive_start
+
+
+def _timed(fn):
+    import torch
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record()
+    fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e)
+
+
+def walk(fmt, mode, walkers=65536, steps=2000):
+    W = tfg.Walkers([(fmt, mode, naive_start(*fmt), walkers)], seed=0,
+                    params=tfg.tfg_default_params(plateau_len=50_000, use_graph=0))
+    W.walk(16).sync()
+    ms = _timed(lambda: W.walk(steps))
+    return {"walkers": walkers, "steps": steps, "ms": ms, "steps_per_s": walkers * steps / ms * 1e3}
+
+
+def mlp_score(rows=1 << 20):
+    import torch
+    rng = np.random.default_rng(0)
+    from .learned import init_params
+    params = init_params(0)
+    x = torch.from_numpy(rng.integers(0, 9, size=(rows, 32)).astype(np.float32)).cuda().bfloat16()
+    tfg.tfg_mlp_score(params, x[:1024])
+    ms = _timed(lambda: tfg.tfg_mlp_score(params, x))
+    flops = rows * 2 * (32 * 128 + 128 * 128 + 128)
+    return {"rows": rows, "ms": ms, "tflops": flops / ms / 1e9}
+
+
+def mlp_grad(rows=1 << 18):
+    import torch
+    rng = np.random.default_rng(1)
+    from .learned import init_params
+    params = init_params(1)
+    x = torch.from_numpy(rng.integers(0, 9, size=(rows, 32)).astype(np.float32)).cuda().bfloat16()
+    lab = torch.from_numpy((rng.random(rows) < 0.1).astype(np.float32)).cuda()
+    wt = torch.full((rows,), 1.0 / rows, device="cuda")
+    tfg.tfg_mlp_grad(params, x[:1024], lab[:1024], wt[:1024])
+    ms = _timed(lambda: tfg.tfg_mlp_grad(params, x, lab, wt))
+    # forward 2 products, backward 3 (dH1, dW2, dW1)
+    flops = rows * 2 * (32 * 128 + 128 * 128) + rows * 2 * (128 * 128 + 128 * 128 + 128 * 32)
+    return {"rows": rows, "ms": ms, "tflops": flops / ms / 1e9}
+
+
+def window(fmt=(4, 4, 4), walkers=16384):
+    W = tfg.Walkers([(fmt, 0, naive_start(*fmt), walkers)], seed=0, params=tfg.tfg_default_params(plateau_len=500))
+    W.walk_window(2, policy=0)
+    W.sync()
+    ms = _timed(lambda: W.walk_window(1, policy=0))
+    return {"walkers": walkers, "ms_per_window_step": ms}
+
+
+CASES = {
+    "walk_zt333": lambda: walk((3, 3, 3), 0),
+    "walk_z2333": lambda: walk((3, 3, 3), 1),
+    "walk_zt222": lambda: walk((2, 2, 2), 0),
+    "walk_zt445": lambda: walk((4, 4, 5), 0, walkers=80660, steps=500),
+    "mlp_score": mlp_score,
+    "mlp_grad": mlp_grad,
+    "window_444": window,
+}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="all")
+    args = ap.parse_args()
+    import torch
+    torch.cuda.set_device(0)
+    names = list(CASES) if args.case == "all" else args.case.split(",")
+    for n in names:
+        t0 = time.perf_counter()
+        res = CASES[n]()
+        print(n, res, f"wall {time.perf_counter() - t0:.2f}s", flush=True)
+
+
+if __name__ == "__main__":
+    main()
