@@ -297,6 +297,15 @@ def run_ours(args):
     line["accepted_flips_per_s"] = value * sacc / max(walker_steps, 1)
     if lanes is not None:
         line["config"]["autotuned_lanes_per_walker"] = lanes
+    if world > 1:
+        # the one collective of the sharded path: global best scheme per population
+        from paper_2511_20317_gb300 import shard
+        gbest = []
+        for f in range(W.n_formats):
+            sch, r_, wid = W.collect_best(f)
+            g = shard.collect_best_across_ranks(r_, wid, sch, W.pop[f]["r_max"], sch.shape[1], device="cuda")
+            gbest.append({"rank": g[0], "walker": g[1]})
+        line["global_best"] = gbest
     if rank == 0 and args.learned:
         line["learned_vs_uniform"] = learned_ab(args)
     if rank == 0 and args.cpu_baseline:
