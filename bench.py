@@ -125,6 +125,9 @@ def populations(args):
                 ((3, 3, 3), 1, wl.naive_start(3, 3, 3), args.walkers)], 50_000
     if args.workload == "222":
         return [((2, 2, 2), 0, wl.naive_start(2, 2, 2), 1024)], 10_000
+    if args.workload == "large":
+        from paper_2511_20317_gb300 import starts
+        return starts.large_populations(args.walkers), 50_000
     if args.workload == "mixed":
         w = wl.workload_mixed()
         return [(p.fmt, 0, p.start_scheme(), p.walkers) for p in w.populations], 50_000

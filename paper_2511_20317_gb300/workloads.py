@@ -30,6 +30,15 @@ def naive_start(m: int, n: int, p: int) -> np.ndarray:
     return out
 
 
+def strassen_start() -> np.ndarray:
+    """Strassen's rank-7 (2,2,2) scheme (Numer. Math. 13, 1969), textbook products
+    M1..M7 in the row layout u | v | w (w in the C^T order c11 c21 c12 c22)."""
+    U = [[1, 0, 0, 1], [0, 0, 1, 1], [1, 0, 0, 0], [0, 0, 0, 1], [1, 1, 0, 0], [-1, 0, 1, 0], [0, 1, 0, -1]]
+    V = [[1, 0, 0, 1], [1, 0, 0, 0], [0, 1, 0, -1], [-1, 0, 1, 0], [0, 0, 0, 1], [1, 1, 0, 0], [0, 0, 1, 1]]
+    W = [[1, 0, 0, 1], [0, 1, 0, -1], [0, 0, 1, 1], [1, 1, 0, 0], [-1, 0, 1, 0], [0, 0, 0, 1], [1, 0, 0, 0]]
+    return np.concatenate([np.array(U), np.array(V), np.array(W)], axis=1).astype(np.int8)
+
+
 def read_scheme(path: str):
     """Parse the text format of tests/golden: 'format m n p', 'rank r', then the
     U, V and W blocks (one row per term).  Returns ((m,n,p), int8 [r, LT])."""

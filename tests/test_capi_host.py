@@ -142,3 +142,22 @@ def test_meta_chain_large_start():
     assert f4 == (4, 5, 12) and s4.shape[0] == 202 and tfg.tfg_verify(f4, s4)
     with pytest.raises(tfg.TfgError):
         tfg.tfg_product(f4, s4, *S)   # (8,10,24) exceeds 64 entries per factor
+
+
+def test_large_format_starts():
+    """The meta-operator starts of the large formats: formats, ranks, Eq. (1),
+    and the same schemes as the oracle's meta operators produce."""
+    from paper_2511_20317_gb300 import starts
+    from paper_2511_20317_gb300.workloads import strassen_start
+    fmt_s, S = gold("strassen_2x2x2_r7.txt")
+    assert np.array_equal(strassen_start(), S)
+    for (f, s), want_fmt, want_r in [(starts.start_4_5_12(), (4, 5, 12), 202), (starts.start_5_6_10(), (5, 6, 10), 285),
+                                     (starts.start_6_7_9(), (6, 7, 9), 351)]:
+        assert f == want_fmt and s.shape[0] == want_r
+        assert oracle.brent_valid(f, s)
+    # same construction through the oracle's operators
+    f1, s1 = oracle.extend(fmt_s, S, 2)
+    f2, s2 = oracle.double(f1, s1, 2)
+    f3, s3 = oracle.product(fmt_s, S, f2, s2)
+    f4, s4 = oracle.extend(f3, s3, 1)
+    assert np.array_equal(s4, starts.start_4_5_12()[1])
