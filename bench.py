@@ -134,6 +134,29 @@ def populations(args):
     raise SystemExit(f"unknown workload {args.workload}")
 
 
+DATA = {
+    "333": "synthetic: naive rank-27 starts (catalogue starts unavailable)",
+    "222": "synthetic: naive rank-8 start",
+    "mixed": "synthetic: naive rank-mnp starts",
+    "large": "synthetic: meta-operator starts built on the host from Strassen's scheme and naive schemes",
+}
+
+
+def workload_name(args, pops, plateau):
+    fmts = " + ".join(f"{f[0]}x{f[1]}x{f[2]}{'' if m == 0 else ' Z_2'} r{len(s)} x{n}" for f, m, s, n in pops)
+    budget = {"333": "1e6", "222": "1e5", "mixed": "1e6", "large": "1e7"}[args.workload]
+    return (f"{args.workload}: {fmts}; {args.chunk} steps per walker per bench step "
+            f"({budget} = full budget), plateau {plateau}")
+
+
+def mapping_name(pop):
+    if pop["slots_per_lane"] == 0:
+        return "warp per walker, shared-memory signature search"
+    if pop["lanes"] == 1:
+        return f"thread per walker, {pop['slots_per_lane']} slots"
+    return f"{pop['lanes']} lanes x {pop['slots_per_lane']} slots"
+
+
 def dist_setup(args):
     rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -233,12 +256,12 @@ def run_ours(args):
         steps_f = a1["steps"] - a0["steps"]
         acc, rej = a1["accepted"] - a0["accepted"], a1["rejected"] - a0["rejected"]
         ops += algorithmic_ops(mode, steps_f, acc, rej, mean_r)
-        per_mode["ZT" if mode == 0 else "Z2"] = {
+        per_mode[f"{'ZT' if mode == 0 else 'Z2'} {fmt[0]}x{fmt[1]}x{fmt[2]}"] = {
             "lowest_rank": a1["min_best_r"], "mean_live_rank": round(mean_r, 2),
             "rank_hist": {int(k): int(v) for k, v in enumerate(W.stats(f)[1]) if v},
             "accepted_frac": round(acc / max(steps_f, 1), 4),
             "reductions_per_1e9_flips": round((a1["reductions"] - a0["reductions"]) / max(steps_f, 1) * 1e9, 1),
-            "mapping": f"G={W.pop[f]['lanes']} S={W.pop[f]['slots_per_lane']}"}
+            "mapping": mapping_name(W.pop[f])}
     walk_s = sum(walk_ms) / 1e3
     achieved = ops / walk_s / 1e12          # Tops/s
     # integer ALU pipe: one warp instruction per 2 cycles per SM sub-partition (16 lanes/clk),
@@ -278,9 +301,8 @@ def run_ours(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "u32",
-        "data": "synthetic: naive rank-27 starts (catalogue starts unavailable)",
-        "config": {"workload": f"3x3x3 naive27 Z_T+Z_2, {args.walkers} walkers each, {args.chunk} steps "
-                               f"per walker per bench step (1e6 = full budget), plateau {plateau}",
+        "data": DATA[args.workload],
+        "config": {"workload": workload_name(args, pops, plateau),
                    "walkers_per_gpu": per_rank, "steps_per_walker_per_step": args.chunk,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"walker shards x{world}"},
         "accepted_flips_per_s": None,

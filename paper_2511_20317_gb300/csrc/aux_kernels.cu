@@ -1,5 +1,6 @@
 // Auxiliary kernels around the walk: population set-up, exact verification of
 // best schemes (Eq. (1)), best-walker selection and population statistics.
+#include <algorithm>
 #include <cstdint>
 
 #include "tfg_internal.h"
@@ -34,48 +35,82 @@ __global__ void replicate_kernel(const SegDesc d, const Wd *__restrict__ start, 
     }
 }
 
-// ---- Eq. (1) on one walker's best scheme per block.  Coefficients are
-// unpacked into shared memory; every tensor entry (a, b, c) sums r products.
+// ---- Eq. (1) on one walker's best scheme per block, by sparse accumulation:
+// the tensor sum_l u_l (x) v_l (x) w_l is built in shared memory from the
+// non-zero coefficients of each term (a few products per term instead of r
+// products per tensor entry), one slab of u-indices a at a time, and every
+// entry of the slab is compared with the matrix-multiplication tensor
+// (1 iff a = (i,k), b = (k,j), c = (j,i)); over Z_2 the difference must be even.
 template <class Wd>
-__global__ void verify_best_kernel(const SegDesc d, int64_t first, int mode,
-                                   unsigned long long *failures) {
-    extern __shared__ int8_t coef[];   // [r][LT]
+struct Bits {
+    static constexpr int WB = (int)sizeof(Wd) * 8;
+    // calls f(bit, sign) for every non-zero coefficient with bit index in [lo, hi)
+    template <class F>
+    __device__ static void each(const Wd *pos, const Wd *neg, int lo, int hi, F f) {
+        for (int q = lo / WB; q * WB < hi; ++q) {
+            const int o0 = max(lo - q * WB, 0), o1 = min(hi - q * WB, WB);
+            Wd mask = (o1 == WB) ? ~Wd(0) : ((Wd(1) << o1) - 1);
+            mask &= ~((Wd(1) << o0) - 1);
+            Wd nz = (pos[q] | (neg ? neg[q] : Wd(0))) & mask;
+            while (nz) {
+                const int o = (sizeof(Wd) == 8) ? __ffsll((long long)nz) - 1 : __ffs((int)nz) - 1;
+                nz &= nz - 1;
+                const int sgn = (neg && ((neg[q] >> o) & 1)) ? -1 : 1;
+                f(q * WB + o, sgn);
+            }
+        }
+    }
+};
+
+template <class Wd>
+__global__ void __launch_bounds__(256) verify_best_kernel(const SegDesc d, int64_t first, int mode, int slab_rows,
+                                                          unsigned long long *failures) {
+    extern __shared__ __align__(16) unsigned char vsm[];
     __shared__ int bad;
     const int64_t w = first + blockIdx.x;
     if (w >= d.n_walkers) return;
     const int m = d.m, n = d.n, p = d.p;
-    const int LU = m * n, LV = n * p, LW = p * m, LT = LU + LV + LW;
+    const int LU = m * n, LV = n * p, LW = p * m, LT = LU + LV + LW, LVW = LV * LW;
     const int r = d.hdr[w].best_r;
-    const int WB = (int)sizeof(Wd) * 8;
+    Wd *terms = reinterpret_cast<Wd *>(vsm);                                       // [R][nws]
+    int *slab = reinterpret_cast<int *>(vsm + (((size_t)d.R * d.nws * sizeof(Wd) + 15) & ~(size_t)15));
     const Wd *b = reinterpret_cast<const Wd *>(d.best) + (size_t)d.R * d.nws * w;
-    if (threadIdx.x == 0) bad = 0;
-    for (int e = threadIdx.x; e < r * LT; e += blockDim.x) {
-        const int l = e / LT, bit = e - l * LT;
-        const int q = bit / WB, o = bit - q * WB;
-        int v = (int)((b[(size_t)l * d.nws + q] >> o) & 1);
-        if (mode == TFG_MODE_ZT) v -= (int)((b[(size_t)l * d.nws + d.tw + q] >> o) & 1);
-        coef[e] = (int8_t)v;
-    }
+    if (threadIdx.x == 0) bad = (r < 0 || r > d.R) ? 1 : 0;
+    const int rr = (r < 0 || r > d.R) ? 0 : r;
+    for (int e = threadIdx.x; e < rr * d.nws; e += blockDim.x) terms[e] = b[e];
     __syncthreads();
-    const int E = LU * LV * LW;
+    const bool zt = (mode == TFG_MODE_ZT);
+    const int bu = d.fbase[0], bv = d.fbase[1], bw = d.fbase[2];   // factor bit offsets
+    (void)LT;
     int mine = 0;
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        const int a = e / (LV * LW);
-        const int rem = e - a * LV * LW;
-        const int bb = rem / LW;
-        const int c = rem - bb * LW;
-        int sum = 0;
-        for (int l = 0; l < r; ++l) {
-            const int8_t *row = coef + (size_t)l * LT;
-            sum += (int)row[a] * (int)row[LU + bb] * (int)row[LU + LV + c];
+    for (int a0 = 0; a0 < LU; a0 += slab_rows) {
+        const int a1 = min(LU, a0 + slab_rows);
+        const int ne = (a1 - a0) * LVW;
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) slab[e] = 0;
+        __syncthreads();
+        for (int l = threadIdx.x; l < rr; l += blockDim.x) {
+            const Wd *pos = terms + (size_t)l * d.nws;
+            const Wd *neg = zt ? pos + d.tw : nullptr;
+            Bits<Wd>::each(pos, neg, bu + a0, bu + a1, [&](int ia, int sa) {
+                Bits<Wd>::each(pos, neg, bv, bv + LV, [&](int ib, int sb) {
+                    Bits<Wd>::each(pos, neg, bw, bw + LW, [&](int ic, int sc) {
+                        atomicAdd(&slab[(ia - bu - a0) * LVW + (ib - bv) * LW + (ic - bw)], sa * sb * sc);
+                    });
+                });
+            });
         }
-        // a = i*n + k, bb = k2*p + j, c = j2*m + i2; target 1 iff k==k2, j==j2, i==i2
-        const int i = a / n, k = a - i * n;
-        const int k2 = bb / p, j = bb - k2 * p;
-        const int j2 = c / m, i2 = c - j2 * m;
-        const int want = (k == k2 && j == j2 && i == i2) ? 1 : 0;
-        const int diff = sum - want;
-        if (mode == TFG_MODE_ZT ? (diff != 0) : ((diff & 1) != 0)) mine = 1;
+        __syncthreads();
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+            const int a = a0 + e / LVW;
+            const int rem = e - (a - a0) * LVW;
+            const int bb = rem / LW, c = rem - bb * LW;
+            const int i = a / n, k = a - i * n;
+            const int k2 = bb / p, j = bb - k2 * p;
+            const int j2 = c / m, i2 = c - j2 * m;
+            const int diff = slab[e] - ((k == k2 && j == j2 && i == i2) ? 1 : 0);
+            if (zt ? (diff != 0) : ((diff & 1) != 0)) mine = 1;
+        }
+        __syncthreads();
     }
     if (mine) atomicOr(&bad, 1);
     __syncthreads();
@@ -136,14 +171,18 @@ void launch_replicate(const SegDesc &d, const void *start_words, int32_t r0, uin
 void launch_verify_best(const SegDesc &d, int64_t first, int64_t count, int mode, int64_t *d_failures,
                         cudaStream_t st) {
     if (count <= 0) return;
-    const size_t smem = (size_t)d.R * d.lt;
+    // slab of u-indices sized to about 64 KB of int accumulators
+    const int lu = d.m * d.n, lvw = (d.n * d.p) * (d.p * d.m);
+    const int slab_rows = std::max(1, std::min(lu, 16384 / lvw));
+    const size_t term_bytes = ((size_t)d.R * d.nws * (d.word_bits / 8) + 15) & ~(size_t)15;
+    const size_t smem = term_bytes + (size_t)slab_rows * lvw * sizeof(int);
     auto *fail = reinterpret_cast<unsigned long long *>(d_failures);
     if (d.word_bits == 32) {
         cudaFuncSetAttribute(verify_best_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        verify_best_kernel<uint32_t><<<(unsigned)count, 256, smem, st>>>(d, first, mode, fail);
+        verify_best_kernel<uint32_t><<<(unsigned)count, 256, smem, st>>>(d, first, mode, slab_rows, fail);
     } else {
         cudaFuncSetAttribute(verify_best_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        verify_best_kernel<uint64_t><<<(unsigned)count, 256, smem, st>>>(d, first, mode, fail);
+        verify_best_kernel<uint64_t><<<(unsigned)count, 256, smem, st>>>(d, first, mode, slab_rows, fail);
     }
 }
 

@@ -36,18 +36,28 @@ constexpr size_t kAuxBytes = (sizeof(Aux) + kAlign - 1) / kAlign * kAlign;
 struct Segment {
     tfg_format fmt{};
     int r0 = 0, R = 0, word_bits = 32, lt = 0, tw = 1, nws = 2;
+    int fbase[3] = {0, 0, 0};   // bit offset of each factor in a packed term
     int64_t n = 0, first = 0;
     size_t off_hdr = 0, off_slots = 0, off_best = 0, off_start = 0;
     const tfg::WalkVariant *var = nullptr;
     std::vector<int8_t> start_rows;
 };
 
-// Packed term geometry: LT coefficient bits per sign in TW words of 32 bits
-// (LT <= 32) or 64 bits; NWS words per slot (both signs in Z_T).
+// Packed term geometry.  Terms of at most 64 coefficients: the coefficient
+// bits of u | v | w concatenated in one word per sign (32 bits when LT <= 32).
+// Longer terms: factor-aligned, factor f in word f of 64 bits per sign.
 void set_geometry(Segment &s) {
-    s.lt = s.fmt.m * s.fmt.n + s.fmt.n * s.fmt.p + s.fmt.p * s.fmt.m;
-    s.word_bits = s.lt <= 32 ? 32 : 64;
-    s.tw = (s.lt + s.word_bits - 1) / s.word_bits;
+    const int lu = s.fmt.m * s.fmt.n, lv = s.fmt.n * s.fmt.p;
+    s.lt = lu + lv + s.fmt.p * s.fmt.m;
+    if (s.lt <= 64) {
+        s.word_bits = s.lt <= 32 ? 32 : 64;
+        s.tw = 1;
+        s.fbase[0] = 0; s.fbase[1] = lu; s.fbase[2] = lu + lv;
+    } else {
+        s.word_bits = 64;
+        s.tw = 3;
+        s.fbase[0] = 0; s.fbase[1] = 64; s.fbase[2] = 128;
+    }
     s.nws = (s.fmt.mode == TFG_MODE_ZT ? 2 : 1) * s.tw;
 }
 
@@ -127,14 +137,14 @@ struct tfg_ctx {
         d.R = s.R;
         d.m = s.fmt.m; d.n = s.fmt.n; d.p = s.fmt.p;
         d.lt = s.lt; d.tw = s.tw; d.nws = s.nws; d.word_bits = s.word_bits;
-        const int off[3] = {0, s.fmt.m * s.fmt.n, s.fmt.m * s.fmt.n + s.fmt.n * s.fmt.p};
         const int len[3] = {s.fmt.m * s.fmt.n, s.fmt.n * s.fmt.p, s.fmt.p * s.fmt.m};
+        for (int f = 0; f < 3; ++f) d.fbase[f] = s.fbase[f];
         for (int f = 0; f < 3; ++f)
             for (int q = 0; q < 3; ++q) {
                 uint64_t mword = 0;
                 for (int b = 0; b < s.word_bits; ++b) {
                     const int bit = q * s.word_bits + b;
-                    if (bit >= off[f] && bit < off[f] + len[f]) mword |= 1ull << b;
+                    if (bit >= s.fbase[f] && bit < s.fbase[f] + len[f]) mword |= 1ull << b;
                 }
                 d.fmask[f][q] = mword;
             }
@@ -292,7 +302,7 @@ int tfg_workspace_size(int32_t n_formats, const tfg_format *fmts, const int32_t 
 static void pack_terms(const Segment &s, const std::vector<HTerm> &t, std::vector<uint8_t> &buf) {
     const size_t wb = (size_t)s.word_bits / 8;
     buf.assign((size_t)s.R * s.nws * wb, 0);
-    const int off[3] = {0, s.fmt.m * s.fmt.n, s.fmt.m * s.fmt.n + s.fmt.n * s.fmt.p};
+    const int *off = s.fbase;
     const int len[3] = {s.fmt.m * s.fmt.n, s.fmt.n * s.fmt.p, s.fmt.p * s.fmt.m};
     const int signs = s.fmt.mode == TFG_MODE_ZT ? 2 : 1;
     for (size_t l = 0; l < t.size(); ++l)
@@ -320,7 +330,7 @@ static void pack_terms(const Segment &s, const std::vector<HTerm> &t, std::vecto
 
 static void unpack_terms(const Segment &s, const uint8_t *words, int r, int8_t *rows) {
     const size_t wb = (size_t)s.word_bits / 8;
-    const int off[3] = {0, s.fmt.m * s.fmt.n, s.fmt.m * s.fmt.n + s.fmt.n * s.fmt.p};
+    const int *off = s.fbase;
     const int len[3] = {s.fmt.m * s.fmt.n, s.fmt.n * s.fmt.p, s.fmt.p * s.fmt.m};
     const int signs = s.fmt.mode == TFG_MODE_ZT ? 2 : 1;
     std::vector<HTerm> t((size_t)r);

@@ -31,6 +31,8 @@ struct SegDesc {
     int32_t plus_attempts;
     int32_t plus_enabled;
     int32_t pad;
+    int32_t fbase[3];     // bit offset of factor u, v, w in a packed term
+    int32_t pad2;
 };
 
 // One compiled variant of the walk kernel.
@@ -44,7 +46,8 @@ struct WalkVariant {
     void (*launch)(const SegDesc &d, int32_t steps, int grid, int block, cudaStream_t st);
     const void *kernel;  // for cudaFuncGetAttributes
     void (*prepare)();   // one-time kernel attribute set-up (may be null)
-    int capacity() const { return G == 1 ? S : G * S; }
+    int cap = 0;         // slot capacity when not given by G and S
+    int capacity() const { return cap ? cap : (G == 1 ? S : G * S); }
 };
 
 // Registry of compiled variants (filled by the instantiation units).

@@ -1,4 +1,4 @@
-// Lane-group walk kernel variants (64).
+// Lane-group walk kernel variants for 64-bit terms (m*n + n*p + p*m <= 64).
 #include "walk_group.cuh"
 
 namespace tfg {
@@ -12,12 +12,6 @@ const WalkVariant *walk_variants_group_64(int *n) {
         TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 1, 32, 2),
         TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 1, 32, 3),
         TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 1, 32, 4),
-        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 2, 32, 4),
-        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 2, 32, 7),
-        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 2, 32, 8),
-        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 3, 32, 6),
-        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 3, 32, 8),
-        TFG_GROUP_VARIANT(TFG_MODE_ZT, uint64_t, 64, 3, 32, 12),
         TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 1, 8, 4),
         TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 1, 8, 8),
         TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 1, 8, 12),
@@ -26,12 +20,6 @@ const WalkVariant *walk_variants_group_64(int *n) {
         TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 1, 32, 2),
         TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 1, 32, 3),
         TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 1, 32, 4),
-        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 2, 32, 4),
-        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 2, 32, 7),
-        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 2, 32, 8),
-        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 3, 32, 6),
-        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 3, 32, 8),
-        TFG_GROUP_VARIANT(TFG_MODE_Z2, uint64_t, 64, 3, 32, 12),
     };
     *n = (int)(sizeof(v) / sizeof(v[0]));
     return v;

@@ -7,6 +7,7 @@ namespace tfg {
 const WalkVariant *walk_variants_group_zt32(int *n);
 const WalkVariant *walk_variants_group_z232(int *n);
 const WalkVariant *walk_variants_group_64(int *n);
+const WalkVariant *walk_variants_wide(int *n);
 const WalkVariant *walk_variants_solo_zt32(int *n);
 const WalkVariant *walk_variants_solo_z232(int *n);
 const WalkVariant *walk_variants_solo_zt64(int *n);
@@ -19,6 +20,7 @@ const WalkVariant *walk_variants(int *count) {
             walk_variants_group_zt32,
             walk_variants_group_z232,
             walk_variants_group_64,
+            walk_variants_wide,
             walk_variants_solo_zt32,
             walk_variants_solo_z232,
             walk_variants_solo_zt64,

@@ -1,0 +1,605 @@
+// Wide-term flip-graph walk kernel for sm_103a: formats whose terms have more
+// than 64 coefficients (m*n + n*p + p*m > 64; every factor still <= 64).
+//
+// Layout.  A term is factor-aligned: factor f (u, v, w) is word f of the
+// positive-coefficient words and word f of the negative ones (Section 3.5.1's
+// digits/signs masks, one 64-bit word per factor and sign), so every
+// operation of Section 3.5.2 touches one word and needs no mask.
+//
+// Mapping.  One warp per walker; lane l owns the slots k*32 + l (strided, so
+// that runs of related terms spread over the lanes).  The walker's terms live
+// in shared memory together with 32-bit signatures of each factor (hashes of
+// u, v and of w up to sign, plus the sign of w).  The candidate search of
+// try_flip (Algorithm 1) compares signatures only and verifies every
+// signature hit against the full factor words, so the candidate list is
+// exact; the chosen candidate is located in slot order by a walk over the
+// per-pass ballots.  The reduction checks (Section 3.4.1) are filtered the
+// same way.  All walker-uniform bookkeeping is replicated in every lane;
+// lane 0 writes shared memory and __syncwarp orders the writes.
+//
+// The step contract (draws, candidate order, flip, rejection, removal,
+// normalisation, reduction cascade, best/plateau bookkeeping, plus
+// transitions, trajectory digest) is the one of the lane-group and
+// thread-per-walker kernels.
+#include <cstdint>
+
+#include "tfg_internal.h"
+#include "pterm.cuh"
+
+namespace tfg {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <bool ZT>
+struct FTerm {
+    uint64_t p[3];
+    uint64_t n[3];   // kept zero in Z_2
+};
+
+__device__ __forceinline__ uint64_t w_of(const uint64_t (&x)[3], int f) { return f == 0 ? x[0] : (f == 1 ? x[1] : x[2]); }
+__device__ __forceinline__ void set_w(uint64_t (&x)[3], int f, uint64_t v) {
+    x[0] = f == 0 ? v : x[0];
+    x[1] = f == 1 ? v : x[1];
+    x[2] = f == 2 ? v : x[2];
+}
+
+// 32-bit signature of one factor (p, n): a multiply-xor hash, upper half.
+__device__ __forceinline__ uint32_t fsig(uint64_t p, uint64_t n) {
+    const uint64_t h = (p ^ (n * 0xD6E8FEB86659FD93ull)) * 0x9E3779B97F4A7C15ull;
+    return (uint32_t)(h >> 32);
+}
+
+template <int MODE>
+struct WideWalker {
+    static constexpr bool ZT = (MODE == TFG_MODE_ZT);
+    static constexpr int NWG = ZT ? 6 : 3;   // words per slot in HBM (p0 p1 p2 [n0 n1 n2])
+    static constexpr int NWS = ZT ? 6 : 4;   // words per slot in shared memory (16-byte rows)
+    using T = FTerm<ZT>;
+
+    uint64_t *W;    // [R][NWS] factor-grouped: (p0 n0)(p1 n1)(p2 n2), Z_2: (p0 p1)(p2 -)
+    uint4 *SG;      // [32 * KM] signatures (u, v, w up to sign, sign of w)
+    int lane, KM;
+    int r, best_r, R;
+    int64_t t, plateau, best_t;
+    uint64_t dig;
+    uint32_t wid, key0, key1;
+    uint32_t c_acc, c_rej, c_noc, c_drp, c_mrg, c_pls, c_red;
+    int qlen, q0, q1, q2;
+
+    // ---- term operations (factor f = word f)
+    __device__ __forceinline__ static bool add(const T &a, const T &b, int f, bool neg, T &res) {
+        res = a;
+        const uint64_t ap = w_of(a.p, f);
+        if constexpr (ZT) {
+            const uint64_t an = w_of(a.n, f);
+            const uint64_t bp = neg ? w_of(b.n, f) : w_of(b.p, f);
+            const uint64_t bn = neg ? w_of(b.p, f) : w_of(b.n, f);
+            set_w(res.p, f, (ap | bp) & ~(an | bn));
+            set_w(res.n, f, (an | bn) & ~(ap | bp));
+            return ((ap & bp) | (an & bn)) == 0ull;
+        } else {
+            set_w(res.p, f, ap ^ w_of(b.p, f));
+            return true;
+        }
+    }
+    __device__ __forceinline__ static bool zero(const T &a, int f) {
+        return (w_of(a.p, f) | (ZT ? w_of(a.n, f) : 0ull)) == 0ull;
+    }
+    __device__ __forceinline__ static void take(T &dst, const T &src, int f) {
+        set_w(dst.p, f, w_of(src.p, f));
+        if constexpr (ZT) set_w(dst.n, f, w_of(src.n, f));
+    }
+    // Section 3.6: first non-zero of u, then of v, made +1; w absorbs the sign.
+    __device__ __forceinline__ static void canon(T &a) {
+        if constexpr (ZT) {
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                const uint64_t d = a.p[f] | a.n[f];
+                if (a.n[f] & d & (0ull - d)) {
+                    const uint64_t tp = a.p[f]; a.p[f] = a.n[f]; a.n[f] = tp;
+                    const uint64_t wp = a.p[2]; a.p[2] = a.n[2]; a.n[2] = wp;
+                }
+            }
+        }
+    }
+    __device__ __forceinline__ static bool eq(const T &a, const T &b, int f) {
+        return a.p[f] == b.p[f] && (!ZT || a.n[f] == b.n[f]);
+    }
+    __device__ __forceinline__ static bool eqneg(const T &a, const T &b, int f) {
+        return ZT && a.p[f] == b.n[f] && a.n[f] == b.p[f];
+    }
+    __device__ __forceinline__ static bool sum_ok(const T &a, const T &b, int f, bool neg) {
+        if constexpr (ZT) {
+            const uint64_t bp = neg ? b.n[f] : b.p[f], bn = neg ? b.p[f] : b.n[f];
+            return ((a.p[f] & bp) | (a.n[f] & bn)) == 0ull;
+        } else {
+            return true;
+        }
+    }
+    __device__ __forceinline__ static uint4 sig(const T &a) {
+        uint4 s;
+        s.x = fsig(a.p[0], a.n[0]);
+        s.y = fsig(a.p[1], a.n[1]);
+        if constexpr (ZT) {
+            const uint64_t d = a.p[2] | a.n[2];
+            const bool ng = (a.n[2] & d & (0ull - d)) != 0ull;
+            s.z = fsig(ng ? a.n[2] : a.p[2], ng ? a.p[2] : a.n[2]);
+            s.w = ng ? 1u : 0u;
+        } else {
+            s.z = fsig(a.p[2], 0ull);
+            s.w = 0u;
+        }
+        return s;
+    }
+
+    // ---- shared-memory slots
+    __device__ __forceinline__ T get(int s) const {
+        T out;
+        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(W + (size_t)s * NWS);
+        const ulonglong2 a = src[0], b = src[1];
+        if constexpr (ZT) {
+            const ulonglong2 c = src[2];
+            out.p[0] = a.x; out.n[0] = a.y;
+            out.p[1] = b.x; out.n[1] = b.y;
+            out.p[2] = c.x; out.n[2] = c.y;
+        } else {
+            out.p[0] = a.x; out.p[1] = a.y; out.p[2] = b.x;
+            out.n[0] = out.n[1] = out.n[2] = 0ull;
+        }
+        return out;
+    }
+    // factor f of slot s only (one 16-byte load in Z_T)
+    __device__ __forceinline__ void get_factor(int s, int f, uint64_t &p, uint64_t &n) const {
+        if constexpr (ZT) {
+            const ulonglong2 a = reinterpret_cast<const ulonglong2 *>(W + (size_t)s * NWS)[f];
+            p = a.x; n = a.y;
+        } else {
+            p = W[(size_t)s * NWS + f];
+            n = 0ull;
+        }
+    }
+    __device__ __forceinline__ void put(int s, const T &v) {
+        const uint4 g = sig(v);
+        if (lane == 0) {
+            ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(W + (size_t)s * NWS);
+            if constexpr (ZT) {
+                dst[0] = make_ulonglong2(v.p[0], v.n[0]);
+                dst[1] = make_ulonglong2(v.p[1], v.n[1]);
+                dst[2] = make_ulonglong2(v.p[2], v.n[2]);
+            } else {
+                dst[0] = make_ulonglong2(v.p[0], v.p[1]);
+                dst[1] = make_ulonglong2(v.p[2], 0ull);
+            }
+            SG[s] = g;
+        }
+        __syncwarp();
+    }
+    __device__ __forceinline__ void move(int from, int to) {
+        if (lane < NWS / 2) {
+            const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(W + (size_t)from * NWS);
+            ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(W + (size_t)to * NWS);
+            dst[lane] = src[lane];
+        } else if (lane == NWS / 2) {
+            SG[to] = SG[from];
+        }
+        __syncwarp();
+    }
+
+    // ---- reduction queue (slot indices), walker-uniform
+    __device__ __forceinline__ void q_push(int s) {
+        q0 = (qlen == 0) ? s : q0;
+        q1 = (qlen == 1) ? s : q1;
+        q2 = (qlen == 2) ? s : q2;
+        qlen += 1;
+    }
+    __device__ __forceinline__ int q_pop() {
+        const int s = q0;
+        q0 = q1; q1 = q2;
+        qlen -= 1;
+        return s;
+    }
+    __device__ __forceinline__ void q_remove(int s) {
+        const bool k0 = qlen > 0 && q0 != s, k1 = qlen > 1 && q1 != s, k2 = qlen > 2 && q2 != s;
+        const int n0 = k0 ? q0 : (k1 ? q1 : q2);
+        const int n1 = k0 ? (k1 ? q1 : q2) : q2;
+        q0 = n0; q1 = n1;
+        qlen = (int)k0 + (int)k1 + (int)k2;
+    }
+    __device__ __forceinline__ void q_rename(int from, int to) {
+        q0 = (qlen > 0 && q0 == from) ? to : q0;
+        q1 = (qlen > 1 && q1 == from) ? to : q1;
+        q2 = (qlen > 2 && q2 == from) ? to : q2;
+    }
+
+    // Remove slot h: the last live term moves into the hole.
+    __device__ __forceinline__ void drop(int h) {
+        const int last = r - 1;
+        q_remove(h);
+        if (h != last) {
+            move(last, h);
+            q_rename(last, h);
+        }
+        r -= 1;
+    }
+
+    // Does any other live slot share two factors (signatures) with the terms
+    // in slots sa or sb?  A superset of the reduction test: the cascade that
+    // follows a positive answer checks exactly.
+    __device__ __forceinline__ bool pair_filter(int sa, int sb) const {
+        const uint4 A = SG[sa], B = SG[sb];
+        bool hit = false;
+#pragma unroll 4
+        for (int k = 0; k < KM; ++k) {
+            const int s = (k << 5) + lane;
+            const uint4 g = SG[s];
+            const int ma = (int)(g.x == A.x) + (int)(g.y == A.y) + (int)(g.z == A.z);
+            const int mb = (int)(g.x == B.x) + (int)(g.y == B.y) + (int)(g.z == B.z);
+            hit |= s < r && ((s != sa && ma >= 2) || (s != sb && mb >= 2));
+        }
+        return __any_sync(kFull, hit);
+    }
+
+    // Reduction of the term in slot s with the lowest slot sharing (u,v), else
+    // (u,w), else (v,w), whose merged third factor stays ternary; the merged
+    // term keeps s's pair factors and goes to the lower slot.
+    __device__ __forceinline__ void reduce_one(int s) {
+        const T v = get(s);
+        const uint4 vs = SG[s];
+        uint32_t c0 = 0, c1 = 0, c2 = 0;   // bit k: slot k*32 + lane shares the pair by signature
+#pragma unroll 4
+        for (int k = 0; k < KM; ++k) {
+            const int slot = (k << 5) + lane;
+            const uint4 g = SG[slot];
+            const bool live = slot < r && slot != s;
+            const bool eu = g.x == vs.x, ev = g.y == vs.y, ew = g.z == vs.z;
+            c0 |= (uint32_t)(live && eu && ev) << k;
+            c1 |= (uint32_t)(live && eu && ew) << k;
+            c2 |= (uint32_t)(live && ev && ew) << k;
+        }
+        uint32_t m0 = 0, m1 = 0, m2 = 0;   // verified, with a ternary merged third factor
+        uint32_t any = c0 | c1 | c2;
+#pragma unroll 1
+        while (any) {
+            const int k = __ffs(any) - 1;
+            any &= any - 1u;
+            const uint32_t bit = 1u << k;
+            const T u = get((k << 5) + lane);
+            const bool xu = eq(u, v, 0), xv = eq(u, v, 1), xwp = eq(u, v, 2), xwn = eqneg(u, v, 2);
+            if ((c0 & bit) && xu && xv && sum_ok(v, u, 2, false)) m0 |= bit;
+            if ((c1 & bit) && xu && (xwp || xwn) && sum_ok(v, u, 1, xwn)) m1 |= bit;
+            if ((c2 & bit) && xv && (xwp || xwn) && sum_ok(v, u, 0, xwn)) m2 |= bit;
+        }
+        const unsigned b0 = __ballot_sync(kFull, m0 != 0u), b1 = __ballot_sync(kFull, m1 != 0u),
+                       b2 = __ballot_sync(kFull, m2 != 0u);
+        if ((b0 | b1 | b2) == 0u) return;
+        const int P = b0 ? 0 : (b1 ? 1 : 2);
+        const uint32_t mp = P == 0 ? m0 : (P == 1 ? m1 : m2);
+        // lowest slot (k*32 + lane) with a partner of pair type P
+        const unsigned mine = mp ? (unsigned)(((__ffs(mp) - 1) << 5) + lane) : 0xffffffffu;
+        const int k = (int)__reduce_min_sync(kFull, mine);
+        const T kv = get(k);
+        const bool kneg = (P != 0) && eqneg(kv, v, 2);
+        const int F = 2 - P;   // third factor: w, v, u
+        T mv;
+        add(v, kv, F, kneg, mv);
+        const bool z = zero(mv, F);
+        canon(mv);
+        const int lo = s < k ? s : k;
+        const int hi = s < k ? k : s;
+        q_remove(k);
+        put(lo, mv);
+        c_mrg += 1;
+        drop(hi);
+        if (z) {
+            drop(lo);
+            c_drp += 1;
+        } else {
+            q_push(lo);
+        }
+    }
+
+    __device__ __forceinline__ void cascade() {
+#pragma unroll 1
+        while (qlen > 0) reduce_one(q_pop());
+    }
+
+    __device__ __forceinline__ void snapshot(uint64_t *bestp) const {
+#pragma unroll 1
+        for (int e = lane; e < r * NWG; e += 32) {
+            const int s = e / NWG, g = e - s * NWG;
+            bestp[e] = W[(size_t)s * NWS + (ZT ? (g < 3 ? 2 * g : 2 * (g - 3) + 1) : g)];
+        }
+    }
+
+    // Plus transition (Section 3.3.1): three new terms, queued for the cascade;
+    // returns the digest record (0 when no attempt passed).
+    __device__ __forceinline__ uint64_t plus_setup(const SegDesc &d) {
+#pragma unroll 1
+        for (int a = 1; a <= d.plus_attempts; ++a) {
+            const U4 y = philox10((uint32_t)t, (uint32_t)(t >> 32), wid, (uint32_t)a, key0, key1);
+            const int pi = (int)__umulhi(y.x, (uint32_t)r);
+            const int pj = (pi + 1 + (int)__umulhi(y.y, (uint32_t)(r - 1))) % r;
+            const int perm = (int)__umulhi(y.z, 6u);
+            int A, B, C;
+            plus_roles(perm, A, B, C);
+            const T ti = get(pi), tj = get(pj);
+            T nb, nc, na;
+            bool ok = add(ti, tj, B, false, nb);   // B_i + B_j
+            ok &= add(tj, ti, C, true, nc);        // C_j - C_i
+            ok &= add(tj, ti, A, true, na);        // A_j - A_i
+            ok = ok && !zero(nb, B) && !zero(nc, C) && !zero(na, A);
+            if (!ok) continue;
+            canon(na);                 // (A_j - A_i, B_j, C_j)
+            put(r, na);
+            take(nc, ti, A);           // (A_i, B_j, C_j - C_i)
+            canon(nc);
+            put(pj, nc);
+            canon(nb);                 // (A_i, B_i + B_j, C_i)
+            put(pi, nb);
+            r += 1;
+            plateau = 0;
+            c_pls += 1;
+            qlen = 0;
+            q_push(pi);
+            q_push(pj);
+            q_push(r - 1);
+            return plus_record(a, perm, pi, pj);
+        }
+        return 0;
+    }
+
+    __device__ __forceinline__ void run(const SegDesc &d, int64_t w, int32_t steps, unsigned char *sm) {
+        lane = threadIdx.x & 31;
+        R = d.R;
+        KM = (R + 31) >> 5;
+        W = reinterpret_cast<uint64_t *>(sm);
+        SG = reinterpret_cast<uint4 *>(W + (size_t)R * NWS);
+        tfg_walker_info *H = d.hdr + w;
+        r = H->r; best_r = H->best_r;
+        t = H->t; plateau = H->plateau; best_t = H->best_t;
+        dig = H->digest; wid = H->walker_id;
+        key0 = d.key0; key1 = d.key1;
+        c_acc = c_rej = c_noc = c_drp = c_mrg = c_pls = c_red = 0;
+        qlen = 0; q0 = q1 = q2 = 0;
+        const uint64_t *src = reinterpret_cast<const uint64_t *>(d.slots) + (size_t)w * R * NWG;
+        uint64_t *bestp = reinterpret_cast<uint64_t *>(d.best) + (size_t)w * R * NWG;
+        // HBM rows (p0 p1 p2 [n0 n1 n2]) -> shared rows grouped by factor
+#pragma unroll 1
+        for (int e = lane; e < R * NWS; e += 32) {
+            const int s = e / NWS, q = e - s * NWS;
+            const int g = ZT ? ((q & 1) ? 3 + (q >> 1) : (q >> 1)) : q;   // source word of shared word q
+            W[e] = g < NWG ? src[(size_t)s * NWG + g] : 0ull;
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int s = lane; s < 32 * KM; s += 32) SG[s] = s < R ? sig(get(s)) : make_uint4(0u, 0u, 0u, 0u);
+        __syncwarp();
+
+        uint32_t xr0 = 0, xr1 = 0, xr2 = 0;
+        int kb = 32;
+#pragma unroll 1
+        for (int32_t step = 0; step < steps; ++step) {
+            // ---- draw: lane l holds the Philox output of step (batch start + l)
+            if (kb == 32) {
+                const uint64_t tl = (uint64_t)t + (uint64_t)lane;
+                const U4 x = philox10((uint32_t)tl, (uint32_t)(tl >> 32), wid, 0u, key0, key1);
+                xr0 = x.x; xr1 = x.y; xr2 = x.z;
+                kb = 0;
+            }
+            const uint32_t x0 = __shfl_sync(kFull, xr0, kb), x1 = __shfl_sync(kFull, xr1, kb),
+                           x2 = __shfl_sync(kFull, xr2, kb);
+            kb += 1;
+
+            const int r_before = r;
+            const int i = (int)__umulhi(x0, (uint32_t)r);
+            int action = kNoCand, X = 0, j = 0, rho = 0, sneg = 0;
+            {
+                const T ti = get(i);
+                const uint4 si = SG[i];
+                // ---- try_flip: candidates (X, j) with X_j = +-X_i, ordered (X, slot)
+                uint32_t bu = 0, bv = 0, bw = 0;   // bit k: slot k*32 + lane is a candidate
+#pragma unroll 4
+                for (int k = 0; k < KM; ++k) {
+                    const int s = (k << 5) + lane;
+                    const uint4 g = SG[s];
+                    const bool live = s < r && s != i;
+                    bu |= (uint32_t)(live && g.x == si.x) << k;
+                    bv |= (uint32_t)(live && g.y == si.y) << k;
+                    bw |= (uint32_t)(live && g.z == si.z) << k;
+                }
+                uint32_t any = bu | bv | bw;   // signature hits: verify on the full words
+#pragma unroll 1
+                while (any) {
+                    const int k = __ffs(any) - 1;
+                    any &= any - 1u;
+                    const uint32_t bit = 1u << k;
+                    const int s = (k << 5) + lane;
+                    uint64_t p, n;
+                    if (bu & bit) {
+                        get_factor(s, 0, p, n);
+                        if (p != ti.p[0] || n != ti.n[0]) bu &= ~bit;
+                    }
+                    if (bv & bit) {
+                        get_factor(s, 1, p, n);
+                        if (p != ti.p[1] || n != ti.n[1]) bv &= ~bit;
+                    }
+                    if (bw & bit) {
+                        get_factor(s, 2, p, n);
+                        if (!((p == ti.p[2] && n == ti.n[2]) || (ZT && p == ti.n[2] && n == ti.p[2]))) bw &= ~bit;
+                    }
+                }
+                const uint32_t tot = __reduce_add_sync(kFull, (uint32_t)__popc(bu) | ((uint32_t)__popc(bv) << 10) |
+                                                                  ((uint32_t)__popc(bw) << 20));
+                const int nU = (int)(tot & 1023u), nV = (int)((tot >> 10) & 1023u), nW = (int)(tot >> 20);
+                const int K = 2 * (nU + nV + nW);
+
+                if (K > 0) {
+                    const int c = (int)__umulhi(x1, (uint32_t)K);
+                    rho = c & 1;
+                    const int mi = c >> 1;
+                    int idx;
+                    if (mi < nU) { X = 0; idx = mi; }
+                    else if (mi < nU + nV) { X = 1; idx = mi - nU; }
+                    else { X = 2; idx = mi - nU - nV; }
+                    // the idx-th candidate of factor X in slot order (k, then lane)
+                    const uint32_t mk = X == 0 ? bu : (X == 1 ? bv : bw);
+                    int k = 0;
+                    unsigned b = __ballot_sync(kFull, mk & 1u);
+#pragma unroll 1
+                    for (; k + 1 < KM; ) {
+                        const int cnt = __popc(b);
+                        if (idx < cnt) break;
+                        idx -= cnt;
+                        ++k;
+                        b = __ballot_sync(kFull, (mk >> k) & 1u);
+                    }
+#pragma unroll 1
+                    for (int q = 0; q < idx && b; ++q) b &= b - 1u;
+                    j = (k << 5) + __ffs(b) - 1;
+                    const T tj = get(j);
+                    sneg = (X == 2 && eqneg(tj, ti, 2)) ? 1 : 0;
+
+                    // flip: (Y, Z) cyclic after X, rho swaps; Y_i += Y_j, Z_j -= s Z_i
+                    int Y = X == 0 ? 1 : (X == 1 ? 2 : 0);
+                    int Z = X == 0 ? 2 : (X == 1 ? 0 : 1);
+                    if (rho) { const int tmp = Y; Y = Z; Z = tmp; }
+                    T ti2, tj2;
+                    bool ok = add(ti, tj, Y, false, ti2);
+                    ok &= add(tj, ti, Z, sneg == 0, tj2);
+                    if (!ok) {
+                        action = kReject;
+                        c_rej += 1;
+                    } else {
+                        action = kAccept;
+                        c_acc += 1;
+                        const bool zi = zero(ti2, Y);
+                        const bool zj = zero(tj2, Z);
+                        canon(ti2);
+                        canon(tj2);
+                        put(i, ti2);
+                        put(j, tj2);
+                        qlen = 0;
+                        if (zi || zj) {
+                            q_push(i);
+                            q_push(j);
+                            const int hi = i > j ? i : j, lo = i > j ? j : i;
+                            const bool zhi = (hi == i) ? zi : zj, zlo = (lo == i) ? zi : zj;
+                            if (zhi) { drop(hi); c_drp += 1; }
+                            if (zlo) { drop(lo); c_drp += 1; }
+                        } else if (pair_filter(i, j)) {
+                            q_push(i);
+                            q_push(j);
+                        }
+                    }
+                } else {
+                    c_noc += 1;
+                }
+            }
+
+            // ---- reduction cascade (flip), then bookkeeping, then plus + cascade
+            bool plus_phase = false;
+            uint64_t rec2 = 0;
+#pragma unroll 1
+            for (;;) {
+                cascade();
+                if (plus_phase) {
+                    dig = digest_mix(dig, rec2 | ((uint64_t)(uint32_t)r << 44));
+                    break;
+                }
+                if (r < r_before) c_red += 1;
+                dig = digest_mix(dig, flip_record(action, X, rho, sneg, i, j, r));
+                if (r < best_r) {
+                    snapshot(bestp);
+                    best_r = r;
+                    best_t = t;
+                    plateau = 0;
+                } else {
+                    if (r == best_r && x2 < d.refresh_thresh) snapshot(bestp);
+                    plateau += 1;
+                }
+                if (d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2) {
+                    rec2 = plus_setup(d);
+                    if (rec2) { plus_phase = true; continue; }
+                }
+                break;
+            }
+            t += 1;
+        }
+
+        // ---- write back
+        uint64_t *dst = reinterpret_cast<uint64_t *>(d.slots) + (size_t)w * R * NWG;
+#pragma unroll 1
+        for (int e = lane; e < R * NWG; e += 32) {
+            const int s = e / NWG, g = e - s * NWG;
+            dst[e] = W[(size_t)s * NWS + (ZT ? (g < 3 ? 2 * g : 2 * (g - 3) + 1) : g)];
+        }
+        if (lane == 0) {
+            H->r = r; H->best_r = best_r;
+            H->t = t; H->plateau = plateau; H->best_t = best_t;
+            H->digest = dig;
+            H->accepted += c_acc; H->rejected += c_rej; H->nocand += c_noc;
+            H->drops += c_drp; H->merges += c_mrg; H->plus += c_pls; H->reductions += c_red;
+        }
+    }
+};
+
+template <int MODE>
+__host__ __device__ constexpr size_t wide_walker_bytes(int R) {
+    return (size_t)R * (MODE == TFG_MODE_ZT ? 6 : 4) * 8 + (size_t)((R + 31) / 32) * 32 * 16;
+}
+
+constexpr int kWideWarps = 2;   // walkers (warps) per block
+
+template <int MODE>
+__global__ void __launch_bounds__(32 * kWideWarps) walk_wide_kernel(const SegDesc d, const int32_t steps) {
+    extern __shared__ __align__(16) unsigned char wide_sm[];
+    const int warp = threadIdx.x >> 5;
+    const int64_t w = (int64_t)blockIdx.x * kWideWarps + warp;
+    if (w >= d.n_walkers) return;   // whole warps exit together
+    WideWalker<MODE> wk;
+    wk.run(d, w, steps, wide_sm + wide_walker_bytes<MODE>(d.R) * warp);
+}
+
+}  // namespace dev
+
+namespace {
+
+constexpr int kWideMaxSmem = 227 * 1024;
+
+template <int MODE>
+void prepare_walk_wide() {
+    static bool attr = [] {
+        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
+        return true;
+    }();
+    (void)attr;
+}
+
+template <int MODE>
+void launch_walk_wide(const SegDesc &d, int32_t steps, int /*grid*/, int /*block*/, cudaStream_t st) {
+    prepare_walk_wide<MODE>();
+    const size_t smem = dev::wide_walker_bytes<MODE>(d.R) * dev::kWideWarps;
+    if (d.n_walkers <= 0 || smem > (size_t)kWideMaxSmem) return;
+    const int64_t grid = (d.n_walkers + dev::kWideWarps - 1) / dev::kWideWarps;
+    dev::walk_wide_kernel<MODE><<<(unsigned)grid, 32 * dev::kWideWarps, smem, st>>>(d, steps);
+}
+
+}  // namespace
+
+// Factor-aligned terms: 3 words of 64 bits per sign; capacity 1023 slots
+// (the shared-memory need of two walkers per block stays under 227 KB).
+const WalkVariant *walk_variants_wide(int *n) {
+    static const WalkVariant v[] = {
+        WalkVariant{TFG_MODE_ZT, 64, 3, 32, 0, 0, &launch_walk_wide<TFG_MODE_ZT>,
+                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_ZT>), &prepare_walk_wide<TFG_MODE_ZT>,
+                    1023},
+        WalkVariant{TFG_MODE_Z2, 64, 3, 32, 0, 0, &launch_walk_wide<TFG_MODE_Z2>,
+                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_Z2>), &prepare_walk_wide<TFG_MODE_Z2>,
+                    1023},
+    };
+    *n = (int)(sizeof(v) / sizeof(v[0]));
+    return v;
+}
+
+}  // namespace tfg

@@ -28,12 +28,21 @@ def _timed(fn):
     return s.elapsed_time(e)
 
 
-def walk(fmt, mode, walkers=65536, steps=2000):
-    W = tfg.Walkers([(fmt, mode, naive_start(*fmt), walkers)], seed=0,
-                    params=tfg.tfg_default_params(plateau_len=50_000, use_graph=0))
+def walk(fmt, mode, walkers=65536, steps=2000, start=None, mapping=0):
+    start = naive_start(*fmt) if start is None else start
+    params = tfg.tfg_default_params(plateau_len=50_000, use_graph=0)
+    params.mapping = mapping
+    W = tfg.Walkers([(fmt, mode, start, walkers)], seed=0, params=params)
     W.walk(16).sync()
     ms = _timed(lambda: W.walk(steps))
-    return {"walkers": walkers, "steps": steps, "ms": ms, "steps_per_s": walkers * steps / ms * 1e3}
+    return {"walkers": walkers, "steps": steps, "ms": ms, "steps_per_s": walkers * steps / ms * 1e3,
+            "mapping": (W.pop[0]["lanes"], W.pop[0]["slots_per_lane"])}
+
+
+def walk_large(which, walkers=16384, steps=300):
+    from . import starts
+    fmt, start = {"4512": starts.start_4_5_12, "5610": starts.start_5_6_10, "679": starts.start_6_7_9}[which]()
+    return walk(fmt, 0, walkers=walkers, steps=steps, start=start)
 
 
 def mlp_score(rows=1 << 20):
@@ -76,6 +85,9 @@ CASES = {
     "walk_z2333": lambda: walk((3, 3, 3), 1),
     "walk_zt222": lambda: walk((2, 2, 2), 0),
     "walk_zt445": lambda: walk((4, 4, 5), 0, walkers=80660, steps=500),
+    "walk_zt4512": lambda: walk_large("4512"),
+    "walk_zt5610": lambda: walk_large("5610"),
+    "walk_zt679": lambda: walk_large("679"),
     "mlp_score": mlp_score,
     "mlp_grad": mlp_grad,
     "window_444": window,

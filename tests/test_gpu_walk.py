@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 from paper_2511_20317_gb300 import tfg
+from paper_2511_20317_gb300.tfg import WALKER_INFO_DTYPE, term_len
 from paper_2511_20317_gb300.workloads import golden_dir, naive_start, read_scheme, workload_mixed
 
 pytestmark = pytest.mark.gpu
@@ -183,24 +184,43 @@ def test_start_from_paper_scheme_and_edge_formats():
         assert W.verify_all() == 0
 
 
-@pytest.mark.parametrize("lanes", [0, 32])
-def test_large_formats_from_meta_operator_starts(lanes):
-    """Large formats need two and three 64-bit words per sign: (4,5,12) from
-    product(Strassen, double(extend(Strassen))) extended on n (rank 202), and
-    (6,7,9) from the naive rank-378 scheme."""
+def _start_4_5_12():
     fmt_s, S = read_scheme(os.path.join(golden_dir(), "strassen_2x2x2_r7.txt"))
     f1, s1 = tfg.tfg_extend(fmt_s, S, 2)
     f2, s2 = tfg.tfg_double(f1, s1, 2)
     f3, s3 = tfg.tfg_product(fmt_s, S, f2, s2)
     f4, s4 = tfg.tfg_extend(f3, s3, 1)
     assert f4 == (4, 5, 12) and s4.shape[0] == 202
-    for fmt, start, nw, steps, L in [(f4, s4, 40, 1500, 300), ((6, 7, 9), naive_start(6, 7, 9), 12, 400, 100)]:
-        W = gpu_walkers(fmt, 0, start, nw, 4, steps, plateau_len=L, mapping=lanes)
-        info, slots, best = W.read_walkers(0, nw)
-        ref = oracle.Walkers(fmt, start, np.arange(nw), seed=4, plateau_len=L).walk(steps, THREADS)
-        assert_parity(info, slots, best, ref, range(nw), f"large {fmt} lanes={lanes}")
-        assert W.verify_all() == 0
-        W.close()
+    return f4, s4
+
+
+@pytest.mark.parametrize("mode", [tfg.TFG_MODE_ZT, tfg.TFG_MODE_Z2])
+@pytest.mark.parametrize("case", ["4x5x5", "4x5x12", "8x8x1", "1x8x8", "6x7x9"])
+def test_wide_terms_parity(case, mode):
+    """Terms longer than 64 coefficients (factor-aligned words, shared-memory
+    signature search): naive (4,5,5) and (6,7,9), the meta-operator (4,5,12)
+    start of rank 202, and factors of exactly 64 coefficients."""
+    if case == "4x5x12":
+        fmt, start = _start_4_5_12()
+        nw, steps, L = 40, 1500, 300
+    else:
+        fmt = tuple(int(x) for x in case.split("x"))
+        start = naive_start(*fmt)
+        nw, steps, L = {"4x5x5": (64, 3000, 300), "8x8x1": (64, 2000, 200), "1x8x8": (64, 2000, 200),
+                        "6x7x9": (12, 400, 100)}[case]
+    if case == "6x7x9" and mode == tfg.TFG_MODE_Z2:
+        pytest.skip("one mode suffices at rank 378")
+    if mode == tfg.TFG_MODE_Z2:
+        start = np.abs(start).astype(np.int8)   # a Z_T scheme read mod 2
+    W = gpu_walkers(fmt, mode, start, nw, 4, steps, chunks=2, plateau_len=L)
+    assert W.pop[0]["slots_per_lane"] == 0, "wide-term kernel expected"
+    info, slots, best = W.read_walkers(0, nw)
+    ref = oracle.Walkers(fmt, start, np.arange(nw), seed=4, mode=mode, plateau_len=L).walk(steps, THREADS)
+    if case in ("4x5x5", "8x8x1"):
+        assert (ref.info["merges"] > 0).any() and (ref.info["plus"] > 0).any()
+    assert_parity(info, slots, best, ref, range(nw), f"wide {fmt} mode={mode}")
+    assert W.verify_all() == 0
+    W.close()
 
 
 def test_graph_launch_equals_stream_launch_and_autotune_restores_state():
@@ -222,3 +242,73 @@ def test_graph_launch_equals_stream_launch_and_autotune_restores_state():
         ib, sb, bb = B.read_walkers(pop["first"], pop["walkers"])
         assert np.array_equal(ia, ib) and np.array_equal(sa, sb) and np.array_equal(ba, bb), pop["fmt"]
     assert A.verify_all() == 0
+
+
+def _best_region(W, f):
+    """Where population f's best slots sit inside a checkpoint blob: the blob
+    starts at the first walker record; records, live slots, best slots and the
+    packed start follow one another, each padded to 256 bytes.  Terms of at
+    most 64 coefficients concatenate u|v|w in one word per sign (32-bit words
+    up to 32 coefficients); longer ones hold factor f in 64-bit word f."""
+    p = W.pop[f]
+    assert f == 0
+    fmt, mode, n, R = p["fmt"], p["mode"], p["walkers"], p["r_max"]
+    m, nn, pp = fmt
+    lt = term_len(fmt)
+    if lt <= 64:
+        wb, tw = (4 if lt <= 32 else 8), 1
+        coef_bit = np.arange(lt)
+    else:
+        wb, tw = 8, 3
+        lens = [m * nn, nn * pp, pp * m]
+        coef_bit = np.concatenate([64 * x + np.arange(lens[x]) for x in range(3)])
+    nws = (2 if mode == tfg.TFG_MODE_ZT else 1) * tw
+    per = R * nws * wb
+    up = lambda x: (x + 255) // 256 * 256
+    off_best = up(n * WALKER_INFO_DTYPE.itemsize) + up(n * per)
+    return off_best, per, wb, tw, nws, coef_bit
+
+
+@pytest.mark.parametrize("which", ["333zt", "333z2", "4512zt", "569z2"])
+def test_verify_all_flags_exactly_the_corrupted_walkers(which):
+    """Eq. (1) on the device: change one coefficient of the best scheme of some
+    walkers (through a checkpoint blob) and exactly those walkers fail."""
+    from paper_2511_20317_gb300 import starts
+    if which == "333zt":
+        fmt, mode, start = (3, 3, 3), tfg.TFG_MODE_ZT, naive_start(3, 3, 3)
+    elif which == "333z2":
+        fmt, mode, start = (3, 3, 3), tfg.TFG_MODE_Z2, naive_start(3, 3, 3)
+    elif which == "4512zt":
+        (fmt, start), mode = starts.start_4_5_12(), tfg.TFG_MODE_ZT
+    else:
+        fmt, mode, start = (5, 6, 9), tfg.TFG_MODE_Z2, naive_start(5, 6, 9)
+    n = 48
+    W = tfg.Walkers([(fmt, mode, start, n)], seed=3, params=tfg.tfg_default_params(plateau_len=400))
+    W.walk(300).sync()
+    assert W.verify_all() == 0
+    info, _, best = W.read_walkers(0, n, slots=False)
+    blob = np.frombuffer(W.checkpoint(), dtype=np.uint8).copy()
+    off, per, wb, tw, nws, coef_bit = _best_region(W, 0)
+    words = blob[off: off + n * per].view(np.uint32 if wb == 4 else np.uint64).reshape(n, -1, nws)
+    # the located region decodes to the walkers' best schemes
+    lt = term_len(fmt)
+    bits = wb * 8
+    for w in (0, n - 1):
+        r = int(info["best_r"][w])
+        e = coef_bit
+        ww = words[w][:r]                                  # [r, nws]
+        sh = (e % bits).astype(words.dtype)
+        pos = (ww[:, e // bits] >> sh) & 1
+        neg = ((ww[:, tw + e // bits] >> sh) & 1) if nws > tw else 0 * pos
+        assert np.array_equal(pos.astype(np.int8) - neg.astype(np.int8), best[w, :r])
+    bad = [1, 7, 30]
+    rng = np.random.default_rng(5)
+    for w in bad:
+        term = int(rng.integers(info["best_r"][w]))
+        coef = int(coef_bit[int(rng.integers(lt))])
+        words[w, term, coef // bits] ^= words.dtype.type(1) << words.dtype.type(coef % bits)   # +1 bit toggled
+        if nws > tw:
+            words[w, term, tw + coef // bits] &= ~(words.dtype.type(1) << words.dtype.type(coef % bits))
+    W.restore(blob.tobytes())
+    assert W.verify_all() == len(bad)
+    W.close()
