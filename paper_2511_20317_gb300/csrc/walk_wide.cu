@@ -14,8 +14,11 @@
 // signature hit against the full factor words, so the candidate list is
 // exact; the chosen candidate is located in slot order by a walk over the
 // per-pass ballots.  The reduction checks (Section 3.4.1) are filtered the
-// same way.  All walker-uniform bookkeeping is replicated in every lane;
-// lane 0 writes shared memory and __syncwarp orders the writes.
+// same way.  All walker-uniform bookkeeping is replicated in every lane.
+// The arithmetic of a flip, a merge or a plus transition works on one factor
+// per lane (lane f < 3 holds factor f of each term involved): additions,
+// normalisation, signatures and stores are a handful of lane-parallel
+// instructions; __syncwarp orders the shared-memory writes.
 //
 // The step contract (draws, candidate order, flip, rejection, removal,
 // normalisation, reduction cascade, best/plateau bookkeeping, plus
@@ -67,42 +70,7 @@ struct WideWalker {
     uint32_t c_acc, c_rej, c_noc, c_drp, c_mrg, c_pls, c_red;
     int qlen, q0, q1, q2;
 
-    // ---- term operations (factor f = word f)
-    __device__ __forceinline__ static bool add(const T &a, const T &b, int f, bool neg, T &res) {
-        res = a;
-        const uint64_t ap = w_of(a.p, f);
-        if constexpr (ZT) {
-            const uint64_t an = w_of(a.n, f);
-            const uint64_t bp = neg ? w_of(b.n, f) : w_of(b.p, f);
-            const uint64_t bn = neg ? w_of(b.p, f) : w_of(b.n, f);
-            set_w(res.p, f, (ap | bp) & ~(an | bn));
-            set_w(res.n, f, (an | bn) & ~(ap | bp));
-            return ((ap & bp) | (an & bn)) == 0ull;
-        } else {
-            set_w(res.p, f, ap ^ w_of(b.p, f));
-            return true;
-        }
-    }
-    __device__ __forceinline__ static bool zero(const T &a, int f) {
-        return (w_of(a.p, f) | (ZT ? w_of(a.n, f) : 0ull)) == 0ull;
-    }
-    __device__ __forceinline__ static void take(T &dst, const T &src, int f) {
-        set_w(dst.p, f, w_of(src.p, f));
-        if constexpr (ZT) set_w(dst.n, f, w_of(src.n, f));
-    }
-    // Section 3.6: first non-zero of u, then of v, made +1; w absorbs the sign.
-    __device__ __forceinline__ static void canon(T &a) {
-        if constexpr (ZT) {
-#pragma unroll
-            for (int f = 0; f < 2; ++f) {
-                const uint64_t d = a.p[f] | a.n[f];
-                if (a.n[f] & d & (0ull - d)) {
-                    const uint64_t tp = a.p[f]; a.p[f] = a.n[f]; a.n[f] = tp;
-                    const uint64_t wp = a.p[2]; a.p[2] = a.n[2]; a.n[2] = wp;
-                }
-            }
-        }
-    }
+    // ---- full-term comparisons (hit verification)
     __device__ __forceinline__ static bool eq(const T &a, const T &b, int f) {
         return a.p[f] == b.p[f] && (!ZT || a.n[f] == b.n[f]);
     }
@@ -133,6 +101,75 @@ struct WideWalker {
         return s;
     }
 
+    // ---- one factor per lane: lane f < 3 holds factor f (lanes 3..31 mirror factor 0)
+    struct DF { uint64_t p, n; };
+    int fl;   // this lane's factor
+
+    __device__ __forceinline__ DF dof(const T &a) const { return DF{w_of(a.p, fl), w_of(a.n, fl)}; }
+    __device__ __forceinline__ DF dget(int s) const {
+        if constexpr (ZT) {
+            const ulonglong2 a = reinterpret_cast<const ulonglong2 *>(W + (size_t)s * NWS)[fl];
+            return DF{a.x, a.y};
+        } else {
+            return DF{W[(size_t)s * NWS + fl], 0ull};
+        }
+    }
+    // res = a with factor f := a_f + b_f (neg: a_f - b_f); false when a
+    // coefficient leaves the coefficient set (Section 3.5.2)
+    __device__ __forceinline__ bool dadd(const DF &a, const DF &b, int f, bool neg, DF &res) const {
+        const bool me = lane == f;
+        bool bad = false;
+        if constexpr (ZT) {
+            const uint64_t bp = neg ? b.n : b.p, bn = neg ? b.p : b.n;
+            res.p = me ? ((a.p | bp) & ~(a.n | bn)) : a.p;
+            res.n = me ? ((a.n | bn) & ~(a.p | bp)) : a.n;
+            bad = me && ((a.p & bp) | (a.n & bn)) != 0ull;
+        } else {
+            res.p = me ? (a.p ^ b.p) : a.p;
+            res.n = 0ull;
+        }
+        return !__any_sync(kFull, bad);
+    }
+    __device__ __forceinline__ bool dzero(const DF &a, int f) const {
+        return (__ballot_sync(kFull, (a.p | a.n) == 0ull) >> f) & 1u;
+    }
+    __device__ __forceinline__ void dtake(DF &dst, const DF &src, int f) const {
+        if (lane == f) dst = src;
+    }
+    // Section 3.6: first non-zero of u, then of v, made +1; w absorbs the signs
+    __device__ __forceinline__ void dcanon(DF &a) const {
+        if constexpr (ZT) {
+            const uint64_t d = a.p | a.n;
+            const unsigned neg = __ballot_sync(kFull, (a.n & d & (0ull - d)) != 0ull);
+            const bool f0 = neg & 1u, f1 = (neg >> 1) & 1u;
+            const bool sw = (lane == 0 && f0) || (lane == 1 && f1) || (lane == 2 && f0 != f1);
+            const uint64_t p = sw ? a.n : a.p, n = sw ? a.p : a.n;
+            a.p = p; a.n = n;
+        }
+    }
+    // w of a equals -w of b
+    __device__ __forceinline__ bool dwneg(const DF &a, const DF &b) const {
+        return ZT && ((__ballot_sync(kFull, a.p == b.n && a.n == b.p) >> 2) & 1u);
+    }
+    __device__ __forceinline__ void dput(int s, const DF &a) {
+        uint64_t cp = a.p, cn = a.n;
+        uint32_t ng = 0u;
+        if constexpr (ZT) {
+            const uint64_t d = a.p | a.n;
+            ng = (lane == 2 && (a.n & d & (0ull - d)) != 0ull) ? 1u : 0u;
+            if (ng) { cp = a.n; cn = a.p; }
+        }
+        const uint32_t h = fsig(cp, cn);
+        if (lane < 3) {
+            if constexpr (ZT) reinterpret_cast<ulonglong2 *>(W + (size_t)s * NWS)[lane] = make_ulonglong2(a.p, a.n);
+            else W[(size_t)s * NWS + lane] = a.p;
+            uint32_t *g = reinterpret_cast<uint32_t *>(SG + s);
+            g[lane] = h;
+            if (lane == 2) g[3] = ng;
+        }
+        __syncwarp();
+    }
+
     // ---- shared-memory slots
     __device__ __forceinline__ T get(int s) const {
         T out;
@@ -158,22 +195,6 @@ struct WideWalker {
             p = W[(size_t)s * NWS + f];
             n = 0ull;
         }
-    }
-    __device__ __forceinline__ void put(int s, const T &v) {
-        const uint4 g = sig(v);
-        if (lane == 0) {
-            ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(W + (size_t)s * NWS);
-            if constexpr (ZT) {
-                dst[0] = make_ulonglong2(v.p[0], v.n[0]);
-                dst[1] = make_ulonglong2(v.p[1], v.n[1]);
-                dst[2] = make_ulonglong2(v.p[2], v.n[2]);
-            } else {
-                dst[0] = make_ulonglong2(v.p[0], v.p[1]);
-                dst[1] = make_ulonglong2(v.p[2], 0ull);
-            }
-            SG[s] = g;
-        }
-        __syncwarp();
     }
     __device__ __forceinline__ void move(int from, int to) {
         if (lane < NWS / 2) {
@@ -278,17 +299,17 @@ struct WideWalker {
         // lowest slot (k*32 + lane) with a partner of pair type P
         const unsigned mine = mp ? (unsigned)(((__ffs(mp) - 1) << 5) + lane) : 0xffffffffu;
         const int k = (int)__reduce_min_sync(kFull, mine);
-        const T kv = get(k);
-        const bool kneg = (P != 0) && eqneg(kv, v, 2);
+        const DF dv = dof(v), dk = dget(k);
+        const bool kneg = (P != 0) && dwneg(dk, dv);
         const int F = 2 - P;   // third factor: w, v, u
-        T mv;
-        add(v, kv, F, kneg, mv);
-        const bool z = zero(mv, F);
-        canon(mv);
+        DF mv;
+        dadd(dv, dk, F, kneg, mv);
+        const bool z = dzero(mv, F);
+        dcanon(mv);
         const int lo = s < k ? s : k;
         const int hi = s < k ? k : s;
         q_remove(k);
-        put(lo, mv);
+        dput(lo, mv);
         c_mrg += 1;
         drop(hi);
         if (z) {
@@ -323,20 +344,20 @@ struct WideWalker {
             const int perm = (int)__umulhi(y.z, 6u);
             int A, B, C;
             plus_roles(perm, A, B, C);
-            const T ti = get(pi), tj = get(pj);
-            T nb, nc, na;
-            bool ok = add(ti, tj, B, false, nb);   // B_i + B_j
-            ok &= add(tj, ti, C, true, nc);        // C_j - C_i
-            ok &= add(tj, ti, A, true, na);        // A_j - A_i
-            ok = ok && !zero(nb, B) && !zero(nc, C) && !zero(na, A);
-            if (!ok) continue;
-            canon(na);                 // (A_j - A_i, B_j, C_j)
-            put(r, na);
-            take(nc, ti, A);           // (A_i, B_j, C_j - C_i)
-            canon(nc);
-            put(pj, nc);
-            canon(nb);                 // (A_i, B_i + B_j, C_i)
-            put(pi, nb);
+            const DF ti = dget(pi), tj = dget(pj);
+            DF nb, nc, na;
+            bool ok = dadd(ti, tj, B, false, nb);   // B_i + B_j
+            ok &= dadd(tj, ti, C, true, nc);        // C_j - C_i
+            ok &= dadd(tj, ti, A, true, na);        // A_j - A_i
+            const bool z = dzero(nb, B) || dzero(nc, C) || dzero(na, A);
+            if (!ok || z) continue;
+            dcanon(na);                // (A_j - A_i, B_j, C_j)
+            dput(r, na);
+            dtake(nc, ti, A);          // (A_i, B_j, C_j - C_i)
+            dcanon(nc);
+            dput(pj, nc);
+            dcanon(nb);                // (A_i, B_i + B_j, C_i)
+            dput(pi, nb);
             r += 1;
             plateau = 0;
             c_pls += 1;
@@ -351,6 +372,7 @@ struct WideWalker {
 
     __device__ __forceinline__ void run(const SegDesc &d, int64_t w, int32_t steps, unsigned char *sm) {
         lane = threadIdx.x & 31;
+        fl = lane < 3 ? lane : 0;
         R = d.R;
         KM = (R + 31) >> 5;
         W = reinterpret_cast<uint64_t *>(sm);
@@ -457,28 +479,28 @@ struct WideWalker {
 #pragma unroll 1
                     for (int q = 0; q < idx && b; ++q) b &= b - 1u;
                     j = (k << 5) + __ffs(b) - 1;
-                    const T tj = get(j);
-                    sneg = (X == 2 && eqneg(tj, ti, 2)) ? 1 : 0;
+                    const DF di = dof(ti), dj = dget(j);
+                    sneg = (X == 2 && dwneg(dj, di)) ? 1 : 0;
 
                     // flip: (Y, Z) cyclic after X, rho swaps; Y_i += Y_j, Z_j -= s Z_i
                     int Y = X == 0 ? 1 : (X == 1 ? 2 : 0);
                     int Z = X == 0 ? 2 : (X == 1 ? 0 : 1);
                     if (rho) { const int tmp = Y; Y = Z; Z = tmp; }
-                    T ti2, tj2;
-                    bool ok = add(ti, tj, Y, false, ti2);
-                    ok &= add(tj, ti, Z, sneg == 0, tj2);
+                    DF ti2, tj2;
+                    bool ok = dadd(di, dj, Y, false, ti2);
+                    ok &= dadd(dj, di, Z, sneg == 0, tj2);
                     if (!ok) {
                         action = kReject;
                         c_rej += 1;
                     } else {
                         action = kAccept;
                         c_acc += 1;
-                        const bool zi = zero(ti2, Y);
-                        const bool zj = zero(tj2, Z);
-                        canon(ti2);
-                        canon(tj2);
-                        put(i, ti2);
-                        put(j, tj2);
+                        const bool zi = dzero(ti2, Y);
+                        const bool zj = dzero(tj2, Z);
+                        dcanon(ti2);
+                        dcanon(tj2);
+                        dput(i, ti2);
+                        dput(j, tj2);
                         qlen = 0;
                         if (zi || zj) {
                             q_push(i);
