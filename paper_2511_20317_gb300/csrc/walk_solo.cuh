@@ -16,47 +16,72 @@
 //   reduction cascade -> best/plateau -> plus transition (+ cascade).
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "pterm.cuh"
 
 namespace tfg {
 namespace dev {
 
-// Bit set over RMAX slots (words of 64 bits, slot index compile-time in loops).
+// Bit set over RMAX slots: one 32-bit word when RMAX <= 32, else words of 64
+// bits (slot index compile-time in loops).
 template <int RMAX>
 struct SlotBits {
-    static constexpr int NW = (RMAX + 63) / 64;
-    uint64_t w[NW];
+    using B = typename std::conditional<(RMAX <= 32), uint32_t, uint64_t>::type;
+    static constexpr int WB = (int)sizeof(B) * 8;
+    static constexpr int NW = (RMAX + WB - 1) / WB;
+    B w[NW];
     __device__ __forceinline__ void clear() {
 #pragma unroll
         for (int a = 0; a < NW; ++a) w[a] = 0;
     }
+    __device__ __forceinline__ static int pc(B x) {
+        if constexpr (sizeof(B) == 8) return __popcll(x);
+        else return __popc(x);
+    }
     __device__ __forceinline__ int count() const {
         int c = 0;
 #pragma unroll
-        for (int a = 0; a < NW; ++a) c += __popcll(w[a]);
+        for (int a = 0; a < NW; ++a) c += pc(w[a]);
         return c;
     }
     __device__ __forceinline__ bool test(int k) const {
-        uint64_t v = w[0];
+        B v = w[0];
 #pragma unroll
-        for (int a = 1; a < NW; ++a) v = (k >> 6) == a ? w[a] : v;
-        return (v >> (k & 63)) & 1ull;
+        for (int a = 1; a < NW; ++a) v = (k / WB) == a ? w[a] : v;
+        return (v >> (k % WB)) & 1u;
+    }
+    __device__ __forceinline__ void set_if(int k, bool c) {   // k compile-time in unrolled loops
+        w[k / WB] |= c ? (B(1) << (k % WB)) : B(0);
+    }
+    // keep bits [0, r) other than bit i
+    __device__ __forceinline__ void keep_live(int r, int i) {
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+            const int lo = r - WB * q;
+            B lm = lo >= WB ? ~B(0) : (lo > 0 ? ((B(1) << lo) - 1u) : B(0));
+            if ((i / WB) == q) lm &= ~(B(1) << (i % WB));
+            w[q] &= lm;
+        }
     }
     // position of the n-th (0-based) set bit; the set must hold more than n bits
     __device__ __forceinline__ int nth(int n) const {
         int base = 0;
-        uint64_t x = w[0];
+        B x = w[0];
 #pragma unroll
         for (int a = 1; a < NW; ++a) {
-            const int c = __popcll(x);
-            if (n >= c && base == (a - 1) * 64) { n -= c; base = a * 64; x = w[a]; }
+            const int c = pc(x);
+            if (n >= c && base == (a - 1) * WB) { n -= c; base = a * WB; x = w[a]; }
         }
         int pos = 0;
         uint32_t y;
-        int c = __popc((uint32_t)x);
-        if (n >= c) { n -= c; pos = 32; y = (uint32_t)(x >> 32); } else { y = (uint32_t)x; }
-        c = __popc(y & 0xffffu);
+        if constexpr (sizeof(B) == 8) {
+            const int c = __popc((uint32_t)x);
+            if (n >= c) { n -= c; pos = 32; y = (uint32_t)(x >> 32); } else { y = (uint32_t)x; }
+        } else {
+            y = x;
+        }
+        int c = __popc(y & 0xffffu);
         if (n >= c) { n -= c; pos += 16; y >>= 16; }
         c = __popc(y & 0xffu);
         if (n >= c) { n -= c; pos += 8; y >>= 8; }
@@ -66,6 +91,13 @@ struct SlotBits {
         if (n >= c) { n -= c; pos += 2; y >>= 2; }
         if (n >= (int)(y & 1u)) pos += 1;
         return base + pos;
+    }
+    // this set, or a's / b's by a run-time choice (no divergent branches)
+    __device__ __forceinline__ static SlotBits pick(int x, const SlotBits &a, const SlotBits &b, const SlotBits &c) {
+        SlotBits o;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) o.w[q] = x == 0 ? a.w[q] : (x == 1 ? b.w[q] : c.w[q]);
+        return o;
     }
 };
 
@@ -81,6 +113,8 @@ struct SoloWalker {
     // padded by one element so that walking one thread's column across the
     // lanes of a warp (cooperative filter and snapshot) spreads over the banks.
     static constexpr int RS = (BT + 1) * NWS;   // words per row
+    // the reduction filter interleaves two walkers per round on small capacities
+    static constexpr bool kPairRounds2 = RMAX <= 32;
     Wd *sm;      // this thread's column: slot k at sm[k * RS]
     M mk;
     int r, best_r, R;
@@ -264,39 +298,87 @@ struct SoloWalker {
         if (__popc(pend) * 4 > RMAX * 3) return need && pair_hit2(ti2, i, tj2, j);
         bool mine = false;
         const int packed = i | (j << 10) | (r << 20);
+        if constexpr (kPairRounds2) {
+            // two pending walkers per round, their scans interleaved
 #pragma unroll 1
-        while (pend) {
-            const int a = __ffs(pend) - 1;
-            pend &= pend - 1;
-            T A, B;
-            A.p[0] = __shfl_sync(wmask, ti2.p[0], a);
-            B.p[0] = __shfl_sync(wmask, tj2.p[0], a);
-            if constexpr (ZT) {
-                A.n[0] = __shfl_sync(wmask, ti2.n[0], a);
-                B.n[0] = __shfl_sync(wmask, tj2.n[0], a);
-            } else {
-                A.n[0] = 0; B.n[0] = 0;
-            }
-            const int pa = __shfl_sync(wmask, packed, a);
-            const int ia = pa & 1023, ja = (pa >> 10) & 1023, ra = pa >> 20;
-            const Wd *col = sm + (a - lane) * NWS;   // walker a's column
-            bool hit = false;
+            while (pend) {
+                const int a1 = __ffs(pend) - 1;
+                pend &= pend - 1;
+                const int a2 = pend ? __ffs(pend) - 1 : a1;
+                pend &= pend - 1;
+                const T A1 = shfl_term(wmask, ti2, a1), B1 = shfl_term(wmask, tj2, a1);
+                const T A2 = shfl_term(wmask, ti2, a2), B2 = shfl_term(wmask, tj2, a2);
+                const int p1 = __shfl_sync(wmask, packed, a1), p2 = __shfl_sync(wmask, packed, a2);
+                const Wd *col1 = sm + (a1 - lane) * NWS, *col2 = sm + (a2 - lane) * NWS;   // the walkers' columns
+                bool h1 = false, h2 = false;
+                if (nl == 32) {
+#pragma unroll
+                    for (int kk = 0; kk < (RMAX + 31) / 32; ++kk) {
+                        const int k = lane + 32 * kk;
+                        h1 |= slot_shares_pair(col1, k, p1, A1, B1);
+                        h2 |= slot_shares_pair(col2, k, p2, A2, B2);
+                    }
+                } else {
 #pragma unroll 1
-            for (int k = lane; k < ra; k += nl) {
-                const T c = ld_from(col, k);
-                bool eu, ev, ewp, ewn;
-                O::compare(c, A, mk, eu, ev, ewp, ewn);
-                bool ew = ewp || ewn;
-                const bool ha = (eu && ev) || (eu && ew) || (ev && ew);
-                O::compare(c, B, mk, eu, ev, ewp, ewn);
-                ew = ewp || ewn;
-                const bool hb = (eu && ev) || (eu && ew) || (ev && ew);
-                hit = hit || (ha && k != ia) || (hb && k != ja);
+                    for (int k = lane; k < RMAX; k += nl) {
+                        h1 |= slot_shares_pair(col1, k, p1, A1, B1);
+                        h2 |= slot_shares_pair(col2, k, p2, A2, B2);
+                    }
+                }
+                const unsigned hv1 = __ballot_sync(wmask, h1), hv2 = __ballot_sync(wmask, h2);
+                if (lane == a1) mine = hv1 != 0u;
+                if (lane == a2) mine = hv2 != 0u;
             }
-            const unsigned hv = __ballot_sync(wmask, hit);
-            if (lane == a) mine = hv != 0u;
+        } else {
+            // one pending walker per round
+#pragma unroll 1
+            while (pend) {
+                const int a = __ffs(pend) - 1;
+                pend &= pend - 1;
+                const T A = shfl_term(wmask, ti2, a), B = shfl_term(wmask, tj2, a);
+                const int pa = __shfl_sync(wmask, packed, a);
+                const Wd *col = sm + (a - lane) * NWS;   // walker a's column
+                const int ra = pa >> 20;
+                const int ia = pa & 1023, ja = (pa >> 10) & 1023;
+                bool hit = false;
+#pragma unroll 1
+                for (int k = lane; k < ra; k += nl) {
+                    const T c = ld_from(col, k);
+                    bool eu, ev, ewp, ewn;
+                    O::compare(c, A, mk, eu, ev, ewp, ewn);
+                    bool ew = ewp || ewn;
+                    const bool ha = (eu && ev) || (eu && ew) || (ev && ew);
+                    O::compare(c, B, mk, eu, ev, ewp, ewn);
+                    ew = ewp || ewn;
+                    const bool hb = (eu && ev) || (eu && ew) || (ev && ew);
+                    hit = hit || (ha && k != ia) || (hb && k != ja);
+                }
+                const unsigned hv = __ballot_sync(wmask, hit);
+                if (lane == a) mine = hv != 0u;
+            }
         }
         return mine;
+    }
+    __device__ __forceinline__ static T shfl_term(unsigned wmask, const T &v, int src) {
+        T o;
+        o.p[0] = __shfl_sync(wmask, v.p[0], src);
+        o.n[0] = ZT ? __shfl_sync(wmask, v.n[0], src) : Wd(0);
+        return o;
+    }
+    // Does slot k of a walker's column share a factor pair with A (its slot
+    // ia) or B (slot ja)?  packed = ia | ja << 10 | r << 20; k >= r is false.
+    __device__ __forceinline__ bool slot_shares_pair(const Wd *col, int k, int packed, const T &A, const T &B) const {
+        const int ia = packed & 1023, ja = (packed >> 10) & 1023, ra = packed >> 20;
+        if (k >= RMAX) return false;
+        const T c = ld_from(col, k);
+        bool eu, ev, ewp, ewn;
+        O::compare(c, A, mk, eu, ev, ewp, ewn);
+        bool ew = ewp || ewn;
+        const bool ha = (eu && ev) || (eu && ew) || (ev && ew);
+        O::compare(c, B, mk, eu, ev, ewp, ewn);
+        ew = ewp || ewn;
+        const bool hb = (eu && ev) || (eu && ew) || (ev && ew);
+        return k < ra && ((ha && k != ia) || (hb && k != ja));
     }
 
     // Warp-cooperative best snapshot: lanes copy consecutive slots of each
@@ -497,35 +579,37 @@ struct SoloWalker {
                 const T ti = ld(i);
                 // ---- try_flip candidates: X_j = +-X_i, ordered (X, slot, rho)
                 SlotBits<RMAX> mu, mv, mw, mwn;
-                mu.clear(); mv.clear(); mw.clear(); mwn.clear();
+                mu.clear(); mv.clear(); mw.clear();
+                if constexpr (ZT) mwn.clear();
 #pragma unroll
                 for (int k = 0; k < RMAX; ++k) {
                     const T c = ld(k);
                     bool eu, ev, ewp, ewn;
                     O::compare(c, ti, mk, eu, ev, ewp, ewn);
-                    const uint64_t bit = 1ull << (k & 63);
-                    mu.w[k >> 6] |= eu ? bit : 0ull;
-                    mv.w[k >> 6] |= ev ? bit : 0ull;
-                    mw.w[k >> 6] |= (ewp || ewn) ? bit : 0ull;
-                    if constexpr (ZT) mwn.w[k >> 6] |= ewn ? bit : 0ull;
+                    mu.set_if(k, eu);
+                    mv.set_if(k, ev);
+                    mw.set_if(k, ewp || ewn);
+                    if constexpr (ZT) mwn.set_if(k, ewn);
                 }
                 // keep live slots [0, r) other than i
-#pragma unroll
-                for (int q = 0; q < SlotBits<RMAX>::NW; ++q) {
-                    const int lo = r - 64 * q;
-                    uint64_t lm = lo >= 64 ? ~0ull : (lo > 0 ? ((1ull << lo) - 1ull) : 0ull);
-                    if ((i >> 6) == q) lm &= ~(1ull << (i & 63));
-                    mu.w[q] &= lm; mv.w[q] &= lm; mw.w[q] &= lm; mwn.w[q] &= lm;
-                }
+                mu.keep_live(r, i); mv.keep_live(r, i); mw.keep_live(r, i);
+                if constexpr (ZT) mwn.keep_live(r, i);
                 const int nU = mu.count(), nV = mv.count(), nW = mw.count();
                 const int K = 2 * (nU + nV + nW);
                 if (K > 0) {
                     const int c = (int)__umulhi(x.y, (uint32_t)K);
                     rho = c & 1;
                     const int mi = c >> 1;
-                    if (mi < nU) { X = 0; j = mu.nth(mi); }
-                    else if (mi < nU + nV) { X = 1; j = mv.nth(mi - nU); }
-                    else { X = 2; j = mw.nth(mi - nU - nV); sneg = ZT ? (int)mwn.test(j) : 0; }
+                    if constexpr (SlotBits<RMAX>::NW == 1) {
+                        X = mi < nU ? 0 : (mi < nU + nV ? 1 : 2);
+                        const int idx = mi - (X == 0 ? 0 : (X == 1 ? nU : nU + nV));
+                        j = SlotBits<RMAX>::pick(X, mu, mv, mw).nth(idx);
+                        sneg = (ZT && X == 2) ? (int)mwn.test(j) : 0;
+                    } else {
+                        if (mi < nU) { X = 0; j = mu.nth(mi); }
+                        else if (mi < nU + nV) { X = 1; j = mv.nth(mi - nU); }
+                        else { X = 2; j = mw.nth(mi - nU - nV); sneg = ZT ? (int)mwn.test(j) : 0; }
+                    }
                     apply_candidate(ti, i, X, j, sneg, rho, action, need_check, ti2, tj2);
                 } else {
                     c_noc += 1;
@@ -538,14 +622,33 @@ struct SoloWalker {
 };
 
 template <int MODE, class Wd, int RMAX, int BT>
-__global__ void __launch_bounds__(BT) walk_solo_kernel(const SegDesc d, const int32_t steps) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void walk_solo_body(const SegDesc &d, int32_t steps, unsigned char *smem_raw) {
     const int64_t w = (int64_t)blockIdx.x * BT + threadIdx.x;
     if (w >= d.n_walkers) return;   // no block-wide barrier is used
     SoloWalker<MODE, Wd, RMAX, BT> wk;
     constexpr int NWS = (MODE == TFG_MODE_ZT) ? 2 : 1;
     wk.sm = reinterpret_cast<Wd *>(smem_raw) + (size_t)threadIdx.x * NWS;
     wk.run(d, w, steps);
+}
+
+template <int MODE, class Wd, int RMAX, int BT>
+__global__ void __launch_bounds__(BT) walk_solo_kernel(const SegDesc d, const int32_t steps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    walk_solo_body<MODE, Wd, RMAX, BT>(d, steps, smem_raw);
+}
+
+// The same kernel with registers capped for four resident blocks per SM
+// (measured faster for Z_T terms of one 32-bit word at capacity 32).
+template <int MODE, class Wd, int RMAX, int BT>
+__global__ void __launch_bounds__(BT, 4) walk_solo_kernel_occ4(const SegDesc d, const int32_t steps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    walk_solo_body<MODE, Wd, RMAX, BT>(d, steps, smem_raw);
+}
+
+template <int MODE, class Wd, int RMAX, int BT>
+constexpr auto solo_kernel() {
+    if constexpr (MODE == TFG_MODE_ZT && sizeof(Wd) == 4 && RMAX == 32) return &walk_solo_kernel_occ4<MODE, Wd, RMAX, BT>;
+    else return &walk_solo_kernel<MODE, Wd, RMAX, BT>;
 }
 
 }  // namespace dev
@@ -558,7 +661,7 @@ constexpr size_t solo_smem_bytes() {
 template <int MODE, class Wd, int RMAX, int BT>
 void prepare_walk_solo() {
     static bool attr = [] {
-        cudaFuncSetAttribute(dev::walk_solo_kernel<MODE, Wd, RMAX, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(dev::solo_kernel<MODE, Wd, RMAX, BT>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)solo_smem_bytes<MODE, Wd, RMAX, BT>());
         return true;
     }();
@@ -568,12 +671,12 @@ void prepare_walk_solo() {
 template <int MODE, class Wd, int RMAX, int BT>
 void launch_walk_solo(const SegDesc &d, int32_t steps, int grid, int /*block*/, cudaStream_t st) {
     prepare_walk_solo<MODE, Wd, RMAX, BT>();
-    dev::walk_solo_kernel<MODE, Wd, RMAX, BT><<<grid, BT, solo_smem_bytes<MODE, Wd, RMAX, BT>(), st>>>(d, steps);
+    dev::solo_kernel<MODE, Wd, RMAX, BT>()<<<grid, BT, solo_smem_bytes<MODE, Wd, RMAX, BT>(), st>>>(d, steps);
 }
 
 #define TFG_SOLO_VARIANT(MODE, WD, BITS, RMAX, BT) \
     WalkVariant{MODE, BITS, 1, 1, RMAX, BT, &launch_walk_solo<MODE, WD, RMAX, BT>, \
-                reinterpret_cast<const void *>(&dev::walk_solo_kernel<MODE, WD, RMAX, BT>), \
+                reinterpret_cast<const void *>(dev::solo_kernel<MODE, WD, RMAX, BT>()), \
                 &prepare_walk_solo<MODE, WD, RMAX, BT>}
 
 }  // namespace tfg

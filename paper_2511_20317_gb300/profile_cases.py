@@ -85,6 +85,10 @@ CASES = {
     "walk_z2333": lambda: walk((3, 3, 3), 1),
     "walk_zt222": lambda: walk((2, 2, 2), 0),
     "walk_zt445": lambda: walk((4, 4, 5), 0, walkers=80660, steps=500),
+    "walk_zt245": lambda: walk((2, 4, 5), 0, walkers=20165, steps=1000),
+    "walk_zt334": lambda: walk((3, 3, 4), 0, walkers=40330, steps=1000),
+    "walk_zt345": lambda: walk((3, 4, 5), 0, walkers=40330, steps=1000),
+    "walk_zt444": lambda: walk((4, 4, 4), 0, walkers=80660, steps=500),
     "walk_zt4512": lambda: walk_large("4512"),
     "walk_zt5610": lambda: walk_large("5610"),
     "walk_zt679": lambda: walk_large("679"),
