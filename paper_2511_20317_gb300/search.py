@@ -1,0 +1,141 @@
+"""Search driver: run a walker population to a step budget and report what the
+flip-graph walks found.
+
+    python -m paper_2511_20317_gb300.search --workload 333 --steps 1000000
+    python -m paper_2511_20317_gb300.search --workload large --steps 100000 --lift-333-steps 200000
+
+For every population it prints one JSON line with the lowest rank reached, the
+histogram of the walkers' best ranks, the number of walkers at the lowest
+rank, and the best scheme's rank and naive additive complexity after an
+independent host check of Eq. (1); `--out DIR` also writes each best scheme
+as text (the format `workloads.read_scheme` reads).
+
+`--lift-333-steps N` first searches (3,3,3) over Z_T for N steps and builds
+the (6,7,9) start from the best (3,3,3) scheme found (Section 3.3.2: product
+with the (2,2,3:11) scheme, then extension), the way the paper lifts schemes
+of small formats to larger ones.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+
+from . import tfg
+from .workloads import largest_remainder_split, naive_start
+
+MIXED = [(2, 4, 5), (3, 3, 4), (3, 4, 5), (4, 4, 4), (4, 4, 5)]
+
+
+def populations(name: str, walkers: int | None, scheme_333=None):
+    """(populations, plateau length) of a named workload."""
+    from . import starts
+    if name == "222":
+        return [((2, 2, 2), tfg.TFG_MODE_ZT, naive_start(2, 2, 2), walkers or 1024)], 10_000
+    if name == "333":
+        n = walkers or 65536
+        return [((3, 3, 3), tfg.TFG_MODE_ZT, naive_start(3, 3, 3), n),
+                ((3, 3, 3), tfg.TFG_MODE_Z2, naive_start(3, 3, 3), n)], 50_000
+    if name == "333zt":
+        return [((3, 3, 3), tfg.TFG_MODE_ZT, naive_start(3, 3, 3), walkers or 65536)], 50_000
+    if name == "mixed":
+        split = largest_remainder_split(walkers or 262144, [1, 2, 2, 4, 4])
+        return [(f, tfg.TFG_MODE_ZT, naive_start(*f), n) for f, n in zip(MIXED, split)], 50_000
+    if name == "large":
+        return starts.large_populations(walkers or 131072, scheme_333), 50_000
+    raise SystemExit(f"unknown workload {name}")
+
+
+def write_scheme(path: str, fmt, scheme: np.ndarray, note: str = ""):
+    m, n, p = fmt
+    LU, LV = m * n, n * p
+    with open(path, "w") as fh:
+        if note:
+            fh.write(f"# {note}\n")
+        fh.write(f"format {m} {n} {p}\nrank {scheme.shape[0]}\n")
+        for name, blk in (("U", scheme[:, :LU]), ("V", scheme[:, LU:LU + LV]), ("W", scheme[:, LU + LV:])):
+            fh.write(name + "\n")
+            for row in blk:
+                fh.write(" ".join(str(int(x)) for x in row) + "\n")
+
+
+def run(pops, steps: int, chunk: int, seed: int, plateau: int, out_dir: str | None = None, label: str = "",
+        quiet: bool = False):
+    import torch
+    params = tfg.tfg_default_params(plateau_len=plateau)
+    W = tfg.Walkers(pops, seed=seed, params=params)
+    W.autotune(trial_steps=200, trial_walkers=16384)
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        c = min(chunk, steps - done)
+        W.walk(c)
+        W.sync()
+        done += c
+        if not quiet:
+            lows = [W.stats(f)[0]["min_best_r"] for f in range(W.n_formats)]
+            print(json.dumps({"progress": done, "seconds": round(time.perf_counter() - t0, 2),
+                              "lowest_ranks": lows}), flush=True)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    fails = W.verify_all()
+    results = []
+    for f, (fmt, mode, start, nw) in enumerate(pops):
+        st, hist = W.stats(f)
+        scheme, rank, walker = W.collect_best(f)
+        ok = tfg.tfg_verify(fmt, scheme, mode=mode)
+        res = {
+            "label": label, "format": list(fmt), "mode": "Z_T" if mode == tfg.TFG_MODE_ZT else "Z_2",
+            "walkers": nw, "steps_per_walker": steps, "start_rank": int(np.asarray(start).shape[0]),
+            "prepared_start_rank": W.pop[f]["r0"],
+            "lowest_rank": int(rank), "best_walker": int(walker),
+            "walkers_at_lowest": int(hist[rank]) if rank < len(hist) else None,
+            "rank_histogram": {int(k): int(v) for k, v in enumerate(hist) if v},
+            "best_scheme_verified_host": bool(ok),
+            "additive_complexity": int(tfg.tfg_additive_complexity(fmt, scheme)) if mode == tfg.TFG_MODE_ZT else None,
+            "accepted": int(st["accepted"]), "reductions": int(st["reductions"]), "plus": int(st["plus"]),
+            "device_check_failures": int(fails), "seconds": round(secs, 2),
+            "steps_per_s": nw * steps / secs,
+        }
+        if out_dir:
+            os.makedirs(out_dir, exist_ok=True)
+            tag = "zt" if mode == tfg.TFG_MODE_ZT else "z2"
+            path = os.path.join(out_dir, f"best_{fmt[0]}x{fmt[1]}x{fmt[2]}_{tag}_r{rank}.txt")
+            write_scheme(path, fmt, scheme, f"walker {walker}, seed {seed}, {steps} steps")
+            res["file"] = path
+        results.append((res, scheme))
+    W.close()
+    return results
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="333")
+    ap.add_argument("--walkers", type=int, default=None)
+    ap.add_argument("--steps", type=float, default=1e6)
+    ap.add_argument("--chunk", type=int, default=100_000)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--plateau", type=int, default=None)
+    ap.add_argument("--lift-333-steps", type=float, default=0)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--quiet", action="store_true")
+    args = ap.parse_args()
+    import torch
+    torch.cuda.set_device(0)
+    scheme_333 = None
+    if args.workload == "large" and args.lift_333_steps > 0:
+        pops, plateau = populations("333zt", None)
+        (res, scheme_333), = run(pops, int(args.lift_333_steps), args.chunk, args.seed, plateau, args.out,
+                                 "lift (3,3,3)", args.quiet)
+        print(json.dumps(res), flush=True)
+    pops, plateau = populations(args.workload, args.walkers, scheme_333)
+    for res, _ in run(pops, int(args.steps), args.chunk, args.seed, args.plateau or plateau, args.out,
+                      args.workload, args.quiet):
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -161,3 +161,14 @@ def test_large_format_starts():
     f3, s3 = oracle.product(fmt_s, S, f2, s2)
     f4, s4 = oracle.extend(f3, s3, 1)
     assert np.array_equal(s4, starts.start_4_5_12()[1])
+
+
+def test_search_scheme_files_round_trip(tmp_path):
+    """The search driver's scheme files read back to the same format and rows."""
+    from paper_2511_20317_gb300.search import write_scheme
+    for name in ["paper_2x2x3_r11.txt", "strassen_2x2x2_r7.txt"]:
+        fmt, s = gold(name)
+        path = str(tmp_path / name)
+        write_scheme(path, fmt, s, "round trip")
+        f2, s2 = read_scheme(path)
+        assert f2 == fmt and np.array_equal(s2, s)
