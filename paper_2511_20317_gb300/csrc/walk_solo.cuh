@@ -113,8 +113,12 @@ struct SoloWalker {
     // padded by one element so that walking one thread's column across the
     // lanes of a warp (cooperative filter and snapshot) spreads over the banks.
     static constexpr int RS = (BT + 1) * NWS;   // words per row
-    // the reduction filter interleaves two walkers per round on small capacities
-    static constexpr bool kPairRounds2 = RMAX <= 32;
+    // walkers per round of the cooperative reduction filter (interleaved scans
+    // on small capacities)
+#ifndef TFG_SOLO_ROUND_WALKERS
+#define TFG_SOLO_ROUND_WALKERS 2
+#endif
+    static constexpr int kRoundWalkers = RMAX <= 32 ? TFG_SOLO_ROUND_WALKERS : 1;
     Wd *sm;      // this thread's column: slot k at sm[k * RS]
     M mk;
     int r, best_r, R;
@@ -298,36 +302,46 @@ struct SoloWalker {
         if (__popc(pend) * 4 > RMAX * 3) return need && pair_hit2(ti2, i, tj2, j);
         bool mine = false;
         const int packed = i | (j << 10) | (r << 20);
-        if constexpr (kPairRounds2) {
-            // two pending walkers per round, their scans interleaved
+        if constexpr (kRoundWalkers > 1) {
+            // kRoundWalkers pending walkers per round, their scans interleaved
+            constexpr int WR = kRoundWalkers;
 #pragma unroll 1
             while (pend) {
-                const int a1 = __ffs(pend) - 1;
-                pend &= pend - 1;
-                const int a2 = pend ? __ffs(pend) - 1 : a1;
-                pend &= pend - 1;
-                const T A1 = shfl_term(wmask, ti2, a1), B1 = shfl_term(wmask, tj2, a1);
-                const T A2 = shfl_term(wmask, ti2, a2), B2 = shfl_term(wmask, tj2, a2);
-                const int p1 = __shfl_sync(wmask, packed, a1), p2 = __shfl_sync(wmask, packed, a2);
-                const Wd *col1 = sm + (a1 - lane) * NWS, *col2 = sm + (a2 - lane) * NWS;   // the walkers' columns
-                bool h1 = false, h2 = false;
+                int a[WR];
+#pragma unroll
+                for (int q = 0; q < WR; ++q) {
+                    a[q] = pend ? __ffs(pend) - 1 : a[0];   // a repeated walker recomputes the same answer
+                    pend &= pend - 1;
+                }
+                T A[WR], B[WR];
+                int pk[WR];
+                bool h[WR];
+#pragma unroll
+                for (int q = 0; q < WR; ++q) {
+                    A[q] = shfl_term(wmask, ti2, a[q]);
+                    B[q] = shfl_term(wmask, tj2, a[q]);
+                    pk[q] = __shfl_sync(wmask, packed, a[q]);
+                    h[q] = false;
+                }
                 if (nl == 32) {
 #pragma unroll
                     for (int kk = 0; kk < (RMAX + 31) / 32; ++kk) {
                         const int k = lane + 32 * kk;
-                        h1 |= slot_shares_pair(col1, k, p1, A1, B1);
-                        h2 |= slot_shares_pair(col2, k, p2, A2, B2);
+#pragma unroll
+                        for (int q = 0; q < WR; ++q) h[q] |= slot_shares_pair(sm + (a[q] - lane) * NWS, k, pk[q], A[q], B[q]);
                     }
                 } else {
 #pragma unroll 1
                     for (int k = lane; k < RMAX; k += nl) {
-                        h1 |= slot_shares_pair(col1, k, p1, A1, B1);
-                        h2 |= slot_shares_pair(col2, k, p2, A2, B2);
+#pragma unroll
+                        for (int q = 0; q < WR; ++q) h[q] |= slot_shares_pair(sm + (a[q] - lane) * NWS, k, pk[q], A[q], B[q]);
                     }
                 }
-                const unsigned hv1 = __ballot_sync(wmask, h1), hv2 = __ballot_sync(wmask, h2);
-                if (lane == a1) mine = hv1 != 0u;
-                if (lane == a2) mine = hv2 != 0u;
+#pragma unroll
+                for (int q = 0; q < WR; ++q) {
+                    const unsigned hv = __ballot_sync(wmask, h[q]);
+                    if (lane == a[q]) mine = hv != 0u;
+                }
             }
         } else {
             // one pending walker per round

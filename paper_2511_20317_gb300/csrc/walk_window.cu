@@ -52,8 +52,7 @@ __device__ __forceinline__ void cand_features(const PTerm<Wd, 1, true> &a, const
     const bool vz = (((b.p[0] & zp) | (b.n[0] & zn)) & MZ) == Wd(0);
     const Wd szd = (((b.p[0] | zp) & ~(b.n[0] | zn)) | ((b.n[0] | zn) & ~(b.p[0] | zp))) & MZ;
 #pragma unroll
-    for (int k = 0; k < kFeat; ++k) f[k] = 0.f;
-    f[X] = 1.f;
+    for (int k = 0; k < kFeat; ++k) f[k] = (k == X) ? 1.f : 0.f;   // one-hot X in f[0..2]
     f[3] = (float)rho;
     f[4] = (float)sneg;
     f[5] = (float)popc_w<Wd>(ad & MX);
@@ -79,10 +78,18 @@ __device__ __forceinline__ void cand_features(const PTerm<Wd, 1, true> &a, const
     f[31] = 1.f;
 }
 
+// One warp per walker.  Phase 1: eight terms i0 + g (g = lane / 4, then the
+// next eight while the window has room); the four lanes of a group scan
+// consecutive quarters of the slots for the term's try_flip candidates, and
+// every candidate's descriptor goes to its window position in shared memory
+// (order: term, then factor, then slot, then rho).  Phase 2: the lanes take
+// window rows l, l+32, ... and compute and store the feature rows (coalesced
+// 64-byte rows).
 template <class Wd>
 __global__ void __launch_bounds__(128) window_kernel(const SegDesc d, __nv_bfloat16 *__restrict__ feat,
                                                      uint32_t *__restrict__ desc, int *__restrict__ kwin) {
     __shared__ __align__(16) Wd sp[4][kWinMaxSlots], sn[4][kWinMaxSlots];
+    __shared__ uint32_t sdesc[4][kWin], sinfo[4][kWin];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * 4 + warp;
     if (w >= d.n_walkers) return;
@@ -100,78 +107,112 @@ __global__ void __launch_bounds__(128) window_kernel(const SegDesc d, __nv_bfloa
         sn[warp][k] = src[(size_t)k * 2 + 1];
     }
     __syncwarp();
-    __nv_bfloat16 *fw = feat + (size_t)w * kWin * kFeat;
-    uint32_t *dw = desc + (size_t)w * kWin;
+    // ---- phase 1: candidate descriptors in window order
+    const int g = lane >> 2, sub = lane & 3;
+    const int chunk = (r + 3) >> 2;                  // <= 32 slots per lane
+    const int jb = sub * chunk, je = min(r, jb + chunk);
     int carry = 0;
-    for (int base = 0; base < r && carry < kWin; base += 32) {
-        const int q = base + lane;
+    for (int base = 0; base < r && carry < kWin; base += 8) {
+        const int q = base + g;
         const bool has = q < r;
         const int i = has ? (i0 + q) % r : 0;
         T ti;
         ti.p[0] = sp[warp][i];
         ti.n[0] = sn[warp][i];
-        uint64_t mu[2] = {0, 0}, mv[2] = {0, 0}, mw[2] = {0, 0}, mwn[2] = {0, 0};
+        // bit (j - jb): slot j of this lane's quarter is a candidate of factor u / v / w (w negated)
+        uint32_t bu = 0, bv = 0, bw = 0, bn = 0;
         if (has) {
-            for (int j = 0; j < r; ++j) {
+            for (int j = jb; j < je; ++j) {
                 if (j == i) continue;
                 T c;
                 c.p[0] = sp[warp][j];
                 c.n[0] = sn[warp][j];
                 bool eu, ev, ewp, ewn;
                 O::compare(c, ti, mk, eu, ev, ewp, ewn);
-                const uint64_t bit = 1ull << (j & 63);
-                const int hw = j >> 6;
-                if (eu) mu[hw] |= bit;
-                if (ev) mv[hw] |= bit;
-                if (ewp || ewn) mw[hw] |= bit;
-                if (ewn) mwn[hw] |= bit;
+                const uint32_t bit = 1u << (j - jb);
+                bu |= eu ? bit : 0u;
+                bv |= ev ? bit : 0u;
+                bw |= (ewp || ewn) ? bit : 0u;
+                bn |= ewn ? bit : 0u;
             }
         }
-        const int ki = 2 * (__popcll(mu[0]) + __popcll(mu[1]) + __popcll(mv[0]) + __popcll(mv[1]) +
-                            __popcll(mw[0]) + __popcll(mw[1]));
-        int incl = ki;
+        // per-factor counts: this lane, earlier lanes of the group, the whole term
+        const uint32_t own = (uint32_t)__popc(bu) | ((uint32_t)__popc(bv) << 8) | ((uint32_t)__popc(bw) << 16);
+        uint32_t gin = own;
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, gin, o, 4);
+            if (sub >= o) gin += y;
+        }
+        const uint32_t gtot = __shfl_sync(0xffffffffu, gin, 3, 4);
+        const uint32_t gex = gin - own;
+        const int nU = (int)(gtot & 255u), nV = (int)((gtot >> 8) & 255u), nW = (int)(gtot >> 16);
+        const int ki = 2 * (nU + nV + nW);
+        // window offset of the term: counts of the earlier terms of this round
+        int incl = sub == 0 ? ki : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        int pos = carry + incl - ki;
-        // this term's candidates in (factor, slot, rho) order while the window has room
-        for (int X = 0; X < 3 && pos < kWin; ++X) {
-            const uint64_t *mX = X == 0 ? mu : (X == 1 ? mv : mw);
-            for (int hw = 0; hw < 2 && pos < kWin; ++hw) {
-                uint64_t bits = mX[hw];
-                while (bits && pos < kWin) {
-                    const int j = hw * 64 + (__ffsll((long long)bits) - 1);
-                    bits &= bits - 1;
-                    const int sneg = (X == 2) ? (int)((mwn[hw] >> (j & 63)) & 1ull) : 0;
-                    T tj;
-                    tj.p[0] = sp[warp][j];
-                    tj.n[0] = sn[warp][j];
-                    for (int rho = 0; rho < 2 && pos < kWin; ++rho) {
-                        float f[kFeat];
-                        cand_features<Wd>(ti, tj, mk, X, sneg, rho, ki, q, r, best_r, d.m, d.n, d.p, f);
-                        __align__(16) __nv_bfloat16 hb[kFeat];
-#pragma unroll
-                        for (int k = 0; k < kFeat; ++k) hb[k] = __float2bfloat16_rn(f[k]);
-                        uint4 *dst = reinterpret_cast<uint4 *>(fw + (size_t)pos * kFeat);
-#pragma unroll
-                        for (int k = 0; k < kFeat / 8; ++k) dst[k] = reinterpret_cast<const uint4 *>(hb)[k];
-                        dw[pos] = pack_cand(i, X, j, sneg, rho);
-                        ++pos;
-                    }
+        const int tpos = carry + incl - ki;
+        const uint32_t info = (uint32_t)(ki < 64 ? ki : 64) | ((uint32_t)(q < 64 ? q : 64) << 8);
+        // this lane's candidates: factor X, slot order, rho 0 then 1
+        for (int X = 0; X < 3; ++X) {
+            const int before = X == 0 ? 0 : (X == 1 ? nU : nU + nV);
+            const int lex = (int)((gex >> (8 * X)) & 255u);
+            int pos = tpos + 2 * (before + lex);
+            uint32_t bits = X == 0 ? bu : (X == 1 ? bv : bw);
+            while (bits && pos < kWin) {
+                const int o = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const int j = jb + o;
+                const int sneg = (X == 2) ? (int)((bn >> o) & 1u) : 0;
+                sdesc[warp][pos] = pack_cand(i, X, j, sneg, 0);
+                sinfo[warp][pos] = info;
+                if (pos + 1 < kWin) {
+                    sdesc[warp][pos + 1] = pack_cand(i, X, j, sneg, 1);
+                    sinfo[warp][pos + 1] = info;
                 }
+                pos += 2;
             }
         }
         carry += total;
     }
     const int K = carry < kWin ? carry : kWin;
-    // rows past the window are zero (scored, never chosen)
-    for (int p = K + lane; p < kWin; p += 32) {
-        uint4 *dst = reinterpret_cast<uint4 *>(fw + (size_t)p * kFeat);
+    __syncwarp();
+    // ---- phase 2: feature rows (rows past the window are zero: scored, never chosen)
+    __nv_bfloat16 *fw = feat + (size_t)w * kWin * kFeat;
+    uint32_t *dw = desc + (size_t)w * kWin;
+    for (int row = lane; row < kWin; row += 32) {
+        uint4 *dst = reinterpret_cast<uint4 *>(fw + (size_t)row * kFeat);
+        if (row < K) {
+            const uint32_t dc = sdesc[warp][row], in = sinfo[warp][row];
+            const int i = (int)(dc & 1023u), X = (int)((dc >> 10) & 3u), j = (int)((dc >> 12) & 1023u);
+            const int sneg = (int)((dc >> 22) & 1u), rho = (int)((dc >> 23) & 1u);
+            T ti, tj;
+            ti.p[0] = sp[warp][i];
+            ti.n[0] = sn[warp][i];
+            tj.p[0] = sp[warp][j];
+            tj.n[0] = sn[warp][j];
+            float f[kFeat];
+            cand_features<Wd>(ti, tj, mk, X, sneg, rho, (int)(in & 255u), (int)(in >> 8), r, best_r, d.m, d.n, d.p, f);
 #pragma unroll
-        for (int k = 0; k < kFeat / 8; ++k) dst[k] = make_uint4(0, 0, 0, 0);
+            for (int k = 0; k < kFeat / 8; ++k) {
+                uint32_t wv[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[8 * k + 2 * h], f[8 * k + 2 * h + 1]);
+                    wv[h] = *reinterpret_cast<const uint32_t *>(&b2);
+                }
+                dst[k] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
+            dw[row] = dc;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kFeat / 8; ++k) dst[k] = make_uint4(0, 0, 0, 0);
+        }
     }
     if (lane == 0) kwin[w] = K;
 }

@@ -93,8 +93,10 @@ CASES = {
     "walk_zt5610": lambda: walk_large("5610"),
     "walk_zt679": lambda: walk_large("679"),
     "mlp_score": mlp_score,
+    "mlp_score_33m": lambda: mlp_score(rows=1 << 25),
     "mlp_grad": mlp_grad,
     "window_444": window,
+    "window_444_262k": lambda: window(walkers=262144),
 }
 
 
