@@ -20,6 +20,9 @@
 // normalisation, signatures and stores are a handful of lane-parallel
 // instructions; __syncwarp orders the shared-memory writes.
 //
+// Terms of large walkers (capacity >= 256 slots) stay in their HBM slots and
+// only the signatures sit in shared memory (more walkers resident per SM).
+//
 // The step contract (draws, candidate order, flip, rejection, removal,
 // normalisation, reduction cascade, best/plateau bookkeeping, plus
 // transitions, trajectory digest) is the one of the lane-group and
@@ -53,14 +56,16 @@ __device__ __forceinline__ uint32_t fsig(uint64_t p, uint64_t n) {
     return (uint32_t)(h >> 32);
 }
 
-template <int MODE>
+// GW: the term words stay in the walker's HBM slots (only the signatures are
+// in shared memory), else they are staged in shared memory for the launch.
+template <int MODE, bool GW>
 struct WideWalker {
     static constexpr bool ZT = (MODE == TFG_MODE_ZT);
     static constexpr int NWG = ZT ? 6 : 3;   // words per slot in HBM (p0 p1 p2 [n0 n1 n2])
     static constexpr int NWS = ZT ? 6 : 4;   // words per slot in shared memory (16-byte rows)
     using T = FTerm<ZT>;
 
-    uint64_t *W;    // [R][NWS] factor-grouped: (p0 n0)(p1 n1)(p2 n2), Z_2: (p0 p1)(p2 -)
+    uint64_t *W;    // GW: HBM slots [R][NWG] (p0 p1 p2 [n0 n1 n2]); else shared [R][NWS] factor-grouped: (p0 n0)(p1 n1)(p2 n2), Z_2: (p0 p1)(p2 -)
     uint4 *SG;      // [32 * KM] signatures (u, v, w up to sign, sign of w)
     int lane, KM;
     int r, best_r, R;
@@ -107,7 +112,9 @@ struct WideWalker {
 
     __device__ __forceinline__ DF dof(const T &a) const { return DF{w_of(a.p, fl), w_of(a.n, fl)}; }
     __device__ __forceinline__ DF dget(int s) const {
-        if constexpr (ZT) {
+        if constexpr (GW) {
+            return DF{W[(size_t)s * NWG + fl], ZT ? W[(size_t)s * NWG + 3 + fl] : 0ull};
+        } else if constexpr (ZT) {
             const ulonglong2 a = reinterpret_cast<const ulonglong2 *>(W + (size_t)s * NWS)[fl];
             return DF{a.x, a.y};
         } else {
@@ -161,8 +168,14 @@ struct WideWalker {
         }
         const uint32_t h = fsig(cp, cn);
         if (lane < 3) {
-            if constexpr (ZT) reinterpret_cast<ulonglong2 *>(W + (size_t)s * NWS)[lane] = make_ulonglong2(a.p, a.n);
-            else W[(size_t)s * NWS + lane] = a.p;
+            if constexpr (GW) {
+                W[(size_t)s * NWG + lane] = a.p;
+                if constexpr (ZT) W[(size_t)s * NWG + 3 + lane] = a.n;
+            } else if constexpr (ZT) {
+                reinterpret_cast<ulonglong2 *>(W + (size_t)s * NWS)[lane] = make_ulonglong2(a.p, a.n);
+            } else {
+                W[(size_t)s * NWS + lane] = a.p;
+            }
             uint32_t *g = reinterpret_cast<uint32_t *>(SG + s);
             g[lane] = h;
             if (lane == 2) g[3] = ng;
@@ -173,6 +186,19 @@ struct WideWalker {
     // ---- shared-memory slots
     __device__ __forceinline__ T get(int s) const {
         T out;
+        if constexpr (GW) {
+            const uint64_t *g = W + (size_t)s * NWG;
+            if constexpr (ZT) {
+                const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(g);   // 48-byte rows: 16-byte aligned
+                const ulonglong2 a = q[0], b = q[1], c = q[2];
+                out.p[0] = a.x; out.p[1] = a.y; out.p[2] = b.x;
+                out.n[0] = b.y; out.n[1] = c.x; out.n[2] = c.y;
+            } else {
+                out.p[0] = g[0]; out.p[1] = g[1]; out.p[2] = g[2];
+                out.n[0] = out.n[1] = out.n[2] = 0ull;
+            }
+            return out;
+        }
         const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(W + (size_t)s * NWS);
         const ulonglong2 a = src[0], b = src[1];
         if constexpr (ZT) {
@@ -188,7 +214,10 @@ struct WideWalker {
     }
     // factor f of slot s only (one 16-byte load in Z_T)
     __device__ __forceinline__ void get_factor(int s, int f, uint64_t &p, uint64_t &n) const {
-        if constexpr (ZT) {
+        if constexpr (GW) {
+            p = W[(size_t)s * NWG + f];
+            n = ZT ? W[(size_t)s * NWG + 3 + f] : 0ull;
+        } else if constexpr (ZT) {
             const ulonglong2 a = reinterpret_cast<const ulonglong2 *>(W + (size_t)s * NWS)[f];
             p = a.x; n = a.y;
         } else {
@@ -197,6 +226,12 @@ struct WideWalker {
         }
     }
     __device__ __forceinline__ void move(int from, int to) {
+        if constexpr (GW) {
+            if (lane < NWG) W[(size_t)to * NWG + lane] = W[(size_t)from * NWG + lane];
+            else if (lane == NWG) SG[to] = SG[from];
+            __syncwarp();
+            return;
+        }
         if (lane < NWS / 2) {
             const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(W + (size_t)from * NWS);
             ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(W + (size_t)to * NWS);
@@ -328,8 +363,12 @@ struct WideWalker {
     __device__ __forceinline__ void snapshot(uint64_t *bestp) const {
 #pragma unroll 1
         for (int e = lane; e < r * NWG; e += 32) {
-            const int s = e / NWG, g = e - s * NWG;
-            bestp[e] = W[(size_t)s * NWS + (ZT ? (g < 3 ? 2 * g : 2 * (g - 3) + 1) : g)];
+            if constexpr (GW) {
+                bestp[e] = W[e];
+            } else {
+                const int s = e / NWG, g = e - s * NWG;
+                bestp[e] = W[(size_t)s * NWS + (ZT ? (g < 3 ? 2 * g : 2 * (g - 3) + 1) : g)];
+            }
         }
     }
 
@@ -375,8 +414,13 @@ struct WideWalker {
         fl = lane < 3 ? lane : 0;
         R = d.R;
         KM = (R + 31) >> 5;
-        W = reinterpret_cast<uint64_t *>(sm);
-        SG = reinterpret_cast<uint4 *>(W + (size_t)R * NWS);
+        if constexpr (GW) {
+            W = reinterpret_cast<uint64_t *>(d.slots) + (size_t)w * R * NWG;
+            SG = reinterpret_cast<uint4 *>(sm);
+        } else {
+            W = reinterpret_cast<uint64_t *>(sm);
+            SG = reinterpret_cast<uint4 *>(W + (size_t)R * NWS);
+        }
         tfg_walker_info *H = d.hdr + w;
         r = H->r; best_r = H->best_r;
         t = H->t; plateau = H->plateau; best_t = H->best_t;
@@ -386,14 +430,16 @@ struct WideWalker {
         qlen = 0; q0 = q1 = q2 = 0;
         const uint64_t *src = reinterpret_cast<const uint64_t *>(d.slots) + (size_t)w * R * NWG;
         uint64_t *bestp = reinterpret_cast<uint64_t *>(d.best) + (size_t)w * R * NWG;
-        // HBM rows (p0 p1 p2 [n0 n1 n2]) -> shared rows grouped by factor
+        if constexpr (!GW) {
+            // HBM rows (p0 p1 p2 [n0 n1 n2]) -> shared rows grouped by factor
 #pragma unroll 1
-        for (int e = lane; e < R * NWS; e += 32) {
-            const int s = e / NWS, q = e - s * NWS;
-            const int g = ZT ? ((q & 1) ? 3 + (q >> 1) : (q >> 1)) : q;   // source word of shared word q
-            W[e] = g < NWG ? src[(size_t)s * NWG + g] : 0ull;
+            for (int e = lane; e < R * NWS; e += 32) {
+                const int s = e / NWS, q = e - s * NWS;
+                const int g = ZT ? ((q & 1) ? 3 + (q >> 1) : (q >> 1)) : q;   // source word of shared word q
+                W[e] = g < NWG ? src[(size_t)s * NWG + g] : 0ull;
+            }
+            __syncwarp();
         }
-        __syncwarp();
 #pragma unroll 1
         for (int s = lane; s < 32 * KM; s += 32) SG[s] = s < R ? sig(get(s)) : make_uint4(0u, 0u, 0u, 0u);
         __syncwarp();
@@ -551,10 +597,12 @@ struct WideWalker {
 
         // ---- write back
         uint64_t *dst = reinterpret_cast<uint64_t *>(d.slots) + (size_t)w * R * NWG;
+        if constexpr (!GW) {
 #pragma unroll 1
-        for (int e = lane; e < R * NWG; e += 32) {
-            const int s = e / NWG, g = e - s * NWG;
-            dst[e] = W[(size_t)s * NWS + (ZT ? (g < 3 ? 2 * g : 2 * (g - 3) + 1) : g)];
+            for (int e = lane; e < R * NWG; e += 32) {
+                const int s = e / NWG, g = e - s * NWG;
+                dst[e] = W[(size_t)s * NWS + (ZT ? (g < 3 ? 2 * g : 2 * (g - 3) + 1) : g)];
+            }
         }
         if (lane == 0) {
             H->r = r; H->best_r = best_r;
@@ -566,21 +614,23 @@ struct WideWalker {
     }
 };
 
-template <int MODE>
+template <int MODE, bool GW>
 __host__ __device__ constexpr size_t wide_walker_bytes(int R) {
-    return (size_t)R * (MODE == TFG_MODE_ZT ? 6 : 4) * 8 + (size_t)((R + 31) / 32) * 32 * 16;
+    return (GW ? (size_t)0 : (size_t)R * (MODE == TFG_MODE_ZT ? 6 : 4) * 8) + (size_t)((R + 31) / 32) * 32 * 16;
 }
 
 constexpr int kWideWarps = 2;   // walkers (warps) per block
 
-template <int MODE>
-__global__ void __launch_bounds__(32 * kWideWarps) walk_wide_kernel(const SegDesc d, const int32_t steps) {
+// With the term words in HBM, registers bound residency: capped for 16
+// two-warp blocks per SM (measured +4-8% on ranks 285 and 351).
+template <int MODE, bool GW>
+__global__ void __launch_bounds__(32 * kWideWarps, GW ? 16 : 1) walk_wide_kernel(const SegDesc d, const int32_t steps) {
     extern __shared__ __align__(16) unsigned char wide_sm[];
     const int warp = threadIdx.x >> 5;
     const int64_t w = (int64_t)blockIdx.x * kWideWarps + warp;
     if (w >= d.n_walkers) return;   // whole warps exit together
-    WideWalker<MODE> wk;
-    wk.run(d, w, steps, wide_sm + wide_walker_bytes<MODE>(d.R) * warp);
+    WideWalker<MODE, GW> wk;
+    wk.run(d, w, steps, wide_sm + wide_walker_bytes<MODE, GW>(d.R) * warp);
 }
 
 }  // namespace dev
@@ -589,22 +639,35 @@ namespace {
 
 constexpr int kWideMaxSmem = 227 * 1024;
 
+// Term words stay in HBM from this capacity on: shared-memory residency (22.8 KB
+// per walker at 354 slots) limits the larger ranks.  Measured on 16384 walkers:
+// rank 202 (capacity 205) 1.00e9 shared vs 0.98e9 HBM steps/s; rank 285: 0.69e9 vs
+// 0.85e9; rank 351: 0.46e9 vs 0.73e9.
+constexpr int kWideHbmWordsMinR = 256;
+
 template <int MODE>
 void prepare_walk_wide() {
     static bool attr = [] {
-        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
+        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
+        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
         return true;
     }();
     (void)attr;
 }
 
+template <int MODE, bool GW>
+void launch_wide_as(const SegDesc &d, int32_t steps, cudaStream_t st) {
+    const size_t smem = dev::wide_walker_bytes<MODE, GW>(d.R) * dev::kWideWarps;
+    if (d.n_walkers <= 0 || smem > (size_t)kWideMaxSmem) return;
+    const int64_t grid = (d.n_walkers + dev::kWideWarps - 1) / dev::kWideWarps;
+    dev::walk_wide_kernel<MODE, GW><<<(unsigned)grid, 32 * dev::kWideWarps, smem, st>>>(d, steps);
+}
+
 template <int MODE>
 void launch_walk_wide(const SegDesc &d, int32_t steps, int /*grid*/, int /*block*/, cudaStream_t st) {
     prepare_walk_wide<MODE>();
-    const size_t smem = dev::wide_walker_bytes<MODE>(d.R) * dev::kWideWarps;
-    if (d.n_walkers <= 0 || smem > (size_t)kWideMaxSmem) return;
-    const int64_t grid = (d.n_walkers + dev::kWideWarps - 1) / dev::kWideWarps;
-    dev::walk_wide_kernel<MODE><<<(unsigned)grid, 32 * dev::kWideWarps, smem, st>>>(d, steps);
+    if (d.R >= kWideHbmWordsMinR) launch_wide_as<MODE, true>(d, steps, st);
+    else launch_wide_as<MODE, false>(d, steps, st);
 }
 
 }  // namespace
@@ -614,10 +677,10 @@ void launch_walk_wide(const SegDesc &d, int32_t steps, int /*grid*/, int /*block
 const WalkVariant *walk_variants_wide(int *n) {
     static const WalkVariant v[] = {
         WalkVariant{TFG_MODE_ZT, 64, 3, 32, 0, 0, &launch_walk_wide<TFG_MODE_ZT>,
-                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_ZT>), &prepare_walk_wide<TFG_MODE_ZT>,
+                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_ZT, true>), &prepare_walk_wide<TFG_MODE_ZT>,
                     1023},
         WalkVariant{TFG_MODE_Z2, 64, 3, 32, 0, 0, &launch_walk_wide<TFG_MODE_Z2>,
-                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_Z2>), &prepare_walk_wide<TFG_MODE_Z2>,
+                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_Z2, true>), &prepare_walk_wide<TFG_MODE_Z2>,
                     1023},
     };
     *n = (int)(sizeof(v) / sizeof(v[0]));

@@ -195,7 +195,7 @@ def _start_4_5_12():
 
 
 @pytest.mark.parametrize("mode", [tfg.TFG_MODE_ZT, tfg.TFG_MODE_Z2])
-@pytest.mark.parametrize("case", ["4x5x5", "4x5x12", "8x8x1", "1x8x8", "6x7x9"])
+@pytest.mark.parametrize("case", ["4x5x5", "4x5x12", "8x8x1", "1x8x8", "6x7x9", "8x8x8"])
 def test_wide_terms_parity(case, mode):
     """Terms longer than 64 coefficients (factor-aligned words, shared-memory
     signature search): naive (4,5,5) and (6,7,9), the meta-operator (4,5,12)
@@ -207,9 +207,9 @@ def test_wide_terms_parity(case, mode):
         fmt = tuple(int(x) for x in case.split("x"))
         start = naive_start(*fmt)
         nw, steps, L = {"4x5x5": (64, 3000, 300), "8x8x1": (64, 2000, 200), "1x8x8": (64, 2000, 200),
-                        "6x7x9": (12, 400, 100)}[case]
-    if case == "6x7x9" and mode == tfg.TFG_MODE_Z2:
-        pytest.skip("one mode suffices at rank 378")
+                        "6x7x9": (12, 400, 100), "8x8x8": (6, 300, 60)}[case]
+    if case in ("6x7x9", "8x8x8") and mode == tfg.TFG_MODE_Z2:
+        pytest.skip("one mode suffices at ranks 378 and 512")
     if mode == tfg.TFG_MODE_Z2:
         start = np.abs(start).astype(np.int8)   # a Z_T scheme read mod 2
     W = gpu_walkers(fmt, mode, start, nw, 4, steps, chunks=2, plateau_len=L)
