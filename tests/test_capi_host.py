@@ -172,3 +172,15 @@ def test_search_scheme_files_round_trip(tmp_path):
         write_scheme(path, fmt, s, "round trip")
         f2, s2 = read_scheme(path)
         assert f2 == fmt and np.array_equal(s2, s)
+
+
+def test_lifted_6_7_9_start_from_a_walked_333_scheme():
+    """(6,7,9) = extend_n((2,2,3:11) (x) S333): rank 11 r + 54 for any valid (3,3,3)
+    scheme S333 of rank r (here one the oracle's walk produced)."""
+    from paper_2511_20317_gb300 import starts
+    W = oracle.Walkers((3, 3, 3), naive_start(3, 3, 3), np.arange(8), seed=2, plateau_len=400).walk(6000)
+    w = int(np.argmin(W.info["best_r"]))
+    s333 = W.best_scheme(w)
+    fmt, s = starts.start_6_7_9(s333)
+    assert fmt == (6, 7, 9) and s.shape[0] == 11 * s333.shape[0] + 54
+    assert oracle.brent_valid(fmt, s)

@@ -1,0 +1,41 @@
+"""The search driver end to end on small populations: its report agrees with
+the walkers' statistics, every best scheme it writes reads back and satisfies
+Eq. (1) (checked by the oracle)."""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_20317_gb300 import search, tfg
+from paper_2511_20317_gb300.workloads import naive_start, read_scheme
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2511_20317_gb300 import _build
+    _build.build()
+    tfg.lib()
+    torch.cuda.set_device(0)
+
+
+def test_search_reports_and_files(tmp_path):
+    pops = [((2, 2, 2), tfg.TFG_MODE_ZT, naive_start(2, 2, 2), 512),
+            ((3, 3, 3), tfg.TFG_MODE_Z2, naive_start(3, 3, 3), 256)]
+    out = search.run(pops, steps=20000, chunk=7000, seed=3, plateau=2000, out_dir=str(tmp_path), quiet=True)
+    assert len(out) == 2
+    for (res, scheme), (fmt, mode, _, nw) in zip(out, pops):
+        json.dumps(res)
+        hist = res["rank_histogram"]
+        assert sum(hist.values()) == nw
+        assert res["lowest_rank"] == min(hist) and res["walkers_at_lowest"] == hist[res["lowest_rank"]]
+        assert res["best_scheme_verified_host"] and res["device_check_failures"] == 0
+        f2, s2 = read_scheme(res["file"])
+        assert f2 == fmt and np.array_equal(s2, scheme) and s2.shape[0] == res["lowest_rank"]
+        assert oracle.brent_valid(fmt, s2, mode)
+        if mode == tfg.TFG_MODE_ZT:
+            assert res["additive_complexity"] == oracle.additive_complexity(fmt, s2)

@@ -312,3 +312,31 @@ def test_verify_all_flags_exactly_the_corrupted_walkers(which):
     W.restore(blob.tobytes())
     assert W.verify_all() == len(bad)
     W.close()
+
+
+@pytest.mark.parametrize("graph", [0, 1, 2])
+def test_empty_populations_and_zero_steps(graph):
+    """Populations of zero walkers are carried through every call: walks skip
+    them (also inside a captured graph), statistics and checks ignore them,
+    collecting their best scheme is an error; zero-step walks change nothing."""
+    fmt = (2, 2, 2)
+    p = tfg.tfg_default_params(plateau_len=100, use_graph=graph)
+    W = tfg.Walkers([((3, 3, 3), 0, naive_start(3, 3, 3), 0), (fmt, 0, naive_start(*fmt), 100)], seed=5, params=p)
+    before = W.checkpoint()
+    W.walk(0).sync()
+    assert W.checkpoint() == before
+    W.walk(500).sync()
+    assert W.verify_all() == 0
+    with pytest.raises(tfg.TfgError) as e:
+        W.collect_best(0)
+    assert e.value.code == tfg.TFG_EINVAL
+    scheme, rank, walker = W.collect_best(1)
+    assert tfg.tfg_verify(fmt, scheme) and rank == scheme.shape[0]
+    info, slots, best = W.read_walkers(W.pop[1]["first"], 100)
+    ref = oracle.Walkers(fmt, naive_start(*fmt), np.arange(100), seed=5, plateau_len=100).walk(500, THREADS)
+    assert_parity(info, slots, best, ref, range(100), f"empty+222 graph={graph}")
+    W.close()
+    E = tfg.Walkers([((3, 3, 3), 0, naive_start(3, 3, 3), 0)], seed=5, params=p)
+    E.walk(10).sync()
+    assert E.verify_all() == 0
+    E.close()
