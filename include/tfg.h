@@ -105,6 +105,23 @@ int tfg_verify(const tfg_format *fmt, int32_t rank, const int8_t *scheme);
 /* Section 4.5: naive additive complexity nnz(U)+nnz(V)+nnz(W) - 2r - m*p. */
 int tfg_additive_complexity(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int64_t *out);
 
+/* Isotropy invariants of a scheme (section "Isotropy Invariants and Novelty
+ * Verification"): for every term the ranks of its factors read as matrices
+ * U_i (m x n, entry (i,k) = u[i*n+k]), V_i (n x p) and W_i (p x m, the C^T
+ * order), over Q for TFG_MODE_ZT and over GF(2) for TFG_MODE_Z2; from them
+ *   type_poly[a][b][c] = number of terms with ranks (a, b, c): the coefficients
+ *                        of the type polynomial sum_i X^a Y^b Z^c;
+ *   sym_poly[a][b][c]  = the type polynomial summed over the six permutations
+ *                        of its variables (the symmetric invariant);
+ *   rank_sums[3]       = sum_i rank U_i, sum_i rank V_i, sum_i rank W_i (the
+ *                        exponents of the rank-sum polynomial).
+ * type_poly and sym_poly are caller arrays of 9*9*9 int64, row-major [a][b][c]
+ * (a factor of at most 64 entries has rank at most 8); term_ranks is [rank][3]
+ * int32.  Any output pointer may be NULL.  TFG_EINVAL for a bad format, rank
+ * or coefficient; the scheme is not required to satisfy Eq. (1). */
+int tfg_isotropy_invariants(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int32_t *term_ranks,
+                            int64_t *type_poly, int64_t *sym_poly, int64_t *rank_sums);
+
 /* Section 3.6: per term, make the first non-zero of u and of v equal +1, w
  * absorbing the signs (in place; Z_T only, Z_2 unchanged). */
 int tfg_canonicalize(const tfg_format *fmt, int32_t rank, int8_t *scheme);

@@ -193,6 +193,33 @@ int tfg_additive_complexity(const tfg_format *fmt, int32_t rank, const int8_t *s
     return TFG_OK;
 }
 
+int tfg_isotropy_invariants(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int32_t *term_ranks,
+                            int64_t *type_poly, int64_t *sym_poly, int64_t *rank_sums) {
+    if (!tfg::host::format_ok(fmt)) { set_error("bad format"); return TFG_EINVAL; }
+    std::vector<HTerm> t;
+    int rc = tfg::host::parse(*fmt, rank, scheme, t);
+    if (rc) return rc;
+    constexpr int D = 9;
+    if (type_poly) std::memset(type_poly, 0, sizeof(int64_t) * D * D * D);
+    if (sym_poly) std::memset(sym_poly, 0, sizeof(int64_t) * D * D * D);
+    int64_t sums[3] = {0, 0, 0};
+    static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    for (size_t l = 0; l < t.size(); ++l) {
+        int rk[3];
+        for (int x = 0; x < 3; ++x) {
+            rk[x] = tfg::host::factor_rank(*fmt, t[l], x);
+            sums[x] += rk[x];
+            if (term_ranks) term_ranks[l * 3 + x] = rk[x];
+        }
+        if (type_poly) type_poly[(rk[0] * D + rk[1]) * D + rk[2]] += 1;
+        if (sym_poly)
+            for (const auto &pm : perms) sym_poly[(rk[pm[0]] * D + rk[pm[1]]) * D + rk[pm[2]]] += 1;
+    }
+    if (rank_sums)
+        for (int x = 0; x < 3; ++x) rank_sums[x] = sums[x];
+    return TFG_OK;
+}
+
 int tfg_canonicalize(const tfg_format *fmt, int32_t rank, int8_t *scheme) {
     if (!tfg::host::format_ok(fmt)) { set_error("bad format"); return TFG_EINVAL; }
     std::vector<HTerm> t;

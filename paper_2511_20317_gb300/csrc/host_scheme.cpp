@@ -455,5 +455,57 @@ int swap_sizes(const tfg_format *f, int r, const int8_t *rows, int perm, tfg_for
     return finish(d, of, out, cap, orank);
 }
 
+// ---- isotropy invariants: matrix ranks of the factors
+// Over Q: fraction-free (Bareiss) elimination on integers; every intermediate
+// is a minor of the matrix, at most 8^4 in size for an 8 x 8 matrix of
+// entries in {-1, 0, 1}.  Over GF(2): elimination on row bit masks.
+int factor_rank(const tfg_format &f, const HTerm &h, int x) {
+    const int rows = x == 0 ? f.m : (x == 1 ? f.n : f.p);
+    const int cols = x == 0 ? f.n : (x == 1 ? f.p : f.m);
+    if (f.mode == TFG_MODE_Z2) {
+        std::vector<uint64_t> r((size_t)rows, 0);
+        for (int a = 0; a < rows; ++a)
+            for (int b = 0; b < cols; ++b)
+                if ((h.p[x] >> (a * cols + b)) & 1) r[(size_t)a] |= 1ull << b;
+        int rank = 0;
+        for (int c = 0; c < cols && rank < rows; ++c) {
+            int piv = -1;
+            for (int a = rank; a < rows; ++a)
+                if ((r[(size_t)a] >> c) & 1) { piv = a; break; }
+            if (piv < 0) continue;
+            std::swap(r[(size_t)rank], r[(size_t)piv]);
+            for (int a = 0; a < rows; ++a)
+                if (a != rank && ((r[(size_t)a] >> c) & 1)) r[(size_t)a] ^= r[(size_t)rank];
+            ++rank;
+        }
+        return rank;
+    }
+    std::vector<int64_t> M((size_t)rows * cols, 0);
+    for (int a = 0; a < rows; ++a)
+        for (int b = 0; b < cols; ++b) {
+            const int e = a * cols + b;
+            M[(size_t)a * cols + b] = (int64_t)((h.p[x] >> e) & 1) - (int64_t)((h.n[x] >> e) & 1);
+        }
+    int rank = 0;
+    int64_t prev = 1;
+    for (int c = 0; c < cols && rank < rows; ++c) {
+        int piv = -1;
+        for (int a = rank; a < rows; ++a)
+            if (M[(size_t)a * cols + c] != 0) { piv = a; break; }
+        if (piv < 0) continue;
+        if (piv != rank)
+            for (int b = 0; b < cols; ++b) std::swap(M[(size_t)piv * cols + b], M[(size_t)rank * cols + b]);
+        const int64_t pv = M[(size_t)rank * cols + c];
+        for (int a = rank + 1; a < rows; ++a) {
+            const int64_t f0 = M[(size_t)a * cols + c];
+            for (int b = 0; b < cols; ++b)
+                M[(size_t)a * cols + b] = (pv * M[(size_t)a * cols + b] - f0 * M[(size_t)rank * cols + b]) / prev;
+        }
+        prev = pv;
+        ++rank;
+    }
+    return rank;
+}
+
 }  // namespace host
 }  // namespace tfg

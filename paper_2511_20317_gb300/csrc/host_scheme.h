@@ -39,5 +39,9 @@ int product(const tfg_format *fa, int ra, const int8_t *sa, const tfg_format *fb
 int swap_sizes(const tfg_format *f, int r, const int8_t *rows, int perm, tfg_format *of, int8_t *out, int cap,
                int *orank);
 
+// Rank of factor x of a term read as a matrix (u: m x n, v: n x p, w: p x m),
+// over Q (Z_T) or GF(2) (Z_2).
+int factor_rank(const tfg_format &f, const HTerm &h, int x);
+
 }  // namespace host
 }  // namespace tfg

@@ -6,8 +6,9 @@ flip-graph walks found.
 
 For every population it prints one JSON line with the lowest rank reached, the
 histogram of the walkers' best ranks, the number of walkers at the lowest
-rank, and the best scheme's rank and naive additive complexity after an
-independent host check of Eq. (1); `--out DIR` also writes each best scheme
+rank, and the best scheme's rank, naive additive complexity and isotropy
+invariants (type polynomial, rank sums) after an independent host check of
+Eq. (1); `--out DIR` also writes each best scheme
 as text (the format `workloads.read_scheme` reads).
 
 `--lift-333-steps N` first searches (3,3,3) over Z_T for N steps and builds
@@ -62,6 +63,15 @@ def write_scheme(path: str, fmt, scheme: np.ndarray, note: str = ""):
                 fh.write(" ".join(str(int(x)) for x in row) + "\n")
 
 
+def invariants(fmt, scheme, mode):
+    """Type polynomial (as {"a b c": coefficient} for X^a Y^b Z^c) and rank sums
+    of a scheme's factor matrices."""
+    _, typ, _, sums = tfg.tfg_isotropy_invariants(fmt, scheme, mode)
+    terms = tfg.polynomial_terms(typ)
+    return {"type_polynomial": {f"{a} {b} {c}": v for (a, b, c), v in sorted(terms.items(), reverse=True)},
+            "rank_sums": [int(x) for x in sums]}
+
+
 def run(pops, steps: int, chunk: int, seed: int, plateau: int, out_dir: str | None = None, label: str = "",
         quiet: bool = False):
     import torch
@@ -96,6 +106,7 @@ def run(pops, steps: int, chunk: int, seed: int, plateau: int, out_dir: str | No
             "rank_histogram": {int(k): int(v) for k, v in enumerate(hist) if v},
             "best_scheme_verified_host": bool(ok),
             "additive_complexity": int(tfg.tfg_additive_complexity(fmt, scheme)) if mode == tfg.TFG_MODE_ZT else None,
+            "isotropy_invariants": invariants(fmt, scheme, mode),
             "accepted": int(st["accepted"]), "reductions": int(st["reductions"]), "plus": int(st["plus"]),
             "device_check_failures": int(fails), "seconds": round(secs, 2),
             "steps_per_s": nw * steps / secs,

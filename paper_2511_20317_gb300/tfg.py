@@ -63,7 +63,8 @@ WALKER_INFO_DTYPE = np.dtype([("r", np.int32), ("best_r", np.int32), ("r_max", n
                               ("reductions", np.int64), ("walker_id", np.uint32), ("pad", np.uint32)])
 
 # every symbol include/tfg.h declares
-EXPORTED = ["tfg_default_params", "tfg_last_error", "tfg_verify", "tfg_additive_complexity", "tfg_canonicalize",
+EXPORTED = ["tfg_default_params", "tfg_last_error", "tfg_verify", "tfg_additive_complexity", "tfg_isotropy_invariants",
+            "tfg_canonicalize",
             "tfg_prepare", "tfg_project", "tfg_extend", "tfg_merge", "tfg_double", "tfg_product",
             "tfg_swap_sizes", "tfg_workspace_size", "tfg_init", "tfg_walk", "tfg_sync", "tfg_collect_best",
             "tfg_verify_all_async", "tfg_stats_get", "tfg_read_walkers", "tfg_population", "tfg_checkpoint",
@@ -91,6 +92,7 @@ def lib() -> ctypes.CDLL:
                 "tfg_last_error": (ctypes.c_char_p, []),
                 "tfg_verify": (i32, [F, i32, P]),
                 "tfg_additive_complexity": (i32, [F, i32, P, ctypes.POINTER(ctypes.c_int64)]),
+                "tfg_isotropy_invariants": (i32, [F, i32, P, P, P, P, P]),
                 "tfg_canonicalize": (i32, [F, i32, P]),
                 "tfg_prepare": (i32, [F, i32, P, P, i32, ctypes.POINTER(ctypes.c_int32)]),
                 "tfg_project": (i32, [F, i32, P, i32, i32, F, P, i32, ctypes.POINTER(ctypes.c_int32)]),
@@ -185,6 +187,24 @@ def tfg_additive_complexity(fmt, scheme) -> int:
     out = ctypes.c_int64()
     _check(lib().tfg_additive_complexity(ctypes.byref(_fmt(fmt)), s.shape[0], _ptr(s), ctypes.byref(out)))
     return out.value
+
+
+def tfg_isotropy_invariants(fmt, scheme, mode=TFG_MODE_ZT):
+    """(term ranks int32 [r, 3], type polynomial int64 [9, 9, 9], symmetric
+    polynomial int64 [9, 9, 9], rank sums int64 [3])."""
+    s = _rows(fmt, scheme)
+    tr = np.zeros((s.shape[0], 3), dtype=np.int32)
+    typ = np.zeros((9, 9, 9), dtype=np.int64)
+    sym = np.zeros((9, 9, 9), dtype=np.int64)
+    sums = np.zeros(3, dtype=np.int64)
+    _check(lib().tfg_isotropy_invariants(ctypes.byref(_fmt(fmt, mode)), s.shape[0], _ptr(s), _ptr(tr), _ptr(typ),
+                                         _ptr(sym), _ptr(sums)))
+    return tr, typ, sym, sums
+
+
+def polynomial_terms(coeffs) -> dict:
+    """{(a, b, c): coefficient} of the non-zero entries of a [9, 9, 9] table."""
+    return {tuple(int(v) for v in idx): int(coeffs[idx]) for idx in zip(*np.nonzero(coeffs))}
 
 
 def tfg_canonicalize(fmt, scheme, mode=TFG_MODE_ZT) -> np.ndarray:

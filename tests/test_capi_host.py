@@ -184,3 +184,39 @@ def test_lifted_6_7_9_start_from_a_walked_333_scheme():
     fmt, s = starts.start_6_7_9(s333)
     assert fmt == (6, 7, 9) and s.shape[0] == 11 * s333.shape[0] + 54
     assert oracle.brent_valid(fmt, s)
+
+
+def _poly_dict(t):
+    return {tuple(int(v) for v in idx): int(t[idx]) for idx in zip(*np.nonzero(t))}
+
+
+def test_isotropy_invariants_match_oracle():
+    """tfg_isotropy_invariants against the oracle's definitions: term ranks, type
+    and symmetric polynomials, rank sums, over Q (Z_T) and GF(2) (Z_2)."""
+    from oracle import invariants as inv
+    from paper_2511_20317_gb300 import starts
+    cases = [gold("strassen_2x2x2_r7.txt"), gold("paper_2x2x3_r11.txt"), ((3, 4, 5), naive_start(3, 4, 5)),
+             starts.start_4_5_12()]
+    for fmt in [(2, 3, 4), (3, 3, 3), (4, 4, 4)]:
+        W = oracle.Walkers(fmt, naive_start(*fmt), np.arange(3), seed=12, plateau_len=400).walk(4000)
+        cases += [(fmt, W.best_scheme(w)) for w in range(3)]
+    for fmt, s in cases:
+        tr, typ, sym, sums = tfg.tfg_isotropy_invariants(fmt, s)
+        otr, otyp, osym, osums = inv.isotropy_invariants(fmt, s)
+        assert [tuple(t) for t in tr.tolist()] == otr
+        assert _poly_dict(typ) == otyp and _poly_dict(sym) == osym and tuple(sums.tolist()) == osums
+    for fmt in [(2, 2, 2), (3, 3, 3)]:
+        W = oracle.Walkers(fmt, naive_start(*fmt), np.arange(3), seed=5, mode=oracle.MODE_Z2, plateau_len=300).walk(3000)
+        for w in range(3):
+            s = W.best_scheme(w)
+            tr, typ, sym, sums = tfg.tfg_isotropy_invariants(fmt, s, mode=tfg.TFG_MODE_Z2)
+            otr, otyp, osym, osums = inv.isotropy_invariants(fmt, s, mode=inv.MODE_Z2)
+            assert [tuple(t) for t in tr.tolist()] == otr and _poly_dict(typ) == otyp and tuple(sums.tolist()) == osums
+    # full-rank 8 x 8 factors: (8,8,1) naive terms and a dense +-1 test matrix row
+    fmt = (8, 8, 1)
+    s = naive_start(*fmt)
+    rng = np.random.default_rng(3)
+    dense = s[:1].copy()
+    dense[0, :64] = rng.choice([-1, 1], size=64)
+    tr, _, _, _ = tfg.tfg_isotropy_invariants(fmt, dense)
+    assert tuple(tr[0]) == inv.term_ranks(fmt, dense)[0]

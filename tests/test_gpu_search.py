@@ -39,3 +39,8 @@ def test_search_reports_and_files(tmp_path):
         assert oracle.brent_valid(fmt, s2, mode)
         if mode == tfg.TFG_MODE_ZT:
             assert res["additive_complexity"] == oracle.additive_complexity(fmt, s2)
+        from oracle import invariants as inv
+        _, typ, _, sums = inv.isotropy_invariants(fmt, s2, mode)
+        assert res["isotropy_invariants"]["type_polynomial"] == {f"{a} {b} {c}": v for (a, b, c), v in
+                                                                  sorted(typ.items(), reverse=True)}
+        assert res["isotropy_invariants"]["rank_sums"] == list(sums)
