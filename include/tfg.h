@@ -70,7 +70,16 @@ typedef struct {
     int32_t use_graph;        /* tfg_walk launches one captured CUDA graph of all populations' kernels:
                                  1 chained (default), 2 forked onto one stream per population
                                  (concurrent); 0 plain launches on the context stream */
-    int32_t reserved[4];
+    int32_t walk_policy;      /* expansions (Section 3.3.1, Algorithm 1):
+                                 0 (default): a plus transition after plateau_len steps without a
+                                   new best rank, when r <= best + 2;
+                                 1: Algorithm 1 -- a failed try_flip (no candidate, or the flip
+                                   leaves Z_T) expands and ends the step; after a flip, expand
+                                   when draw x3 < expand_thresh and r <= best + 2.  An expansion
+                                   is plus or split with probability 1/2 each.
+                                 Both need a free slot (r < r_max); window mode needs policy 0 */
+    uint32_t expand_thresh;   /* policy 1: floor(p_expand * 2^32) */
+    int32_t reserved[2];
 } tfg_params;
 
 /* Per-walker record.  t is the number of steps taken, digest a rolling hash of

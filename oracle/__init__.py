@@ -52,7 +52,9 @@ class Params(ctypes.Structure):
                 ("refresh_thresh", ctypes.c_uint32),
                 ("plus_attempts", ctypes.c_int32),
                 ("plus_enabled", ctypes.c_int32),
-                ("debug_checks", ctypes.c_int32)]
+                ("debug_checks", ctypes.c_int32),
+                ("policy", ctypes.c_int32),          # 0: plateau plus, 1: Algorithm 1 expansions
+                ("expand_thresh", ctypes.c_uint32)]  # policy 1: p_expand * 2^32
 
 
 INFO_DTYPE = np.dtype([("r", np.int32), ("best_r", np.int32), ("r_max", np.int32), ("pad", np.int32),
@@ -192,7 +194,8 @@ class Walkers:
 
     def __init__(self, fmt, start, walker_ids, seed, *, mode=MODE_ZT, r_slack=3,
                  plateau_len=10_000, refresh_thresh=REFRESH_THRESH_DEFAULT,
-                 plus_attempts=16, plus_enabled=True, debug_checks=False, prepared=False):
+                 plus_attempts=16, plus_enabled=True, debug_checks=False, prepared=False,
+                 policy=0, expand_thresh=0):
         self.fmt = tuple(int(x) for x in fmt)
         self.mode = int(mode)
         self.LT = term_len(self.fmt)
@@ -204,7 +207,7 @@ class Walkers:
         self.walker_ids = np.ascontiguousarray(walker_ids, dtype=np.uint32)
         nw = self.walker_ids.size
         self.params = Params(int(plateau_len), int(refresh_thresh), int(plus_attempts),
-                             int(bool(plus_enabled)), int(bool(debug_checks)))
+                             int(bool(plus_enabled)), int(bool(debug_checks)), int(policy), int(expand_thresh))
         self.slots = np.zeros((nw, self.r_max, self.LT), dtype=np.int8)
         self.best = np.zeros((nw, self.r_max, self.LT), dtype=np.int8)
         self.info = np.zeros(nw, dtype=INFO_DTYPE)

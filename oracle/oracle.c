@@ -208,6 +208,9 @@ typedef struct {
     int32_t plus_attempts;   /* Philox sub-streams 1..plus_attempts */
     int32_t plus_enabled;
     int32_t debug_checks;    /* re-verify the invariants after every step */
+    int32_t policy;          /* 0: plus transition on a plateau; 1: Algorithm 1 (expand when try_flip
+                                fails, and after a flip with probability p_expand) */
+    uint32_t expand_thresh;  /* policy 1: expand after a flip when x3 < floor(p_expand * 2^32) */
 } orc_params;
 
 typedef struct {
@@ -438,14 +441,19 @@ static void debug_check(walker *wk)
         wk->info->debug_failures += 1;
 }
 
-/* Plus transition (Section 3.3.1) on a plateau: roles (A,B,C) are a
- * permutation of (u,v,w); the pair (i, j) becomes three terms
- *   A_i (x) (B_i + B_j) (x) C_i  +  A_i (x) B_j (x) (C_j - C_i)  +  (A_j - A_i) (x) B_j (x) C_j.
- * Each of the three new factors must be non-zero and stay in the coefficient
- * set.  Returns the attempt index (1-based) that succeeded, or 0. */
+/* Expansions (Section 3.3.1).  Roles (A,B,C) are a permutation of (u,v,w).
+ * Plus: the pair (i, j) becomes three terms
+ *   A_i (x) (B_i + B_j) (x) C_i  +  A_i (x) B_j (x) (C_j - C_i)  +  (A_j - A_i) (x) B_j (x) C_j;
+ * each of the three new factors must be non-zero and stay in the coefficient set.
+ * Split (policy 1 only): term i becomes A_j (x) B_i (x) C_i and the new term
+ *   (A_i - A_j) (x) B_i (x) C_i  is appended (term j unchanged); A_i - A_j must be
+ * non-zero (A_i != A_j) and stay in the coefficient set.
+ * Attempt a = 1..plus_attempts draws Philox sub-stream a: i from y0, j != i from
+ * y1, the role permutation from y2, and (policy 1) split when y3 >= 2^31, else
+ * plus.  The new term goes to slot r.  Returns the attempt that succeeded, or 0. */
 static const int PERM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 
-static int try_plus(walker *wk, uint64_t t, int *pi_out, int *pj_out, int *perm_out)
+static int try_expand(walker *wk, uint64_t t, int *pi_out, int *pj_out, int *perm_out, int *split_out)
 {
     const orc_fmt *f = wk->f;
     int r = wk->info->r;
@@ -456,31 +464,71 @@ static int try_plus(walker *wk, uint64_t t, int *pi_out, int *pj_out, int *perm_
         int i = (int)mulhi_range(y[0], (uint32_t)r);
         int j = (int)((i + 1 + (int)mulhi_range(y[1], (uint32_t)(r - 1))) % r);
         int pi = (int)mulhi_range(y[2], 6u);
+        int split = (wk->prm->policy == 1) && (y[3] >= 0x80000000u);
         int A = PERM[pi][0], B = PERM[pi][1], C = PERM[pi][2];
-        int8_t nb[64], nc[64], na[64];
-        int ok = vec_add(nb, factor(f, wk->slots, i, B), factor(f, wk->slots, j, B), +1, f->len[B], f->mode);
-        ok &= vec_add(nc, factor(f, wk->slots, j, C), factor(f, wk->slots, i, C), -1, f->len[C], f->mode);
-        ok &= vec_add(na, factor(f, wk->slots, j, A), factor(f, wk->slots, i, A), -1, f->len[A], f->mode);
-        if (!ok || vec_is_zero(nb, f->len[B]) || vec_is_zero(nc, f->len[C]) || vec_is_zero(na, f->len[A]))
-            continue;
         int nt = r;
-        /* new term r: (A_j - A_i, B_j, C_j) */
-        memcpy(factor(f, wk->slots, nt, A), na, (size_t)f->len[A]);
-        memcpy(factor(f, wk->slots, nt, B), factor(f, wk->slots, j, B), (size_t)f->len[B]);
-        memcpy(factor(f, wk->slots, nt, C), factor(f, wk->slots, j, C), (size_t)f->len[C]);
-        /* term j: (A_i, B_j, C_j - C_i) */
-        memcpy(factor(f, wk->slots, j, A), factor(f, wk->slots, i, A), (size_t)f->len[A]);
-        memcpy(factor(f, wk->slots, j, C), nc, (size_t)f->len[C]);
-        /* term i: (A_i, B_i + B_j, C_i) */
-        memcpy(factor(f, wk->slots, i, B), nb, (size_t)f->len[B]);
-        wk->info->r = r + 1;
-        canonicalize_term(f, wk->slots, i);
-        canonicalize_term(f, wk->slots, j);
-        canonicalize_term(f, wk->slots, nt);
-        *pi_out = i; *pj_out = j; *perm_out = pi;
+        if (split) {
+            int8_t na[64];
+            if (!vec_add(na, factor(f, wk->slots, i, A), factor(f, wk->slots, j, A), -1, f->len[A], f->mode) ||
+                vec_is_zero(na, f->len[A]))
+                continue;
+            /* new term r: (A_i - A_j, B_i, C_i) */
+            memcpy(factor(f, wk->slots, nt, A), na, (size_t)f->len[A]);
+            memcpy(factor(f, wk->slots, nt, B), factor(f, wk->slots, i, B), (size_t)f->len[B]);
+            memcpy(factor(f, wk->slots, nt, C), factor(f, wk->slots, i, C), (size_t)f->len[C]);
+            /* term i: (A_j, B_i, C_i) */
+            memcpy(factor(f, wk->slots, i, A), factor(f, wk->slots, j, A), (size_t)f->len[A]);
+            wk->info->r = r + 1;
+            canonicalize_term(f, wk->slots, i);
+            canonicalize_term(f, wk->slots, nt);
+        } else {
+            int8_t nb[64], nc[64], na[64];
+            int ok = vec_add(nb, factor(f, wk->slots, i, B), factor(f, wk->slots, j, B), +1, f->len[B], f->mode);
+            ok &= vec_add(nc, factor(f, wk->slots, j, C), factor(f, wk->slots, i, C), -1, f->len[C], f->mode);
+            ok &= vec_add(na, factor(f, wk->slots, j, A), factor(f, wk->slots, i, A), -1, f->len[A], f->mode);
+            if (!ok || vec_is_zero(nb, f->len[B]) || vec_is_zero(nc, f->len[C]) || vec_is_zero(na, f->len[A]))
+                continue;
+            /* new term r: (A_j - A_i, B_j, C_j) */
+            memcpy(factor(f, wk->slots, nt, A), na, (size_t)f->len[A]);
+            memcpy(factor(f, wk->slots, nt, B), factor(f, wk->slots, j, B), (size_t)f->len[B]);
+            memcpy(factor(f, wk->slots, nt, C), factor(f, wk->slots, j, C), (size_t)f->len[C]);
+            /* term j: (A_i, B_j, C_j - C_i) */
+            memcpy(factor(f, wk->slots, j, A), factor(f, wk->slots, i, A), (size_t)f->len[A]);
+            memcpy(factor(f, wk->slots, j, C), nc, (size_t)f->len[C]);
+            /* term i: (A_i, B_i + B_j, C_i) */
+            memcpy(factor(f, wk->slots, i, B), nb, (size_t)f->len[B]);
+            wk->info->r = r + 1;
+            canonicalize_term(f, wk->slots, i);
+            canonicalize_term(f, wk->slots, j);
+            canonicalize_term(f, wk->slots, nt);
+        }
+        *pi_out = i; *pj_out = j; *perm_out = pi; *split_out = split;
         return a;
     }
     return 0;
+}
+
+/* An expansion followed by the reduction cascade over the changed terms, and
+ * its digest record; a successful one restarts the plateau.  Returns whether
+ * an attempt succeeded. */
+static int expand_step(walker *wk, uint64_t t)
+{
+    orc_info *in = wk->info;
+    int pi = 0, pj = 0, perm = 0, split = 0;
+    int a = try_expand(wk, t, &pi, &pj, &perm, &split);
+    if (a == 0) return 0;
+    in->plus += 1;
+    in->plateau = 0;
+    queue_t q; q.len = 0;
+    q_push(&q, pi);
+    if (!split) q_push(&q, pj);
+    q_push(&q, in->r - 1);
+    reduction_cascade(wk, &q);
+    uint64_t rec2 = 0xFull | ((uint64_t)a << 4) | ((uint64_t)perm << 9) |
+                    ((uint64_t)(uint32_t)pi << 12) | ((uint64_t)(uint32_t)pj << 28) |
+                    ((uint64_t)(uint32_t)in->r << 44) | ((uint64_t)split << 62);
+    in->digest = digest_mix(in->digest, rec2);
+    return 1;
 }
 
 /* Flip (Section 3.3.1) of candidate c on sampled term i, followed by the
@@ -538,8 +586,13 @@ int orc_apply_flip(int m, int n, int p, int mode, int r, int8_t *scheme, int i,
 
 /* Rest of a step after the flip: rank-reduction count, digest record, best
  * scheme (strictly better always, equal rank when x2 < 0.01 * 2^32), plateau,
- * and the plus transition when the plateau is long and the rank is close to
- * the best (Algorithm 1's expand guard r <= best + 2). */
+ * and the expansion:
+ *   policy 0: a plus transition when the plateau is long and the rank is close
+ *             to the best (Algorithm 1's expand guard r <= best + 2);
+ *   policy 1: Algorithm 1 -- a failed try_flip (no candidate, or rejected)
+ *             expands and ends the iteration; after a flip, expand when
+ *             x3 < p_expand * 2^32 and r <= best + 2.
+ * Every expansion needs a free slot (r < r_max). */
 static void finish_step(walker *wk, const uint32_t *x, int r_before, int action, int X, int rho, int s, int i,
                         int j)
 {
@@ -552,6 +605,14 @@ static void finish_step(walker *wk, const uint32_t *x, int r_before, int action,
                    ((uint64_t)(uint32_t)j << 24) | ((uint64_t)(uint32_t)in->r << 40);
     in->digest = digest_mix(in->digest, rec);
 
+    if (wk->prm->policy == 1 && action != ORC_ACCEPT) {
+        in->plateau += 1;
+        if (in->r < in->r_max) expand_step(wk, t);
+        in->t += 1;
+        if (wk->prm->debug_checks) debug_check(wk);
+        return;
+    }
+
     if (in->r < in->best_r) {
         take_best(wk);
         in->best_r = in->r;
@@ -562,29 +623,17 @@ static void finish_step(walker *wk, const uint32_t *x, int r_before, int action,
         in->plateau += 1;
     }
 
-    if (wk->prm->plus_enabled && in->plateau >= wk->prm->plateau_len &&
-        in->r <= in->best_r + 2 && in->r < in->r_max) {
-        int pi = 0, pj = 0, perm = 0;
-        int a = try_plus(wk, t, &pi, &pj, &perm);
-        if (a > 0) {
-            in->plus += 1;
-            in->plateau = 0;
-            queue_t q; q.len = 0;
-            q_push(&q, pi);
-            q_push(&q, pj);
-            q_push(&q, in->r - 1);
-            reduction_cascade(wk, &q);
-            uint64_t rec2 = 0xFull | ((uint64_t)a << 4) | ((uint64_t)perm << 9) |
-                            ((uint64_t)(uint32_t)pi << 12) | ((uint64_t)(uint32_t)pj << 28) |
-                            ((uint64_t)(uint32_t)in->r << 44);
-            in->digest = digest_mix(in->digest, rec2);
-        }
+    if (wk->prm->policy == 1) {
+        if (x[3] < wk->prm->expand_thresh && in->r <= in->best_r + 2 && in->r < in->r_max) expand_step(wk, t);
+    } else if (wk->prm->plus_enabled && in->plateau >= wk->prm->plateau_len &&
+               in->r <= in->best_r + 2 && in->r < in->r_max) {
+        expand_step(wk, t);
     }
     in->t += 1;
     if (wk->prm->debug_checks) debug_check(wk);
 }
 
-/* One step of the walk (Algorithm 1 with the plateau-triggered plus policy). */
+/* One step of the walk (Algorithm 1, with the plateau or the p_expand expansion policy). */
 static void walk_step(walker *wk, cand_t *cbuf)
 {
     orc_info *in = wk->info;

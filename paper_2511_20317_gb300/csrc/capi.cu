@@ -154,6 +154,8 @@ struct tfg_ctx {
         d.refresh_thresh = prm.refresh_thresh;
         d.plus_attempts = prm.plus_attempts;
         d.plus_enabled = prm.plus_enabled;
+        d.walk_policy = prm.walk_policy;
+        d.expand_thresh = prm.expand_thresh;
         return d;
     }
     Aux *aux() const { return reinterpret_cast<Aux *>(ws); }
@@ -277,6 +279,10 @@ static int check_params(const tfg_params &p) {
     }
     if (p.use_graph < 0 || p.use_graph > 2) {
         set_error("use_graph must be 0 (plain launches), 1 (chained graph) or 2 (forked graph)");
+        return TFG_EINVAL;
+    }
+    if (p.walk_policy != 0 && p.walk_policy != 1) {
+        set_error("walk_policy must be 0 (plateau plus transitions) or 1 (Algorithm 1 expansions)");
         return TFG_EINVAL;
     }
     if (p.mapping != 0 && p.mapping != 1 && p.mapping != 4 && p.mapping != 8 && p.mapping != 16 && p.mapping != 32) {
@@ -836,6 +842,7 @@ int tfg_walk_window(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_m
     tfg_window_scratch_bytes(ctx, &need);
     if (scratch_bytes < need) { set_error("window scratch too small"); return TFG_ENOMEM; }
     if ((uintptr_t)d_scratch % 16) { set_error("scratch must be 16-byte aligned"); return TFG_EINVAL; }
+    if (ctx->prm.walk_policy != 0) { set_error("window mode needs walk_policy 0"); return TFG_EINVAL; }
     for (const Segment &s : ctx->segs) {
         if (s.fmt.mode != TFG_MODE_ZT || s.tw != 1 || s.R > 128 ||
             tfg::window_apply_capacity(s.word_bits, s.R) == 0) {
@@ -930,6 +937,7 @@ extern "C" int tfg_walk_window_noalloc(tfg_ctx *ctx, int64_t steps, int32_t poli
                   " (at most " + std::to_string(kNoAllocScratchBytes / (window_row_bytes() + 4)) + " walkers)");
         return TFG_EINVAL;
     }
+    if (ctx->prm.walk_policy != 0) { set_error("window mode needs walk_policy 0"); return TFG_EINVAL; }
     for (const Segment &s : ctx->segs) {
         if (s.fmt.mode != TFG_MODE_ZT || s.tw != 1 || s.R > 128 ||
             tfg::window_apply_capacity(s.word_bits, s.R) == 0) {

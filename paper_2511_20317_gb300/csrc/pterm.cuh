@@ -46,9 +46,9 @@ __device__ __forceinline__ uint64_t flip_record(int action, int X, int rho, int 
            ((uint64_t)(uint32_t)i << 8) | ((uint64_t)(uint32_t)j << 24) | ((uint64_t)(uint32_t)r << 40);
 }
 
-__device__ __forceinline__ uint64_t plus_record(int attempt, int perm, int i, int j) {
+__device__ __forceinline__ uint64_t plus_record(int attempt, int perm, int i, int j, int split = 0) {
     return 0xFull | ((uint64_t)attempt << 4) | ((uint64_t)perm << 9) | ((uint64_t)(uint32_t)i << 12) |
-           ((uint64_t)(uint32_t)j << 28);
+           ((uint64_t)(uint32_t)j << 28) | ((uint64_t)split << 62);
 }
 
 // Role permutations of a plus transition: (A,B,C) over (u,v,w), index 0..5

@@ -32,7 +32,9 @@ struct SegDesc {
     int32_t plus_enabled;
     int32_t pad;
     int32_t fbase[3];     // bit offset of factor u, v, w in a packed term
-    int32_t pad2;
+    int32_t walk_policy;  // 0: plateau plus transitions; 1: Algorithm 1 expansions
+    uint32_t expand_thresh;
+    int32_t pad3;
 };
 
 // One compiled variant of the walk kernel.

@@ -232,8 +232,9 @@ struct GroupWalker {
         }
     }
 
-    // Plus transition (Section 3.3.1): writes the three new terms and queues
-    // them; returns the digest record (0 when no attempt passed).
+    // Expansion (Section 3.3.1): plus, or split under walk policy 1 when y3 >= 2^31;
+    // writes the new terms and queues them; returns the digest record (0 when no
+    // attempt passed).
     __device__ __forceinline__ uint64_t plus_setup(const SegDesc &d) {
 #pragma unroll 1
         for (int a = 1; a <= d.plus_attempts; ++a) {
@@ -244,6 +245,25 @@ struct GroupWalker {
             int A, B, C;
             plus_roles(perm, A, B, C);
             const T ti = fetch(pi), tj = fetch(pj);
+            if (d.walk_policy == 1 && y.w >= 0x80000000u) {
+                // split: term i = (A_j, B_i, C_i), new term (A_i - A_j, B_i, C_i)
+                T ns;
+                const bool ok = O::add(ti, tj, A, true, mk, ns);
+                if (!ok || O::zero(ns, A, mk)) continue;
+                O::canon(ns, mk);
+                store(ns, r);
+                T ti2 = ti;
+                O::take(ti2, tj, A, mk);
+                O::canon(ti2, mk);
+                store(ti2, pi);
+                r += 1;
+                plateau = 0;
+                c_pls += 1;
+                qlen = 0;
+                q_push(pi);
+                q_push(r - 1);
+                return plus_record(a, perm, pi, pj, 1);
+            }
             T nb, nc, na;
             bool ok = O::add(ti, tj, B, false, mk, nb);      // B_i + B_j
             ok &= O::add(tj, ti, C, true, mk, nc);           // C_j - C_i
@@ -290,7 +310,7 @@ struct GroupWalker {
             }
         }
 
-        uint32_t xr0 = 0, xr1 = 0, xr2 = 0;
+        uint32_t xr0 = 0, xr1 = 0, xr2 = 0, xr3 = 0;
         int kb = G;
 #pragma unroll 1
         for (int32_t step = 0; step < steps; ++step) {
@@ -298,10 +318,10 @@ struct GroupWalker {
             if (kb == G) {
                 const uint64_t tl = (uint64_t)t + (uint64_t)g.lane;
                 const U4 x = philox10((uint32_t)tl, (uint32_t)(tl >> 32), wid, 0u, key0, key1);
-                xr0 = x.x; xr1 = x.y; xr2 = x.z;
+                xr0 = x.x; xr1 = x.y; xr2 = x.z; xr3 = x.w;
                 kb = 0;
             }
-            const uint32_t x0 = g.shfl(xr0, kb), x1 = g.shfl(xr1, kb), x2 = g.shfl(xr2, kb);
+            const uint32_t x0 = g.shfl(xr0, kb), x1 = g.shfl(xr1, kb), x2 = g.shfl(xr2, kb), x3 = g.shfl(xr3, kb);
             kb += 1;
 
             const int r_before = r;
@@ -417,8 +437,12 @@ struct GroupWalker {
                 }
                 if (r < r_before) c_red += 1;
                 dig = digest_mix(dig, flip_record(action, X, rho, sneg, i, j, r));
+                // walk policy 1: a failed try_flip expands and ends the step (no best update)
+                const bool failed = d.walk_policy == 1 && action != kAccept;
                 // best scheme: always when better, with probability 0.01 when equal
-                if (r < best_r) {
+                if (failed) {
+                    plateau += 1;
+                } else if (r < best_r) {
                     snapshot(bestp);
                     best_r = r;
                     best_t = t;
@@ -427,8 +451,14 @@ struct GroupWalker {
                     if (r == best_r && x2 < d.refresh_thresh) snapshot(bestp);
                     plateau += 1;
                 }
-                // plus transition on a plateau, only near the best rank
-                if (d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2) {
+                // expansion: plus on a plateau near the best rank (policy 0), or Algorithm 1's
+                // expand after a failed try_flip / with probability p_expand (policy 1)
+                bool expand;
+                if (d.walk_policy == 1)
+                    expand = failed ? (r < R && r >= 2) : (x3 < d.expand_thresh && r <= best_r + 2 && r < R && r >= 2);
+                else
+                    expand = d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2;
+                if (expand) {
                     rec2 = plus_setup(d);
                     if (rec2) { plus_phase = true; continue; }
                 }

@@ -419,8 +419,10 @@ struct SoloWalker {
         }
     }
 
-    // Plus transition (Section 3.3.1): writes the three new terms and queues
-    // them; returns the digest record (0 when no attempt passed).
+    // Expansion (Section 3.3.1): plus (three terms from the pair) or, under
+    // walk policy 1 when y3 >= 2^31, split (term i = (A_j, B_i, C_i), new term
+    // (A_i - A_j, B_i, C_i)); writes the new terms, queues them for the cascade
+    // and returns the digest record (0 when no attempt passed).
     __device__ __forceinline__ uint64_t plus_setup(const SegDesc &d) {
 #pragma unroll 1
         for (int a = 1; a <= d.plus_attempts; ++a) {
@@ -428,9 +430,28 @@ struct SoloWalker {
             const int pi = (int)__umulhi(y.x, (uint32_t)r);
             const int pj = (pi + 1 + (int)__umulhi(y.y, (uint32_t)(r - 1))) % r;
             const int perm = (int)__umulhi(y.z, 6u);
+            const bool split = d.walk_policy == 1 && y.w >= 0x80000000u;
             int A, B, C;
             plus_roles(perm, A, B, C);
             const T ti = ld(pi), tj = ld(pj);
+            if (split) {
+                T na;                                       // (A_i - A_j, B_i, C_i)
+                const bool ok = O::add(ti, tj, A, true, mk, na);
+                if (!ok || O::zero(na, A, mk)) continue;
+                O::canon(na, mk);
+                st(r, na);
+                T ti2 = ti;                                 // (A_j, B_i, C_i)
+                O::take(ti2, tj, A, mk);
+                O::canon(ti2, mk);
+                st(pi, ti2);
+                r += 1;
+                plateau = 0;
+                c_pls += 1;
+                qlen = 0;
+                q_push(pi);
+                q_push(r - 1);
+                return plus_record(a, perm, pi, pj, 1);
+            }
             T nb, nc, na;
             bool ok = O::add(ti, tj, B, false, mk, nb);      // B_i + B_j
             ok &= O::add(tj, ti, C, true, mk, nc);           // C_j - C_i
@@ -538,8 +559,9 @@ struct SoloWalker {
     // ---- rest of a step, warp-converged: reduction filter and cascade, digest,
     // best / plateau bookkeeping and snapshot, plus transition and its cascade.
     __device__ __forceinline__ void finish_step(const SegDesc &d, unsigned wmask, int lane, int nl, Wd *bestp,
-                                                uint32_t x2, int r_before, int action, int X, int rho, int sneg,
-                                                int i, int j, bool need_check, const T &ti2, const T &tj2) {
+                                                uint32_t x2, uint32_t x3, int r_before, int action, int X, int rho,
+                                                int sneg, int i, int j, bool need_check, const T &ti2,
+                                                const T &tj2) {
         if (coop_pair_hit(wmask, lane, nl, need_check, ti2, i, tj2, j)) {
             q_push(i);
             q_push(j);
@@ -551,8 +573,12 @@ struct SoloWalker {
             if (phase == 0) {
                 if (r < r_before) c_red += 1;
                 dig = digest_mix(dig, flip_record(action, X, rho, sneg, i, j, r));
+                // walk policy 1: a failed try_flip expands and ends the step (no best update)
+                const bool failed = d.walk_policy == 1 && action != kAccept;
                 bool want = false;
-                if (r < best_r) {
+                if (failed) {
+                    plateau += 1;
+                } else if (r < best_r) {
                     want = true;
                     best_r = r;
                     best_t = t;
@@ -562,8 +588,12 @@ struct SoloWalker {
                     plateau += 1;
                 }
                 coop_snapshot(wmask, lane, nl, want, bestp);
-                if (d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2)
-                    rec2 = plus_setup(d);
+                bool expand;
+                if (d.walk_policy == 1)
+                    expand = failed ? (r < R && r >= 2) : (x3 < d.expand_thresh && r <= best_r + 2 && r < R && r >= 2);
+                else
+                    expand = d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2;
+                if (expand) rec2 = plus_setup(d);
             } else if (rec2) {
                 dig = digest_mix(dig, rec2 | ((uint64_t)(uint32_t)r << 44));
             }
@@ -629,7 +659,8 @@ struct SoloWalker {
                     c_noc += 1;
                 }
             }
-            finish_step(d, wmask, lane, nl, bestp, x.z, r_before, action, X, rho, sneg, i, j, need_check, ti2, tj2);
+            finish_step(d, wmask, lane, nl, bestp, x.z, x.w, r_before, action, X, rho, sneg, i, j, need_check, ti2,
+                        tj2);
         }
         store(d, w);
     }

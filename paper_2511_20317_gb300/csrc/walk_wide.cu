@@ -372,7 +372,8 @@ struct WideWalker {
         }
     }
 
-    // Plus transition (Section 3.3.1): three new terms, queued for the cascade;
+    // Expansion (Section 3.3.1): plus (three new terms), or split under walk policy 1
+    // when y3 >= 2^31; the changed terms are queued for the cascade;
     // returns the digest record (0 when no attempt passed).
     __device__ __forceinline__ uint64_t plus_setup(const SegDesc &d) {
 #pragma unroll 1
@@ -384,6 +385,26 @@ struct WideWalker {
             int A, B, C;
             plus_roles(perm, A, B, C);
             const DF ti = dget(pi), tj = dget(pj);
+            if (d.walk_policy == 1 && y.w >= 0x80000000u) {
+                // split: term i = (A_j, B_i, C_i), new term (A_i - A_j, B_i, C_i)
+                DF ns;
+                const bool ok = dadd(ti, tj, A, true, ns);
+                const bool z = dzero(ns, A);
+                if (!ok || z) continue;
+                dcanon(ns);
+                dput(r, ns);
+                DF ti2 = ti;
+                dtake(ti2, tj, A);
+                dcanon(ti2);
+                dput(pi, ti2);
+                r += 1;
+                plateau = 0;
+                c_pls += 1;
+                qlen = 0;
+                q_push(pi);
+                q_push(r - 1);
+                return plus_record(a, perm, pi, pj, 1);
+            }
             DF nb, nc, na;
             bool ok = dadd(ti, tj, B, false, nb);   // B_i + B_j
             ok &= dadd(tj, ti, C, true, nc);        // C_j - C_i
@@ -444,7 +465,7 @@ struct WideWalker {
         for (int s = lane; s < 32 * KM; s += 32) SG[s] = s < R ? sig(get(s)) : make_uint4(0u, 0u, 0u, 0u);
         __syncwarp();
 
-        uint32_t xr0 = 0, xr1 = 0, xr2 = 0;
+        uint32_t xr0 = 0, xr1 = 0, xr2 = 0, xr3 = 0;
         int kb = 32;
 #pragma unroll 1
         for (int32_t step = 0; step < steps; ++step) {
@@ -452,11 +473,11 @@ struct WideWalker {
             if (kb == 32) {
                 const uint64_t tl = (uint64_t)t + (uint64_t)lane;
                 const U4 x = philox10((uint32_t)tl, (uint32_t)(tl >> 32), wid, 0u, key0, key1);
-                xr0 = x.x; xr1 = x.y; xr2 = x.z;
+                xr0 = x.x; xr1 = x.y; xr2 = x.z; xr3 = x.w;
                 kb = 0;
             }
             const uint32_t x0 = __shfl_sync(kFull, xr0, kb), x1 = __shfl_sync(kFull, xr1, kb),
-                           x2 = __shfl_sync(kFull, xr2, kb);
+                           x2 = __shfl_sync(kFull, xr2, kb), x3 = __shfl_sync(kFull, xr3, kb);
             kb += 1;
 
             const int r_before = r;
@@ -577,7 +598,12 @@ struct WideWalker {
                 }
                 if (r < r_before) c_red += 1;
                 dig = digest_mix(dig, flip_record(action, X, rho, sneg, i, j, r));
-                if (r < best_r) {
+                // walk policy 1: a failed try_flip expands and ends the step (no best update)
+                const bool failed = d.walk_policy == 1 && action != kAccept;
+                // best scheme: always when better, with probability 0.01 when equal
+                if (failed) {
+                    plateau += 1;
+                } else if (r < best_r) {
                     snapshot(bestp);
                     best_r = r;
                     best_t = t;
@@ -586,7 +612,14 @@ struct WideWalker {
                     if (r == best_r && x2 < d.refresh_thresh) snapshot(bestp);
                     plateau += 1;
                 }
-                if (d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2) {
+                // expansion: plus on a plateau near the best rank (policy 0), or Algorithm 1's
+                // expand after a failed try_flip / with probability p_expand (policy 1)
+                bool expand;
+                if (d.walk_policy == 1)
+                    expand = failed ? (r < R && r >= 2) : (x3 < d.expand_thresh && r <= best_r + 2 && r < R && r >= 2);
+                else
+                    expand = d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2;
+                if (expand) {
                     rec2 = plus_setup(d);
                     if (rec2) { plus_phase = true; continue; }
                 }

@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const
     } else {
         wk.c_noc += 1;
     }
-    wk.finish_step(d, wmask, lane, nl, bestp, x.z, r_before, action, X, rho, sneg, i, j, need_check, ti2, tj2);
+    wk.finish_step(d, wmask, lane, nl, bestp, x.z, x.w, r_before, action, X, rho, sneg, i, j, need_check, ti2, tj2);
     if (choices) choices[w] = c;
     if (log.d_entries && c >= 0) {
         const bool positive = wk.c_red > 0;   // the flip's reductions lowered the rank this step

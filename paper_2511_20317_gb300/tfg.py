@@ -37,7 +37,8 @@ class tfg_params(ctypes.Structure):
                 ("plus_attempts", ctypes.c_int32), ("plus_enabled", ctypes.c_int32),
                 ("r_slack", ctypes.c_int32), ("mapping", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("walker_id_base", ctypes.c_uint32),
-                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("use_graph", ctypes.c_int32), ("walk_policy", ctypes.c_int32),
+                ("expand_thresh", ctypes.c_uint32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class tfg_stats(ctypes.Structure):
@@ -169,7 +170,10 @@ def _rows(fmt, scheme) -> np.ndarray:
 def tfg_default_params(**overrides) -> tfg_params:
     p = tfg_params()
     lib().tfg_default_params(ctypes.byref(p))
+    names = {f[0] for f in tfg_params._fields_}
     for k, v in overrides.items():
+        if k not in names:
+            raise TypeError(f"tfg_params has no field {k!r}")
         setattr(p, k, v)
     return p
 

@@ -340,3 +340,35 @@ def test_empty_populations_and_zero_steps(graph):
     E.walk(10).sync()
     assert E.verify_all() == 0
     E.close()
+
+
+@pytest.mark.parametrize("mode", [tfg.TFG_MODE_ZT, tfg.TFG_MODE_Z2])
+@pytest.mark.parametrize("fmt,lanes,nw", [((2, 2, 2), 1, 200), ((3, 3, 3), 1, 150), ((2, 3, 4), 8, 100),
+                                          ((3, 3, 3), 32, 64), ((4, 5, 5), 32, 40), ((6, 7, 9), 32, 8)])
+def test_algorithm1_policy_parity(fmt, lanes, nw, mode):
+    """Walk policy 1 (Algorithm 1 expansions, plus or split) on the thread-per-walker,
+    lane-group and wide-term kernels against the oracle."""
+    if fmt == (6, 7, 9) and mode == tfg.TFG_MODE_Z2:
+        pytest.skip("one mode suffices at rank 378")
+    start = naive_start(*fmt)
+    steps, slack, thr = (1500, 10, int(0.03 * 2**32)) if fmt != (6, 7, 9) else (300, 8, int(0.05 * 2**32))
+    if fmt == (3, 3, 3) and lanes == 1:
+        slack = 5                      # capacity 32: the largest 32-bit thread-per-walker variant
+    W = gpu_walkers(fmt, mode, start, nw, 9, steps, chunks=2, plateau_len=10**6, r_slack=slack, walk_policy=1,
+                    expand_thresh=thr, mapping=lanes)
+    info, slots, best = W.read_walkers(0, nw)
+    ref = oracle.Walkers(fmt, start, np.arange(nw), seed=9, mode=mode, plateau_len=10**6, r_slack=slack, policy=1,
+                         expand_thresh=thr).walk(steps, THREADS)
+    assert (ref.info["plus"] > 0).any()
+    assert_parity(info, slots, best, ref, range(nw), f"policy 1 {fmt} G={lanes} mode={mode}")
+    assert W.verify_all() == 0
+    W.close()
+
+
+def test_window_mode_rejects_policy1():
+    W = tfg.Walkers([((3, 3, 3), 0, naive_start(3, 3, 3), 32)], seed=1,
+                    params=tfg.tfg_default_params(walk_policy=1, expand_thresh=1000))
+    with pytest.raises(tfg.TfgError) as e:
+        W.walk_window(1, policy=0)
+    assert e.value.code == tfg.TFG_EINVAL
+    W.close()

@@ -125,3 +125,34 @@ def test_reaches_rank7_from_naive_z2():
     W = oracle.Walkers(fmt, naive_start(*fmt), np.arange(32), seed=0, mode=oracle.MODE_Z2,
                        plateau_len=1000).walk(20000)
     assert (W.info["best_r"] == 7).all()
+
+
+@pytest.mark.parametrize("mode", [oracle.MODE_ZT, oracle.MODE_Z2])
+@pytest.mark.parametrize("fmt", [(2, 2, 2), (2, 3, 3), (3, 3, 3)])
+def test_algorithm1_policy_invariants(fmt, mode):
+    """Walk policy 1 (Algorithm 1: expand after a failed try_flip and with
+    probability p_expand; expand = plus or split): Eq. (1), normal form, no zero
+    factor and no reducible pair after every step; expansions happen, the rank
+    never exceeds the capacity, and the best rank is the running minimum."""
+    W = oracle.Walkers(fmt, naive_start(*fmt), np.arange(6), seed=21, mode=mode, r_slack=10, policy=1,
+                       expand_thresh=int(0.03 * 2**32), debug_checks=True)
+    best_seen = np.full(6, W.r0)
+    for _ in range(10):
+        W.walk(300)
+        best_seen = np.minimum(best_seen, W.info["r"])
+        assert (W.info["best_r"] <= best_seen).all()
+    info = W.info
+    assert (info["debug_failures"] == 0).all()
+    assert (info["plus"] > 0).all()
+    assert (info["r"] <= W.r_max).all() and (info["r"] > 0).all()
+    for w in range(6):
+        assert oracle.brent_valid(fmt, W.best_scheme(w), mode) and oracle.brent_valid(fmt, W.scheme(w), mode)
+
+
+def test_policy0_unaffected_by_expand_threshold():
+    """The p_expand threshold and the split operator exist only under policy 1."""
+    fmt = (2, 3, 3)
+    A = oracle.Walkers(fmt, naive_start(*fmt), np.arange(4), seed=5, plateau_len=200).walk(3000)
+    B = oracle.Walkers(fmt, naive_start(*fmt), np.arange(4), seed=5, plateau_len=200,
+                       expand_thresh=2**31).walk(3000)
+    assert np.array_equal(A.info, B.info) and np.array_equal(A.slots, B.slots)
