@@ -225,6 +225,18 @@ int tfg_verify_all_async(tfg_ctx *ctx, int64_t *d_failures);
  * best_r == k for k < hist_len.  Synchronous. */
 int tfg_stats_get(tfg_ctx *ctx, int32_t format_idx, tfg_stats *out, int64_t *rank_hist, int32_t hist_len);
 
+/* Exploratory search (the Resize / population-synchronisation steps of the
+ * paper's search loop): replace walkers [first, first + count) -- global ids,
+ * all in one population -- by `scheme` (rank rows, the population's format
+ * and mode).  The scheme must satisfy Eq. (1) (TFG_ESCHEME otherwise); it is
+ * prepared like a start (tfg_prepare) and written to every walker's live and
+ * best slots.  Each record restarts at rank = best rank = the prepared rank,
+ * plateau 0, best step = its current step count; the walker id, step count,
+ * counters and trajectory digest continue, so the walker's random stream goes
+ * on.  TFG_ENOSPC when the prepared rank exceeds the population's r_max,
+ * TFG_EINVAL for a bad range.  Ordered on the context stream and synchronous. */
+int tfg_reseed(tfg_ctx *ctx, int64_t first, int64_t count, int32_t rank, const int8_t *scheme);
+
 /* Copy walkers [first, first+count) (context-global positions) to the host:
  * info[count]; slots and best (either may be NULL) as int8 schemes of
  * [count][r_max][LT] of that walker's population (all walkers of the range

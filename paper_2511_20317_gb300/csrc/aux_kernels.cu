@@ -35,6 +35,30 @@ __global__ void replicate_kernel(const SegDesc d, const Wd *__restrict__ start, 
     }
 }
 
+// ---- re-seeding: walker `first`'s live slots hold the new packed scheme;
+// copy them to the live slots of walkers first+1 .. first+count-1 and to the
+// best slots of all of them, and restart their records at rank r.
+template <class Wd>
+__global__ void reseed_kernel(const SegDesc d, int64_t first, int32_t r) {
+    const int64_t w = first + blockIdx.x;
+    const size_t per = (size_t)d.R * d.nws;
+    const Wd *src = reinterpret_cast<const Wd *>(d.slots) + per * first;
+    Wd *s = reinterpret_cast<Wd *>(d.slots) + per * w;
+    Wd *b = reinterpret_cast<Wd *>(d.best) + per * w;
+    for (size_t e = threadIdx.x; e < per; e += blockDim.x) {
+        const Wd v = src[e];
+        if (w != first) s[e] = v;
+        b[e] = v;
+    }
+    if (threadIdx.x == 0) {
+        tfg_walker_info &h = d.hdr[w];
+        h.r = r;
+        h.best_r = r;
+        h.plateau = 0;
+        h.best_t = h.t;
+    }
+}
+
 // ---- Eq. (1) on one walker's best scheme per block, by sparse accumulation:
 // the tensor sum_l u_l (x) v_l (x) w_l is built in shared memory from the
 // non-zero coefficients of each term (a few products per term instead of r
@@ -184,6 +208,12 @@ void launch_verify_best(const SegDesc &d, int64_t first, int64_t count, int mode
         cudaFuncSetAttribute(verify_best_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         verify_best_kernel<uint64_t><<<(unsigned)count, 256, smem, st>>>(d, first, mode, slab_rows, fail);
     }
+}
+
+void launch_reseed(const SegDesc &d, int64_t first, int64_t count, int32_t r, cudaStream_t st) {
+    if (count <= 0) return;
+    if (d.word_bits == 32) reseed_kernel<uint32_t><<<(unsigned)count, 128, 0, st>>>(d, first, r);
+    else reseed_kernel<uint64_t><<<(unsigned)count, 128, 0, st>>>(d, first, r);
 }
 
 void launch_argmin_best(const SegDesc &d, unsigned long long *d_key, cudaStream_t st) {

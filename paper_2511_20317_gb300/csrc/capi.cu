@@ -705,6 +705,37 @@ int tfg_stats_get(tfg_ctx *ctx, int32_t format_idx, tfg_stats *out, int64_t *ran
     return TFG_OK;
 }
 
+int tfg_reseed(tfg_ctx *ctx, int64_t first, int64_t count, int32_t rank, const int8_t *scheme) {
+    if (!ctx || first < 0 || count < 1 || first + count > ctx->total) { set_error("walker range out of bounds"); return TFG_EINVAL; }
+    const Segment *sp = nullptr;
+    for (const Segment &s : ctx->segs)
+        if (first >= s.first && first + count <= s.first + s.n) sp = &s;
+    if (!sp) { set_error("walker range spans several populations"); return TFG_EINVAL; }
+    const Segment &s = *sp;
+    int rc = tfg::host::check_input(&s.fmt, rank, scheme);
+    if (rc) return rc;
+    std::vector<HTerm> t;
+    rc = tfg::host::parse(s.fmt, rank, scheme, t);
+    if (rc) return rc;
+    tfg::host::prepare(s.fmt, t);
+    if ((int)t.size() > s.R) { set_error("prepared rank exceeds the population's r_max"); return TFG_ENOSPC; }
+    if (t.empty()) { set_error("empty scheme"); return TFG_EINVAL; }
+    std::vector<uint8_t> buf;
+    pack_terms(s, t, buf);
+    const size_t per = buf.size();
+    const int64_t lo = first - s.first;
+    // stage the packed scheme in the first walker's live slots, then copy on the device
+    cudaError_t e = cudaMemcpyAsync(ctx->ws + s.off_slots + per * lo, buf.data(), per, cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reseed copy");
+    tfg::SegDesc d = ctx->desc(s);
+    tfg::launch_reseed(d, lo, count, (int32_t)t.size(), ctx->stream);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reseed");
+    return TFG_OK;
+}
+
 int tfg_read_walkers(tfg_ctx *ctx, int64_t first, int64_t count, tfg_walker_info *info, int8_t *slots, int8_t *best,
                      int32_t r_max_cap) {
     if (!ctx || first < 0 || count < 0 || first + count > ctx->total) { set_error("walker range out of bounds"); return TFG_EINVAL; }

@@ -15,6 +15,16 @@ as text (the format `workloads.read_scheme` reads).
 the (6,7,9) start from the best (3,3,3) scheme found (Section 3.3.2: product
 with the (2,2,3:11) scheme, then extension), the way the paper lifts schemes
 of small formats to larger ones.
+
+`--explore CYCLES` runs the exploratory search of the paper's loop over a set
+of formats (one population each): every cycle walks all populations, collects
+each format's best scheme (population synchronisation), applies the Resize
+moves to those schemes -- swap sizes with probability 1/2, then a merge with a
+random best scheme, else with probability p_resize one of project (5%),
+product with a random best scheme (50%), double (30%), extend (15%) -- and
+re-seeds a block of walkers of any population whose best rank a result
+beats.  Populations keep one format each, so the walk kernels stay
+specialised; schemes move between populations between walk chunks.
 """
 from __future__ import annotations
 
@@ -73,9 +83,10 @@ def invariants(fmt, scheme, mode):
 
 
 def run(pops, steps: int, chunk: int, seed: int, plateau: int, out_dir: str | None = None, label: str = "",
-        quiet: bool = False):
+        quiet: bool = False, policy: int = 0, p_expand: float = 0.0, r_slack: int = 3):
     import torch
-    params = tfg.tfg_default_params(plateau_len=plateau)
+    params = tfg.tfg_default_params(plateau_len=plateau, walk_policy=policy,
+                                    expand_thresh=min(int(p_expand * 2**32), 2**32 - 1), r_slack=r_slack)
     W = tfg.Walkers(pops, seed=seed, params=params)
     W.autotune(trial_steps=200, trial_walkers=16384)
     t0 = time.perf_counter()
@@ -122,6 +133,111 @@ def run(pops, steps: int, chunk: int, seed: int, plateau: int, out_dir: str | No
     return results
 
 
+EXPLORE_FORMATS = [(2, 2, 2), (2, 2, 3), (2, 2, 4), (2, 3, 3), (2, 3, 4), (3, 3, 3), (2, 4, 4), (3, 3, 4),
+                   (4, 4, 4)]
+
+
+def resize_move(rng, fmt, scheme, bests, p_resize=0.5):
+    """One Resize move (the paper's Resize kernel) on a scheme; returns
+    (format, scheme, operator) or None.  bests: {format: scheme}."""
+    ops = []
+    if rng.random() < 0.5:
+        perm = int(rng.integers(6))
+        fmt, scheme = tfg.tfg_swap_sizes(fmt, scheme, perm)
+        ops.append(f"swap{perm}")
+    keys = list(bests)
+    other = keys[int(rng.integers(len(keys)))]
+    axes = [a for a in range(3) if all(fmt[b] == other[b] for b in range(3) if b != a)]
+    if axes:
+        axis = axes[int(rng.integers(len(axes)))]
+        try:
+            f2, s2 = tfg.tfg_merge(fmt, scheme, other, bests[other], axis)
+            return f2, s2, "+".join(ops + [f"merge{axis}"])
+        except tfg.TfgError:
+            pass
+    if rng.random() >= p_resize:
+        return (fmt, scheme, "+".join(ops)) if ops else None
+    u = rng.random()
+    try:
+        if u < 0.05:
+            axis = int(rng.integers(3))
+            if fmt[axis] < 2:
+                return None
+            f2, s2 = tfg.tfg_project(fmt, scheme, axis, int(rng.integers(fmt[axis])))
+            op = f"project{axis}"
+        elif u < 0.55:
+            other = keys[int(rng.integers(len(keys)))]
+            f2, s2 = tfg.tfg_product(fmt, scheme, other, bests[other])
+            op = "product"
+        elif u < 0.85:
+            axis = int(rng.integers(3))
+            f2, s2 = tfg.tfg_double(fmt, scheme, axis)
+            op = f"double{axis}"
+        else:
+            axis = int(rng.integers(3))
+            f2, s2 = tfg.tfg_extend(fmt, scheme, axis)
+            op = f"extend{axis}"
+    except tfg.TfgError:
+        return None
+    return f2, s2, "+".join(ops + [op])
+
+
+def explore(formats, walkers: int, cycles: int, steps_per_cycle: int, seed: int, plateau: int = 50_000,
+            reseed_frac: float = 0.25, p_resize: float = 0.5, moves_per_cycle: int = 8, starts: dict | None = None,
+            r_slack: int = 3, quiet: bool = False):
+    """Exploratory search over `formats` (Z_T, one population each, naive starts
+    unless `starts` gives one).  Returns (per-population results, transfer log)."""
+    rng = np.random.default_rng(seed)
+    starts = starts or {}
+    pops = [(f, tfg.TFG_MODE_ZT, starts.get(f, naive_start(*f)), walkers) for f in formats]
+    W = tfg.Walkers(pops, seed=seed, params=tfg.tfg_default_params(plateau_len=plateau, r_slack=r_slack))
+    index = {f: a for a, f in enumerate(formats)}
+    block = max(1, int(walkers * reseed_frac))
+    next_block = {f: 0 for f in formats}
+    transfers = []
+    for cycle in range(cycles):
+        W.walk(steps_per_cycle)
+        W.sync()
+        bests = {}
+        for f in formats:
+            sch, r, _ = W.collect_best(index[f])
+            bests[f] = sch
+        for _ in range(moves_per_cycle):
+            src = formats[int(rng.integers(len(formats)))]
+            out = resize_move(rng, src, bests[src], bests, p_resize)
+            if out is None:
+                continue
+            f2, s2, op = out
+            f2 = tuple(f2)
+            if f2 not in index:
+                continue
+            prepared = tfg.tfg_prepare(f2, s2)
+            if prepared.shape[0] >= bests[f2].shape[0] or prepared.shape[0] > W.pop[index[f2]]["r_max"]:
+                continue
+            first = W.pop[index[f2]]["first"] + next_block[f2]
+            W.reseed(first, block, prepared)
+            next_block[f2] = (next_block[f2] + block) % max(1, walkers - block + 1)
+            bests[f2] = prepared
+            transfers.append({"cycle": cycle, "from": list(src), "to": list(f2), "op": op,
+                              "rank": int(prepared.shape[0])})
+            if not quiet:
+                print(json.dumps({"transfer": transfers[-1]}), flush=True)
+        if not quiet:
+            print(json.dumps({"cycle": cycle, "best_ranks": {"x".join(map(str, f)): int(bests[f].shape[0])
+                                                              for f in formats}}), flush=True)
+    fails = W.verify_all()
+    results = []
+    for f in formats:
+        sch, r, w = W.collect_best(index[f])
+        results.append({"format": list(f), "lowest_rank": int(r), "best_walker": int(w),
+                        "best_scheme_verified_host": bool(tfg.tfg_verify(f, sch)),
+                        "additive_complexity": int(tfg.tfg_additive_complexity(f, sch)),
+                        "isotropy_invariants": invariants(f, sch, tfg.TFG_MODE_ZT),
+                        "device_check_failures": int(fails)})
+    W.close()
+    return results, transfers
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="333")
@@ -132,19 +248,31 @@ def main():
     ap.add_argument("--plateau", type=int, default=None)
     ap.add_argument("--lift-333-steps", type=float, default=0)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--walk-policy", type=int, default=0,
+                    help="0: plus transitions on plateaus; 1: Algorithm 1 expansions (plus or split)")
+    ap.add_argument("--p-expand", type=float, default=0.0, help="walk policy 1: expansion probability after a flip")
+    ap.add_argument("--r-slack", type=int, default=3, help="slots per walker beyond the start rank")
+    ap.add_argument("--explore", type=int, default=0, help="exploratory search: number of walk + resize cycles")
     ap.add_argument("--quiet", action="store_true")
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
+    if args.explore > 0:
+        res, transfers = explore(EXPLORE_FORMATS, args.walkers or 16384, args.explore, int(args.steps), args.seed,
+                                 plateau=args.plateau or 50_000, r_slack=args.r_slack, quiet=args.quiet)
+        for r in res:
+            print(json.dumps(r), flush=True)
+        print(json.dumps({"transfers": len(transfers)}), flush=True)
+        return
     scheme_333 = None
     if args.workload == "large" and args.lift_333_steps > 0:
         pops, plateau = populations("333zt", None)
         (res, scheme_333), = run(pops, int(args.lift_333_steps), args.chunk, args.seed, plateau, args.out,
-                                 "lift (3,3,3)", args.quiet)
+                                 "lift (3,3,3)", args.quiet, args.walk_policy, args.p_expand, args.r_slack)
         print(json.dumps(res), flush=True)
     pops, plateau = populations(args.workload, args.walkers, scheme_333)
     for res, _ in run(pops, int(args.steps), args.chunk, args.seed, args.plateau or plateau, args.out,
-                      args.workload, args.quiet):
+                      args.workload, args.quiet, args.walk_policy, args.p_expand, args.r_slack):
         print(json.dumps(res), flush=True)
 
 

@@ -68,7 +68,8 @@ EXPORTED = ["tfg_default_params", "tfg_last_error", "tfg_verify", "tfg_additive_
             "tfg_canonicalize",
             "tfg_prepare", "tfg_project", "tfg_extend", "tfg_merge", "tfg_double", "tfg_product",
             "tfg_swap_sizes", "tfg_workspace_size", "tfg_init", "tfg_walk", "tfg_sync", "tfg_collect_best",
-            "tfg_verify_all_async", "tfg_stats_get", "tfg_read_walkers", "tfg_population", "tfg_checkpoint",
+            "tfg_verify_all_async", "tfg_stats_get", "tfg_read_walkers", "tfg_reseed", "tfg_population",
+            "tfg_checkpoint",
             "tfg_restore", "tfg_mapping", "tfg_autotune", "tfg_destroy", "tfg_philox_device", "tfg_mlp_param_bytes",
             "tfg_mlp_score", "tfg_mlp_grad", "tfg_mlp_train_state_bytes", "tfg_mlp_train_init",
             "tfg_mlp_train_step", "tfg_window_scratch_bytes", "tfg_walk_window", "tfg_walk_window_noalloc"]
@@ -112,6 +113,7 @@ def lib() -> ctypes.CDLL:
                 "tfg_verify_all_async": (i32, [P, P]),
                 "tfg_stats_get": (i32, [P, i32, ctypes.POINTER(tfg_stats), P, i32]),
                 "tfg_read_walkers": (i32, [P, i64, i64, P, P, P, i32]),
+                "tfg_reseed": (i32, [P, i64, i64, i32, P]),
                 "tfg_population": (i32, [P, i32, F, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
                 "tfg_checkpoint": (i32, [P, P, sz, ctypes.POINTER(sz)]),
@@ -483,6 +485,15 @@ class Walkers:
         return info, s, b
 
     read_walkers = tfg_read_walkers
+
+    def tfg_reseed(self, first: int, count: int, scheme):
+        """Replace walkers [first, first + count) of one population by `scheme`."""
+        f = next(a for a, p in enumerate(self.pop) if p["first"] <= first < p["first"] + p["walkers"])
+        s = _rows(self.pop[f]["fmt"], scheme)
+        _check(lib().tfg_reseed(self.ctx, int(first), int(count), s.shape[0], _ptr(s)))
+        return self
+
+    reseed = tfg_reseed
 
     def tfg_walk_window(self, steps: int, policy: int = 0, mlp_params=None, eps_thresh: int = 0,
                         record_choices: bool = False, log=None):

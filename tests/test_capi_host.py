@@ -220,3 +220,26 @@ def test_isotropy_invariants_match_oracle():
     dense[0, :64] = rng.choice([-1, 1], size=64)
     tr, _, _, _ = tfg.tfg_isotropy_invariants(fmt, dense)
     assert tuple(tr[0]) == inv.term_ranks(fmt, dense)[0]
+
+
+def test_resize_moves_give_valid_schemes():
+    """The Resize moves of the exploratory search (swap sizes, merge with a best
+    scheme, project, product, double, extend) on valid schemes give schemes that
+    satisfy Eq. (1) (checked by the oracle) and stay within the 64-entry factor limit."""
+    from paper_2511_20317_gb300 import search
+    from paper_2511_20317_gb300.workloads import strassen_start
+    bests = {(2, 2, 2): strassen_start(), (2, 2, 3): gold("paper_2x2x3_r11.txt")[1],
+             (2, 3, 3): naive_start(2, 3, 3), (3, 3, 3): naive_start(3, 3, 3)}
+    rng = np.random.default_rng(4)
+    seen = set()
+    for _ in range(300):
+        src = list(bests)[int(rng.integers(len(bests)))]
+        out = search.resize_move(rng, src, bests[src], bests, p_resize=0.9)
+        if out is None:
+            continue
+        fmt, s, op = out
+        seen.add(op.split("+")[-1].rstrip("0123456789"))
+        m, n, p = fmt
+        assert m * n <= 64 and n * p <= 64 and p * m <= 64
+        assert oracle.brent_valid(fmt, s), (src, fmt, op)
+    assert {"merge", "product", "double", "extend", "project"} <= seen

@@ -44,3 +44,28 @@ def test_search_reports_and_files(tmp_path):
         assert res["isotropy_invariants"]["type_polynomial"] == {f"{a} {b} {c}": v for (a, b, c), v in
                                                                   sorted(typ.items(), reverse=True)}
         assert res["isotropy_invariants"]["rank_sums"] == list(sums)
+
+
+def test_exploratory_search_moves_schemes_between_formats():
+    """Exploratory search over (2,2,2) seeded with Strassen's scheme and formats
+    reachable by Resize moves: better schemes are transferred into the other
+    populations (re-seeding), every transfer beats the target's best at the
+    time, and every final best scheme satisfies Eq. (1)."""
+    from paper_2511_20317_gb300.workloads import strassen_start
+    formats = [(2, 2, 2), (2, 2, 3), (2, 2, 4), (4, 4, 4), (2, 4, 4)]
+    res, transfers = search.explore(formats, walkers=256, cycles=6, steps_per_cycle=500, seed=1,
+                                    starts={(2, 2, 2): strassen_start()}, p_resize=0.9, quiet=True)
+    assert transfers, "no scheme was transferred"
+    naive = {f: f[0] * f[1] * f[2] for f in formats}
+    last = dict(naive)
+    for t in transfers:
+        to = tuple(t["to"])
+        assert t["rank"] < last[to]
+        last[to] = t["rank"]
+    for r in res:
+        f = tuple(r["format"])
+        assert r["best_scheme_verified_host"] and r["device_check_failures"] == 0
+        assert r["lowest_rank"] <= last[f]
+    by = {tuple(r["format"]): r["lowest_rank"] for r in res}
+    assert by[(2, 2, 2)] == 7
+    assert min(by[f] for f in formats if f != (2, 2, 2)) < min(naive[f] for f in formats if f != (2, 2, 2))

@@ -372,3 +372,51 @@ def test_window_mode_rejects_policy1():
         W.walk_window(1, policy=0)
     assert e.value.code == tfg.TFG_EINVAL
     W.close()
+
+
+def test_reseed_continues_the_walkers_streams():
+    """tfg_reseed replaces a block of walkers by a new scheme: their records restart
+    at the prepared rank while the step count, counters and digest go on, so they
+    walk on exactly like oracle walkers started from that scheme with those
+    records; the other walkers are untouched."""
+    fmt, n, L, slack = (2, 3, 3), 64, 300, 4
+    start = naive_start(*fmt)
+    A = gpu_walkers(fmt, 0, start, n, 6, 1000, plateau_len=L, r_slack=slack)
+    B = gpu_walkers(fmt, 0, start, n, 6, 1000, plateau_len=L, r_slack=slack)
+    R = A.pop[0]["r_max"]
+    S = oracle.Walkers(fmt, start, [999], seed=1, plateau_len=L).walk(3000).scheme(0)   # a walked state
+    prepared = oracle.prepare_start(fmt, S)
+    A.reseed(10, 20, S)
+    info0, _, _ = A.read_walkers(10, 20, slots=False, best=False)
+    r0 = prepared.shape[0]
+    assert (info0["r"] == r0).all() and (info0["best_r"] == r0).all()
+    assert (info0["plateau"] == 0).all() and (info0["best_t"] == info0["t"]).all() and (info0["t"] == 1000).all()
+    A.walk(700).sync()
+    B.walk(700).sync()
+    ia, sa, ba = A.read_walkers(0, n)
+    ib, sb, bb = B.read_walkers(0, n)
+    keep = np.r_[0:10, 30:n]
+    assert np.array_equal(ia[keep], ib[keep]) and np.array_equal(sa[keep], sb[keep]) and np.array_equal(ba[keep], bb[keep])
+    ref = oracle.Walkers(fmt, S, np.arange(10, 30), seed=6, plateau_len=L, r_slack=R - r0)
+    assert ref.r_max == R
+    for f in ["t", "plateau", "best_t", "digest", "accepted", "rejected", "nocand", "drops", "merges", "plus",
+              "reductions"]:
+        ref.info[f] = info0[f]
+    ref.walk(700, THREADS)
+    assert_parity(ia[10:30], sa[10:30], ba[10:30], ref, range(20), "reseeded")
+    # errors: a range outside one population, a scheme violating Eq. (1), a rank above r_max
+    with pytest.raises(tfg.TfgError) as e:
+        A.reseed(60, 10, S)
+    assert e.value.code == tfg.TFG_EINVAL
+    bad = S.copy()
+    bad[0, 0] = 0 if bad[0, 0] else 1
+    with pytest.raises(tfg.TfgError) as e:
+        A.reseed(0, 4, bad)
+    assert e.value.code == tfg.TFG_ESCHEME
+    grown = oracle.Walkers(fmt, start, np.arange(8), seed=2, r_slack=12, policy=1).walk(200)   # expansions
+    big = next(grown.scheme(w) for w in range(8) if oracle.prepare_start(fmt, grown.scheme(w)).shape[0] > R)
+    with pytest.raises(tfg.TfgError) as e:
+        A.reseed(0, 4, big)
+    assert e.value.code == tfg.TFG_ENOSPC
+    A.close()
+    B.close()
