@@ -131,6 +131,21 @@ int tfg_additive_complexity(const tfg_format *fmt, int32_t rank, const int8_t *s
 int tfg_isotropy_invariants(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int32_t *term_ranks,
                             int64_t *type_poly, int64_t *sym_poly, int64_t *rank_sums);
 
+/* Z_2 -> Z_T sign lifting (section "Ternary Lifting Script"): give every
+ * non-zero coefficient of `scheme` -- a Z_2 scheme of format fmt (m, n, p;
+ * the mode field is ignored), coefficients 0/1, Eq. (1) modulo 2 -- a sign so
+ * that Eq. (1) holds over the integers, by exact search (entries covered by
+ * one or two terms are linear equations over GF(2) in the sign bits; the free
+ * bits are searched depth-first against the other entries; per term the first
+ * non-zero of u and of v is +1).  out: caller buffer of rank rows; the result
+ * has the same non-zero pattern, is sign-normalised and satisfies Eq. (1).
+ * *nodes_used (may be NULL) receives the number of search nodes.
+ * TFG_OK; TFG_ESCHEME when no sign assignment exists (exhaustive search);
+ * TFG_ETIMEOUT when max_nodes nodes did not decide; TFG_EINVAL for a bad
+ * format or rank, coefficients other than 0/1, or Eq. (1) failing mod 2. */
+int tfg_lift_signs(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int64_t max_nodes, int8_t *out,
+                   int64_t *nodes_used);
+
 /* Section 3.6: per term, make the first non-zero of u and of v equal +1, w
  * absorbing the signs (in place; Z_T only, Z_2 unchanged). */
 int tfg_canonicalize(const tfg_format *fmt, int32_t rank, int8_t *scheme);

@@ -75,6 +75,8 @@ def lib():
             i32, i64, u32, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
             L.orc_philox4x32_10.argtypes = [P, P, P]
             L.orc_brent_valid.argtypes = [i32, i32, i32, i32, i32, P]
+            L.orc_lift_bruteforce.argtypes = [i32, i32, i32, i32, P, i32, P]
+            L.orc_lift_backtrack.argtypes = [i32, i32, i32, i32, P, ctypes.c_int64, P]
             L.orc_brent_valid.restype = i32
             L.orc_canonicalize.argtypes = [i32, i32, i32, i32, i32, P]
             L.orc_additive_complexity.argtypes = [i32, i32, i32, i32, P]
@@ -125,6 +127,32 @@ def brent_valid(fmt, scheme, mode=MODE_ZT) -> bool:
     m, n, p = fmt
     s = np.ascontiguousarray(scheme, dtype=np.int8).reshape(-1, term_len(fmt))
     return bool(lib().orc_brent_valid(m, n, p, mode, s.shape[0], _ptr(s)))
+
+
+def lift_bruteforce(fmt, z2_scheme, max_bits: int = 24):
+    """Every sign assignment (first non-zero of u and v per term +1) of a Z_2
+    scheme checked with Eq. (1): (True, signed scheme), (False, None), or None
+    when there are more than max_bits free signs."""
+    m, n, p = fmt
+    s = np.ascontiguousarray(z2_scheme, dtype=np.int8).reshape(-1, term_len(fmt))
+    out = np.zeros_like(s)
+    rc = lib().orc_lift_bruteforce(m, n, p, s.shape[0], _ptr(s), int(max_bits), _ptr(out))
+    if rc < 0:
+        return None
+    return (True, out) if rc == 1 else (False, None)
+
+
+def lift_backtrack(fmt, z2_scheme, max_nodes: int = 10**8):
+    """Plain backtracking over the free signs, each tensor entry checked with
+    Eq. (1) once its signs are set: (True, signed scheme), (False, None), or
+    None when the node budget runs out."""
+    m, n, p = fmt
+    s = np.ascontiguousarray(z2_scheme, dtype=np.int8).reshape(-1, term_len(fmt))
+    out = np.zeros_like(s)
+    rc = lib().orc_lift_backtrack(m, n, p, s.shape[0], _ptr(s), int(max_nodes), _ptr(out))
+    if rc < 0:
+        return None
+    return (True, out) if rc == 1 else (False, None)
 
 
 def canonicalize(fmt, scheme, mode=MODE_ZT) -> np.ndarray:

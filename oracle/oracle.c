@@ -932,3 +932,119 @@ void orc_walk_window(int m, int n, int p, const orc_params *prm, int r_max, uint
 
 int orc_info_size(void) { return (int)sizeof(orc_info); }
 int orc_params_size(void) { return (int)sizeof(orc_params); }
+
+/* ------------------------------------------------------------------------ */
+/* Sign lifting by brute force (the check for the library's exact search):  */
+/* every assignment of signs to the non-zero coefficients of a Z_2 scheme,  */
+/* with the first non-zero of u and of v of each term fixed to +1 (flipping */
+/* two factors of a term changes nothing), each checked with Eq. (1) over   */
+/* the integers.  Returns 1 and the first valid signed scheme (binary       */
+/* counter over the free coefficients in row order) in out, 0 when none,    */
+/* -1 when there are more than max_bits free coefficients.                  */
+/* ------------------------------------------------------------------------ */
+int orc_lift_bruteforce(int m, int n, int p, int r, const int8_t *z2, int max_bits, int8_t *out)
+{
+    orc_fmt f = make_fmt(m, n, p, ORC_MODE_ZT);
+    const int LT = f.LT;
+    int nfree = 0;
+    int *pos = (int *)malloc(sizeof(int) * (size_t)r * (size_t)LT);
+    for (int t = 0; t < r; ++t) {
+        int first_u = -1, first_v = -1;
+        for (int e = 0; e < f.len[0]; ++e) if (z2[t * LT + e]) { first_u = e; break; }
+        for (int e = 0; e < f.len[1]; ++e) if (z2[t * LT + f.len[0] + e]) { first_v = f.len[0] + e; break; }
+        for (int e = 0; e < LT; ++e)
+            if (z2[t * LT + e] && e != first_u && e != first_v) pos[nfree++] = t * LT + e;
+    }
+    if (nfree > max_bits) { free(pos); return -1; }
+    int found = 0;
+    for (uint64_t mask = 0; mask < (1ull << nfree) && !found; ++mask) {
+        for (int e = 0; e < r * LT; ++e) out[e] = z2[e] ? 1 : 0;
+        for (int b = 0; b < nfree; ++b)
+            if ((mask >> b) & 1ull) out[pos[b]] = -1;
+        if (orc_brent_valid(m, n, p, ORC_MODE_ZT, r, out)) found = 1;
+    }
+    free(pos);
+    return found;
+}
+
+/* Sign lifting by plain backtracking (no linear algebra): the free signs in
+ * row order, each tensor entry checked with Eq. (1) over the integers as soon
+ * as its last non-zero coefficient has a sign.  Exhaustive unless the node
+ * budget runs out.  Returns 1 (out = the first valid signed scheme in that
+ * order), 0 (none exists), -1 (budget exhausted). */
+int orc_lift_backtrack(int m, int n, int p, int r, const int8_t *z2, int64_t max_nodes, int8_t *out)
+{
+    orc_fmt f = make_fmt(m, n, p, ORC_MODE_ZT);
+    const int LT = f.LT, LU = f.len[0], LV = f.len[1], LW = f.len[2];
+    const int NC = r * LT;
+    int *order = (int *)malloc(sizeof(int) * (size_t)NC);   /* coefficient index -> position, -1 fixed or zero */
+    int nfree = 0;
+    for (int e = 0; e < NC; ++e) order[e] = -1;
+    int *free_at = (int *)malloc(sizeof(int) * (size_t)NC);
+    for (int t = 0; t < r; ++t) {
+        int first_u = -1, first_v = -1;
+        for (int e = 0; e < LU; ++e) if (z2[t * LT + e]) { first_u = e; break; }
+        for (int e = 0; e < LV; ++e) if (z2[t * LT + LU + e]) { first_v = LU + e; break; }
+        for (int e = 0; e < LT; ++e)
+            if (z2[t * LT + e] && e != first_u && e != first_v) { order[t * LT + e] = nfree; free_at[nfree++] = t * LT + e; }
+    }
+    /* entries with at least one covering term, grouped by the position of their last free coefficient */
+    int nent = LU * LV * LW;
+    int *ent_last = (int *)malloc(sizeof(int) * (size_t)nent);
+    for (int q = 0; q < nent; ++q) {
+        int a = q / (LV * LW), b = (q / LW) % LV, c = q % LW, last = -1, any = 0;
+        for (int t = 0; t < r; ++t) {
+            int ia = t * LT + a, ib = t * LT + LU + b, ic = t * LT + LU + LV + c;
+            if (!(z2[ia] && z2[ib] && z2[ic])) continue;
+            any = 1;
+            if (order[ia] > last) last = order[ia];
+            if (order[ib] > last) last = order[ib];
+            if (order[ic] > last) last = order[ic];
+        }
+        ent_last[q] = any ? last : -2;
+    }
+    for (int e = 0; e < NC; ++e) out[e] = z2[e] ? 1 : 0;
+    /* check of one entry with the current signs */
+    #define ENTRY_OK(q) ({ int a_ = (q) / (LV * LW), b_ = ((q) / LW) % LV, c_ = (q) % LW; \
+        int i_ = a_ / n, k_ = a_ % n, k2_ = b_ / p, j_ = b_ % p, j2_ = c_ / m, i2_ = c_ % m; \
+        int want_ = (k_ == k2_ && j_ == j2_ && i_ == i2_) ? 1 : 0, sum_ = 0; \
+        for (int t_ = 0; t_ < r; ++t_) sum_ += out[t_ * LT + a_] * out[t_ * LT + LU + b_] * out[t_ * LT + LU + LV + c_]; \
+        sum_ == want_; })
+    int result = 1;
+    /* entries without free coefficients */
+    for (int q = 0; q < nent; ++q)
+        if (ent_last[q] == -1 && !ENTRY_OK(q)) { result = 0; break; }
+    /* entries grouped by the position of their last free sign */
+    int *ent_start = (int *)calloc((size_t)nfree + 2, sizeof(int));
+    int *ent_list = (int *)malloc(sizeof(int) * (size_t)(nent > 0 ? nent : 1));
+    for (int q = 0; q < nent; ++q) if (ent_last[q] >= 0) ent_start[ent_last[q] + 1] += 1;
+    for (int d = 0; d < nfree; ++d) ent_start[d + 1] += ent_start[d];
+    {
+        int *fill = (int *)calloc((size_t)nfree + 1, sizeof(int));
+        for (int q = 0; q < nent; ++q)
+            if (ent_last[q] >= 0) ent_list[ent_start[ent_last[q]] + fill[ent_last[q]]++] = q;
+        free(fill);
+    }
+    if (result == 1 && nfree > 0) {
+        int *val = (int *)malloc(sizeof(int) * (size_t)nfree);
+        for (int d = 0; d < nfree; ++d) val[d] = -1;
+        int d = 0;
+        int64_t nodes = 0;
+        result = 0;
+        while (d >= 0) {
+            if (d == nfree) { result = 1; break; }
+            if (val[d] >= 1) { val[d] = -1; out[free_at[d]] = 1; --d; continue; }
+            val[d] += 1;
+            out[free_at[d]] = val[d] ? -1 : 1;
+            if (++nodes > max_nodes) { result = -1; break; }
+            int ok = 1;
+            for (int k = ent_start[d]; k < ent_start[d + 1] && ok; ++k)
+                if (!ENTRY_OK(ent_list[k])) ok = 0;
+            if (ok) ++d;
+        }
+        free(val);
+    }
+    #undef ENTRY_OK
+    free(order); free(free_at); free(ent_last); free(ent_start); free(ent_list);
+    return result;
+}

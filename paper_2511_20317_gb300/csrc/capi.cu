@@ -222,6 +222,33 @@ int tfg_isotropy_invariants(const tfg_format *fmt, int32_t rank, const int8_t *s
     return TFG_OK;
 }
 
+int tfg_lift_signs(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int64_t max_nodes, int8_t *out,
+                   int64_t *nodes_used) {
+    if (!fmt || !out || rank < 1 || !scheme || max_nodes < 0) { set_error("bad arguments"); return TFG_EINVAL; }
+    tfg_format f = *fmt;
+    f.mode = TFG_MODE_Z2;
+    if (!tfg::host::format_ok(&f)) { set_error("bad format"); return TFG_EINVAL; }
+    const int LT = tfg::host::term_len(f);
+    for (int64_t e = 0; e < (int64_t)rank * LT; ++e)
+        if (scheme[e] != 0 && scheme[e] != 1) { set_error("coefficients of a Z_2 scheme must be 0 or 1"); return TFG_EINVAL; }
+    int rc = tfg::host::check_input(&f, rank, scheme);
+    if (rc == TFG_ESCHEME) { set_error("not a Z_2 scheme (Eq. (1) fails modulo 2)"); return TFG_EINVAL; }
+    if (rc) return rc;
+    std::vector<int8_t> res((size_t)rank * LT);
+    rc = tfg::host::lift_signs(f, rank, scheme, max_nodes, res.data(), nodes_used);
+    if (rc) return rc;
+    tfg_format ft = f;
+    ft.mode = TFG_MODE_ZT;
+    std::vector<HTerm> t;
+    if (tfg::host::parse(ft, rank, res.data(), t) != TFG_OK || !tfg::host::brent_ok(ft, t)) {
+        set_error("internal: lifted scheme fails Eq. (1)");
+        return TFG_EINTERNAL;
+    }
+    for (HTerm &h : t) tfg::host::canon_term(ft, h);
+    tfg::host::emit(ft, t, out);
+    return TFG_OK;
+}
+
 int tfg_canonicalize(const tfg_format *fmt, int32_t rank, int8_t *scheme) {
     if (!tfg::host::format_ok(fmt)) { set_error("bad format"); return TFG_EINVAL; }
     std::vector<HTerm> t;

@@ -43,5 +43,9 @@ int swap_sizes(const tfg_format *f, int r, const int8_t *rows, int perm, tfg_for
 // over Q (Z_T) or GF(2) (Z_2).
 int factor_rank(const tfg_format &f, const HTerm &h, int x);
 
+// Z_2 -> Z_T sign lifting (lift.cpp): rows hold a Z_2 scheme (0/1); out gets the
+// signed scheme.  TFG_OK, TFG_ESCHEME (no assignment exists), TFG_ETIMEOUT, TFG_EINVAL.
+int lift_signs(const tfg_format &f, int r, const int8_t *rows, int64_t max_nodes, int8_t *out, int64_t *nodes_used);
+
 }  // namespace host
 }  // namespace tfg

@@ -4,6 +4,9 @@ flip-graph walks found.
     python -m paper_2511_20317_gb300.search --workload 333 --steps 1000000
     python -m paper_2511_20317_gb300.search --workload large --steps 100000 --lift-333-steps 200000
 
+Z_2 populations also report the Z_2 -> Z_T sign lifting (the paper's ternary
+lifting step) of the best schemes of their lowest-rank walkers.
+
 For every population it prints one JSON line with the lowest rank reached, the
 histogram of the walkers' best ranks, the number of walkers at the lowest
 rank, and the best scheme's rank, naive additive complexity and isotropy
@@ -82,6 +85,28 @@ def invariants(fmt, scheme, mode):
             "rank_sums": [int(x) for x in sums]}
 
 
+def lift_population(W, f, max_tries: int = 256, max_nodes: int = 10**6):
+    """Z_2 -> Z_T sign lifting of the best schemes of the walkers at a Z_2
+    population's lowest rank (up to max_tries of them): how many lift, and the
+    first ternary scheme found."""
+    pop = W.pop[f]
+    info, _, _ = W.read_walkers(pop["first"], pop["walkers"], slots=False, best=False)
+    low = int(info["best_r"].min())
+    cands = np.flatnonzero(info["best_r"] == low)[:max_tries]
+    lifted, first = 0, None
+    for w in cands:
+        _, _, best = W.read_walkers(pop["first"] + int(w), 1, slots=False)
+        s = best[0, :low]
+        try:
+            zt, _ = tfg.tfg_lift_signs(pop["fmt"], s, max_nodes=max_nodes)
+        except tfg.TfgError:
+            continue
+        lifted += 1
+        if first is None:
+            first = zt
+    return low, len(cands), lifted, first
+
+
 def run(pops, steps: int, chunk: int, seed: int, plateau: int, out_dir: str | None = None, label: str = "",
         quiet: bool = False, policy: int = 0, p_expand: float = 0.0, r_slack: int = 3):
     import torch
@@ -122,6 +147,17 @@ def run(pops, steps: int, chunk: int, seed: int, plateau: int, out_dir: str | No
             "device_check_failures": int(fails), "seconds": round(secs, 2),
             "steps_per_s": nw * steps / secs,
         }
+        if mode == tfg.TFG_MODE_Z2:
+            low, tried, lifted, zt = lift_population(W, f)
+            res["ternary_lifting"] = {"rank": low, "tried": tried, "lifted": lifted}
+            if zt is not None:
+                res["ternary_lifting"].update({"additive_complexity": int(tfg.tfg_additive_complexity(fmt, zt)),
+                                               "isotropy_invariants": invariants(fmt, zt, tfg.TFG_MODE_ZT)})
+                if out_dir:
+                    os.makedirs(out_dir, exist_ok=True)
+                    path = os.path.join(out_dir, f"lifted_{fmt[0]}x{fmt[1]}x{fmt[2]}_zt_r{low}.txt")
+                    write_scheme(path, fmt, zt, f"sign lifting of a Z_2 scheme, seed {seed}, {steps} steps")
+                    res["ternary_lifting"]["file"] = path
         if out_dir:
             os.makedirs(out_dir, exist_ok=True)
             tag = "zt" if mode == tfg.TFG_MODE_ZT else "z2"

@@ -65,7 +65,7 @@ WALKER_INFO_DTYPE = np.dtype([("r", np.int32), ("best_r", np.int32), ("r_max", n
 
 # every symbol include/tfg.h declares
 EXPORTED = ["tfg_default_params", "tfg_last_error", "tfg_verify", "tfg_additive_complexity", "tfg_isotropy_invariants",
-            "tfg_canonicalize",
+            "tfg_lift_signs", "tfg_canonicalize",
             "tfg_prepare", "tfg_project", "tfg_extend", "tfg_merge", "tfg_double", "tfg_product",
             "tfg_swap_sizes", "tfg_workspace_size", "tfg_init", "tfg_walk", "tfg_sync", "tfg_collect_best",
             "tfg_verify_all_async", "tfg_stats_get", "tfg_read_walkers", "tfg_reseed", "tfg_population",
@@ -95,6 +95,7 @@ def lib() -> ctypes.CDLL:
                 "tfg_verify": (i32, [F, i32, P]),
                 "tfg_additive_complexity": (i32, [F, i32, P, ctypes.POINTER(ctypes.c_int64)]),
                 "tfg_isotropy_invariants": (i32, [F, i32, P, P, P, P, P]),
+                "tfg_lift_signs": (i32, [F, i32, P, i64, P, ctypes.POINTER(ctypes.c_int64)]),
                 "tfg_canonicalize": (i32, [F, i32, P]),
                 "tfg_prepare": (i32, [F, i32, P, P, i32, ctypes.POINTER(ctypes.c_int32)]),
                 "tfg_project": (i32, [F, i32, P, i32, i32, F, P, i32, ctypes.POINTER(ctypes.c_int32)]),
@@ -206,6 +207,18 @@ def tfg_isotropy_invariants(fmt, scheme, mode=TFG_MODE_ZT):
     _check(lib().tfg_isotropy_invariants(ctypes.byref(_fmt(fmt, mode)), s.shape[0], _ptr(s), _ptr(tr), _ptr(typ),
                                          _ptr(sym), _ptr(sums)))
     return tr, typ, sym, sums
+
+
+def tfg_lift_signs(fmt, scheme, max_nodes: int = 10**7):
+    """Signed (Z_T) scheme with the non-zero pattern of the Z_2 scheme, and the
+    search nodes used.  Raises TfgError (TFG_ESCHEME: no sign assignment exists;
+    TFG_ETIMEOUT: budget exhausted)."""
+    s = _rows(fmt, scheme)
+    out = np.zeros_like(s)
+    nodes = ctypes.c_int64()
+    _check(lib().tfg_lift_signs(ctypes.byref(_fmt(fmt, TFG_MODE_Z2)), s.shape[0], _ptr(s), int(max_nodes), _ptr(out),
+                                ctypes.byref(nodes)))
+    return out, nodes.value
 
 
 def polynomial_terms(coeffs) -> dict:

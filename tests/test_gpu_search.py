@@ -44,6 +44,9 @@ def test_search_reports_and_files(tmp_path):
         assert res["isotropy_invariants"]["type_polynomial"] == {f"{a} {b} {c}": v for (a, b, c), v in
                                                                   sorted(typ.items(), reverse=True)}
         assert res["isotropy_invariants"]["rank_sums"] == list(sums)
+        if mode == tfg.TFG_MODE_Z2:
+            lift = res["ternary_lifting"]
+            assert lift["rank"] == res["lowest_rank"] and 1 <= lift["tried"] <= 256 and 0 <= lift["lifted"] <= lift["tried"]
 
 
 def test_exploratory_search_moves_schemes_between_formats():
