@@ -70,27 +70,34 @@ typedef struct {
     int32_t use_graph;        /* tfg_walk launches one captured CUDA graph of all populations' kernels:
                                  1 chained (default), 2 forked onto one stream per population
                                  (concurrent); 0 plain launches on the context stream */
-    int32_t walk_policy;      /* expansions (Section 3.3.1, Algorithm 1):
+    int32_t walk_policy;      /* the step's policy (Section 3.3.1, Algorithm 1):
                                  0 (default): a plus transition after plateau_len steps without a
                                    new best rank, when r <= best + 2;
                                  1: Algorithm 1 -- a failed try_flip (no candidate, or the flip
                                    leaves Z_T) expands and ends the step; after a flip, expand
                                    when draw x3 < expand_thresh and r <= best + 2.  An expansion
                                    is plus or split with probability 1/2 each.
-                                 Both need a free slot (r < r_max); window mode needs policy 0 */
+                                 Both need a free slot (r < r_max).
+                                 2: naive additive complexity minimisation: flips and zero-term
+                                   removal only (no reductions, no expansions); the best scheme is
+                                   the one of least (rank, non-zero coefficients).
+                                 Window mode needs policy 0 */
     uint32_t expand_thresh;   /* policy 1: floor(p_expand * 2^32) */
     int32_t reserved[2];
 } tfg_params;
 
 /* Per-walker record.  t is the number of steps taken, digest a rolling hash of
  * every step's action (sampled term, candidate, sign, rank), best_t the step at
- * which best_r last fell.  Counters are cumulative. */
+ * which best_r last fell.  Counters are cumulative.  best_nnz: non-zero
+ * coefficients of the best scheme (its naive additive complexity is best_nnz
+ * - 2 best_r - m p); kept up to date by walk policy 2, the start's count
+ * under the other policies. */
 typedef struct {
     int32_t r, best_r, r_max, format;
     int64_t t, plateau, best_t;
     uint64_t digest;
     int64_t accepted, rejected, nocand, drops, merges, plus, reductions;
-    uint32_t walker_id, pad;
+    uint32_t walker_id, best_nnz;
 } tfg_walker_info;
 
 /* Aggregate counters over all walkers of a context (or of one format). */
@@ -246,7 +253,8 @@ int tfg_stats_get(tfg_ctx *ctx, int32_t format_idx, tfg_stats *out, int64_t *ran
  * and mode).  The scheme must satisfy Eq. (1) (TFG_ESCHEME otherwise); it is
  * prepared like a start (tfg_prepare) and written to every walker's live and
  * best slots.  Each record restarts at rank = best rank = the prepared rank,
- * plateau 0, best step = its current step count; the walker id, step count,
+ * plateau 0, best step = its current step count, best_nnz its non-zero
+ * coefficients; the walker id, step count,
  * counters and trajectory digest continue, so the walker's random stream goes
  * on.  TFG_ENOSPC when the prepared rank exceeds the population's r_max,
  * TFG_EINVAL for a bad range.  Ordered on the context stream and synchronous. */

@@ -53,11 +53,12 @@ class Params(ctypes.Structure):
                 ("plus_attempts", ctypes.c_int32),
                 ("plus_enabled", ctypes.c_int32),
                 ("debug_checks", ctypes.c_int32),
-                ("policy", ctypes.c_int32),          # 0: plateau plus, 1: Algorithm 1 expansions
+                ("policy", ctypes.c_int32),          # 0: plateau plus, 1: Algorithm 1 expansions,
+                                                     # 2: additive complexity minimisation
                 ("expand_thresh", ctypes.c_uint32)]  # policy 1: p_expand * 2^32
 
 
-INFO_DTYPE = np.dtype([("r", np.int32), ("best_r", np.int32), ("r_max", np.int32), ("pad", np.int32),
+INFO_DTYPE = np.dtype([("r", np.int32), ("best_r", np.int32), ("r_max", np.int32), ("best_nnz", np.int32),
                        ("t", np.int64), ("plateau", np.int64), ("best_t", np.int64),
                        ("digest", np.uint64),
                        ("accepted", np.int64), ("rejected", np.int64), ("nocand", np.int64),

@@ -209,12 +209,14 @@ typedef struct {
     int32_t plus_enabled;
     int32_t debug_checks;    /* re-verify the invariants after every step */
     int32_t policy;          /* 0: plus transition on a plateau; 1: Algorithm 1 (expand when try_flip
-                                fails, and after a flip with probability p_expand) */
+                                fails, and after a flip with probability p_expand); 2: naive additive
+                                complexity minimisation (flips and zero-term removal only, the best
+                                scheme is the one of least (rank, non-zero coefficients)) */
     uint32_t expand_thresh;  /* policy 1: expand after a flip when x3 < floor(p_expand * 2^32) */
 } orc_params;
 
 typedef struct {
-    int32_t r, best_r, r_max, pad;
+    int32_t r, best_r, r_max, best_nnz;   /* best_nnz: non-zero coefficients of the best scheme */
     int64_t t, plateau, best_t;
     uint64_t digest;
     int64_t accepted, rejected, nocand, drops, merges, plus, reductions;
@@ -436,8 +438,9 @@ static int no_reducible_pair(walker *wk)
 static void debug_check(walker *wk)
 {
     const orc_fmt *f = wk->f;
+    /* policy 2 has no reduction edges, so reducible pairs may remain */
     if (!orc_brent_valid(f->m, f->n, f->p, f->mode, wk->info->r, wk->slots) ||
-        !all_canonical(wk) || !no_zero_factor(wk) || !no_reducible_pair(wk))
+        !all_canonical(wk) || !no_zero_factor(wk) || (wk->prm->policy != 2 && !no_reducible_pair(wk)))
         wk->info->debug_failures += 1;
 }
 
@@ -564,7 +567,7 @@ static int apply_flip(walker *wk, int i, cand_t c)
     if (zhi) { drop_slot(wk, hi, &q); in->drops += 1; }
     if (zlo) { drop_slot(wk, lo, &q); in->drops += 1; }
     for (int a = 0; a < q.len; ++a) canonicalize_term(f, wk->slots, q.item[a]);
-    reduction_cascade(wk, &q);
+    if (wk->prm->policy != 2) reduction_cascade(wk, &q);   /* policy 2: no reduction edges */
     return ORC_ACCEPT;
 }
 
@@ -576,8 +579,9 @@ int orc_apply_flip(int m, int n, int p, int mode, int r, int8_t *scheme, int i,
 {
     orc_fmt f = make_fmt(m, n, p, mode);
     orc_info info; memset(&info, 0, sizeof info); info.r = r;
+    orc_params prm; memset(&prm, 0, sizeof prm);   /* policy 0: the flip with its reduction cascade */
     walker wk; memset(&wk, 0, sizeof wk);
-    wk.f = &f; wk.slots = scheme; wk.info = &info;
+    wk.f = &f; wk.prm = &prm; wk.slots = scheme; wk.info = &info;
     cand_t c; c.X = X; c.j = j; c.s = s; c.rho = rho;
     int action = apply_flip(&wk, i, c);
     *r_out = info.r;
@@ -604,6 +608,25 @@ static void finish_step(walker *wk, const uint32_t *x, int r_before, int action,
                    ((uint64_t)(s < 0) << 7) | ((uint64_t)(uint32_t)i << 8) |
                    ((uint64_t)(uint32_t)j << 24) | ((uint64_t)(uint32_t)in->r << 40);
     in->digest = digest_mix(in->digest, rec);
+
+    if (wk->prm->policy == 2) {
+        /* best = least (rank, non-zero coefficients); equal pairs refresh with x2 */
+        int nz = 0;
+        for (int e = 0; e < in->r * wk->f->LT; ++e) nz += wk->slots[e] != 0;
+        if (in->r < in->best_r || (in->r == in->best_r && nz < in->best_nnz)) {
+            take_best(wk);
+            in->best_r = in->r;
+            in->best_nnz = nz;
+            in->best_t = (int64_t)t;
+            in->plateau = 0;
+        } else {
+            if (in->r == in->best_r && nz == in->best_nnz && x[2] < wk->prm->refresh_thresh) take_best(wk);
+            in->plateau += 1;
+        }
+        in->t += 1;
+        if (wk->prm->debug_checks) debug_check(wk);
+        return;
+    }
 
     if (wk->prm->policy == 1 && action != ORC_ACCEPT) {
         in->plateau += 1;
@@ -827,6 +850,9 @@ void orc_init_walkers(int m, int n, int p, int mode, int r0, const int8_t *start
         orc_info *in = info + w;
         memset(in, 0, sizeof *in);
         in->r = r0; in->best_r = r0; in->r_max = r_max;
+        int nz = 0;
+        for (int e = 0; e < r0 * f.LT; ++e) nz += start[e] != 0;
+        in->best_nnz = nz;
         in->digest = orc_digest_init(walker_ids[w]);
     }
 }

@@ -12,7 +12,7 @@ namespace {
 // ---- population set-up: every walker starts from the prepared start scheme
 template <class Wd>
 __global__ void replicate_kernel(const SegDesc d, const Wd *__restrict__ start, int32_t r0,
-                                 uint32_t id_base, int32_t fidx) {
+                                 uint32_t id_base, int32_t fidx, uint32_t start_nnz) {
     const int64_t w = blockIdx.x;
     if (w >= d.n_walkers) return;
     const size_t per = (size_t)d.R * d.nws;
@@ -30,7 +30,7 @@ __global__ void replicate_kernel(const SegDesc d, const Wd *__restrict__ start, 
         h.walker_id = id_base + (uint32_t)w;
         h.digest = 0xCBF29CE484222325ull ^ (uint64_t)h.walker_id;
         h.accepted = h.rejected = h.nocand = h.drops = h.merges = h.plus = h.reductions = 0;
-        h.pad = 0;
+        h.best_nnz = start_nnz;
         d.hdr[w] = h;
     }
 }
@@ -39,7 +39,7 @@ __global__ void replicate_kernel(const SegDesc d, const Wd *__restrict__ start, 
 // copy them to the live slots of walkers first+1 .. first+count-1 and to the
 // best slots of all of them, and restart their records at rank r.
 template <class Wd>
-__global__ void reseed_kernel(const SegDesc d, int64_t first, int32_t r) {
+__global__ void reseed_kernel(const SegDesc d, int64_t first, int32_t r, uint32_t nnz) {
     const int64_t w = first + blockIdx.x;
     const size_t per = (size_t)d.R * d.nws;
     const Wd *src = reinterpret_cast<const Wd *>(d.slots) + per * first;
@@ -56,6 +56,7 @@ __global__ void reseed_kernel(const SegDesc d, int64_t first, int32_t r) {
         h.best_r = r;
         h.plateau = 0;
         h.best_t = h.t;
+        h.best_nnz = nnz;
     }
 }
 
@@ -182,14 +183,14 @@ __global__ void philox_kernel(const uint32_t *ctr, int n, uint32_t k0, uint32_t 
 }  // namespace
 
 void launch_replicate(const SegDesc &d, const void *start_words, int32_t r0, uint32_t id_base,
-                      int32_t format_idx, cudaStream_t st) {
+                      int32_t format_idx, uint32_t start_nnz, cudaStream_t st) {
     if (d.n_walkers <= 0) return;
     if (d.word_bits == 32)
         replicate_kernel<uint32_t><<<(unsigned)d.n_walkers, 128, 0, st>>>(
-            d, reinterpret_cast<const uint32_t *>(start_words), r0, id_base, format_idx);
+            d, reinterpret_cast<const uint32_t *>(start_words), r0, id_base, format_idx, start_nnz);
     else
         replicate_kernel<uint64_t><<<(unsigned)d.n_walkers, 128, 0, st>>>(
-            d, reinterpret_cast<const uint64_t *>(start_words), r0, id_base, format_idx);
+            d, reinterpret_cast<const uint64_t *>(start_words), r0, id_base, format_idx, start_nnz);
 }
 
 void launch_verify_best(const SegDesc &d, int64_t first, int64_t count, int mode, int64_t *d_failures,
@@ -210,10 +211,10 @@ void launch_verify_best(const SegDesc &d, int64_t first, int64_t count, int mode
     }
 }
 
-void launch_reseed(const SegDesc &d, int64_t first, int64_t count, int32_t r, cudaStream_t st) {
+void launch_reseed(const SegDesc &d, int64_t first, int64_t count, int32_t r, uint32_t nnz, cudaStream_t st) {
     if (count <= 0) return;
-    if (d.word_bits == 32) reseed_kernel<uint32_t><<<(unsigned)count, 128, 0, st>>>(d, first, r);
-    else reseed_kernel<uint64_t><<<(unsigned)count, 128, 0, st>>>(d, first, r);
+    if (d.word_bits == 32) reseed_kernel<uint32_t><<<(unsigned)count, 128, 0, st>>>(d, first, r, nnz);
+    else reseed_kernel<uint64_t><<<(unsigned)count, 128, 0, st>>>(d, first, r, nnz);
 }
 
 void launch_argmin_best(const SegDesc &d, unsigned long long *d_key, cudaStream_t st) {

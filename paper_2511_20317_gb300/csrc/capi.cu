@@ -308,8 +308,9 @@ static int check_params(const tfg_params &p) {
         set_error("use_graph must be 0 (plain launches), 1 (chained graph) or 2 (forked graph)");
         return TFG_EINVAL;
     }
-    if (p.walk_policy != 0 && p.walk_policy != 1) {
-        set_error("walk_policy must be 0 (plateau plus transitions) or 1 (Algorithm 1 expansions)");
+    if (p.walk_policy < 0 || p.walk_policy > 2) {
+        set_error("walk_policy must be 0 (plateau plus transitions), 1 (Algorithm 1 expansions) or 2 (additive "
+                  "complexity minimisation)");
         return TFG_EINVAL;
     }
     if (p.mapping != 0 && p.mapping != 1 && p.mapping != 4 && p.mapping != 8 && p.mapping != 16 && p.mapping != 32) {
@@ -462,8 +463,10 @@ int tfg_init(int32_t n_formats, const tfg_format *fmts, const int32_t *ranks, co
         e = cudaMemcpyAsync(ctx->ws + s.off_start, buf.data(), buf.size(), cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "copy start"); }
+        uint32_t nnz = 0;
+        for (int8_t c : s.start_rows) nnz += c != 0;
         tfg::launch_replicate(ctx->desc(s), ctx->ws + s.off_start, s.r0, prm.walker_id_base + (uint32_t)s.first, f,
-                              ctx->stream);
+                              nnz, ctx->stream);
         e = cudaGetLastError();
         if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "replicate launch"); }
     }
@@ -756,7 +759,10 @@ int tfg_reseed(tfg_ctx *ctx, int64_t first, int64_t count, int32_t rank, const i
                                     ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "reseed copy");
     tfg::SegDesc d = ctx->desc(s);
-    tfg::launch_reseed(d, lo, count, (int32_t)t.size(), ctx->stream);
+    uint32_t nnz = 0;
+    for (const HTerm &h : t)
+        for (int x = 0; x < 3; ++x) nnz += (uint32_t)__builtin_popcountll(h.p[x] | h.n[x]);
+    tfg::launch_reseed(d, lo, count, (int32_t)t.size(), nnz, ctx->stream);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "reseed");

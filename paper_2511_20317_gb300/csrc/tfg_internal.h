@@ -57,8 +57,8 @@ const WalkVariant *walk_variants(int *count);
 
 // Auxiliary kernels (aux_kernels.cu).
 void launch_replicate(const SegDesc &d, const void *start_words, int32_t r0, uint32_t id_base,
-                      int32_t format_idx, cudaStream_t st);
-void launch_reseed(const SegDesc &d, int64_t first, int64_t count, int32_t r, cudaStream_t st);
+                      int32_t format_idx, uint32_t start_nnz, cudaStream_t st);
+void launch_reseed(const SegDesc &d, int64_t first, int64_t count, int32_t r, uint32_t nnz, cudaStream_t st);
 void launch_verify_best(const SegDesc &d, int64_t first, int64_t count, int mode, int64_t *d_failures,
                         cudaStream_t st);
 void launch_argmin_best(const SegDesc &d, unsigned long long *d_key, cudaStream_t st);

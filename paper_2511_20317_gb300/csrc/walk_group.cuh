@@ -67,6 +67,17 @@ struct GroupWalker {
     uint32_t wid, key0, key1;
     uint32_t c_acc, c_rej, c_noc, c_drp, c_mrg, c_pls, c_red;
     int qlen, q0, q1, q2;   // reduction queue (slot indices)
+    uint32_t nnz, best_nnz; // non-zero coefficients of the live (walk policy 2) / best scheme
+
+    __device__ __forceinline__ static uint32_t nnz_of(const T &v) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < TW; ++w) {
+            const Wd x = ZT ? (v.p[w] | v.n[w]) : v.p[w];
+            c += (uint32_t)(sizeof(Wd) == 8 ? __popcll((unsigned long long)x) : __popc((unsigned)x));
+        }
+        return c;
+    }
 
     __device__ __forceinline__ T fetch(int k) const {
         const int o = k / S, pos = k - o * S;
@@ -295,6 +306,7 @@ struct GroupWalker {
         t = H->t; plateau = H->plateau; best_t = H->best_t;
         dig = H->digest; wid = H->walker_id;
         key0 = d.key0; key1 = d.key1;
+        best_nnz = H->best_nnz;
         mk.load(d);
         c_acc = c_rej = c_noc = c_drp = c_mrg = c_pls = c_red = 0;
         qlen = 0; q0 = q1 = q2 = 0;
@@ -308,6 +320,16 @@ struct GroupWalker {
                 st[p].p[q] = (slot < R) ? src[(size_t)slot * NWS + q] : Wd(0);
                 st[p].n[q] = (ZT && slot < R) ? src[(size_t)slot * NWS + TW + q] : Wd(0);
             }
+        }
+        nnz = 0;
+        if (d.walk_policy == 2) {
+            uint32_t mine = 0;
+#pragma unroll
+            for (int p = 0; p < S; ++p)
+                if (g.lane * S + p < r) mine += nnz_of(st[p]);
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) mine += __shfl_xor_sync(g.mask, mine, o, G);
+            nnz = mine;
         }
 
         uint32_t xr0 = 0, xr1 = 0, xr2 = 0, xr3 = 0;
@@ -399,6 +421,8 @@ struct GroupWalker {
                         c_acc += 1;
                         const bool zi = O::zero(ti2, Y, mk);
                         const bool zj = O::zero(tj2, Z, mk);
+                        if (d.walk_policy == 2)
+                            nnz += (zi ? 0u : nnz_of(ti2)) + (zj ? 0u : nnz_of(tj2)) - nnz_of(ti) - nnz_of(tj);
                         O::canon(ti2, mk);
                         O::canon(tj2, mk);
                         store(ti2, i);
@@ -414,7 +438,8 @@ struct GroupWalker {
                                 const bool z = dd == 0 ? zhi : zlo;
                                 if (z) { drop(dd == 0 ? hi : lo); c_drp += 1; }
                             }
-                        } else if (pair_hit2(ti2, i, tj2, j)) {
+                            if (d.walk_policy == 2) qlen = 0;   // no reduction edges
+                        } else if (d.walk_policy != 2 && pair_hit2(ti2, i, tj2, j)) {
                             // the queue is only needed when a term shares a factor pair
                             q_push(i);
                             q_push(j);
@@ -440,7 +465,19 @@ struct GroupWalker {
                 // walk policy 1: a failed try_flip expands and ends the step (no best update)
                 const bool failed = d.walk_policy == 1 && action != kAccept;
                 // best scheme: always when better, with probability 0.01 when equal
-                if (failed) {
+                // (policy 2: better = least (rank, non-zero coefficients))
+                if (d.walk_policy == 2) {
+                    if (r < best_r || (r == best_r && nnz < best_nnz)) {
+                        snapshot(bestp);
+                        best_r = r;
+                        best_nnz = nnz;
+                        best_t = t;
+                        plateau = 0;
+                    } else {
+                        if (r == best_r && nnz == best_nnz && x2 < d.refresh_thresh) snapshot(bestp);
+                        plateau += 1;
+                    }
+                } else if (failed) {
                     plateau += 1;
                 } else if (r < best_r) {
                     snapshot(bestp);
@@ -454,7 +491,9 @@ struct GroupWalker {
                 // expansion: plus on a plateau near the best rank (policy 0), or Algorithm 1's
                 // expand after a failed try_flip / with probability p_expand (policy 1)
                 bool expand;
-                if (d.walk_policy == 1)
+                if (d.walk_policy == 2)
+                    expand = false;
+                else if (d.walk_policy == 1)
                     expand = failed ? (r < R && r >= 2) : (x3 < d.expand_thresh && r <= best_r + 2 && r < R && r >= 2);
                 else
                     expand = d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2;
@@ -486,6 +525,7 @@ struct GroupWalker {
             H->digest = dig;
             H->accepted += c_acc; H->rejected += c_rej; H->nocand += c_noc;
             H->drops += c_drp; H->merges += c_mrg; H->plus += c_pls; H->reductions += c_red;
+            H->best_nnz = best_nnz;
         }
     }
 };

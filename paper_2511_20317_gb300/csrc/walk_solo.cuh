@@ -127,6 +127,17 @@ struct SoloWalker {
     uint32_t wid, key0, key1;
     uint32_t c_acc, c_rej, c_noc, c_drp, c_mrg, c_pls, c_red;
     int qlen, q0, q1, q2;
+    int policy;                 // walk policy (2: additive complexity minimisation)
+    uint32_t nnz, best_nnz;     // non-zero coefficients of the live / best scheme (nnz: policy 2 only)
+
+    __device__ __forceinline__ static uint32_t nnz_of(const T &v) {
+        if constexpr (ZT) return (uint32_t)popc_word(v.p[0] | v.n[0]);
+        else return (uint32_t)popc_word(v.p[0]);
+    }
+    __device__ __forceinline__ static int popc_word(Wd x) {
+        if constexpr (sizeof(Wd) == 8) return __popcll(x);
+        else return __popc(x);
+    }
 
     __device__ __forceinline__ static T ld_from(const Wd *col, int k) {
         const Wd *a = col + (size_t)k * RS;
@@ -487,6 +498,8 @@ struct SoloWalker {
         t = H->t; plateau = H->plateau; best_t = H->best_t;
         dig = H->digest; wid = H->walker_id;
         key0 = d.key0; key1 = d.key1;
+        policy = d.walk_policy;
+        best_nnz = H->best_nnz;
         mk.load(d);
         c_acc = c_rej = c_noc = c_drp = c_mrg = c_pls = c_red = 0;
         qlen = 0; q0 = q1 = q2 = 0;
@@ -497,6 +510,12 @@ struct SoloWalker {
             v.p[0] = (k < R) ? src[(size_t)k * NWS] : Wd(0);
             v.n[0] = (ZT && k < R) ? src[(size_t)k * NWS + (NWS - 1)] : Wd(0);
             st(k, v);
+        }
+        nnz = 0;
+        if (policy == 2) {
+#pragma unroll
+            for (int k = 0; k < RMAX; ++k)
+                if (k < r) nnz += nnz_of(ld(k));
         }
     }
 
@@ -516,6 +535,7 @@ struct SoloWalker {
         H->digest = dig;
         H->accepted += c_acc; H->rejected += c_rej; H->nocand += c_noc;
         H->drops += c_drp; H->merges += c_mrg; H->plus += c_pls; H->reductions += c_red;
+        H->best_nnz = best_nnz;
     }
 
     // ---- flip of candidate (X, j, sign, rho) on term i (Section 3.3.1) with the
@@ -539,6 +559,7 @@ struct SoloWalker {
         c_acc += 1;
         const bool zi = O::zero(ti2, Y, mk);
         const bool zj = O::zero(tj2, Z, mk);
+        if (policy == 2) nnz += (zi ? 0u : nnz_of(ti2)) + (zj ? 0u : nnz_of(tj2)) - nnz_of(ti) - nnz_of(tj);
         O::canon(ti2, mk);
         O::canon(tj2, mk);
         st(i, ti2);
@@ -551,8 +572,9 @@ struct SoloWalker {
             const bool zhi = (hi == i) ? zi : zj, zlo = (lo == i) ? zi : zj;
             if (zhi) { drop(hi); c_drp += 1; }
             if (zlo) { drop(lo); c_drp += 1; }
+            if (policy == 2) qlen = 0;   // no reduction edges
         } else {
-            need_check = true;
+            need_check = policy != 2;
         }
     }
 
@@ -576,7 +598,19 @@ struct SoloWalker {
                 // walk policy 1: a failed try_flip expands and ends the step (no best update)
                 const bool failed = d.walk_policy == 1 && action != kAccept;
                 bool want = false;
-                if (failed) {
+                if (d.walk_policy == 2) {
+                    // the best scheme is the one of least (rank, non-zero coefficients)
+                    if (r < best_r || (r == best_r && nnz < best_nnz)) {
+                        want = true;
+                        best_r = r;
+                        best_nnz = nnz;
+                        best_t = t;
+                        plateau = 0;
+                    } else {
+                        want = (r == best_r && nnz == best_nnz && x2 < d.refresh_thresh);
+                        plateau += 1;
+                    }
+                } else if (failed) {
                     plateau += 1;
                 } else if (r < best_r) {
                     want = true;
@@ -589,7 +623,9 @@ struct SoloWalker {
                 }
                 coop_snapshot(wmask, lane, nl, want, bestp);
                 bool expand;
-                if (d.walk_policy == 1)
+                if (d.walk_policy == 2)
+                    expand = false;
+                else if (d.walk_policy == 1)
                     expand = failed ? (r < R && r >= 2) : (x3 < d.expand_thresh && r <= best_r + 2 && r < R && r >= 2);
                 else
                     expand = d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2;

@@ -74,6 +74,7 @@ struct WideWalker {
     uint32_t wid, key0, key1;
     uint32_t c_acc, c_rej, c_noc, c_drp, c_mrg, c_pls, c_red;
     int qlen, q0, q1, q2;
+    uint32_t nnz, best_nnz;   // non-zero coefficients of the live (walk policy 2) / best scheme
 
     // ---- full-term comparisons (hit verification)
     __device__ __forceinline__ static bool eq(const T &a, const T &b, int f) {
@@ -153,6 +154,11 @@ struct WideWalker {
             const uint64_t p = sw ? a.n : a.p, n = sw ? a.p : a.n;
             a.p = p; a.n = n;
         }
+    }
+    // non-zero coefficients of a term held one factor per lane
+    __device__ __forceinline__ uint32_t dnnz(const DF &a) const {
+        const uint32_t c = lane < 3 ? (uint32_t)__popcll(a.p | a.n) : 0u;
+        return __reduce_add_sync(kFull, c);
     }
     // w of a equals -w of b
     __device__ __forceinline__ bool dwneg(const DF &a, const DF &b) const {
@@ -447,6 +453,7 @@ struct WideWalker {
         t = H->t; plateau = H->plateau; best_t = H->best_t;
         dig = H->digest; wid = H->walker_id;
         key0 = d.key0; key1 = d.key1;
+        best_nnz = H->best_nnz;
         c_acc = c_rej = c_noc = c_drp = c_mrg = c_pls = c_red = 0;
         qlen = 0; q0 = q1 = q2 = 0;
         const uint64_t *src = reinterpret_cast<const uint64_t *>(d.slots) + (size_t)w * R * NWG;
@@ -464,6 +471,16 @@ struct WideWalker {
 #pragma unroll 1
         for (int s = lane; s < 32 * KM; s += 32) SG[s] = s < R ? sig(get(s)) : make_uint4(0u, 0u, 0u, 0u);
         __syncwarp();
+        nnz = 0;
+        if (d.walk_policy == 2) {
+            uint32_t mine = 0;
+#pragma unroll 1
+            for (int s = lane; s < r; s += 32) {
+                const T v = get(s);
+                for (int x = 0; x < 3; ++x) mine += (uint32_t)__popcll(v.p[x] | v.n[x]);
+            }
+            nnz = __reduce_add_sync(kFull, mine);
+        }
 
         uint32_t xr0 = 0, xr1 = 0, xr2 = 0, xr3 = 0;
         int kb = 32;
@@ -564,6 +581,8 @@ struct WideWalker {
                         c_acc += 1;
                         const bool zi = dzero(ti2, Y);
                         const bool zj = dzero(tj2, Z);
+                        if (d.walk_policy == 2)
+                            nnz += (zi ? 0u : dnnz(ti2)) + (zj ? 0u : dnnz(tj2)) - dnnz(di) - dnnz(dj);
                         dcanon(ti2);
                         dcanon(tj2);
                         dput(i, ti2);
@@ -576,7 +595,8 @@ struct WideWalker {
                             const bool zhi = (hi == i) ? zi : zj, zlo = (lo == i) ? zi : zj;
                             if (zhi) { drop(hi); c_drp += 1; }
                             if (zlo) { drop(lo); c_drp += 1; }
-                        } else if (pair_filter(i, j)) {
+                            if (d.walk_policy == 2) qlen = 0;   // no reduction edges
+                        } else if (d.walk_policy != 2 && pair_filter(i, j)) {
                             q_push(i);
                             q_push(j);
                         }
@@ -601,7 +621,19 @@ struct WideWalker {
                 // walk policy 1: a failed try_flip expands and ends the step (no best update)
                 const bool failed = d.walk_policy == 1 && action != kAccept;
                 // best scheme: always when better, with probability 0.01 when equal
-                if (failed) {
+                // (policy 2: better = least (rank, non-zero coefficients))
+                if (d.walk_policy == 2) {
+                    if (r < best_r || (r == best_r && nnz < best_nnz)) {
+                        snapshot(bestp);
+                        best_r = r;
+                        best_nnz = nnz;
+                        best_t = t;
+                        plateau = 0;
+                    } else {
+                        if (r == best_r && nnz == best_nnz && x2 < d.refresh_thresh) snapshot(bestp);
+                        plateau += 1;
+                    }
+                } else if (failed) {
                     plateau += 1;
                 } else if (r < best_r) {
                     snapshot(bestp);
@@ -615,7 +647,9 @@ struct WideWalker {
                 // expansion: plus on a plateau near the best rank (policy 0), or Algorithm 1's
                 // expand after a failed try_flip / with probability p_expand (policy 1)
                 bool expand;
-                if (d.walk_policy == 1)
+                if (d.walk_policy == 2)
+                    expand = false;
+                else if (d.walk_policy == 1)
                     expand = failed ? (r < R && r >= 2) : (x3 < d.expand_thresh && r <= best_r + 2 && r < R && r >= 2);
                 else
                     expand = d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2;
@@ -643,6 +677,7 @@ struct WideWalker {
             H->digest = dig;
             H->accepted += c_acc; H->rejected += c_rej; H->nocand += c_noc;
             H->drops += c_drp; H->merges += c_mrg; H->plus += c_pls; H->reductions += c_red;
+            H->best_nnz = best_nnz;
         }
     }
 };

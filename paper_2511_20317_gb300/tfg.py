@@ -61,7 +61,7 @@ WALKER_INFO_DTYPE = np.dtype([("r", np.int32), ("best_r", np.int32), ("r_max", n
                               ("digest", np.uint64),
                               ("accepted", np.int64), ("rejected", np.int64), ("nocand", np.int64),
                               ("drops", np.int64), ("merges", np.int64), ("plus", np.int64),
-                              ("reductions", np.int64), ("walker_id", np.uint32), ("pad", np.uint32)])
+                              ("reductions", np.int64), ("walker_id", np.uint32), ("best_nnz", np.uint32)])
 
 # every symbol include/tfg.h declares
 EXPORTED = ["tfg_default_params", "tfg_last_error", "tfg_verify", "tfg_additive_complexity", "tfg_isotropy_invariants",

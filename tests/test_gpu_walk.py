@@ -420,3 +420,25 @@ def test_reseed_continues_the_walkers_streams():
     assert e.value.code == tfg.TFG_ENOSPC
     A.close()
     B.close()
+
+
+@pytest.mark.parametrize("mode", [tfg.TFG_MODE_ZT, tfg.TFG_MODE_Z2])
+@pytest.mark.parametrize("fmt,lanes,nw", [((3, 3, 3), 1, 150), ((2, 3, 4), 8, 100), ((3, 3, 3), 32, 64),
+                                          ((4, 5, 5), 32, 40), ((6, 7, 9), 32, 8)])
+def test_complexity_policy_parity(fmt, lanes, nw, mode):
+    """Walk policy 2 (additive complexity minimisation) on the three kernels
+    against the oracle, including best_nnz, from a walked (non-minimal) start."""
+    if fmt == (6, 7, 9) and mode == tfg.TFG_MODE_Z2:
+        pytest.skip("one mode suffices at rank 378")
+    steps0 = 1500 if fmt != (6, 7, 9) else 150
+    src = oracle.Walkers(fmt, naive_start(*fmt), np.arange(1), seed=3, mode=mode, plateau_len=200).walk(steps0)
+    start = src.scheme(0)
+    steps = 1500 if fmt != (6, 7, 9) else 300
+    # policy 2 never grows the rank: one spare slot keeps (3,3,3) within 32 slots
+    W = gpu_walkers(fmt, mode, start, nw, 9, steps, chunks=2, walk_policy=2, mapping=lanes, r_slack=1)
+    info, slots, best = W.read_walkers(0, nw)
+    ref = oracle.Walkers(fmt, start, np.arange(nw), seed=9, mode=mode, policy=2, r_slack=1).walk(steps, THREADS)
+    assert_parity(info, slots, best, ref, range(nw), f"policy 2 {fmt} G={lanes} mode={mode}")
+    assert np.array_equal(info["best_nnz"], ref.info["best_nnz"].astype(np.uint32))
+    assert W.verify_all() == 0
+    W.close()

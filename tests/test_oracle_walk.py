@@ -156,3 +156,29 @@ def test_policy0_unaffected_by_expand_threshold():
     B = oracle.Walkers(fmt, naive_start(*fmt), np.arange(4), seed=5, plateau_len=200,
                        expand_thresh=2**31).walk(3000)
     assert np.array_equal(A.info, B.info) and np.array_equal(A.slots, B.slots)
+
+
+@pytest.mark.parametrize("mode", [oracle.MODE_ZT, oracle.MODE_Z2])
+@pytest.mark.parametrize("fmt", [(2, 2, 3), (3, 3, 3), (2, 3, 4)])
+def test_complexity_policy(fmt, mode):
+    """Walk policy 2 (naive additive complexity minimisation): flips and zero-term
+    removal only -- no merges, no expansions -- Eq. (1), normal form and no zero
+    factor after every step; best_nnz is the non-zero count of the best scheme and
+    the best (rank, non-zeros) pair is the running minimum."""
+    src = oracle.Walkers(fmt, naive_start(*fmt), np.arange(1), seed=3, mode=mode, plateau_len=300).walk(3000)
+    start = src.scheme(0)                       # a walked state: more non-zeros than needed
+    W = oracle.Walkers(fmt, start, np.arange(6), seed=8, mode=mode, policy=2, debug_checks=True)
+    key = [(int(W.info["best_r"][w]), int(W.info["best_nnz"][w])) for w in range(6)]
+    assert key[0][1] == int((W.start != 0).sum())
+    for _ in range(8):
+        W.walk(400)
+        for w in range(6):
+            now = (int(W.info["best_r"][w]), int(W.info["best_nnz"][w]))
+            assert now <= key[w]
+            key[w] = now
+            b = W.best_scheme(w)
+            assert int((b != 0).sum()) == now[1] and oracle.brent_valid(fmt, b, mode)
+    info = W.info
+    assert (info["debug_failures"] == 0).all()
+    assert (info["merges"] == 0).all() and (info["plus"] == 0).all()
+    assert any(k[1] < int((W.start != 0).sum()) for k in key), "some walker lowers the non-zero count"
