@@ -58,9 +58,12 @@ __device__ __forceinline__ uint32_t fsig(uint64_t p, uint64_t n) {
 
 // GW: the term words stay in the walker's HBM slots (only the signatures are
 // in shared memory), else they are staged in shared memory for the launch.
-template <int MODE, bool GW>
+// PG: the walk policy is read from the descriptor (policies 1 and 2); without
+// it the plateau policy is compiled in alone.
+template <int MODE, bool GW, bool PG>
 struct WideWalker {
     static constexpr bool ZT = (MODE == TFG_MODE_ZT);
+    __device__ __forceinline__ static int policy_of(const SegDesc &d) { return PG ? d.walk_policy : 0; }
     static constexpr int NWG = ZT ? 6 : 3;   // words per slot in HBM (p0 p1 p2 [n0 n1 n2])
     static constexpr int NWS = ZT ? 6 : 4;   // words per slot in shared memory (16-byte rows)
     using T = FTerm<ZT>;
@@ -391,7 +394,7 @@ struct WideWalker {
             int A, B, C;
             plus_roles(perm, A, B, C);
             const DF ti = dget(pi), tj = dget(pj);
-            if (d.walk_policy == 1 && y.w >= 0x80000000u) {
+            if (policy_of(d) == 1 && y.w >= 0x80000000u) {
                 // split: term i = (A_j, B_i, C_i), new term (A_i - A_j, B_i, C_i)
                 DF ns;
                 const bool ok = dadd(ti, tj, A, true, ns);
@@ -472,7 +475,7 @@ struct WideWalker {
         for (int s = lane; s < 32 * KM; s += 32) SG[s] = s < R ? sig(get(s)) : make_uint4(0u, 0u, 0u, 0u);
         __syncwarp();
         nnz = 0;
-        if (d.walk_policy == 2) {
+        if (policy_of(d) == 2) {
             uint32_t mine = 0;
 #pragma unroll 1
             for (int s = lane; s < r; s += 32) {
@@ -494,7 +497,7 @@ struct WideWalker {
                 kb = 0;
             }
             const uint32_t x0 = __shfl_sync(kFull, xr0, kb), x1 = __shfl_sync(kFull, xr1, kb),
-                           x2 = __shfl_sync(kFull, xr2, kb), x3 = __shfl_sync(kFull, xr3, kb);
+                           x2 = __shfl_sync(kFull, xr2, kb), x3 = PG ? __shfl_sync(kFull, xr3, kb) : 0u;
             kb += 1;
 
             const int r_before = r;
@@ -581,7 +584,7 @@ struct WideWalker {
                         c_acc += 1;
                         const bool zi = dzero(ti2, Y);
                         const bool zj = dzero(tj2, Z);
-                        if (d.walk_policy == 2)
+                        if (policy_of(d) == 2)
                             nnz += (zi ? 0u : dnnz(ti2)) + (zj ? 0u : dnnz(tj2)) - dnnz(di) - dnnz(dj);
                         dcanon(ti2);
                         dcanon(tj2);
@@ -595,8 +598,8 @@ struct WideWalker {
                             const bool zhi = (hi == i) ? zi : zj, zlo = (lo == i) ? zi : zj;
                             if (zhi) { drop(hi); c_drp += 1; }
                             if (zlo) { drop(lo); c_drp += 1; }
-                            if (d.walk_policy == 2) qlen = 0;   // no reduction edges
-                        } else if (d.walk_policy != 2 && pair_filter(i, j)) {
+                            if (policy_of(d) == 2) qlen = 0;   // no reduction edges
+                        } else if (policy_of(d) != 2 && pair_filter(i, j)) {
                             q_push(i);
                             q_push(j);
                         }
@@ -619,10 +622,10 @@ struct WideWalker {
                 if (r < r_before) c_red += 1;
                 dig = digest_mix(dig, flip_record(action, X, rho, sneg, i, j, r));
                 // walk policy 1: a failed try_flip expands and ends the step (no best update)
-                const bool failed = d.walk_policy == 1 && action != kAccept;
+                const bool failed = policy_of(d) == 1 && action != kAccept;
                 // best scheme: always when better, with probability 0.01 when equal
                 // (policy 2: better = least (rank, non-zero coefficients))
-                if (d.walk_policy == 2) {
+                if (policy_of(d) == 2) {
                     if (r < best_r || (r == best_r && nnz < best_nnz)) {
                         snapshot(bestp);
                         best_r = r;
@@ -647,9 +650,9 @@ struct WideWalker {
                 // expansion: plus on a plateau near the best rank (policy 0), or Algorithm 1's
                 // expand after a failed try_flip / with probability p_expand (policy 1)
                 bool expand;
-                if (d.walk_policy == 2)
+                if (policy_of(d) == 2)
                     expand = false;
-                else if (d.walk_policy == 1)
+                else if (policy_of(d) == 1)
                     expand = failed ? (r < R && r >= 2) : (x3 < d.expand_thresh && r <= best_r + 2 && r < R && r >= 2);
                 else
                     expand = d.plus_enabled && plateau >= d.plateau_len && r <= best_r + 2 && r < R && r >= 2;
@@ -691,13 +694,13 @@ constexpr int kWideWarps = 2;   // walkers (warps) per block
 
 // With the term words in HBM, registers bound residency: capped for 16
 // two-warp blocks per SM (measured +4-8% on ranks 285 and 351).
-template <int MODE, bool GW>
+template <int MODE, bool GW, bool PG>
 __global__ void __launch_bounds__(32 * kWideWarps, GW ? 16 : 1) walk_wide_kernel(const SegDesc d, const int32_t steps) {
     extern __shared__ __align__(16) unsigned char wide_sm[];
     const int warp = threadIdx.x >> 5;
     const int64_t w = (int64_t)blockIdx.x * kWideWarps + warp;
     if (w >= d.n_walkers) return;   // whole warps exit together
-    WideWalker<MODE, GW> wk;
+    WideWalker<MODE, GW, PG> wk;
     wk.run(d, w, steps, wide_sm + wide_walker_bytes<MODE, GW>(d.R) * warp);
 }
 
@@ -716,8 +719,10 @@ constexpr int kWideHbmWordsMinR = 256;
 template <int MODE>
 void prepare_walk_wide() {
     static bool attr = [] {
-        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
-        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
+        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
+        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
+        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
+        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
         return true;
     }();
     (void)attr;
@@ -728,7 +733,10 @@ void launch_wide_as(const SegDesc &d, int32_t steps, cudaStream_t st) {
     const size_t smem = dev::wide_walker_bytes<MODE, GW>(d.R) * dev::kWideWarps;
     if (d.n_walkers <= 0 || smem > (size_t)kWideMaxSmem) return;
     const int64_t grid = (d.n_walkers + dev::kWideWarps - 1) / dev::kWideWarps;
-    dev::walk_wide_kernel<MODE, GW><<<(unsigned)grid, 32 * dev::kWideWarps, smem, st>>>(d, steps);
+    if (d.walk_policy == 0)
+        dev::walk_wide_kernel<MODE, GW, false><<<(unsigned)grid, 32 * dev::kWideWarps, smem, st>>>(d, steps);
+    else
+        dev::walk_wide_kernel<MODE, GW, true><<<(unsigned)grid, 32 * dev::kWideWarps, smem, st>>>(d, steps);
 }
 
 template <int MODE>
@@ -745,10 +753,10 @@ void launch_walk_wide(const SegDesc &d, int32_t steps, int /*grid*/, int /*block
 const WalkVariant *walk_variants_wide(int *n) {
     static const WalkVariant v[] = {
         WalkVariant{TFG_MODE_ZT, 64, 3, 32, 0, 0, &launch_walk_wide<TFG_MODE_ZT>,
-                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_ZT, true>), &prepare_walk_wide<TFG_MODE_ZT>,
+                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_ZT, true, false>), &prepare_walk_wide<TFG_MODE_ZT>,
                     1023},
         WalkVariant{TFG_MODE_Z2, 64, 3, 32, 0, 0, &launch_walk_wide<TFG_MODE_Z2>,
-                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_Z2, true>), &prepare_walk_wide<TFG_MODE_Z2>,
+                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_Z2, true, false>), &prepare_walk_wide<TFG_MODE_Z2>,
                     1023},
     };
     *n = (int)(sizeof(v) / sizeof(v[0]));
