@@ -131,8 +131,8 @@ int tfg_additive_complexity(const tfg_format *fmt, int32_t rank, const int8_t *s
  *                        of its variables (the symmetric invariant);
  *   rank_sums[3]       = sum_i rank U_i, sum_i rank V_i, sum_i rank W_i (the
  *                        exponents of the rank-sum polynomial).
- * type_poly and sym_poly are caller arrays of 9*9*9 int64, row-major [a][b][c]
- * (a factor of at most 64 entries has rank at most 8); term_ranks is [rank][3]
+ * type_poly and sym_poly are caller arrays of 12*12*12 int64, row-major [a][b][c]
+ * (a factor of at most 128 entries has rank at most 11); term_ranks is [rank][3]
  * int32.  Any output pointer may be NULL.  TFG_EINVAL for a bad format, rank
  * or coefficient; the scheme is not required to satisfy Eq. (1). */
 int tfg_isotropy_invariants(const tfg_format *fmt, int32_t rank, const int8_t *scheme, int32_t *term_ranks,

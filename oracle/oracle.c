@@ -297,7 +297,7 @@ static int try_reduce_term(walker *wk, int t, queue_t *q)
 {
     const orc_fmt *f = wk->f;
     int r = wk->info->r;
-    int8_t tmp[64];
+    int8_t tmp[128];
     int sgn[2] = {1, -1};
     int nsg = (f->mode == ORC_MODE_Z2) ? 1 : 2;
     for (int P = 0; P < 3; ++P) {
@@ -418,7 +418,7 @@ static int no_reducible_pair(walker *wk)
 {
     const orc_fmt *f = wk->f;
     int r = wk->info->r;
-    int8_t tmp[64];
+    int8_t tmp[128];
     int nsg = (f->mode == ORC_MODE_Z2) ? 1 : 2;
     int sgn[2] = {1, -1};
     for (int t = 0; t < r; ++t)
@@ -471,7 +471,7 @@ static int try_expand(walker *wk, uint64_t t, int *pi_out, int *pj_out, int *per
         int A = PERM[pi][0], B = PERM[pi][1], C = PERM[pi][2];
         int nt = r;
         if (split) {
-            int8_t na[64];
+            int8_t na[128];
             if (!vec_add(na, factor(f, wk->slots, i, A), factor(f, wk->slots, j, A), -1, f->len[A], f->mode) ||
                 vec_is_zero(na, f->len[A]))
                 continue;
@@ -485,7 +485,7 @@ static int try_expand(walker *wk, uint64_t t, int *pi_out, int *pj_out, int *per
             canonicalize_term(f, wk->slots, i);
             canonicalize_term(f, wk->slots, nt);
         } else {
-            int8_t nb[64], nc[64], na[64];
+            int8_t nb[128], nc[128], na[128];
             int ok = vec_add(nb, factor(f, wk->slots, i, B), factor(f, wk->slots, j, B), +1, f->len[B], f->mode);
             ok &= vec_add(nc, factor(f, wk->slots, j, C), factor(f, wk->slots, i, C), -1, f->len[C], f->mode);
             ok &= vec_add(na, factor(f, wk->slots, j, A), factor(f, wk->slots, i, A), -1, f->len[A], f->mode);
@@ -546,7 +546,7 @@ static int apply_flip(walker *wk, int i, cand_t c)
     /* (Y, Z) = the two other factors in cyclic order after X; rho swaps them */
     int Y = (X + 1) % 3, Z = (X + 2) % 3;
     if (c.rho) { int tmpf = Y; Y = Z; Z = tmpf; }
-    int8_t ny[64], nz[64];
+    int8_t ny[128], nz[128];
     int ok = vec_add(ny, factor(f, wk->slots, i, Y), factor(f, wk->slots, j, Y), +1, f->len[Y], f->mode);
     ok &= vec_add(nz, factor(f, wk->slots, j, Z), factor(f, wk->slots, i, Z), -s, f->len[Z], f->mode);
     if (!ok) {
@@ -718,7 +718,7 @@ static void window_features(const walker *wk, const wcand_t *c, float *f)
     const orc_fmt *F = wk->f;
     int Y = (c->X + 1) % 3, Z = (c->X + 2) % 3;
     if (c->rho) { int t = Y; Y = Z; Z = t; }
-    int8_t sy[64], sz[64];
+    int8_t sy[128], sz[128];
     int vy = vec_add(sy, factor(F, wk->slots, c->i, Y), factor(F, wk->slots, c->j, Y), +1, F->len[Y], F->mode);
     int vz = vec_add(sz, factor(F, wk->slots, c->j, Z), factor(F, wk->slots, c->i, Z), -c->s, F->len[Z], F->mode);
     int oy = 0, oz = 0;

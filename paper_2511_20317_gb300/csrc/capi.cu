@@ -201,7 +201,7 @@ int tfg_isotropy_invariants(const tfg_format *fmt, int32_t rank, const int8_t *s
     std::vector<HTerm> t;
     int rc = tfg::host::parse(*fmt, rank, scheme, t);
     if (rc) return rc;
-    constexpr int D = 9;
+    constexpr int D = 12;
     if (type_poly) std::memset(type_poly, 0, sizeof(int64_t) * D * D * D);
     if (sym_poly) std::memset(sym_poly, 0, sizeof(int64_t) * D * D * D);
     int64_t sums[3] = {0, 0, 0};
@@ -359,7 +359,7 @@ int tfg_workspace_size(int32_t n_formats, const tfg_format *fmts, const int32_t 
     return plan_segments(n_formats, fmts, ranks, walkers, prm, segs, bytes);
 }
 
-// Host term (one 64-bit mask per factor and sign) -> packed slot words.
+// Host term (a coefficient mask per factor and sign) -> packed slot words.
 static void pack_terms(const Segment &s, const std::vector<HTerm> &t, std::vector<uint8_t> &buf) {
     const size_t wb = (size_t)s.word_bits / 8;
     buf.assign((size_t)s.R * s.nws * wb, 0);
@@ -370,9 +370,9 @@ static void pack_terms(const Segment &s, const std::vector<HTerm> &t, std::vecto
         for (int sg = 0; sg < signs; ++sg) {
             std::vector<uint64_t> words((size_t)s.tw, 0);
             for (int x = 0; x < 3; ++x) {
-                const uint64_t m = sg == 0 ? t[l].p[x] : t[l].n[x];
+                const tfg::host::FMask &m = sg == 0 ? t[l].p[x] : t[l].n[x];
                 for (int e = 0; e < len[x]; ++e)
-                    if ((m >> e) & 1) {
+                    if (m.bit(e)) {
                         const int bit = off[x] + e;
                         words[bit / s.word_bits] |= 1ull << (bit % s.word_bits);
                     }
@@ -404,10 +404,10 @@ static void unpack_terms(const Segment &s, const uint8_t *words, int r, int8_t *
                 else std::memcpy(&w[q], words + idx * 8, 8);
             }
             for (int x = 0; x < 3; ++x) {
-                uint64_t m = 0;
+                tfg::host::FMask m;
                 for (int e = 0; e < len[x]; ++e) {
                     const int bit = off[x] + e;
-                    if ((w[bit / s.word_bits] >> (bit % s.word_bits)) & 1) m |= 1ull << e;
+                    if ((w[bit / s.word_bits] >> (bit % s.word_bits)) & 1) m.set(e);
                 }
                 (sg == 0 ? t[l].p[x] : t[l].n[x]) = m;
             }
@@ -761,7 +761,7 @@ int tfg_reseed(tfg_ctx *ctx, int64_t first, int64_t count, int32_t rank, const i
     tfg::SegDesc d = ctx->desc(s);
     uint32_t nnz = 0;
     for (const HTerm &h : t)
-        for (int x = 0; x < 3; ++x) nnz += (uint32_t)__builtin_popcountll(h.p[x] | h.n[x]);
+        for (int x = 0; x < 3; ++x) nnz += (uint32_t)(h.p[x] | h.n[x]).popcount();
     tfg::launch_reseed(d, lo, count, (int32_t)t.size(), nnz, ctx->stream);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

@@ -21,7 +21,7 @@ const char *last_error() { return g_err.c_str(); }
 bool format_ok(const tfg_format *f) {
     if (!f) return false;
     if (f->m < 1 || f->n < 1 || f->p < 1) return false;
-    if (f->m * f->n > 64 || f->n * f->p > 64 || f->p * f->m > 64) return false;
+    if (f->m * f->n > 128 || f->n * f->p > 128 || f->p * f->m > 128) return false;
     return f->mode == TFG_MODE_ZT || f->mode == TFG_MODE_Z2;
 }
 
@@ -44,8 +44,8 @@ int parse(const tfg_format &f, int rank, const int8_t *rows, std::vector<HTerm> 
                               std::to_string(l));
                     return TFG_ESCHEME;
                 }
-                if (c > 0) out[l].p[x] |= 1ull << e;
-                if (c < 0) out[l].n[x] |= 1ull << e;
+                if (c > 0) out[l].p[x].set(e);
+                if (c < 0) out[l].n[x].set(e);
             }
             off += L;
         }
@@ -60,7 +60,7 @@ void emit(const tfg_format &f, const std::vector<HTerm> &t, int8_t *rows) {
         for (int x = 0; x < 3; ++x) {
             const int L = factor_len(f, x);
             for (int e = 0; e < L; ++e)
-                rows[l * LT + off + e] = (int8_t)((int)((t[l].p[x] >> e) & 1) - (int)((t[l].n[x] >> e) & 1));
+                rows[l * LT + off + e] = (int8_t)((int)t[l].p[x].bit(e) - (int)t[l].n[x].bit(e));
             off += L;
         }
     }
@@ -72,7 +72,7 @@ bool brent_ok(const tfg_format &f, const std::vector<HTerm> &t) {
     const int LU = f.m * f.n, LV = f.n * f.p, LW = f.p * f.m;
     std::vector<int32_t> T((size_t)LU * LV * LW, 0);
     auto coef = [](const HTerm &h, int x, int e) -> int {
-        return (int)((h.p[x] >> e) & 1) - (int)((h.n[x] >> e) & 1);
+        return (int)h.p[x].bit(e) - (int)h.n[x].bit(e);
     };
     for (const HTerm &h : t) {
         for (int a = 0; a < LU; ++a) {
@@ -107,16 +107,15 @@ bool brent_ok(const tfg_format &f, const std::vector<HTerm> &t) {
 void canon_term(const tfg_format &f, HTerm &h) {
     if (f.mode != TFG_MODE_ZT) return;
     for (int x = 0; x < 2; ++x) {
-        const uint64_t d = h.p[x] | h.n[x];
-        const uint64_t low = d & (~d + 1);
-        if (h.n[x] & low) {
+        const FMask low = (h.p[x] | h.n[x]).lowbit();
+        if ((h.n[x] & low).any()) {
             std::swap(h.p[x], h.n[x]);
             std::swap(h.p[2], h.n[2]);
         }
     }
 }
 
-static bool zero_factor(const HTerm &h, int x) { return (h.p[x] | h.n[x]) == 0; }
+static bool zero_factor(const HTerm &h, int x) { return !(h.p[x] | h.n[x]).any(); }
 
 // Sign relation of two factor masks: +1 equal, -1 negated, 0 neither.
 static int relation(const tfg_format &f, const HTerm &a, const HTerm &b, int x) {
@@ -126,11 +125,11 @@ static int relation(const tfg_format &f, const HTerm &a, const HTerm &b, int x) 
 }
 
 // a + s*b on one factor; false when a coefficient leaves the set (Z_T).
-static bool add_factor(const tfg_format &f, const HTerm &a, const HTerm &b, int x, int s, uint64_t &rp,
-                       uint64_t &rn) {
-    if (f.mode == TFG_MODE_Z2) { rp = a.p[x] ^ b.p[x]; rn = 0; return true; }
-    const uint64_t bp = s > 0 ? b.p[x] : b.n[x], bn = s > 0 ? b.n[x] : b.p[x];
-    if ((a.p[x] & bp) | (a.n[x] & bn)) return false;
+static bool add_factor(const tfg_format &f, const HTerm &a, const HTerm &b, int x, int s, FMask &rp,
+                       FMask &rn) {
+    if (f.mode == TFG_MODE_Z2) { rp = a.p[x] ^ b.p[x]; rn = FMask{}; return true; }
+    const FMask bp = s > 0 ? b.p[x] : b.n[x], bn = s > 0 ? b.n[x] : b.p[x];
+    if (((a.p[x] & bp) | (a.n[x] & bn)).any()) return false;
     rp = (a.p[x] | bp) & ~(a.n[x] | bn);
     rn = (a.n[x] | bn) & ~(a.p[x] | bp);
     return true;
@@ -161,7 +160,7 @@ struct Reducer {
                 if (!a) continue;
                 const int b = relation(f, t[k], t[s], PB[P]);
                 if (!b) continue;
-                uint64_t rp, rn;
+                FMask rp, rn;
                 if (!add_factor(f, t[s], t[k], PF[P], a * b, rp, rn)) continue;
                 HTerm mv = t[s];
                 mv.p[PF[P]] = rp;
@@ -171,7 +170,7 @@ struct Reducer {
                 t[lo] = mv;
                 drop(hi);
                 ++merges;
-                if ((rp | rn) == 0) {
+                if (!(rp | rn).any()) {
                     drop(lo);
                 } else {
                     canon_term(f, t[lo]);
@@ -248,7 +247,7 @@ static std::vector<int8_t> to_rows(Dense &d) {
 
 // Validate sizes, coefficients and Eq. (1) of an input scheme.
 int check_input(const tfg_format *f, int rank, const int8_t *rows) {
-    if (!format_ok(f)) { set_error("format sizes must be >= 1 with m*n, n*p, p*m <= 64 and a known mode"); return TFG_EINVAL; }
+    if (!format_ok(f)) { set_error("format sizes must be >= 1 with m*n, n*p, p*m <= 128 and a known mode"); return TFG_EINVAL; }
     std::vector<HTerm> t;
     int rc = parse(*f, rank, rows, t);
     if (rc) return rc;
@@ -466,7 +465,7 @@ int factor_rank(const tfg_format &f, const HTerm &h, int x) {
         std::vector<uint64_t> r((size_t)rows, 0);
         for (int a = 0; a < rows; ++a)
             for (int b = 0; b < cols; ++b)
-                if ((h.p[x] >> (a * cols + b)) & 1) r[(size_t)a] |= 1ull << b;
+                if (h.p[x].bit(a * cols + b)) r[(size_t)a] |= 1ull << b;
         int rank = 0;
         for (int c = 0; c < cols && rank < rows; ++c) {
             int piv = -1;
@@ -484,7 +483,7 @@ int factor_rank(const tfg_format &f, const HTerm &h, int x) {
     for (int a = 0; a < rows; ++a)
         for (int b = 0; b < cols; ++b) {
             const int e = a * cols + b;
-            M[(size_t)a * cols + b] = (int64_t)((h.p[x] >> e) & 1) - (int64_t)((h.n[x] >> e) & 1);
+            M[(size_t)a * cols + b] = (int64_t)h.p[x].bit(e) - (int64_t)h.n[x].bit(e);
         }
     int rank = 0;
     int64_t prev = 1;

@@ -9,16 +9,37 @@
 namespace tfg {
 namespace host {
 
+// Coefficient bits of one factor of at most 128 entries: entry e is bit e % 64
+// of word e / 64.
+struct FMask {
+    uint64_t w[2] = {0, 0};
+    bool bit(int e) const { return (w[e >> 6] >> (e & 63)) & 1ull; }
+    void set(int e) { w[e >> 6] |= 1ull << (e & 63); }
+    bool any() const { return (w[0] | w[1]) != 0; }
+    int popcount() const { return __builtin_popcountll(w[0]) + __builtin_popcountll(w[1]); }
+    FMask operator|(const FMask &o) const { return FMask{{w[0] | o.w[0], w[1] | o.w[1]}}; }
+    FMask operator&(const FMask &o) const { return FMask{{w[0] & o.w[0], w[1] & o.w[1]}}; }
+    FMask operator^(const FMask &o) const { return FMask{{w[0] ^ o.w[0], w[1] ^ o.w[1]}}; }
+    FMask operator~() const { return FMask{{~w[0], ~w[1]}}; }
+    bool operator==(const FMask &o) const { return w[0] == o.w[0] && w[1] == o.w[1]; }
+    bool operator!=(const FMask &o) const { return !(*this == o); }
+    // the lowest set bit alone
+    FMask lowbit() const {
+        if (w[0]) return FMask{{w[0] & (~w[0] + 1), 0}};
+        return FMask{{0, w[1] & (~w[1] + 1)}};
+    }
+};
+
 // One term: positive and negative coefficient masks of u, v, w (Z_2: p only).
 struct HTerm {
-    uint64_t p[3] = {0, 0, 0};
-    uint64_t n[3] = {0, 0, 0};
+    FMask p[3];
+    FMask n[3];
 };
 
 void set_error(const std::string &s);
 const char *last_error();
 
-bool format_ok(const tfg_format *f);
+bool format_ok(const tfg_format *f);   // sizes >= 1, each factor at most 128 entries
 int factor_len(const tfg_format &f, int x);
 int term_len(const tfg_format &f);
 int parse(const tfg_format &f, int rank, const int8_t *rows, std::vector<HTerm> &out);

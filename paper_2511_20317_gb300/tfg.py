@@ -197,12 +197,12 @@ def tfg_additive_complexity(fmt, scheme) -> int:
 
 
 def tfg_isotropy_invariants(fmt, scheme, mode=TFG_MODE_ZT):
-    """(term ranks int32 [r, 3], type polynomial int64 [9, 9, 9], symmetric
-    polynomial int64 [9, 9, 9], rank sums int64 [3])."""
+    """(term ranks int32 [r, 3], type polynomial int64 [12, 12, 12], symmetric
+    polynomial int64 [12, 12, 12], rank sums int64 [3])."""
     s = _rows(fmt, scheme)
     tr = np.zeros((s.shape[0], 3), dtype=np.int32)
-    typ = np.zeros((9, 9, 9), dtype=np.int64)
-    sym = np.zeros((9, 9, 9), dtype=np.int64)
+    typ = np.zeros((12, 12, 12), dtype=np.int64)
+    sym = np.zeros((12, 12, 12), dtype=np.int64)
     sums = np.zeros(3, dtype=np.int64)
     _check(lib().tfg_isotropy_invariants(ctypes.byref(_fmt(fmt, mode)), s.shape[0], _ptr(s), _ptr(tr), _ptr(typ),
                                          _ptr(sym), _ptr(sums)))
@@ -222,7 +222,7 @@ def tfg_lift_signs(fmt, scheme, max_nodes: int = 10**7):
 
 
 def polynomial_terms(coeffs) -> dict:
-    """{(a, b, c): coefficient} of the non-zero entries of a [9, 9, 9] table."""
+    """{(a, b, c): coefficient} of the non-zero entries of a [12, 12, 12] table."""
     return {tuple(int(v) for v in idx): int(coeffs[idx]) for idx in zip(*np.nonzero(coeffs))}
 
 
@@ -241,7 +241,9 @@ def tfg_prepare(fmt, scheme, mode=TFG_MODE_ZT) -> np.ndarray:
     return out[: r.value].copy()
 
 
-def _meta_call(name, args, cap_terms, out_lt_max=192):
+def _meta_call(name, args, cap_terms, out_lt_max=3 * 128):
+    # the library writes cap_terms rows of the result format's length (at most
+    # three factors of 128 entries)
     out_fmt = tfg_format()
     out = np.zeros((max(cap_terms, 1), out_lt_max), dtype=np.int8)
     r = ctypes.c_int32()

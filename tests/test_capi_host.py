@@ -58,7 +58,7 @@ def test_error_codes():
         tfg.tfg_prepare(fmt, bad)
     assert e.value.code == tfg.TFG_ESCHEME
     with pytest.raises(tfg.TfgError) as e:
-        tfg.tfg_prepare((9, 9, 1), np.zeros((1, 81 + 9 + 9), np.int8))
+        tfg.tfg_prepare((12, 12, 1), np.zeros((1, 144 + 12 + 12), np.int8))   # a factor of 144 > 128 entries
     assert e.value.code == tfg.TFG_EINVAL
     assert not tfg.tfg_verify(fmt, s, mode=tfg.TFG_MODE_Z2) or True  # Strassen is also valid mod 2
     with pytest.raises(tfg.TfgError) as e:
@@ -225,7 +225,7 @@ def test_isotropy_invariants_match_oracle():
 def test_resize_moves_give_valid_schemes():
     """The Resize moves of the exploratory search (swap sizes, merge with a best
     scheme, project, product, double, extend) on valid schemes give schemes that
-    satisfy Eq. (1) (checked by the oracle) and stay within the 64-entry factor limit."""
+    satisfy Eq. (1) (checked by the oracle) and stay within the 128-entry factor limit."""
     from paper_2511_20317_gb300 import search
     from paper_2511_20317_gb300.workloads import strassen_start
     bests = {(2, 2, 2): strassen_start(), (2, 2, 3): gold("paper_2x2x3_r11.txt")[1],
@@ -240,6 +240,34 @@ def test_resize_moves_give_valid_schemes():
         fmt, s, op = out
         seen.add(op.split("+")[-1].rstrip("0123456789"))
         m, n, p = fmt
-        assert m * n <= 64 and n * p <= 64 and p * m <= 64
+        assert m * n <= 128 and n * p <= 128 and p * m <= 128
         assert oracle.brent_valid(fmt, s), (src, fmt, op)
     assert {"merge", "product", "double", "extend", "project"} <= seen
+
+
+@pytest.mark.parametrize("fmt", [(9, 8, 2), (2, 9, 8), (8, 2, 9), (11, 11, 1)])
+def test_factors_beyond_64_entries_host(fmt):
+    """Factors of 65..128 entries (two 64-bit words): Eq. (1) on the naive scheme
+    and on single-coefficient changes, start preparation and the meta operators
+    against the oracle, and the isotropy invariants."""
+    from oracle import invariants as inv
+    s = naive_start(*fmt)
+    assert tfg.tfg_verify(fmt, s) and oracle.brent_valid(fmt, s)
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        bad = s.copy()
+        t, e = int(rng.integers(s.shape[0])), int(rng.integers(s.shape[1]))
+        bad[t, e] = 0 if bad[t, e] else 1
+        assert not tfg.tfg_verify(fmt, bad) and not oracle.brent_valid(fmt, bad)
+    W = oracle.Walkers(fmt, s, np.arange(2), seed=3, plateau_len=100).walk(600)
+    for w in range(2):
+        c = W.scheme(w)
+        assert np.array_equal(tfg.tfg_prepare(fmt, c), oracle.prepare_start(fmt, c))
+        for axis in range(3):
+            if fmt[axis] >= 2:
+                f1, s1 = tfg.tfg_project(fmt, c, axis, 1)
+                f2, s2 = oracle.project(fmt, c, axis, 1)
+                assert f1 == f2 and np.array_equal(s1, s2)
+        tr, typ, sym, sums = tfg.tfg_isotropy_invariants(fmt, c)
+        otr, otyp, osym, osums = inv.isotropy_invariants(fmt, c)
+        assert [tuple(x) for x in tr.tolist()] == otr and _poly_dict(typ) == otyp
