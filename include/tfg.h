@@ -15,7 +15,10 @@
  * Section 3.1, in which Eq. (1) reads
  *     sum_l u_l[i*n+k] v_l[k'*p+j] w_l[j'*m+i'] = [k=k'][j=j'][i=i'].
  * In Z_T mode coefficients are -1, 0, 1; in Z_2 mode 0, 1.  Every size
- * m*n, n*p, p*m must be <= 64 (one machine word per factor, Section 4.1).
+ * m*n, n*p, p*m must be <= 128: one 64-bit word per factor and sign as in
+ * Section 3.5.1 up to 64 coefficients (the limit of Section 4.1), two words
+ * beyond.  The window mode and the learned proposal take terms of at most 64
+ * coefficients in all.
  *
  * Errors: every int-returning call returns TFG_OK (0) or a negative TFG_E*
  * code; tfg_last_error() gives a message for the calling thread.  No call

@@ -45,18 +45,20 @@ struct Segment {
 
 // Packed term geometry.  Terms of at most 64 coefficients: the coefficient
 // bits of u | v | w concatenated in one word per sign (32 bits when LT <= 32).
-// Longer terms: factor-aligned, factor f in word f of 64 bits per sign.
+// Longer terms: factor-aligned, factor f in word f of 64 bits per sign, or in
+// words 2f and 2f+1 when a factor has more than 64 coefficients.
 void set_geometry(Segment &s) {
-    const int lu = s.fmt.m * s.fmt.n, lv = s.fmt.n * s.fmt.p;
-    s.lt = lu + lv + s.fmt.p * s.fmt.m;
+    const int lu = s.fmt.m * s.fmt.n, lv = s.fmt.n * s.fmt.p, lw = s.fmt.p * s.fmt.m;
+    s.lt = lu + lv + lw;
     if (s.lt <= 64) {
         s.word_bits = s.lt <= 32 ? 32 : 64;
         s.tw = 1;
         s.fbase[0] = 0; s.fbase[1] = lu; s.fbase[2] = lu + lv;
     } else {
+        const int fw = (lu > 64 || lv > 64 || lw > 64) ? 2 : 1;
         s.word_bits = 64;
-        s.tw = 3;
-        s.fbase[0] = 0; s.fbase[1] = 64; s.fbase[2] = 128;
+        s.tw = 3 * fw;
+        for (int f = 0; f < 3; ++f) s.fbase[f] = 64 * fw * f;
     }
     s.nws = (s.fmt.mode == TFG_MODE_ZT ? 2 : 1) * s.tw;
 }

@@ -11,11 +11,13 @@ namespace tfg {
 enum Action : int { kNoCand = 0, kReject = 1, kAccept = 2 };
 
 // Device view of one walker population ("segment").  A term is packed: its
-// LT = mn + np + pm coefficients (u | v | w concatenated) as TW words of
-// +1 bits followed, in Z_T, by TW words of -1 bits (NWS = 2*TW words per
-// slot; NWS = TW in Z_2).  Walker w's slots are words [w][R][NWS], its best
-// scheme the same shape in `best`, its record hdr[w].  fmask[f][q] selects
-// factor f (u, v, w) in word q.
+// LT = mn + np + pm coefficients as TW words of +1 bits followed, in Z_T, by
+// TW words of -1 bits (NWS = 2*TW words per slot; NWS = TW in Z_2).  Factor f
+// starts at bit fbase[f]: u | v | w concatenated in one word (TW = 1), else
+// factor-aligned in 64-bit words (TW = 3, or 6 when a factor is longer than 64).
+// Walker w's slots are words [w][R][NWS], its best scheme the same shape in
+// `best`, its record hdr[w].  fmask[f][q] selects factor f (u, v, w) in word q
+// (q < 3; read by the kernels of the concatenated layout).
 struct SegDesc {
     void *slots;
     void *best;

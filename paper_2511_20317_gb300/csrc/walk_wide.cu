@@ -1,10 +1,11 @@
 // Wide-term flip-graph walk kernel for sm_103a: formats whose terms have more
-// than 64 coefficients (m*n + n*p + p*m > 64; every factor still <= 64).
+// than 64 coefficients (m*n + n*p + p*m > 64), with factors of up to 128.
 //
-// Layout.  A term is factor-aligned: factor f (u, v, w) is word f of the
-// positive-coefficient words and word f of the negative ones (Section 3.5.1's
-// digits/signs masks, one 64-bit word per factor and sign), so every
-// operation of Section 3.5.2 touches one word and needs no mask.
+// Layout.  A term is factor-aligned: factor f (u, v, w) is words f*FW ..
+// f*FW+FW-1 of the positive-coefficient words and the same words of the
+// negative ones (Section 3.5.1's digits/signs masks, FW = 1 or 2 words of 64
+// bits per factor and sign), so every operation of Section 3.5.2 works word
+// by word and needs no mask.
 //
 // Mapping.  One warp per walker; lane l owns the slots k*32 + l (strided, so
 // that runs of related terms spread over the lanes).  The walker's terms live
@@ -15,10 +16,11 @@
 // exact; the chosen candidate is located in slot order by a walk over the
 // per-pass ballots.  The reduction checks (Section 3.4.1) are filtered the
 // same way.  All walker-uniform bookkeeping is replicated in every lane.
-// The arithmetic of a flip, a merge or a plus transition works on one factor
-// per lane (lane f < 3 holds factor f of each term involved): additions,
-// normalisation, signatures and stores are a handful of lane-parallel
-// instructions; __syncwarp orders the shared-memory writes.
+// The arithmetic of a flip, a merge or a plus transition works on one word
+// per lane (lane q < 3*FW holds word q, of factor q / FW, of each term
+// involved): additions, normalisation, signatures and stores are a handful of
+// lane-parallel instructions and ballots; __syncwarp orders the shared-memory
+// writes.
 //
 // Terms of large walkers (capacity >= 256 slots) stay in their HBM slots and
 // only the signatures sit in shared memory (more walkers resident per SM).
@@ -37,38 +39,47 @@ namespace dev {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-template <bool ZT>
+// FW 64-bit words per factor and sign: word h of factor f is word f*FW + h.
+template <bool ZT, int FW>
 struct FTerm {
-    uint64_t p[3];
-    uint64_t n[3];   // kept zero in Z_2
+    uint64_t p[3 * FW];
+    uint64_t n[3 * FW];   // kept zero in Z_2
 };
 
-__device__ __forceinline__ uint64_t w_of(const uint64_t (&x)[3], int f) { return f == 0 ? x[0] : (f == 1 ? x[1] : x[2]); }
-__device__ __forceinline__ void set_w(uint64_t (&x)[3], int f, uint64_t v) {
-    x[0] = f == 0 ? v : x[0];
-    x[1] = f == 1 ? v : x[1];
-    x[2] = f == 2 ? v : x[2];
+// x[q] for a runtime q, by selects (no local-memory indexing)
+template <int N>
+__device__ __forceinline__ uint64_t pick(const uint64_t (&x)[N], int q) {
+    uint64_t v = x[0];
+#pragma unroll
+    for (int a = 1; a < N; ++a) v = (q == a) ? x[a] : v;
+    return v;
 }
 
-// 32-bit signature of one factor (p, n): a multiply-xor hash, upper half.
-__device__ __forceinline__ uint32_t fsig(uint64_t p, uint64_t n) {
-    const uint64_t h = (p ^ (n * 0xD6E8FEB86659FD93ull)) * 0x9E3779B97F4A7C15ull;
-    return (uint32_t)(h >> 32);
+// 32-bit signature of word h of one factor (p, n): a multiply-xor hash, upper
+// half.  The signature of a factor is the XOR over its words.
+__device__ __forceinline__ uint32_t fsig(uint64_t p, uint64_t n, int h) {
+    const uint64_t k = h ? 0xC2B2AE3D27D4EB4Full : 0x9E3779B97F4A7C15ull;
+    const uint64_t x = (p ^ (n * 0xD6E8FEB86659FD93ull)) * k;
+    return (uint32_t)(x >> 32);
 }
 
 // GW: the term words stay in the walker's HBM slots (only the signatures are
 // in shared memory), else they are staged in shared memory for the launch.
 // PG: the walk policy is read from the descriptor (policies 1 and 2); without
 // it the plateau policy is compiled in alone.
-template <int MODE, bool GW, bool PG>
+// FW: 64-bit words per factor (1: factors of at most 64 coefficients, 2: at most 128).
+template <int MODE, bool GW, bool PG, int FW>
 struct WideWalker {
+    static_assert(FW == 1 || FW == 2, "one or two words per factor");
     static constexpr bool ZT = (MODE == TFG_MODE_ZT);
     __device__ __forceinline__ static int policy_of(const SegDesc &d) { return PG ? d.walk_policy : 0; }
-    static constexpr int NWG = ZT ? 6 : 3;   // words per slot in HBM (p0 p1 p2 [n0 n1 n2])
-    static constexpr int NWS = ZT ? 6 : 4;   // words per slot in shared memory (16-byte rows)
-    using T = FTerm<ZT>;
+    static constexpr int TW = 3 * FW;                          // words per sign
+    static constexpr int NWG = ZT ? 2 * TW : TW;               // words per slot in HBM (p words [n words])
+    static constexpr int NWS = ZT ? 2 * TW : (TW + 1) / 2 * 2; // words per slot in shared memory (16-byte rows)
+    static constexpr unsigned FM = (1u << FW) - 1u;            // a factor's lanes / words in a ballot
+    using T = FTerm<ZT, FW>;
 
-    uint64_t *W;    // GW: HBM slots [R][NWG] (p0 p1 p2 [n0 n1 n2]); else shared [R][NWS] factor-grouped: (p0 n0)(p1 n1)(p2 n2), Z_2: (p0 p1)(p2 -)
+    uint64_t *W;    // GW: HBM slots [R][NWG]; else shared [R][NWS]: Z_T (p_q n_q) pairs, Z_2 p words (padded)
     uint4 *SG;      // [32 * KM] signatures (u, v, w up to sign, sign of w)
     int lane, KM;
     int r, best_r, R;
@@ -79,56 +90,83 @@ struct WideWalker {
     int qlen, q0, q1, q2;
     uint32_t nnz, best_nnz;   // non-zero coefficients of the live (walk policy 2) / best scheme
 
+    // shared-memory word of HBM slot word g
+    __device__ __forceinline__ static int smem_word(int g) { return ZT ? (g < TW ? 2 * g : 2 * (g - TW) + 1) : g; }
+
     // ---- full-term comparisons (hit verification)
     __device__ __forceinline__ static bool eq(const T &a, const T &b, int f) {
-        return a.p[f] == b.p[f] && (!ZT || a.n[f] == b.n[f]);
+        bool e = true;
+#pragma unroll
+        for (int h = 0; h < FW; ++h) e = e && a.p[f * FW + h] == b.p[f * FW + h] && (!ZT || a.n[f * FW + h] == b.n[f * FW + h]);
+        return e;
     }
     __device__ __forceinline__ static bool eqneg(const T &a, const T &b, int f) {
-        return ZT && a.p[f] == b.n[f] && a.n[f] == b.p[f];
+        bool e = ZT;
+#pragma unroll
+        for (int h = 0; h < FW; ++h) e = e && a.p[f * FW + h] == b.n[f * FW + h] && a.n[f * FW + h] == b.p[f * FW + h];
+        return e;
     }
     __device__ __forceinline__ static bool sum_ok(const T &a, const T &b, int f, bool neg) {
         if constexpr (ZT) {
-            const uint64_t bp = neg ? b.n[f] : b.p[f], bn = neg ? b.p[f] : b.n[f];
-            return ((a.p[f] & bp) | (a.n[f] & bn)) == 0ull;
+            uint64_t clash = 0ull;
+#pragma unroll
+            for (int h = 0; h < FW; ++h) {
+                const int q = f * FW + h;
+                const uint64_t bp = neg ? b.n[q] : b.p[q], bn = neg ? b.p[q] : b.n[q];
+                clash |= (a.p[q] & bp) | (a.n[q] & bn);
+            }
+            return clash == 0ull;
         } else {
             return true;
         }
     }
-    __device__ __forceinline__ static uint4 sig(const T &a) {
-        uint4 s;
-        s.x = fsig(a.p[0], a.n[0]);
-        s.y = fsig(a.p[1], a.n[1]);
-        if constexpr (ZT) {
-            const uint64_t d = a.p[2] | a.n[2];
-            const bool ng = (a.n[2] & d & (0ull - d)) != 0ull;
-            s.z = fsig(ng ? a.n[2] : a.p[2], ng ? a.p[2] : a.n[2]);
-            s.w = ng ? 1u : 0u;
-        } else {
-            s.z = fsig(a.p[2], 0ull);
-            s.w = 0u;
+    // the first non-zero coefficient of factor f is negative
+    __device__ __forceinline__ static bool lead_neg(const T &a, int f) {
+        bool ng = false;
+#pragma unroll
+        for (int h = FW - 1; h >= 0; --h) {
+            const uint64_t d = a.p[f * FW + h] | a.n[f * FW + h];
+            ng = d ? ((a.n[f * FW + h] & d & (0ull - d)) != 0ull) : ng;
         }
+        return ng;
+    }
+    __device__ __forceinline__ static uint4 sig(const T &a) {
+        uint4 s = make_uint4(0u, 0u, 0u, 0u);
+        const bool ng = ZT && lead_neg(a, 2);
+#pragma unroll
+        for (int h = 0; h < FW; ++h) {
+            s.x ^= fsig(a.p[h], a.n[h], h);
+            s.y ^= fsig(a.p[FW + h], a.n[FW + h], h);
+            const uint64_t wp = a.p[2 * FW + h], wn = a.n[2 * FW + h];
+            s.z ^= fsig(ng ? wn : wp, ng ? wp : wn, h);
+        }
+        s.w = ng ? 1u : 0u;
         return s;
     }
 
-    // ---- one factor per lane: lane f < 3 holds factor f (lanes 3..31 mirror factor 0)
+    // ---- one word per lane: lane q < 3*FW holds word q (factor q / FW) of each
+    // term involved; lanes 3*FW..31 mirror word 0 and never store
     struct DF { uint64_t p, n; };
-    int fl;   // this lane's factor
+    int fq;   // this lane's word (0 on lanes 3*FW..31)
+    __device__ __forceinline__ bool owns(int f) const { return (lane >> (FW - 1)) == f; }   // holds a word of factor f
+    __device__ __forceinline__ int fh() const { return FW == 1 ? 0 : lane & 1; }         // its word within the factor
+    __device__ __forceinline__ bool fown() const { return lane < 3 * FW; }
 
-    __device__ __forceinline__ DF dof(const T &a) const { return DF{w_of(a.p, fl), w_of(a.n, fl)}; }
+    __device__ __forceinline__ DF dof(const T &a) const { return DF{pick(a.p, fq), pick(a.n, fq)}; }
     __device__ __forceinline__ DF dget(int s) const {
         if constexpr (GW) {
-            return DF{W[(size_t)s * NWG + fl], ZT ? W[(size_t)s * NWG + 3 + fl] : 0ull};
+            return DF{W[(size_t)s * NWG + fq], ZT ? W[(size_t)s * NWG + TW + fq] : 0ull};
         } else if constexpr (ZT) {
-            const ulonglong2 a = reinterpret_cast<const ulonglong2 *>(W + (size_t)s * NWS)[fl];
+            const ulonglong2 a = reinterpret_cast<const ulonglong2 *>(W + (size_t)s * NWS)[fq];
             return DF{a.x, a.y};
         } else {
-            return DF{W[(size_t)s * NWS + fl], 0ull};
+            return DF{W[(size_t)s * NWS + fq], 0ull};
         }
     }
     // res = a with factor f := a_f + b_f (neg: a_f - b_f); false when a
     // coefficient leaves the coefficient set (Section 3.5.2)
     __device__ __forceinline__ bool dadd(const DF &a, const DF &b, int f, bool neg, DF &res) const {
-        const bool me = lane == f;
+        const bool me = owns(f);
         bool bad = false;
         if constexpr (ZT) {
             const uint64_t bp = neg ? b.n : b.p, bn = neg ? b.p : b.n;
@@ -142,97 +180,136 @@ struct WideWalker {
         return !__any_sync(kFull, bad);
     }
     __device__ __forceinline__ bool dzero(const DF &a, int f) const {
-        return (__ballot_sync(kFull, (a.p | a.n) == 0ull) >> f) & 1u;
+        return ((__ballot_sync(kFull, (a.p | a.n) == 0ull) >> (f * FW)) & FM) == FM;
     }
     __device__ __forceinline__ void dtake(DF &dst, const DF &src, int f) const {
-        if (lane == f) dst = src;
+        if (owns(f)) dst = src;
+    }
+    // Sign flags of the leading coefficient of every factor: bit f*FW (of the
+    // returned ballot) is set when factor f's first non-zero coefficient is negative.
+    __device__ __forceinline__ unsigned dlead(const DF &a) const {
+        const uint64_t d = a.p | a.n;
+        const unsigned ng = __ballot_sync(kFull, (a.n & d & (0ull - d)) != 0ull);
+        if constexpr (FW == 1) {
+            return ng;
+        } else {
+            // a factor's second word decides only when its first word is zero
+            const unsigned nz = __ballot_sync(kFull, d != 0ull);
+            return (ng & nz & 0x15u) | ((ng >> 1) & ~nz & 0x15u);
+        }
     }
     // Section 3.6: first non-zero of u, then of v, made +1; w absorbs the signs
     __device__ __forceinline__ void dcanon(DF &a) const {
         if constexpr (ZT) {
-            const uint64_t d = a.p | a.n;
-            const unsigned neg = __ballot_sync(kFull, (a.n & d & (0ull - d)) != 0ull);
-            const bool f0 = neg & 1u, f1 = (neg >> 1) & 1u;
-            const bool sw = (lane == 0 && f0) || (lane == 1 && f1) || (lane == 2 && f0 != f1);
+            const unsigned neg = dlead(a);
+            const bool f0 = neg & 1u, f1 = (neg >> FW) & 1u;
+            const bool sw = (owns(0) && f0) || (owns(1) && f1) || (owns(2) && f0 != f1);
             const uint64_t p = sw ? a.n : a.p, n = sw ? a.p : a.n;
             a.p = p; a.n = n;
         }
     }
-    // non-zero coefficients of a term held one factor per lane
+    // non-zero coefficients of a term held one word per lane
     __device__ __forceinline__ uint32_t dnnz(const DF &a) const {
-        const uint32_t c = lane < 3 ? (uint32_t)__popcll(a.p | a.n) : 0u;
+        const uint32_t c = fown() ? (uint32_t)__popcll(a.p | a.n) : 0u;
         return __reduce_add_sync(kFull, c);
     }
     // w of a equals -w of b
     __device__ __forceinline__ bool dwneg(const DF &a, const DF &b) const {
-        return ZT && ((__ballot_sync(kFull, a.p == b.n && a.n == b.p) >> 2) & 1u);
+        return ZT && ((__ballot_sync(kFull, a.p == b.n && a.n == b.p) >> (2 * FW)) & FM) == FM;
     }
     __device__ __forceinline__ void dput(int s, const DF &a) {
         uint64_t cp = a.p, cn = a.n;
         uint32_t ng = 0u;
         if constexpr (ZT) {
-            const uint64_t d = a.p | a.n;
-            ng = (lane == 2 && (a.n & d & (0ull - d)) != 0ull) ? 1u : 0u;
-            if (ng) { cp = a.n; cn = a.p; }
+            if constexpr (FW == 1) {
+                const uint64_t d = a.p | a.n;
+                ng = (lane == 2 && (a.n & d & (0ull - d)) != 0ull) ? 1u : 0u;   // read by lane 2 alone
+            } else {
+                ng = (dlead(a) >> (2 * FW)) & 1u;
+            }
+            if (ng && owns(2)) { cp = a.n; cn = a.p; }
         }
-        const uint32_t h = fsig(cp, cn);
-        if (lane < 3) {
+        uint32_t h = fsig(cp, cn, fh());
+        if constexpr (FW == 2) h ^= __shfl_xor_sync(kFull, h, 1);   // the factor's two words
+        if (fown()) {
             if constexpr (GW) {
                 W[(size_t)s * NWG + lane] = a.p;
-                if constexpr (ZT) W[(size_t)s * NWG + 3 + lane] = a.n;
+                if constexpr (ZT) W[(size_t)s * NWG + TW + lane] = a.n;
             } else if constexpr (ZT) {
                 reinterpret_cast<ulonglong2 *>(W + (size_t)s * NWS)[lane] = make_ulonglong2(a.p, a.n);
             } else {
                 W[(size_t)s * NWS + lane] = a.p;
             }
-            uint32_t *g = reinterpret_cast<uint32_t *>(SG + s);
-            g[lane] = h;
-            if (lane == 2) g[3] = ng;
+            if (fh() == 0) {
+                uint32_t *g = reinterpret_cast<uint32_t *>(SG + s);
+                g[lane >> (FW - 1)] = h;
+                if (owns(2)) g[3] = ng;
+            }
         }
         __syncwarp();
     }
 
-    // ---- shared-memory slots
+    // ---- term slots
+    __device__ __forceinline__ static void set_word(T &out, int g, uint64_t v) {
+        if (g < TW) out.p[g] = v;
+        else out.n[g - TW] = v;
+    }
     __device__ __forceinline__ T get(int s) const {
         T out;
+        if constexpr (!ZT) {
+#pragma unroll
+            for (int q = 0; q < TW; ++q) out.n[q] = 0ull;
+        }
         if constexpr (GW) {
             const uint64_t *g = W + (size_t)s * NWG;
-            if constexpr (ZT) {
-                const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(g);   // 48-byte rows: 16-byte aligned
-                const ulonglong2 a = q[0], b = q[1], c = q[2];
-                out.p[0] = a.x; out.p[1] = a.y; out.p[2] = b.x;
-                out.n[0] = b.y; out.n[1] = c.x; out.n[2] = c.y;
+            if constexpr (NWG % 2 == 0) {
+                const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(g);   // rows of 16-byte multiples
+#pragma unroll
+                for (int e = 0; e < NWG / 2; ++e) {
+                    const ulonglong2 a = q[e];
+                    set_word(out, 2 * e, a.x);
+                    set_word(out, 2 * e + 1, a.y);
+                }
             } else {
-                out.p[0] = g[0]; out.p[1] = g[1]; out.p[2] = g[2];
-                out.n[0] = out.n[1] = out.n[2] = 0ull;
+#pragma unroll
+                for (int e = 0; e < NWG; ++e) set_word(out, e, g[e]);
             }
             return out;
         }
         const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(W + (size_t)s * NWS);
-        const ulonglong2 a = src[0], b = src[1];
-        if constexpr (ZT) {
-            const ulonglong2 c = src[2];
-            out.p[0] = a.x; out.n[0] = a.y;
-            out.p[1] = b.x; out.n[1] = b.y;
-            out.p[2] = c.x; out.n[2] = c.y;
-        } else {
-            out.p[0] = a.x; out.p[1] = a.y; out.p[2] = b.x;
-            out.n[0] = out.n[1] = out.n[2] = 0ull;
+#pragma unroll
+        for (int e = 0; e < NWS / 2; ++e) {
+            const ulonglong2 a = src[e];
+            if constexpr (ZT) {
+                out.p[e] = a.x; out.n[e] = a.y;
+            } else {
+                out.p[2 * e] = a.x;
+                if (2 * e + 1 < TW) out.p[2 * e + 1] = a.y;
+            }
         }
         return out;
     }
-    // factor f of slot s only (one 16-byte load in Z_T)
-    __device__ __forceinline__ void get_factor(int s, int f, uint64_t &p, uint64_t &n) const {
-        if constexpr (GW) {
-            p = W[(size_t)s * NWG + f];
-            n = ZT ? W[(size_t)s * NWG + 3 + f] : 0ull;
-        } else if constexpr (ZT) {
-            const ulonglong2 a = reinterpret_cast<const ulonglong2 *>(W + (size_t)s * NWS)[f];
-            p = a.x; n = a.y;
-        } else {
-            p = W[(size_t)s * NWS + f];
-            n = 0ull;
+    // factor f of slot s equals factor f of a (wneg: or its negation)
+    __device__ __forceinline__ bool fmatch(int s, int f, const T &a, bool wneg) const {
+        bool ep = true, en = ZT && wneg;
+#pragma unroll
+        for (int h = 0; h < FW; ++h) {
+            const int q = f * FW + h;
+            uint64_t p, n;
+            if constexpr (GW) {
+                p = W[(size_t)s * NWG + q];
+                n = ZT ? W[(size_t)s * NWG + TW + q] : 0ull;
+            } else if constexpr (ZT) {
+                const ulonglong2 x = reinterpret_cast<const ulonglong2 *>(W + (size_t)s * NWS)[q];
+                p = x.x; n = x.y;
+            } else {
+                p = W[(size_t)s * NWS + q];
+                n = 0ull;
+            }
+            ep = ep && p == a.p[q] && n == a.n[q];
+            en = en && p == a.n[q] && n == a.p[q];
         }
+        return ep || en;
     }
     __device__ __forceinline__ void move(int from, int to) {
         if constexpr (GW) {
@@ -376,7 +453,7 @@ struct WideWalker {
                 bestp[e] = W[e];
             } else {
                 const int s = e / NWG, g = e - s * NWG;
-                bestp[e] = W[(size_t)s * NWS + (ZT ? (g < 3 ? 2 * g : 2 * (g - 3) + 1) : g)];
+                bestp[e] = W[(size_t)s * NWS + smem_word(g)];
             }
         }
     }
@@ -441,7 +518,7 @@ struct WideWalker {
 
     __device__ __forceinline__ void run(const SegDesc &d, int64_t w, int32_t steps, unsigned char *sm) {
         lane = threadIdx.x & 31;
-        fl = lane < 3 ? lane : 0;
+        fq = lane < 3 * FW ? lane : 0;
         R = d.R;
         KM = (R + 31) >> 5;
         if constexpr (GW) {
@@ -466,7 +543,7 @@ struct WideWalker {
 #pragma unroll 1
             for (int e = lane; e < R * NWS; e += 32) {
                 const int s = e / NWS, q = e - s * NWS;
-                const int g = ZT ? ((q & 1) ? 3 + (q >> 1) : (q >> 1)) : q;   // source word of shared word q
+                const int g = ZT ? ((q & 1) ? TW + (q >> 1) : (q >> 1)) : q;   // source word of shared word q
                 W[e] = g < NWG ? src[(size_t)s * NWG + g] : 0ull;
             }
             __syncwarp();
@@ -480,7 +557,7 @@ struct WideWalker {
 #pragma unroll 1
             for (int s = lane; s < r; s += 32) {
                 const T v = get(s);
-                for (int x = 0; x < 3; ++x) mine += (uint32_t)__popcll(v.p[x] | v.n[x]);
+                for (int x = 0; x < TW; ++x) mine += (uint32_t)__popcll(v.p[x] | v.n[x]);
             }
             nnz = __reduce_add_sync(kFull, mine);
         }
@@ -524,19 +601,9 @@ struct WideWalker {
                     any &= any - 1u;
                     const uint32_t bit = 1u << k;
                     const int s = (k << 5) + lane;
-                    uint64_t p, n;
-                    if (bu & bit) {
-                        get_factor(s, 0, p, n);
-                        if (p != ti.p[0] || n != ti.n[0]) bu &= ~bit;
-                    }
-                    if (bv & bit) {
-                        get_factor(s, 1, p, n);
-                        if (p != ti.p[1] || n != ti.n[1]) bv &= ~bit;
-                    }
-                    if (bw & bit) {
-                        get_factor(s, 2, p, n);
-                        if (!((p == ti.p[2] && n == ti.n[2]) || (ZT && p == ti.n[2] && n == ti.p[2]))) bw &= ~bit;
-                    }
+                    if ((bu & bit) && !fmatch(s, 0, ti, false)) bu &= ~bit;
+                    if ((bv & bit) && !fmatch(s, 1, ti, false)) bv &= ~bit;
+                    if ((bw & bit) && !fmatch(s, 2, ti, true)) bw &= ~bit;
                 }
                 const uint32_t tot = __reduce_add_sync(kFull, (uint32_t)__popc(bu) | ((uint32_t)__popc(bv) << 10) |
                                                                   ((uint32_t)__popc(bw) << 20));
@@ -671,7 +738,7 @@ struct WideWalker {
 #pragma unroll 1
             for (int e = lane; e < R * NWG; e += 32) {
                 const int s = e / NWG, g = e - s * NWG;
-                dst[e] = W[(size_t)s * NWS + (ZT ? (g < 3 ? 2 * g : 2 * (g - 3) + 1) : g)];
+                dst[e] = W[(size_t)s * NWS + smem_word(g)];
             }
         }
         if (lane == 0) {
@@ -685,23 +752,24 @@ struct WideWalker {
     }
 };
 
-template <int MODE, bool GW>
+template <int MODE, bool GW, int FW>
 __host__ __device__ constexpr size_t wide_walker_bytes(int R) {
-    return (GW ? (size_t)0 : (size_t)R * (MODE == TFG_MODE_ZT ? 6 : 4) * 8) + (size_t)((R + 31) / 32) * 32 * 16;
+    return (GW ? (size_t)0 : (size_t)R * WideWalker<MODE, GW, false, FW>::NWS * 8) + (size_t)((R + 31) / 32) * 32 * 16;
 }
 
 constexpr int kWideWarps = 2;   // walkers (warps) per block
 
 // With the term words in HBM, registers bound residency: capped for 16
-// two-warp blocks per SM (measured +4-8% on ranks 285 and 351).
-template <int MODE, bool GW, bool PG>
-__global__ void __launch_bounds__(32 * kWideWarps, GW ? 16 : 1) walk_wide_kernel(const SegDesc d, const int32_t steps) {
+// two-warp blocks per SM with one word per factor (measured +4-8% on ranks 285
+// and 351), 8 with two.
+template <int MODE, bool GW, bool PG, int FW>
+__global__ void __launch_bounds__(32 * kWideWarps, GW ? 16 / FW : 1) walk_wide_kernel(const SegDesc d, const int32_t steps) {
     extern __shared__ __align__(16) unsigned char wide_sm[];
     const int warp = threadIdx.x >> 5;
     const int64_t w = (int64_t)blockIdx.x * kWideWarps + warp;
     if (w >= d.n_walkers) return;   // whole warps exit together
-    WideWalker<MODE, GW, PG> wk;
-    wk.run(d, w, steps, wide_sm + wide_walker_bytes<MODE, GW>(d.R) * warp);
+    WideWalker<MODE, GW, PG, FW> wk;
+    wk.run(d, w, steps, wide_sm + wide_walker_bytes<MODE, GW, FW>(d.R) * warp);
 }
 
 }  // namespace dev
@@ -713,51 +781,60 @@ constexpr int kWideMaxSmem = 227 * 1024;
 // Term words stay in HBM from this capacity on: shared-memory residency (22.8 KB
 // per walker at 354 slots) limits the larger ranks.  Measured on 16384 walkers:
 // rank 202 (capacity 205) 1.00e9 shared vs 0.98e9 HBM steps/s; rank 285: 0.69e9 vs
-// 0.85e9; rank 351: 0.46e9 vs 0.73e9.
-constexpr int kWideHbmWordsMinR = 256;
+// 0.85e9; rank 351: 0.46e9 vs 0.73e9.  Two words per factor double the bytes per
+// slot, so the switch comes at half the capacity.
+template <int FW>
+constexpr int wide_hbm_words_min_r() { return 256 / FW; }
 
-template <int MODE>
+template <int MODE, int FW>
 void prepare_walk_wide() {
     static bool attr = [] {
-        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
-        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
-        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
-        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
+        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, false, false, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
+        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, true, false, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
+        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, false, true, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
+        cudaFuncSetAttribute(dev::walk_wide_kernel<MODE, true, true, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideMaxSmem);
         return true;
     }();
     (void)attr;
 }
 
-template <int MODE, bool GW>
+template <int MODE, bool GW, int FW>
 void launch_wide_as(const SegDesc &d, int32_t steps, cudaStream_t st) {
-    const size_t smem = dev::wide_walker_bytes<MODE, GW>(d.R) * dev::kWideWarps;
+    const size_t smem = dev::wide_walker_bytes<MODE, GW, FW>(d.R) * dev::kWideWarps;
     if (d.n_walkers <= 0 || smem > (size_t)kWideMaxSmem) return;
     const int64_t grid = (d.n_walkers + dev::kWideWarps - 1) / dev::kWideWarps;
     if (d.walk_policy == 0)
-        dev::walk_wide_kernel<MODE, GW, false><<<(unsigned)grid, 32 * dev::kWideWarps, smem, st>>>(d, steps);
+        dev::walk_wide_kernel<MODE, GW, false, FW><<<(unsigned)grid, 32 * dev::kWideWarps, smem, st>>>(d, steps);
     else
-        dev::walk_wide_kernel<MODE, GW, true><<<(unsigned)grid, 32 * dev::kWideWarps, smem, st>>>(d, steps);
+        dev::walk_wide_kernel<MODE, GW, true, FW><<<(unsigned)grid, 32 * dev::kWideWarps, smem, st>>>(d, steps);
 }
 
-template <int MODE>
+template <int MODE, int FW>
 void launch_walk_wide(const SegDesc &d, int32_t steps, int /*grid*/, int /*block*/, cudaStream_t st) {
-    prepare_walk_wide<MODE>();
-    if (d.R >= kWideHbmWordsMinR) launch_wide_as<MODE, true>(d, steps, st);
-    else launch_wide_as<MODE, false>(d, steps, st);
+    prepare_walk_wide<MODE, FW>();
+    if (d.R >= wide_hbm_words_min_r<FW>()) launch_wide_as<MODE, true, FW>(d, steps, st);
+    else launch_wide_as<MODE, false, FW>(d, steps, st);
 }
 
 }  // namespace
 
-// Factor-aligned terms: 3 words of 64 bits per sign; capacity 1023 slots
-// (the shared-memory need of two walkers per block stays under 227 KB).
+// Factor-aligned terms: 3 (factors of at most 64 coefficients) or 6 (at most
+// 128) words of 64 bits per sign; capacity 1023 slots (the shared-memory need
+// of two walkers per block stays under 227 KB).
 const WalkVariant *walk_variants_wide(int *n) {
     static const WalkVariant v[] = {
-        WalkVariant{TFG_MODE_ZT, 64, 3, 32, 0, 0, &launch_walk_wide<TFG_MODE_ZT>,
-                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_ZT, true, false>), &prepare_walk_wide<TFG_MODE_ZT>,
-                    1023},
-        WalkVariant{TFG_MODE_Z2, 64, 3, 32, 0, 0, &launch_walk_wide<TFG_MODE_Z2>,
-                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_Z2, true, false>), &prepare_walk_wide<TFG_MODE_Z2>,
-                    1023},
+        WalkVariant{TFG_MODE_ZT, 64, 3, 32, 0, 0, &launch_walk_wide<TFG_MODE_ZT, 1>,
+                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_ZT, true, false, 1>),
+                    &prepare_walk_wide<TFG_MODE_ZT, 1>, 1023},
+        WalkVariant{TFG_MODE_Z2, 64, 3, 32, 0, 0, &launch_walk_wide<TFG_MODE_Z2, 1>,
+                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_Z2, true, false, 1>),
+                    &prepare_walk_wide<TFG_MODE_Z2, 1>, 1023},
+        WalkVariant{TFG_MODE_ZT, 64, 6, 32, 0, 0, &launch_walk_wide<TFG_MODE_ZT, 2>,
+                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_ZT, true, false, 2>),
+                    &prepare_walk_wide<TFG_MODE_ZT, 2>, 1023},
+        WalkVariant{TFG_MODE_Z2, 64, 6, 32, 0, 0, &launch_walk_wide<TFG_MODE_Z2, 2>,
+                    reinterpret_cast<const void *>(&dev::walk_wide_kernel<TFG_MODE_Z2, true, false, 2>),
+                    &prepare_walk_wide<TFG_MODE_Z2, 2>, 1023},
     };
     *n = (int)(sizeof(v) / sizeof(v[0]));
     return v;

@@ -92,6 +92,9 @@ CASES = {
     "walk_zt4512": lambda: walk_large("4512"),
     "walk_zt5610": lambda: walk_large("5610"),
     "walk_zt679": lambda: walk_large("679"),
+    "walk_zt982": lambda: walk((9, 8, 2), 0, walkers=16384, steps=300),
+    "walk_zt1111": lambda: walk((11, 11, 1), 0, walkers=16384, steps=300),
+    "walk_z2982": lambda: walk((9, 8, 2), 1, walkers=16384, steps=300),
     "mlp_score": mlp_score,
     "mlp_score_33m": lambda: mlp_score(rows=1 << 25),
     "mlp_grad": mlp_grad,

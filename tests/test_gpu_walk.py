@@ -223,6 +223,36 @@ def test_wide_terms_parity(case, mode):
     W.close()
 
 
+@pytest.mark.parametrize("policy", [0, 1, 2])
+@pytest.mark.parametrize("mode", [tfg.TFG_MODE_ZT, tfg.TFG_MODE_Z2])
+@pytest.mark.parametrize("case", ["9x1x8", "1x9x9", "11x11x1", "9x8x2", "2x9x8"])
+def test_two_word_factor_parity(case, mode, policy):
+    """Factors longer than 64 coefficients (two 64-bit words per factor and
+    sign): the long factor in each of the u, v and w positions; shared-memory
+    terms (ranks 72-121) and HBM terms (rank 144); the three walk policies."""
+    fmt = tuple(int(x) for x in case.split("x"))
+    if policy and case not in ("9x1x8", "9x8x2"):
+        pytest.skip("walk policies 1 and 2 on one shared-memory and one HBM case")
+    start = naive_start(*fmt)
+    if mode == tfg.TFG_MODE_Z2:
+        start = np.abs(start).astype(np.int8)
+    big = fmt[0] * fmt[1] * fmt[2] > 128
+    nw, steps, L = (16, 3000, 200) if big else (32, 1500, 150)
+    kw = dict(plateau_len=L, walk_policy=policy)
+    if policy == 1:
+        kw["expand_thresh"] = 1 << 27
+    W = gpu_walkers(fmt, mode, start, nw, 6, steps, chunks=2, **kw)
+    assert W.pop[0]["slots_per_lane"] == 0, "wide-term kernel expected"
+    info, slots, best = W.read_walkers(0, nw)
+    ref = oracle.Walkers(fmt, start, np.arange(nw), seed=6, mode=mode, plateau_len=L, policy=policy,
+                         expand_thresh=kw.get("expand_thresh", 0)).walk(steps, THREADS)
+    if policy == 0 and not big:
+        assert (ref.info["merges"] > 0).any() and (ref.info["plus"] > 0).any()
+    assert_parity(info, slots, best, ref, range(nw), f"two-word {fmt} mode={mode} policy={policy}")
+    assert W.verify_all() == 0
+    W.close()
+
+
 def test_graph_launch_equals_stream_launch_and_autotune_restores_state():
     """The mixed populations run as one captured graph (forked: one concurrent
     branch per format) or as plain launches on one stream: identical results.  The autotuner's
