@@ -153,7 +153,8 @@ def mapping_name(pop):
     if pop["slots_per_lane"] == 0:
         return "warp per walker, shared-memory signature search"
     if pop["lanes"] == 1:
-        return f"thread per walker, {pop['slots_per_lane']} slots"
+        sliced = ", bit-sliced slot search" if pop.get("slice_len") else ""
+        return f"thread per walker, {pop['slots_per_lane']} slots{sliced}"
     return f"{pop['lanes']} lanes x {pop['slots_per_lane']} slots"
 
 

@@ -290,8 +290,12 @@ int tfg_restore(tfg_ctx *ctx, const void *buf, size_t size);
  * Synchronous. */
 int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32_t *lanes_out);
 
-/* Mapping chosen for population f (lanes per walker G and slots per lane S). */
-int tfg_mapping(tfg_ctx *ctx, int32_t f, int32_t *lanes, int32_t *slots_per_lane);
+/* Mapping chosen for population f: lanes per walker G, slots per lane S (the
+ * slot capacity for one thread per walker; 0 for the warp-per-walker kernel),
+ * and slice_len > 0 when the thread-per-walker kernel also keeps the slots
+ * bit-sliced (one word per coefficient, bit k = slot k; formats whose factors
+ * have at most slice_len coefficients), else 0.  Each output may be NULL. */
+int tfg_mapping(tfg_ctx *ctx, int32_t f, int32_t *lanes, int32_t *slots_per_lane, int32_t *slice_len);
 
 /* Release the context (host memory only; the workspace stays the caller's). */
 void tfg_destroy(tfg_ctx *ctx);

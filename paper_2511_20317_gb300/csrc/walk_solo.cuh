@@ -101,10 +101,27 @@ struct SlotBits {
     }
 };
 
-template <int MODE, class Wd, int RMAX, int BT>
+// FL > 0: the walker also keeps its slots bit-sliced (formats whose factors
+// have at most FL coefficients, capacity <= 32): for factor f and coefficient
+// e a 32-bit word whose bit k is that coefficient of slot k (+1 in P, -1 in
+// N).  Comparing one factor of a term with every slot then costs a few word
+// operations per coefficient instead of a test per slot.  In Z_T the w
+// slices hold w up to sign (its first non-zero coefficient made +1) and one
+// more word the sign bits, so that the sign changes of the normalisation
+// (Section 3.6) touch one word and a flip rewrites the slices of one factor.
+template <int MODE, class Wd, int RMAX, int BT, int FL = 0>
 struct SoloWalker {
     static constexpr bool ZT = (MODE == TFG_MODE_ZT);
     static constexpr int NWS = ZT ? 2 : 1;   // words per slot (TW = 1)
+    static constexpr bool SL = FL > 0;
+    static_assert(!SL || (RMAX <= 32 && sizeof(Wd) == 4), "slices hold 32 slots of 32-bit packed terms");
+    static constexpr int NSL = 3 * FL;       // slices per sign
+    // Z_2: the slices in registers; Z_T: (P, N) pairs in shared memory [slice][thread],
+    // then the w sign word (row NSL, .x)
+    uint32_t S[(SL && !ZT) ? NSL : 1];
+    uint2 *ss;                               // Z_T: this thread's slice column, slice q at ss[q * BT]
+    int fb1, fb2;                            // bit offsets of v and w in a packed term
+    uint32_t lm0, lm1, lm2;                  // coefficient masks of u, v, w (low bits)
     using T = PTerm<Wd, 1, ZT>;
     using O = Ops<Wd, 1, ZT>;
     using M = Masks<Wd, 1>;
@@ -182,6 +199,141 @@ struct SoloWalker {
         } else {
             a[0] = v.p[0];
         }
+        if constexpr (SL) sl_put(k, v);
+    }
+    // store of a flipped term (factor f changed; see sl_put_flip)
+    __device__ __forceinline__ void st_flip(int k, const T &v, int f) {
+        Wd *a = sm + (size_t)k * RS;
+        if constexpr (ZT) {
+            if constexpr (sizeof(Wd) == 4) *reinterpret_cast<uint2 *>(a) = make_uint2(v.p[0], v.n[0]);
+            else *reinterpret_cast<ulonglong2 *>(a) = make_ulonglong2(v.p[0], v.n[0]);
+        } else {
+            a[0] = v.p[0];
+        }
+        if constexpr (SL) sl_put_flip(k, v, f);
+    }
+
+    // ---- bit slices (FL > 0)
+    // coefficients of factor f (compile-time) of packed word x, in the low bits
+    __device__ __forceinline__ uint32_t fx(uint32_t x, int f) const {
+        return f == 0 ? (x & lm0) : (f == 1 ? ((x >> fb1) & lm1) : ((x >> fb2) & lm2));
+    }
+    // all ones when bit e (compile-time) of y is set, else zero
+    __device__ __forceinline__ static uint32_t bc(uint32_t y, int e) {
+        return (uint32_t)((int32_t)(y << (31 - e)) >> 31);
+    }
+    // factor f (run-time) of packed word x, in the low bits
+    __device__ __forceinline__ uint32_t fx_rt(uint32_t x, int f) const {
+        const int sh = f == 0 ? 0 : (f == 1 ? fb1 : fb2);
+        const uint32_t m = f == 0 ? lm0 : (f == 1 ? lm1 : lm2);
+        return (x >> sh) & m;
+    }
+    // the first non-zero coefficient of the factor (xp, xn) is -1
+    __device__ __forceinline__ static bool lead_neg(uint32_t xp, uint32_t xn) {
+        const uint32_t d = xp | xn;
+        return (xn & d & (0u - d)) != 0u;
+    }
+    // slices of factor f (f compile-time, or run-time through base) at slot k := (xp, xn);
+    // w (f = 2) up to sign, its sign bit in the sign word
+    __device__ __forceinline__ void sl_write(uint2 *base, uint32_t kb, uint32_t xp, uint32_t xn) const {
+#pragma unroll
+        for (int e = 0; e < FL; ++e) {
+            uint2 w = base[e * BT];
+            w.x = (w.x & ~kb) | (bc(xp, e) & kb);
+            w.y = (w.y & ~kb) | (bc(xn, e) & kb);
+            base[e * BT] = w;
+        }
+    }
+    __device__ __forceinline__ void sl_sign(uint32_t kb, bool neg) const {
+        uint2 *g = ss + NSL * BT;
+        g->x = (g->x & ~kb) | (neg ? kb : 0u);
+    }
+    // slot k of every slice := term v
+    __device__ __forceinline__ void sl_put(int k, const T &v) {
+        const uint32_t kb = 1u << k;
+        if constexpr (ZT) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                uint32_t xp = fx((uint32_t)v.p[0], f), xn = fx((uint32_t)v.n[0], f);
+                if (f == 2) {
+                    const bool ng = lead_neg(xp, xn);
+                    sl_sign(kb, ng);
+                    if (ng) { const uint32_t t = xp; xp = xn; xn = t; }
+                }
+                sl_write(ss + f * FL * BT, kb, xp, xn);
+            }
+        } else {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const uint32_t xp = fx((uint32_t)v.p[0], f);
+#pragma unroll
+                for (int e = 0; e < FL; ++e) {
+                    const int q = f * FL + e;
+                    S[q] = (S[q] & ~kb) | (bc(xp, e) & kb);
+                }
+            }
+        }
+    }
+    // slot k := term v that differs from the slot's previous term in factor f
+    // (run-time) only, up to the sign changes of the normalisation (u and v
+    // keep their own signs; w's sign is one bit).  Z_2: every slice.
+    __device__ __forceinline__ void sl_put_flip(int k, const T &v, int f) {
+        if constexpr (ZT) {
+            const uint32_t kb = 1u << k;
+            uint32_t xp = fx_rt((uint32_t)v.p[0], f), xn = fx_rt((uint32_t)v.n[0], f);
+            const uint32_t wp = fx((uint32_t)v.p[0], 2), wn = fx((uint32_t)v.n[0], 2);
+            const bool ng = lead_neg(wp, wn);
+            sl_sign(kb, ng);
+            if (f == 2 && ng) { const uint32_t t = xp; xp = xn; xn = t; }
+            sl_write(ss + f * FL * BT, kb, xp, xn);
+        } else {
+            sl_put(k, v);
+        }
+    }
+    // Slots (any of the 32) whose u / v / w equal term a's: w either sign (mw)
+    // and w negated (mwn, Z_T).
+    __device__ __forceinline__ void sl_match(const T &a, uint32_t &mu, uint32_t &mv, uint32_t &mw,
+                                             uint32_t &mwn) const {
+        uint32_t du = 0, dv = 0, dw = 0;   // bit k: slot k differs
+        bool wneg = false;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            uint32_t xp = fx((uint32_t)a.p[0], f);
+            uint32_t xn = ZT ? fx((uint32_t)a.n[0], f) : 0u;
+            if (ZT && f == 2) {
+                wneg = lead_neg(xp, xn);
+                if (wneg) { const uint32_t t = xp; xp = xn; xn = t; }
+            }
+#pragma unroll
+            for (int e = 0; e < FL; ++e) {
+                const int q = f * FL + e;
+                uint32_t dd;
+                if constexpr (ZT) {
+                    const uint2 w = ss[q * BT];
+                    dd = (w.x ^ bc(xp, e)) | (w.y ^ bc(xn, e));
+                } else {
+                    dd = S[q] ^ bc(xp, e);
+                }
+                if (f == 0) du |= dd;
+                else if (f == 1) dv |= dd;
+                else dw |= dd;
+            }
+        }
+        mu = ~du;
+        mv = ~dv;
+        mw = ~dw;
+        if constexpr (ZT) mwn = mw & (ss[NSL * BT].x ^ (wneg ? ~0u : 0u));
+        else mwn = 0u;
+    }
+    // Any live slot other than i (j) sharing a factor pair with term a (b)?
+    __device__ __forceinline__ bool sl_pair_hit(const T &a, int i, const T &b, int j) const {
+        uint32_t mu, mv, mw, mwn;
+        sl_match(a, mu, mv, mw, mwn);
+        const uint32_t pa = ((mu & mv) | (mu & mw) | (mv & mw)) & ~(1u << i);
+        sl_match(b, mu, mv, mw, mwn);
+        const uint32_t pb = ((mu & mv) | (mu & mw) | (mv & mw)) & ~(1u << j);
+        const uint32_t live = r >= 32 ? ~0u : ((1u << r) - 1u);
+        return ((pa | pb) & live) != 0u;
     }
 
     // ---- reduction queue (slot indices)
@@ -310,6 +462,11 @@ struct SoloWalker {
     __device__ __forceinline__ bool coop_pair_hit(unsigned wmask, int lane, int nl, bool need, const T &ti2,
                                                   int i, const T &tj2, int j) const {
         unsigned pend = __ballot_sync(wmask, need);
+        if constexpr (SL) {
+            // per thread on the slices: ~2*3*FL (Z_2) / ~2*9*FL (Z_T) word operations
+            // against ~15 (Z_2) / ~20 (Z_T) per pending walker and slot for the lanes
+            if (__popc(pend) > (ZT ? 10 : 3)) return need && sl_pair_hit(ti2, i, tj2, j);
+        }
         if (__popc(pend) * 4 > RMAX * 3) return need && pair_hit2(ti2, i, tj2, j);
         bool mine = false;
         const int packed = i | (j << 10) | (r << 20);
@@ -501,6 +658,19 @@ struct SoloWalker {
         policy = d.walk_policy;
         best_nnz = H->best_nnz;
         mk.load(d);
+        if constexpr (SL) {
+            fb1 = d.fbase[1];
+            fb2 = d.fbase[2];
+            const int l0 = d.m * d.n, l1 = d.n * d.p, l2 = d.p * d.m;
+            lm0 = (1u << l0) - 1u;
+            lm1 = (1u << l1) - 1u;
+            lm2 = (1u << l2) - 1u;
+#pragma unroll
+            for (int q = 0; q < NSL + 1; ++q) {
+                if constexpr (ZT) ss[q * BT] = make_uint2(0u, 0u);
+                else if (q < NSL) S[q] = 0u;
+            }
+        }
         c_acc = c_rej = c_noc = c_drp = c_mrg = c_pls = c_red = 0;
         qlen = 0; q0 = q1 = q2 = 0;
         const Wd *src = reinterpret_cast<const Wd *>(d.slots) + (size_t)w * R * NWS;
@@ -562,8 +732,8 @@ struct SoloWalker {
         if (policy == 2) nnz += (zi ? 0u : nnz_of(ti2)) + (zj ? 0u : nnz_of(tj2)) - nnz_of(ti) - nnz_of(tj);
         O::canon(ti2, mk);
         O::canon(tj2, mk);
-        st(i, ti2);
-        st(j, tj2);
+        st_flip(i, ti2, Y);
+        st_flip(j, tj2, Z);
         qlen = 0;
         if (zi || zj) {
             q_push(i);
@@ -661,15 +831,22 @@ struct SoloWalker {
                 SlotBits<RMAX> mu, mv, mw, mwn;
                 mu.clear(); mv.clear(); mw.clear();
                 if constexpr (ZT) mwn.clear();
+                if constexpr (SL) {
+                    uint32_t a0, a1, a2, a3;
+                    sl_match(ti, a0, a1, a2, a3);
+                    mu.w[0] = a0; mv.w[0] = a1; mw.w[0] = a2;
+                    if constexpr (ZT) mwn.w[0] = a3;
+                } else {
 #pragma unroll
-                for (int k = 0; k < RMAX; ++k) {
-                    const T c = ld(k);
-                    bool eu, ev, ewp, ewn;
-                    O::compare(c, ti, mk, eu, ev, ewp, ewn);
-                    mu.set_if(k, eu);
-                    mv.set_if(k, ev);
-                    mw.set_if(k, ewp || ewn);
-                    if constexpr (ZT) mwn.set_if(k, ewn);
+                    for (int k = 0; k < RMAX; ++k) {
+                        const T c = ld(k);
+                        bool eu, ev, ewp, ewn;
+                        O::compare(c, ti, mk, eu, ev, ewp, ewn);
+                        mu.set_if(k, eu);
+                        mv.set_if(k, ev);
+                        mw.set_if(k, ewp || ewn);
+                        if constexpr (ZT) mwn.set_if(k, ewn);
+                    }
                 }
                 // keep live slots [0, r) other than i
                 mu.keep_live(r, i); mv.keep_live(r, i); mw.keep_live(r, i);
@@ -702,13 +879,21 @@ struct SoloWalker {
     }
 };
 
-template <int MODE, class Wd, int RMAX, int BT>
+template <int MODE, class Wd, int RMAX, int BT, int FL = 0>
+__host__ __device__ constexpr size_t solo_packed_bytes() {
+    return (size_t)RMAX * (BT + 1) * ((MODE == TFG_MODE_ZT) ? 2 : 1) * sizeof(Wd);
+}
+
+template <int MODE, class Wd, int RMAX, int BT, int FL = 0>
 __device__ __forceinline__ void walk_solo_body(const SegDesc &d, int32_t steps, unsigned char *smem_raw) {
     const int64_t w = (int64_t)blockIdx.x * BT + threadIdx.x;
     if (w >= d.n_walkers) return;   // no block-wide barrier is used
-    SoloWalker<MODE, Wd, RMAX, BT> wk;
+    SoloWalker<MODE, Wd, RMAX, BT, FL> wk;
     constexpr int NWS = (MODE == TFG_MODE_ZT) ? 2 : 1;
     wk.sm = reinterpret_cast<Wd *>(smem_raw) + (size_t)threadIdx.x * NWS;
+    if constexpr (FL > 0 && MODE == TFG_MODE_ZT)
+        wk.ss = reinterpret_cast<uint2 *>(smem_raw + ((solo_packed_bytes<MODE, Wd, RMAX, BT>() + 15) & ~(size_t)15)) +
+                threadIdx.x;
     wk.run(d, w, steps);
 }
 
@@ -726,38 +911,61 @@ __global__ void __launch_bounds__(BT, 4) walk_solo_kernel_occ4(const SegDesc d, 
     walk_solo_body<MODE, Wd, RMAX, BT>(d, steps, smem_raw);
 }
 
-template <int MODE, class Wd, int RMAX, int BT>
+// Bit-sliced variant (factors of at most FL coefficients, capacity 32).
+#ifndef TFG_SLICED_ZT_MIN_BLOCKS
+#define TFG_SLICED_ZT_MIN_BLOCKS 7
+#endif
+#ifndef TFG_SLICED_Z2_MIN_BLOCKS
+#define TFG_SLICED_Z2_MIN_BLOCKS 4
+#endif
+template <int MODE, class Wd, int RMAX, int BT, int FL>
+__global__ void __launch_bounds__(BT, MODE == TFG_MODE_ZT ? TFG_SLICED_ZT_MIN_BLOCKS : TFG_SLICED_Z2_MIN_BLOCKS)
+    walk_solo_kernel_sliced(const SegDesc d, const int32_t steps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    walk_solo_body<MODE, Wd, RMAX, BT, FL>(d, steps, smem_raw);
+}
+
+template <int MODE, class Wd, int RMAX, int BT, int FL = 0>
 constexpr auto solo_kernel() {
-    if constexpr (MODE == TFG_MODE_ZT && sizeof(Wd) == 4 && RMAX == 32) return &walk_solo_kernel_occ4<MODE, Wd, RMAX, BT>;
+    if constexpr (FL > 0) return &walk_solo_kernel_sliced<MODE, Wd, RMAX, BT, FL>;
+    else if constexpr (MODE == TFG_MODE_ZT && sizeof(Wd) == 4 && RMAX == 32) return &walk_solo_kernel_occ4<MODE, Wd, RMAX, BT>;
     else return &walk_solo_kernel<MODE, Wd, RMAX, BT>;
 }
 
 }  // namespace dev
 
-template <int MODE, class Wd, int RMAX, int BT>
+template <int MODE, class Wd, int RMAX, int BT, int FL = 0>
 constexpr size_t solo_smem_bytes() {
-    return (size_t)RMAX * (BT + 1) * ((MODE == TFG_MODE_ZT) ? 2 : 1) * sizeof(Wd);
+    const size_t packed = dev::solo_packed_bytes<MODE, Wd, RMAX, BT>();
+    if constexpr (FL > 0 && MODE == TFG_MODE_ZT) return ((packed + 15) & ~(size_t)15) + (size_t)(3 * FL + 1) * BT * 8;
+    else return packed;
 }
 
-template <int MODE, class Wd, int RMAX, int BT>
+template <int MODE, class Wd, int RMAX, int BT, int FL = 0>
 void prepare_walk_solo() {
     static bool attr = [] {
-        cudaFuncSetAttribute(dev::solo_kernel<MODE, Wd, RMAX, BT>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)solo_smem_bytes<MODE, Wd, RMAX, BT>());
+        cudaFuncSetAttribute(dev::solo_kernel<MODE, Wd, RMAX, BT, FL>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)solo_smem_bytes<MODE, Wd, RMAX, BT, FL>());
         return true;
     }();
     (void)attr;
 }
 
-template <int MODE, class Wd, int RMAX, int BT>
+template <int MODE, class Wd, int RMAX, int BT, int FL = 0>
 void launch_walk_solo(const SegDesc &d, int32_t steps, int grid, int /*block*/, cudaStream_t st) {
-    prepare_walk_solo<MODE, Wd, RMAX, BT>();
-    dev::solo_kernel<MODE, Wd, RMAX, BT>()<<<grid, BT, solo_smem_bytes<MODE, Wd, RMAX, BT>(), st>>>(d, steps);
+    prepare_walk_solo<MODE, Wd, RMAX, BT, FL>();
+    dev::solo_kernel<MODE, Wd, RMAX, BT, FL>()<<<grid, BT, solo_smem_bytes<MODE, Wd, RMAX, BT, FL>(), st>>>(d, steps);
 }
 
 #define TFG_SOLO_VARIANT(MODE, WD, BITS, RMAX, BT) \
     WalkVariant{MODE, BITS, 1, 1, RMAX, BT, &launch_walk_solo<MODE, WD, RMAX, BT>, \
                 reinterpret_cast<const void *>(dev::solo_kernel<MODE, WD, RMAX, BT>()), \
                 &prepare_walk_solo<MODE, WD, RMAX, BT>}
+
+// bit-sliced: formats whose factors have at most FL coefficients
+#define TFG_SOLO_SLICED_VARIANT(MODE, WD, BITS, RMAX, BT, FL) \
+    WalkVariant{MODE, BITS, 1, 1, RMAX, BT, &launch_walk_solo<MODE, WD, RMAX, BT, FL>, \
+                reinterpret_cast<const void *>(dev::solo_kernel<MODE, WD, RMAX, BT, FL>()), \
+                &prepare_walk_solo<MODE, WD, RMAX, BT, FL>, 0, FL}
 
 }  // namespace tfg

@@ -8,6 +8,7 @@ const WalkVariant *walk_variants_solo_z232(int *n) {
         TFG_SOLO_VARIANT(TFG_MODE_Z2, uint32_t, 32, 16, 128),
         TFG_SOLO_VARIANT(TFG_MODE_Z2, uint32_t, 32, 24, 128),
         TFG_SOLO_VARIANT(TFG_MODE_Z2, uint32_t, 32, 32, 128),
+        TFG_SOLO_SLICED_VARIANT(TFG_MODE_Z2, uint32_t, 32, 32, 128, 9),
     };
     *n = (int)(sizeof(v) / sizeof(v[0]));
     return v;

@@ -70,6 +70,8 @@ def test_parity_small_all_mappings(fmt, L, steps, nw, lanes, mode):
     start = naive_start(*fmt)
     W = gpu_walkers(fmt, mode, start, nw, seed, steps, chunks=3, plateau_len=L, mapping=lanes)
     assert W.pop[0]["lanes"] == lanes
+    # thread per walker: capacity 32 with factors of at most 9 coefficients is the bit-sliced kernel
+    assert W.pop[0]["slice_len"] == (9 if lanes == 1 and fmt == (3, 3, 3) else 0)
     info, slots, best = W.read_walkers(0, nw)
     ref = oracle.Walkers(fmt, start, np.arange(nw), seed=seed, mode=mode, plateau_len=L).walk(steps, THREADS)
     assert (ref.info["plus"] > 0).any() and (ref.info["merges"] > 0).any()
