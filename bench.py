@@ -27,7 +27,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "verified flips/sec and reductions per 1e9 flips at 1 GB300, learned vs uniform proposal"
-KERNEL_SRCS = [os.path.join(ROOT, "paper_2511_20317_gb300", "csrc", f) for f in ("walk_solo.cuh", "walk_group.cuh", "pterm.cuh")]
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2511_20317_gb300", "csrc", f)
+               for f in ("walk_solo.cuh", "walk_group.cuh", "pterm.cuh", "walk_solo_zt32.cu", "walk_solo_z232.cu")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "walk_kernel_333_dram_traffic.txt")
 
 # Algorithmic integer work per walker-step (word operations on 32-bit words):
@@ -312,7 +313,8 @@ def run_ours(args):
                      "collected_best_ranks": best_ranks},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
-                     "kernel": "walk_solo_kernel / walk_group_kernel", "walk_ms_per_step": sum(walk_ms) / len(walk_ms)},
+                     "kernel": "walk kernels of the step (" + "; ".join(p["mapping"] for p in per_mode.values()) + ")",
+                     "walk_ms_per_step": sum(walk_ms) / len(walk_ms)},
         "e2e": {"value": e2e_val, "unit": "flips/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h // e2e_steps},
         "gpu_launches": (2 * W.n_formats + 2 * W.n_formats) * args.steps,
@@ -417,7 +419,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=50_000)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--mapping", type=int, default=0)
-    ap.add_argument("--graph", type=int, default=1, help="0 plain launches, 1 chained graph, 2 forked graph")
+    ap.add_argument("--graph", type=int, default=2, help="0 plain launches, 1 chained graph, 2 forked graph (default: the two populations run concurrently)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-learned", dest="learned", action="store_false")
