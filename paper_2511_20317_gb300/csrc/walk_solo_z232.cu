@@ -1,6 +1,10 @@
 // Thread-per-walker walk kernel variants (z232), 128 threads per block.
 #include "walk_solo.cuh"
 
+#ifndef TFG_SLICED_Z2_BLOCK
+#define TFG_SLICED_Z2_BLOCK 128   // threads per block of the bit-sliced kernel (register slices)
+#endif
+
 namespace tfg {
 const WalkVariant *walk_variants_solo_z232(int *n) {
     static const WalkVariant v[] = {
@@ -8,7 +12,7 @@ const WalkVariant *walk_variants_solo_z232(int *n) {
         TFG_SOLO_VARIANT(TFG_MODE_Z2, uint32_t, 32, 16, 128),
         TFG_SOLO_VARIANT(TFG_MODE_Z2, uint32_t, 32, 24, 128),
         TFG_SOLO_VARIANT(TFG_MODE_Z2, uint32_t, 32, 32, 128),
-        TFG_SOLO_SLICED_VARIANT(TFG_MODE_Z2, uint32_t, 32, 32, 128, 9),
+        TFG_SOLO_SLICED_VARIANT(TFG_MODE_Z2, uint32_t, 32, 32, TFG_SLICED_Z2_BLOCK, 9),
     };
     *n = (int)(sizeof(v) / sizeof(v[0]));
     return v;

@@ -80,6 +80,27 @@ def test_parity_small_all_mappings(fmt, L, steps, nw, lanes, mode):
     W.close()
 
 
+@pytest.mark.parametrize("mode", [tfg.TFG_MODE_ZT, tfg.TFG_MODE_Z2])
+@pytest.mark.parametrize("fmt", [(2, 3, 3), (3, 2, 3), (3, 3, 2), (1, 3, 3)])
+def test_bit_sliced_kernel_uneven_factors(fmt, mode):
+    """The bit-sliced thread-per-walker kernel on formats whose factors are
+    shorter than the slice length (6 or 3 of 9 coefficients, factor offsets
+    that are not multiples of 9); the slack lifts the capacity to 32."""
+    start = naive_start(*fmt)
+    if mode == tfg.TFG_MODE_Z2:
+        start = np.abs(start).astype(np.int8)
+    nw, steps, L = 160, 3000, 150
+    slack = 32 - start.shape[0]
+    W = gpu_walkers(fmt, mode, start, nw, 21, steps, chunks=2, plateau_len=L, r_slack=slack, mapping=1)
+    assert W.pop[0]["slice_len"] == 9 and W.pop[0]["r_max"] == 32
+    info, slots, best = W.read_walkers(0, nw)
+    ref = oracle.Walkers(fmt, start, np.arange(nw), seed=21, mode=mode, plateau_len=L, r_slack=slack).walk(steps, THREADS)
+    assert (ref.info["accepted"] > 0).all() and (ref.info["plus"] > 0).any()
+    assert_parity(info, slots, best, ref, range(nw), f"sliced {fmt} mode={mode}")
+    assert W.verify_all() == 0
+    W.close()
+
+
 def test_parity_222_full_workload_all_walkers():
     """(2,2,2) Z_T from the naive rank-8 scheme: 1024 walkers x 1e5 steps,
     plateau 1e4; every walker replayed by the oracle."""
