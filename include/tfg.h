@@ -263,6 +263,51 @@ int tfg_stats_get(tfg_ctx *ctx, int32_t format_idx, tfg_stats *out, int64_t *ran
  * TFG_EINVAL for a bad range.  Ordered on the context stream and synchronous. */
 int tfg_reseed(tfg_ctx *ctx, int64_t first, int64_t count, int32_t rank, const int8_t *scheme);
 
+/* Resize on the device (the Resize kernel of the paper's exploratory search,
+ * Section 3.4, with the meta operators of Section 3.3.2): walker
+ * src_first + k (k < count; global ids, all in one population) has its live
+ * scheme (use_best = 0) or its best scheme (1) transformed by one operator,
+ * and the result replaces the live and best schemes of walker dst_first + k
+ * (another population, whose format must be the operator's result format and
+ * whose mode must be the source's).  Operators (op):
+ *   TFG_RESIZE_PROJECT  axis, index: remove row/column `index` along axis
+ *                       (0: rows of A and C, 1: columns of A / rows of B,
+ *                       2: columns of B and C); terms with a zero factor go
+ *   TFG_RESIZE_EXTEND   axis: merge with the naive scheme of the missing block
+ *   TFG_RESIZE_DOUBLE   axis: merge the scheme with itself
+ *   TFG_RESIZE_MERGE    axis: block concatenation with the aux scheme
+ *   TFG_RESIZE_PRODUCT  Kronecker product with the aux scheme (source terms
+ *                       outer, aux terms inner)
+ *   TFG_RESIZE_SWAP     index = perm: the sizes reordered as
+ *                       (fmt[a] for a in ((0,1,2),(0,2,1),(1,0,2),(1,2,0),(2,0,1),(2,1,0))[perm])
+ * Term order follows the host meta operators (source terms, then the second
+ * block); Z_T results are sign-normalised (Section 3.6).  No reduction pass is
+ * run: the result is a valid scheme, reduced later by the walk.  The
+ * destination record restarts like tfg_reseed (rank = best rank = the result's
+ * rank, plateau 0, best step = its step count, best_nnz); walker id, step
+ * count, counters and digest continue.  A walker whose result would exceed the
+ * destination's r_max is left unchanged and counted in *skipped (then the
+ * call returns TFG_ENOSPC).  The aux scheme (host rows, aux_fmt, the source's
+ * mode) must satisfy Eq. (1).  d_scratch: caller device memory of at least
+ * tfg_resize_scratch_bytes(...) bytes (maps, the aux scheme, a counter).
+ * Ordered on the context stream and synchronous. */
+#define TFG_RESIZE_PROJECT 0
+#define TFG_RESIZE_EXTEND  1
+#define TFG_RESIZE_DOUBLE  2
+#define TFG_RESIZE_MERGE   3
+#define TFG_RESIZE_PRODUCT 4
+#define TFG_RESIZE_SWAP    5
+typedef struct tfg_resize_args {
+    int32_t op, axis, index, use_best;
+    int64_t src_first, dst_first, count;
+    tfg_format aux_fmt;          /* TFG_RESIZE_MERGE / TFG_RESIZE_PRODUCT */
+    int32_t aux_rank;
+    int32_t pad;
+    const int8_t *aux_scheme;    /* host rows [aux_rank][LT of aux_fmt] */
+} tfg_resize_args;
+size_t tfg_resize_scratch_bytes(int32_t aux_rank, const tfg_format *aux_fmt, const tfg_format *out_fmt);
+int tfg_resize(tfg_ctx *ctx, const tfg_resize_args *args, void *d_scratch, size_t scratch_bytes, int64_t *skipped);
+
 /* Copy walkers [first, first+count) (context-global positions) to the host:
  * info[count]; slots and best (either may be NULL) as int8 schemes of
  * [count][r_max][LT] of that walker's population (all walkers of the range

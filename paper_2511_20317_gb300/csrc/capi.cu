@@ -777,6 +777,109 @@ int tfg_reseed(tfg_ctx *ctx, int64_t first, int64_t count, int32_t rank, const i
     return TFG_OK;
 }
 
+// ---- device resize (resize.cu): scratch = [skip counter][maps int16][aux int8]
+static size_t resize_maps_bytes(const tfg_format &out) {
+    return ((size_t)2 * tfg::host::term_len(out) * sizeof(int16_t) + 15) & ~(size_t)15;
+}
+
+size_t tfg_resize_scratch_bytes(int32_t aux_rank, const tfg_format *aux_fmt, const tfg_format *out_fmt) {
+    if (!out_fmt || out_fmt->m < 1 || out_fmt->n < 1 || out_fmt->p < 1) return 0;
+    const tfg_format &o = *out_fmt;
+    // the naive block of an extension has at most max(mn, np, pm) terms of at most LT(out) coefficients
+    const size_t naive = (size_t)std::max(o.m * o.n, std::max(o.n * o.p, o.p * o.m)) * tfg::host::term_len(o);
+    const size_t aux = aux_fmt && aux_rank > 0 ? (size_t)aux_rank * tfg::host::term_len(*aux_fmt) : 0;
+    return 16 + resize_maps_bytes(o) + std::max(naive, aux);
+}
+
+int tfg_resize(tfg_ctx *ctx, const tfg_resize_args *a, void *d_scratch, size_t scratch_bytes, int64_t *skipped) {
+    if (skipped) *skipped = 0;
+    if (!ctx || !a || !d_scratch) { set_error("null argument"); return TFG_EINVAL; }
+    if (a->count < 1 || a->src_first < 0 || a->dst_first < 0 || a->src_first + a->count > ctx->total ||
+        a->dst_first + a->count > ctx->total) {
+        set_error("walker range out of bounds");
+        return TFG_EINVAL;
+    }
+    const Segment *sp = nullptr, *dp = nullptr;
+    for (const Segment &s : ctx->segs) {
+        if (a->src_first >= s.first && a->src_first + a->count <= s.first + s.n) sp = &s;
+        if (a->dst_first >= s.first && a->dst_first + a->count <= s.first + s.n) dp = &s;
+    }
+    if (!sp || !dp) { set_error("a walker range spans several populations"); return TFG_EINVAL; }
+    if (sp == dp && a->src_first < a->dst_first + a->count && a->dst_first < a->src_first + a->count) {
+        set_error("source and destination walkers overlap");
+        return TFG_EINVAL;
+    }
+    if (sp->fmt.mode != dp->fmt.mode) { set_error("source and destination modes differ"); return TFG_EINVAL; }
+    if (a->use_best != 0 && a->use_best != 1) { set_error("use_best must be 0 or 1"); return TFG_EINVAL; }
+    const bool with_aux = a->op == TFG_RESIZE_MERGE || a->op == TFG_RESIZE_PRODUCT;
+    tfg_format aux_fmt = a->aux_fmt;
+    if (with_aux) {
+        if (!a->aux_scheme || a->aux_rank < 1) { set_error("the operator needs an aux scheme"); return TFG_EINVAL; }
+        if (aux_fmt.mode != sp->fmt.mode) { set_error("aux mode differs from the populations'"); return TFG_EINVAL; }
+        int rc = tfg::host::check_input(&aux_fmt, a->aux_rank, a->aux_scheme);
+        if (rc) return rc;
+    }
+    tfg::ResizePlan plan;
+    std::vector<int16_t> maps;
+    tfg_format out{};
+    if (!tfg::build_resize_plan(a->op, a->axis, a->index, sp->fmt, with_aux ? &aux_fmt : nullptr, a->aux_rank, out,
+                                plan, maps)) {
+        set_error("unsupported resize operator or argument for the source format");
+        return TFG_EINVAL;
+    }
+    if (out.m != dp->fmt.m || out.n != dp->fmt.n || out.p != dp->fmt.p) {
+        set_error("the result format (" + std::to_string(out.m) + "," + std::to_string(out.n) + "," +
+                  std::to_string(out.p) + ") is not the destination population's");
+        return TFG_EINVAL;
+    }
+    if (!tfg::host::format_ok(&out)) { set_error("result format too large"); return TFG_EINVAL; }
+    // aux rows: the caller's scheme, or the naive scheme of an extension's block (terms in (i, k, j) order)
+    std::vector<int8_t> aux_rows;
+    if (with_aux) {
+        aux_rows.assign(a->aux_scheme, a->aux_scheme + (size_t)a->aux_rank * tfg::host::term_len(aux_fmt));
+    } else if (a->op == TFG_RESIZE_EXTEND) {
+        const int bm = a->axis == 0 ? 1 : sp->fmt.m, bn = a->axis == 1 ? 1 : sp->fmt.n, bp = a->axis == 2 ? 1 : sp->fmt.p;
+        const int lt = bm * bn + bn * bp + bp * bm;
+        for (int i = 0; i < bm; ++i)
+            for (int k = 0; k < bn; ++k)
+                for (int j = 0; j < bp; ++j) {
+                    std::vector<int8_t> row((size_t)lt, 0);
+                    row[(size_t)i * bn + k] = 1;
+                    row[(size_t)bm * bn + k * bp + j] = 1;
+                    row[(size_t)bm * bn + bn * bp + j * bm + i] = 1;
+                    aux_rows.insert(aux_rows.end(), row.begin(), row.end());
+                }
+    }
+    const size_t need = tfg_resize_scratch_bytes(a->aux_rank, with_aux ? &aux_fmt : nullptr, &out);
+    if (scratch_bytes < need || aux_rows.size() + 16 + resize_maps_bytes(out) > scratch_bytes) {
+        set_error("scratch holds " + std::to_string(scratch_bytes) + " bytes, the resize needs " + std::to_string(need));
+        return TFG_ENOSPC;
+    }
+    if (maps.size() * sizeof(int16_t) > resize_maps_bytes(out)) { set_error("internal: map table"); return TFG_EINTERNAL; }
+    char *sc = static_cast<char *>(d_scratch);
+    auto *d_skip = reinterpret_cast<unsigned long long *>(sc);
+    plan.maps = reinterpret_cast<const int16_t *>(sc + 16);
+    plan.aux = reinterpret_cast<const int8_t *>(sc + 16 + resize_maps_bytes(out));
+    plan.use_best = a->use_best;
+    cudaError_t e = cudaMemsetAsync(d_skip, 0, sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sc + 16, maps.data(), maps.size() * sizeof(int16_t), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && !aux_rows.empty())
+        e = cudaMemcpyAsync(sc + 16 + resize_maps_bytes(out), aux_rows.data(), aux_rows.size(), cudaMemcpyHostToDevice,
+                            ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "resize staging");
+    tfg::launch_resize(ctx->desc(*sp), a->src_first - sp->first, ctx->desc(*dp), a->dst_first - dp->first, a->count,
+                       plan, d_skip, ctx->stream);
+    e = cudaGetLastError();
+    unsigned long long sk = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&sk, d_skip, sizeof(sk), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "resize");
+    if (skipped) *skipped = (int64_t)sk;
+    if (sk) { set_error(std::to_string(sk) + " walkers left unchanged: result above the destination's r_max"); return TFG_ENOSPC; }
+    return TFG_OK;
+}
+
 int tfg_read_walkers(tfg_ctx *ctx, int64_t first, int64_t count, tfg_walker_info *info, int8_t *slots, int8_t *best,
                      int32_t r_max_cap) {
     if (!ctx || first < 0 || count < 0 || first + count > ctx->total) { set_error("walker range out of bounds"); return TFG_EINVAL; }

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/tfg.h"
@@ -54,6 +55,33 @@ struct WalkVariant {
     int fl = 0;          // > 0: formats whose factors have at most fl coefficients only (bit-sliced)
     int capacity() const { return cap ? cap : (G == 1 ? S : G * S); }
 };
+
+// Device resize (resize.cu): output terms come in at most two blocks; a block
+// takes source terms (kResizeSrc), aux terms (kResizeAux) or source x aux
+// pairs (kResizeProduct, source outer); maps[map_a + e] / maps[map_b + e] give
+// the source / aux row index of output coefficient e (-1: zero).
+enum : int32_t { kResizeSrc = 1, kResizeAux = 2, kResizeProduct = 3 };
+constexpr int kResizeMaxTerms = 1024;
+struct ResizeBlock {
+    int32_t kind, map_a, map_b;
+};
+struct ResizePlan {
+    ResizeBlock blk[2];
+    int32_t nblk;
+    int32_t lt_src, mn_src, np_src;   // source row layout (u | v | w)
+    int32_t lt_out, mn_out, np_out;   // result row layout
+    int32_t lt_aux, aux_rank;
+    int32_t canon;       // Z_T: restore the sign normalisation
+    int32_t drop_zero;   // remove terms with a zero factor
+    int32_t use_best;    // source: best scheme instead of the live one
+    const int16_t *maps; // device
+    const int8_t *aux;   // device [aux_rank][lt_aux]
+};
+bool build_resize_plan(int op, int axis, int index, const tfg_format &src, const tfg_format *aux, int aux_rank,
+                       tfg_format &out, ResizePlan &plan, std::vector<int16_t> &maps);
+size_t resize_smem_bytes(const ResizePlan &plan);
+void launch_resize(const SegDesc &src, int64_t src_first, const SegDesc &dst, int64_t dst_first, int64_t count,
+                   const ResizePlan &plan, unsigned long long *d_skipped, cudaStream_t st);
 
 // Registry of compiled variants (filled by the instantiation units).
 const WalkVariant *walk_variants(int *count);

@@ -41,6 +41,16 @@ class tfg_params(ctypes.Structure):
                 ("expand_thresh", ctypes.c_uint32), ("reserved", ctypes.c_int32 * 2)]
 
 
+class tfg_resize_args(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("axis", ctypes.c_int32), ("index", ctypes.c_int32),
+                ("use_best", ctypes.c_int32), ("src_first", ctypes.c_int64), ("dst_first", ctypes.c_int64),
+                ("count", ctypes.c_int64), ("aux_fmt", tfg_format), ("aux_rank", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("aux_scheme", ctypes.c_void_p)]
+
+
+TFG_RESIZE_PROJECT, TFG_RESIZE_EXTEND, TFG_RESIZE_DOUBLE, TFG_RESIZE_MERGE, TFG_RESIZE_PRODUCT, TFG_RESIZE_SWAP = range(6)
+
+
 class tfg_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("walkers", "steps", "accepted", "rejected", "nocand", "drops",
                                               "merges", "plus", "reductions")] + \
@@ -68,7 +78,8 @@ EXPORTED = ["tfg_default_params", "tfg_last_error", "tfg_verify", "tfg_additive_
             "tfg_lift_signs", "tfg_canonicalize",
             "tfg_prepare", "tfg_project", "tfg_extend", "tfg_merge", "tfg_double", "tfg_product",
             "tfg_swap_sizes", "tfg_workspace_size", "tfg_init", "tfg_walk", "tfg_sync", "tfg_collect_best",
-            "tfg_verify_all_async", "tfg_stats_get", "tfg_read_walkers", "tfg_reseed", "tfg_population",
+            "tfg_verify_all_async", "tfg_stats_get", "tfg_read_walkers", "tfg_reseed", "tfg_resize_scratch_bytes",
+            "tfg_resize", "tfg_population",
             "tfg_checkpoint",
             "tfg_restore", "tfg_mapping", "tfg_autotune", "tfg_destroy", "tfg_philox_device", "tfg_mlp_param_bytes",
             "tfg_mlp_score", "tfg_mlp_grad", "tfg_mlp_train_state_bytes", "tfg_mlp_train_init",
@@ -115,6 +126,8 @@ def lib() -> ctypes.CDLL:
                 "tfg_stats_get": (i32, [P, i32, ctypes.POINTER(tfg_stats), P, i32]),
                 "tfg_read_walkers": (i32, [P, i64, i64, P, P, P, i32]),
                 "tfg_reseed": (i32, [P, i64, i64, i32, P]),
+                "tfg_resize_scratch_bytes": (sz, [i32, F, F]),
+                "tfg_resize": (i32, [P, ctypes.POINTER(tfg_resize_args), P, sz, ctypes.POINTER(ctypes.c_int64)]),
                 "tfg_population": (i32, [P, i32, F, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
                 "tfg_checkpoint": (i32, [P, P, sz, ctypes.POINTER(sz)]),
@@ -511,6 +524,41 @@ class Walkers:
         return self
 
     reseed = tfg_reseed
+
+    def tfg_resize(self, op: int, src_first: int, dst_first: int, count: int, axis: int = 0, index: int = 0,
+                   aux=None, use_best: bool = False) -> int:
+        """Device resize: walkers [src_first, +count) transformed by meta operator `op`
+        (TFG_RESIZE_*) into walkers [dst_first, +count) of the result format's
+        population; aux = (fmt, scheme) for merge / product.  Returns the number of
+        walkers left unchanged because their result exceeds the destination's r_max
+        (the library's TFG_ENOSPC); every other error raises TfgError."""
+        a = tfg_resize_args()
+        a.op, a.axis, a.index, a.use_best = int(op), int(axis), int(index), int(bool(use_best))
+        a.src_first, a.dst_first, a.count = int(src_first), int(dst_first), int(count)
+        rows = None
+        src_mode = next(p["mode"] for p in self.pop if p["first"] <= src_first < p["first"] + p["walkers"])
+        if aux is not None:
+            afmt, ascheme = aux
+            rows = _rows(tuple(afmt), ascheme)
+            a.aux_fmt = tfg_format(*afmt, src_mode)
+            a.aux_rank = rows.shape[0]
+            a.aux_scheme = rows.ctypes.data
+        dst = next(p for p in self.pop if p["first"] <= dst_first < p["first"] + p["walkers"])
+        out = tfg_format(*dst["fmt"], dst["mode"])
+        need = lib().tfg_resize_scratch_bytes(a.aux_rank, ctypes.byref(a.aux_fmt) if rows is not None else None,
+                                              ctypes.byref(out))
+        torch = self.torch
+        if getattr(self, "_rscratch", None) is None or self._rscratch.numel() < need:
+            self._rscratch = torch.empty(max(int(need), 1), dtype=torch.uint8, device="cuda")
+        skipped = ctypes.c_int64(0)
+        rc = lib().tfg_resize(self.ctx, ctypes.byref(a), ctypes.c_void_p(self._rscratch.data_ptr()),
+                              self._rscratch.numel(), ctypes.byref(skipped))
+        if rc == TFG_ENOSPC and skipped.value > 0:
+            return int(skipped.value)
+        _check(rc)
+        return 0
+
+    resize = tfg_resize
 
     def tfg_walk_window(self, steps: int, policy: int = 0, mlp_params=None, eps_thresh: int = 0,
                         record_choices: bool = False, log=None):
