@@ -45,6 +45,23 @@ def walk_large(which, walkers=16384, steps=300):
     return walk(fmt, 0, walkers=walkers, steps=steps, start=start)
 
 
+def resize(op_name="extend", walkers=65536):
+    """Device resize of a whole (3,3,3) population (walked 2000 steps) into a
+    (3,3,4) population (extend along p) or a (3,3,3) population (size swap)."""
+    src = (3, 3, 3)
+    op, dst, kw = {"extend": (tfg.TFG_RESIZE_EXTEND, (3, 3, 4), {"axis": 2}),
+                   "swap": (tfg.TFG_RESIZE_SWAP, (3, 3, 3), {"index": 3})}[op_name]
+    pops = [(src, 0, naive_start(*src), walkers), (dst, 0, naive_start(*dst), walkers)]
+    W = tfg.Walkers(pops, seed=0, params=tfg.tfg_default_params(plateau_len=50_000, r_slack=8, use_graph=0))
+    W.walk(2000).sync()
+    first = W.pop[1]["first"]
+    W.resize(op, 0, first, walkers, **kw)
+    t0 = time.perf_counter()   # the call is synchronous: host plan, staging, kernel
+    W.resize(op, 0, first, walkers, **kw)
+    ms = (time.perf_counter() - t0) * 1e3
+    return {"walkers": walkers, "ms": ms, "walkers_per_s": walkers / ms * 1e3}
+
+
 def mlp_score(rows=1 << 20):
     import torch
     rng = np.random.default_rng(0)
@@ -95,6 +112,8 @@ CASES = {
     "walk_zt982": lambda: walk((9, 8, 2), 0, walkers=16384, steps=300),
     "walk_zt1111": lambda: walk((11, 11, 1), 0, walkers=16384, steps=300),
     "walk_z2982": lambda: walk((9, 8, 2), 1, walkers=16384, steps=300),
+    "resize_extend_333": lambda: resize("extend"),
+    "resize_swap_333": lambda: resize("swap"),
     "mlp_score": mlp_score,
     "mlp_score_33m": lambda: mlp_score(rows=1 << 25),
     "mlp_grad": mlp_grad,

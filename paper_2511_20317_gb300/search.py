@@ -218,11 +218,80 @@ def resize_move(rng, fmt, scheme, bests, p_resize=0.5):
     return f2, s2, "+".join(ops + [op])
 
 
+def device_resize_move(rng, W, formats, index, bests, block, next_block, p_resize=0.5):
+    """One Resize move on the device (the paper's Resize kernel, applied per
+    walker): a block of one population's walkers, from their best schemes,
+    transformed by one operator into the next block of the population of the
+    result format.  Operator choice as in resize_move: a size swap with
+    probability 1/2, else a merge with another population's best when the sizes
+    agree, else with probability p_resize project 5% / product 50% /
+    double 30% / extend 15%.  Returns a log entry or None."""
+    src = formats[int(rng.integers(len(formats)))]
+    keys = list(bests)
+    aux, axis, index_arg = None, 0, 0
+    if rng.random() < 0.5:
+        op, index_arg = tfg.TFG_RESIZE_SWAP, int(rng.integers(1, 6))
+        order = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)][index_arg]
+        dst = tuple(src[a] for a in order)
+        name = f"swap{index_arg}"
+    else:
+        other = keys[int(rng.integers(len(keys)))]
+        axes = [a for a in range(3) if all(src[b] == other[b] for b in range(3) if b != a)]
+        if axes:
+            axis = axes[int(rng.integers(len(axes)))]
+            op, aux = tfg.TFG_RESIZE_MERGE, (other, bests[other])
+            dst = tuple(src[b] + (other[b] if b == axis else 0) for b in range(3))
+            name = f"merge{axis}"
+        elif rng.random() < p_resize:
+            u = rng.random()
+            axis = int(rng.integers(3))
+            if u < 0.05:
+                if src[axis] < 2:
+                    return None
+                op, index_arg = tfg.TFG_RESIZE_PROJECT, int(rng.integers(src[axis]))
+                dst = tuple(src[b] - (b == axis) for b in range(3))
+                name = f"project{axis}"
+            elif u < 0.55:
+                other = keys[int(rng.integers(len(keys)))]
+                op, aux = tfg.TFG_RESIZE_PRODUCT, (other, bests[other])
+                dst = tuple(src[b] * other[b] for b in range(3))
+                name = "product"
+            elif u < 0.85:
+                op = tfg.TFG_RESIZE_DOUBLE
+                dst = tuple(src[b] * (2 if b == axis else 1) for b in range(3))
+                name = f"double{axis}"
+            else:
+                op = tfg.TFG_RESIZE_EXTEND
+                dst = tuple(src[b] + (b == axis) for b in range(3))
+                name = f"extend{axis}"
+        else:
+            return None
+    if dst not in index:
+        return None
+    ps, pd = W.pop[index[src]], W.pop[index[dst]]
+    n_s, n_d = ps["walkers"], pd["walkers"]
+    s_off = int(rng.integers(max(1, n_s - block + 1)))
+    d_off = next_block[dst]
+    if src == dst and abs(s_off - d_off) < block:
+        s_off = (d_off + block) % max(1, n_s - block + 1)
+        if abs(s_off - d_off) < block:
+            return None
+    skipped = W.resize(op, ps["first"] + s_off, pd["first"] + d_off, block, axis=axis, index=index_arg, aux=aux,
+                       use_best=True)
+    next_block[dst] = (d_off + block) % max(1, n_d - block + 1)
+    return {"from": list(src), "to": list(dst), "op": name, "walkers": block, "skipped": skipped, "device": True}
+
+
 def explore(formats, walkers: int, cycles: int, steps_per_cycle: int, seed: int, plateau: int = 50_000,
             reseed_frac: float = 0.25, p_resize: float = 0.5, moves_per_cycle: int = 8, starts: dict | None = None,
-            r_slack: int = 3, quiet: bool = False):
+            r_slack: int = 3, quiet: bool = False, device_moves: int = 0, device_frac: float = 0.125):
     """Exploratory search over `formats` (Z_T, one population each, naive starts
-    unless `starts` gives one).  Returns (per-population results, transfer log)."""
+    unless `starts` gives one).  Each cycle: a walk chunk; population sync (each
+    format's best collected and verified); `moves_per_cycle` Resize moves of the
+    best schemes on the host, whose prepared results re-seed a block of the
+    result format's walkers when they beat its best; and `device_moves` Resize
+    moves on the device (device_resize_move: blocks of device_frac of a
+    population, per walker).  Returns (per-population results, transfer log)."""
     rng = np.random.default_rng(seed)
     starts = starts or {}
     pops = [(f, tfg.TFG_MODE_ZT, starts.get(f, naive_start(*f)), walkers) for f in formats]
@@ -230,6 +299,7 @@ def explore(formats, walkers: int, cycles: int, steps_per_cycle: int, seed: int,
     index = {f: a for a, f in enumerate(formats)}
     block = max(1, int(walkers * reseed_frac))
     next_block = {f: 0 for f in formats}
+    next_dblock = {f: 0 for f in formats}
     transfers = []
     for cycle in range(cycles):
         W.walk(steps_per_cycle)
@@ -258,6 +328,14 @@ def explore(formats, walkers: int, cycles: int, steps_per_cycle: int, seed: int,
                               "rank": int(prepared.shape[0])})
             if not quiet:
                 print(json.dumps({"transfer": transfers[-1]}), flush=True)
+        dblock = max(1, int(walkers * device_frac))
+        for _ in range(device_moves):
+            t = device_resize_move(rng, W, formats, index, bests, dblock, next_dblock, p_resize)
+            if t is not None:
+                t["cycle"] = cycle
+                transfers.append(t)
+                if not quiet:
+                    print(json.dumps({"transfer": t}), flush=True)
         if not quiet:
             print(json.dumps({"cycle": cycle, "best_ranks": {"x".join(map(str, f)): int(bests[f].shape[0])
                                                               for f in formats}}), flush=True)
@@ -289,13 +367,16 @@ def main():
     ap.add_argument("--p-expand", type=float, default=0.0, help="walk policy 1: expansion probability after a flip")
     ap.add_argument("--r-slack", type=int, default=3, help="slots per walker beyond the start rank")
     ap.add_argument("--explore", type=int, default=0, help="exploratory search: number of walk + resize cycles")
+    ap.add_argument("--device-moves", type=int, default=0,
+                    help="exploratory search: Resize moves per cycle on the device (blocks of walkers)")
     ap.add_argument("--quiet", action="store_true")
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
     if args.explore > 0:
         res, transfers = explore(EXPLORE_FORMATS, args.walkers or 16384, args.explore, int(args.steps), args.seed,
-                                 plateau=args.plateau or 50_000, r_slack=args.r_slack, quiet=args.quiet)
+                                 plateau=args.plateau or 50_000, r_slack=args.r_slack, quiet=args.quiet,
+                                 device_moves=args.device_moves)
         for r in res:
             print(json.dumps(r), flush=True)
         print(json.dumps({"transfers": len(transfers)}), flush=True)

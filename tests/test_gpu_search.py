@@ -72,3 +72,21 @@ def test_exploratory_search_moves_schemes_between_formats():
     by = {tuple(r["format"]): r["lowest_rank"] for r in res}
     assert by[(2, 2, 2)] == 7
     assert min(by[f] for f in formats if f != (2, 2, 2)) < min(naive[f] for f in formats if f != (2, 2, 2))
+
+
+def test_exploration_with_device_resize_moves():
+    """Exploration whose Resize moves run on the device, per walker (swaps,
+    merges with other populations' bests, projections, products, doublings,
+    extensions of blocks of walkers' best schemes): transfers happen, the
+    walks go on, and every walker's best scheme satisfies Eq. (1) at the end."""
+    from paper_2511_20317_gb300.workloads import strassen_start
+    formats = [(2, 2, 2), (2, 2, 3), (2, 3, 2), (3, 2, 2), (2, 2, 4), (2, 4, 2), (4, 2, 2), (4, 4, 4), (2, 4, 4)]
+    res, transfers = search.explore(formats, walkers=256, cycles=5, steps_per_cycle=400, seed=2,
+                                    starts={(2, 2, 2): strassen_start()}, p_resize=0.9, moves_per_cycle=0,
+                                    device_moves=12, r_slack=12, quiet=True)
+    dev = [t for t in transfers if t.get("device")]
+    assert len(dev) >= 5
+    assert any(t["skipped"] < t["walkers"] for t in dev)
+    assert {t["op"][:4] for t in dev} & {"swap", "merg", "doub", "exte", "prod", "proj"}
+    for r in res:
+        assert r["best_scheme_verified_host"] and r["device_check_failures"] == 0
