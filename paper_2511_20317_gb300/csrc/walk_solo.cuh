@@ -461,12 +461,10 @@ struct SoloWalker {
     // need it, every thread scans its own slots.
     __device__ __forceinline__ bool coop_pair_hit(unsigned wmask, int lane, int nl, bool need, const T &ti2,
                                                   int i, const T &tj2, int j) const {
+        // bit slices: per thread, ~2*3*FL (Z_2) / ~2*9*FL (Z_T) word operations, which
+        // measured faster than the lane-cooperative test at every pending count
+        if constexpr (SL) return need && sl_pair_hit(ti2, i, tj2, j);
         unsigned pend = __ballot_sync(wmask, need);
-        if constexpr (SL) {
-            // per thread on the slices: ~2*3*FL (Z_2) / ~2*9*FL (Z_T) word operations
-            // against ~15 (Z_2) / ~20 (Z_T) per pending walker and slot for the lanes
-            if (__popc(pend) > (ZT ? 10 : 3)) return need && sl_pair_hit(ti2, i, tj2, j);
-        }
         if (__popc(pend) * 4 > RMAX * 3) return need && pair_hit2(ti2, i, tj2, j);
         bool mine = false;
         const int packed = i | (j << 10) | (r << 20);
