@@ -389,6 +389,34 @@ struct SoloWalker {
         const T v = ld(s);
         int k0 = -1, k1 = -1, k2 = -1;
         bool n1 = false, n2 = false;
+        if constexpr (SL) {
+            // pair candidates from the slices, then the lowest one whose merged third
+            // factor stays in the coefficient set
+            uint32_t mu, mv, mw, mwn;
+            sl_match(v, mu, mv, mw, mwn);
+            const uint32_t live = (r >= 32 ? ~0u : ((1u << r) - 1u)) & ~(1u << s);
+            uint32_t c0 = mu & mv & live, c1 = mu & mw & live, c2 = mv & mw & live;
+#pragma unroll 1
+            while (c0 && k0 < 0) {
+                const int k = __ffs(c0) - 1;
+                c0 &= c0 - 1u;
+                if (sum_ok(v, ld(k), mk.m[2][0], false)) k0 = k;
+            }
+#pragma unroll 1
+            while (k0 < 0 && c1 && k1 < 0) {
+                const int k = __ffs(c1) - 1;
+                c1 &= c1 - 1u;
+                const bool ng = (mwn >> k) & 1u;
+                if (sum_ok(v, ld(k), mk.m[1][0], ng)) { k1 = k; n1 = ng; }
+            }
+#pragma unroll 1
+            while (k0 < 0 && k1 < 0 && c2 && k2 < 0) {
+                const int k = __ffs(c2) - 1;
+                c2 &= c2 - 1u;
+                const bool ng = (mwn >> k) & 1u;
+                if (sum_ok(v, ld(k), mk.m[0][0], ng)) { k2 = k; n2 = ng; }
+            }
+        } else {
 #pragma unroll
         for (int k = 0; k < RMAX; ++k) {
             const T c = ld(k);
@@ -402,6 +430,7 @@ struct SoloWalker {
             if (m0 && k0 < 0) k0 = k;
             if (m1 && k1 < 0) { k1 = k; n1 = ewn; }
             if (m2 && k2 < 0) { k2 = k; n2 = ewn; }
+        }
         }
         if (k0 < 0 && k1 < 0 && k2 < 0) return;
         const int P = k0 >= 0 ? 0 : (k1 >= 0 ? 1 : 2);
