@@ -701,12 +701,19 @@ struct SoloWalker {
         c_acc = c_rej = c_noc = c_drp = c_mrg = c_pls = c_red = 0;
         qlen = 0; q0 = q1 = q2 = 0;
         const Wd *src = reinterpret_cast<const Wd *>(d.slots) + (size_t)w * R * NWS;
-#pragma unroll
-        for (int k = 0; k < RMAX; ++k) {
+        auto load_slot = [&](int k) {
             T v;
             v.p[0] = (k < R) ? src[(size_t)k * NWS] : Wd(0);
             v.n[0] = (ZT && k < R) ? src[(size_t)k * NWS + (NWS - 1)] : Wd(0);
             st(k, v);
+        };
+        if constexpr (SL) {
+            // once per launch: a rolled loop keeps the slice writes out of line
+#pragma unroll 1
+            for (int k = 0; k < RMAX; ++k) load_slot(k);
+        } else {
+#pragma unroll
+            for (int k = 0; k < RMAX; ++k) load_slot(k);
         }
         nnz = 0;
         if (policy == 2) {
