@@ -122,6 +122,10 @@ struct SoloWalker {
     uint2 *ss;                               // Z_T: this thread's slice column, slice q at ss[q * BT]
     int fb1, fb2;                            // bit offsets of v and w in a packed term
     uint32_t lm0, lm1, lm2;                  // coefficient masks of u, v, w (low bits)
+    // Z_T: the step's try_flip masks of factors X and Z of term i (live slots other than i)
+    // and the factors Y, Z the flip changes (Y | Z << 2), for the reduction filter
+    uint32_t fmX, fmZ;
+    int fYZ;
     using T = PTerm<Wd, 1, ZT>;
     using O = Ops<Wd, 1, ZT>;
     using M = Masks<Wd, 1>;
@@ -325,6 +329,32 @@ struct SoloWalker {
         if constexpr (ZT) mwn = mw & (ss[NSL * BT].x ^ (wneg ? ~0u : 0u));
         else mwn = 0u;
     }
+    // Slots (any of the 32) whose factor f (run-time) equals term a's (w up to sign); Z_T
+    __device__ __forceinline__ uint32_t sl_factor_match(const T &a, int f) const {
+        uint32_t xp = fx_rt((uint32_t)a.p[0], f), xn = fx_rt((uint32_t)a.n[0], f);
+        if (f == 2 && lead_neg(xp, xn)) { const uint32_t t = xp; xp = xn; xn = t; }
+        const uint2 *base = ss + f * FL * BT;
+        uint32_t dd = 0;
+#pragma unroll
+        for (int e = 0; e < FL; ++e) {
+            const uint2 w = base[e * BT];
+            dd |= (w.x ^ bc(xp, e)) | (w.y ^ bc(xn, e));
+        }
+        return ~dd;
+    }
+    // Z_T reduction filter from the try_flip masks: the new terms are
+    // i' = (X_i, Y_i + Y_j, Z_i) and j' = (X_j, Y_j, Z_j - s Z_i) with X_j = +-X_i, so a
+    // third slot shares a pair with i' iff it matches two of X_i (fmX), Y_i' and Z_i
+    // (fmZ), and with j' iff two of X_j (fmX again), Y_j and Z_j'.  i' and j' never
+    // share a pair with each other: besides X that would need Y_i = 0, or Z_j equal to
+    // 0 or to +-2 Z_i.
+    __device__ __forceinline__ bool sl_pair_hit_flip(const T &a, int i, const T &b, int j) const {
+        const int Y = fYZ & 3, Z = fYZ >> 2;
+        const uint32_t e1 = sl_factor_match(a, Y), e2 = sl_factor_match(b, Y), e3 = sl_factor_match(b, Z);
+        const uint32_t x = fmX, z = fmZ;
+        const uint32_t live = (r >= 32 ? ~0u : ((1u << r) - 1u)) & ~(1u << i) & ~(1u << j);
+        return (((x & z) | (e1 & (x | z)) | (e2 & (x | e3)) | (x & e3)) & live) != 0u;
+    }
     // Any live slot other than i (j) sharing a factor pair with term a (b)?
     __device__ __forceinline__ bool sl_pair_hit(const T &a, int i, const T &b, int j) const {
         uint32_t mu, mv, mw, mwn;
@@ -492,7 +522,10 @@ struct SoloWalker {
                                                   int i, const T &tj2, int j) const {
         // bit slices: per thread, ~2*3*FL (Z_2) / ~2*9*FL (Z_T) word operations, which
         // measured faster than the lane-cooperative test at every pending count
-        if constexpr (SL) return need && sl_pair_hit(ti2, i, tj2, j);
+        if constexpr (SL) {
+            if constexpr (ZT) return need && sl_pair_hit_flip(ti2, i, tj2, j);
+            else return need && sl_pair_hit(ti2, i, tj2, j);
+        }
         unsigned pend = __ballot_sync(wmask, need);
         if (__popc(pend) * 4 > RMAX * 3) return need && pair_hit2(ti2, i, tj2, j);
         bool mine = false;
@@ -900,6 +933,13 @@ struct SoloWalker {
                         if (mi < nU) { X = 0; j = mu.nth(mi); }
                         else if (mi < nU + nV) { X = 1; j = mv.nth(mi - nU); }
                         else { X = 2; j = mw.nth(mi - nU - nV); sneg = ZT ? (int)mwn.test(j) : 0; }
+                    }
+                    if constexpr (SL && ZT) {
+                        const int Xn = X == 0 ? 1 : (X == 1 ? 2 : 0), Xnn = X == 0 ? 2 : (X == 1 ? 0 : 1);
+                        const int Zf = rho ? Xn : Xnn;
+                        fYZ = (rho ? Xnn : Xn) | (Zf << 2);
+                        fmX = SlotBits<RMAX>::pick(X, mu, mv, mw).w[0];
+                        fmZ = SlotBits<RMAX>::pick(Zf, mu, mv, mw).w[0];
                     }
                     apply_candidate(ti, i, X, j, sneg, rho, action, need_check, ti2, tj2);
                 } else {
