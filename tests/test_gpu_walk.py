@@ -192,6 +192,29 @@ def test_mixed_formats_one_context():
     assert W.verify_all() == 0
 
 
+def test_mixed_full_population_sampled():
+    """The mixed workload at its full size (262144 walkers in five populations,
+    one context, one graph launch per chunk): 16 walkers per format, spread over
+    each population, replayed by the oracle with their global walker ids."""
+    wl = workload_mixed()
+    pops = [(p.fmt, 0, p.start_scheme(), p.walkers) for p in wl.populations]
+    assert [p[3] for p in pops] == [20165, 40330, 40330, 80660, 80659]
+    L, steps, seed = 5000, 20000, 0
+    W = tfg.Walkers(pops, seed=seed, params=tfg.tfg_default_params(plateau_len=L))
+    W.walk(steps // 2).walk(steps - steps // 2).sync()
+    for f, pop in enumerate(W.pop):
+        take = np.linspace(0, pop["walkers"] - 1, 16).astype(int)
+        rows = [W.read_walkers(pop["first"] + int(w), 1) for w in take]
+        info = np.concatenate([x[0] for x in rows])
+        ids = pop["first"] + take
+        ref = oracle.Walkers(pop["fmt"], wl.populations[f].start_scheme(), ids, seed=seed,
+                             plateau_len=L).walk(steps, THREADS)
+        assert_parity(info, np.concatenate([x[1] for x in rows]), np.concatenate([x[2] for x in rows]), ref,
+                      range(len(take)), f"mixed full {pop['fmt']}")
+    assert W.verify_all() == 0
+    W.close()
+
+
 def test_start_from_paper_scheme_and_edge_formats():
     """Start from the (2,2,3:11) example of Section 3.1.1; and the degenerate
     formats (1,1,1) (rank 1: no candidate ever) and (1,2,1)."""
