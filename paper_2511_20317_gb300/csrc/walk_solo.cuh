@@ -9,6 +9,11 @@
 // slots past the live rank are predicated off.  No lane of a warp waits on
 // another: the only cross-thread effects are the shared memory banks.
 //
+// The bit-sliced variant (template parameter FL, capacity 32) also keeps the
+// slots transposed, one 32-bit word per coefficient with bit k = slot k, and
+// runs the candidate search, the reduction filter and the cascade's partner
+// search on those words.
+//
 // Step order (Algorithm 1 with the plateau policy) and every tie-break are
 // identical to the lane-group kernel and to the CPU reference:
 //   draw -> sample term i -> try_flip candidates ordered (factor, slot, rho)
