@@ -292,10 +292,29 @@ def explore(formats, walkers: int, cycles: int, steps_per_cycle: int, seed: int,
     result format's walkers when they beat its best; and `device_moves` Resize
     moves on the device (device_resize_move: blocks of device_frac of a
     population, per walker).  Returns (per-population results, transfer log)."""
-    rng = np.random.default_rng(seed)
+    # one process per GPU (torch.distributed initialised): every rank runs its own
+    # walkers of every format (global ids rank * len(formats) * walkers + ...), and the
+    # population synchronisation takes each format's best over all ranks
+    import torch.distributed as dist
+    multi = dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1
+    me = dist.get_rank() if multi else 0
+    id_base = me * len(formats) * walkers
+    rng = np.random.default_rng(seed + 7919 * me)
     starts = starts or {}
     pops = [(f, tfg.TFG_MODE_ZT, starts.get(f, naive_start(*f)), walkers) for f in formats]
-    W = tfg.Walkers(pops, seed=seed, params=tfg.tfg_default_params(plateau_len=plateau, r_slack=r_slack))
+    W = tfg.Walkers(pops, seed=seed, params=tfg.tfg_default_params(plateau_len=plateau, r_slack=r_slack,
+                                                                    walker_id_base=id_base))
+
+    def population_sync():
+        local = {}
+        for f in formats:
+            sch, r, w = W.collect_best(index[f])
+            local[f] = (int(r), id_base + int(w), sch)
+        if multi:
+            from . import shard
+            local = shard.sync_bests(local, {f: tfg.term_len(f) for f in formats},
+                                     {f: W.pop[index[f]]["r_max"] for f in formats})
+        return {f: local[f][2] for f in formats}
     index = {f: a for a, f in enumerate(formats)}
     block = max(1, int(walkers * reseed_frac))
     next_block = {f: 0 for f in formats}
@@ -304,10 +323,7 @@ def explore(formats, walkers: int, cycles: int, steps_per_cycle: int, seed: int,
     for cycle in range(cycles):
         W.walk(steps_per_cycle)
         W.sync()
-        bests = {}
-        for f in formats:
-            sch, r, _ = W.collect_best(index[f])
-            bests[f] = sch
+        bests = population_sync()
         for _ in range(moves_per_cycle):
             src = formats[int(rng.integers(len(formats)))]
             out = resize_move(rng, src, bests[src], bests, p_resize)
@@ -336,7 +352,7 @@ def explore(formats, walkers: int, cycles: int, steps_per_cycle: int, seed: int,
                 transfers.append(t)
                 if not quiet:
                     print(json.dumps({"transfer": t}), flush=True)
-        if not quiet:
+        if not quiet and me == 0:
             print(json.dumps({"cycle": cycle, "best_ranks": {"x".join(map(str, f)): int(bests[f].shape[0])
                                                               for f in formats}}), flush=True)
     fails = W.verify_all()

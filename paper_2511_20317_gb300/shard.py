@@ -3,9 +3,11 @@
 Walkers are independent and a walker's trajectory depends only on (seed,
 global walker id, step), so a population is split into contiguous ranges of
 global ids, one per rank, with no exchange during the walk (weak scaling:
-every rank runs its own walkers).  The only collective is the collection of
-the best scheme: an all-reduce-min over (best rank, global walker id) packed
-into one int64, then a broadcast of the winning scheme from its owner.
+every rank runs its own walkers).  The collectives, all outside the walk: the
+collection of the best scheme (an all-reduce-min over (best rank, global
+walker id) packed into one int64, then a broadcast of the winning scheme from
+its owner), the sums of counters and rank histograms, and, in the exploratory
+search, the per-format best schemes that every rank's Resize moves start from.
 """
 from __future__ import annotations
 
@@ -48,3 +50,25 @@ def collect_best_across_ranks(local_rank_of_scheme: int, local_walker_id: int, l
     dist.broadcast(buf, src=int(owner.item()))
     scheme = buf.cpu().numpy()[: best_rank * term_len].reshape(best_rank, term_len)
     return best_rank, best_walker, scheme
+
+
+def allreduce_counts(values, device=None) -> np.ndarray:
+    """Element-wise sum over ranks of an int64 vector (walker counters, rank
+    histograms); every rank receives the sums."""
+    import torch
+    import torch.distributed as dist
+    t = torch.as_tensor(np.ascontiguousarray(values, dtype=np.int64), device=device).clone()
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t.cpu().numpy()
+
+
+def sync_bests(local: dict, term_lens: dict, max_terms: dict, device=None) -> dict:
+    """Population synchronisation of the exploratory search across ranks: for
+    every format (the same keys, iterated in sorted order, on every rank) the
+    global best scheme from each rank's (rank of scheme, global walker id,
+    scheme).  Returns {format: (rank of scheme, walker id, scheme)}."""
+    out = {}
+    for f in sorted(local):
+        r, w, sch = local[f]
+        out[f] = collect_best_across_ranks(r, w, sch, max_terms=max_terms[f], term_len=term_lens[f], device=device)
+    return out

@@ -87,3 +87,56 @@ def test_two_rank_shards_equal_single_run(tmp_path):
         sch = np.load(tmp_path / f"scheme{r}.npy")
         assert np.array_equal(sch, whole.best_scheme(want[1]))
         assert oracle.brent_valid(FMT, sch)
+
+
+def _rank_sync(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    local, lens, caps = {}, {}, {}
+    counts = []
+    for fmt in [(2, 2, 2), (2, 2, 3)]:
+        first, count = shard.shard_range(rank, world, TOTAL)
+        W = oracle.Walkers(fmt, naive_start(*fmt), np.arange(first, first + count), seed=SEED,
+                           plateau_len=L).walk(STEPS, threads=1)
+        w = int(np.lexsort((np.arange(count), W.info["best_r"]))[0])
+        local[fmt] = (int(W.info["best_r"][w]), first + w, W.best_scheme(w))
+        lens[fmt], caps[fmt] = W.LT, W.r_max
+        hist = np.bincount(W.info["best_r"], minlength=40)
+        counts.append(np.concatenate([[W.info["accepted"].sum(), W.info["merges"].sum()], hist]))
+    got = shard.sync_bests(local, lens, caps)
+    sums = shard.allreduce_counts(np.concatenate(counts))
+    np.save(os.path.join(out_dir, f"sums{rank}.npy"), sums)
+    for fmt, (r, w, sch) in got.items():
+        np.save(os.path.join(out_dir, f"sync{rank}_{fmt[2]}.npy"), np.concatenate([[r, w], sch.reshape(-1)]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_population_sync_and_counter_sums(tmp_path):
+    """The exploratory search's population synchronisation across ranks gives every
+    rank the per-format global best (lowest rank, then walker id); counters and
+    rank histograms sum to the whole population's."""
+    world = 2
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_sync, args=(r, world, port, str(tmp_path))) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    want_counts = []
+    for fmt in [(2, 2, 2), (2, 2, 3)]:
+        whole = oracle.Walkers(fmt, naive_start(*fmt), np.arange(TOTAL), seed=SEED, plateau_len=L).walk(STEPS)
+        hist = np.bincount(whole.info["best_r"], minlength=40)
+        want_counts.append(np.concatenate([[whole.info["accepted"].sum(), whole.info["merges"].sum()], hist]))
+        order = np.lexsort((np.arange(TOTAL), whole.info["best_r"]))
+        br, bw = int(whole.info["best_r"][order[0]]), int(order[0])
+        for r in range(world):
+            got = np.load(tmp_path / f"sync{r}_{fmt[2]}.npy")
+            assert (int(got[0]), int(got[1])) == (br, bw)
+            assert np.array_equal(got[2:].reshape(br, -1), whole.best_scheme(bw))
+    for r in range(world):
+        assert np.array_equal(np.load(tmp_path / f"sums{r}.npy"), np.concatenate(want_counts))
