@@ -326,14 +326,20 @@ def run_ours(args):
     if lanes is not None:
         line["config"]["autotuned_lanes_per_walker"] = lanes
     if world > 1:
-        # the one collective of the sharded path: global best scheme per population
+        # the collectives of the sharded path (after the timed region): global best scheme
+        # per population, and rank histograms summed over ranks
         from paper_2511_20317_gb300 import shard
         gbest = []
         for f in range(W.n_formats):
             sch, r_, wid = W.collect_best(f)
-            g = shard.collect_best_across_ranks(r_, wid, sch, W.pop[f]["r_max"], sch.shape[1], device="cuda")
+            g = shard.collect_best_across_ranks(r_, rank * per_rank + wid, sch, W.pop[f]["r_max"], sch.shape[1],
+                                                device="cuda")
             gbest.append({"rank": g[0], "walker": g[1]})
         line["global_best"] = gbest
+        for f, key in enumerate(per_mode):
+            hist = shard.allreduce_counts(W.stats(f)[1], device="cuda")
+            per_mode[key]["rank_hist"] = {int(k): int(v) for k, v in enumerate(hist) if v}
+            per_mode[key]["lowest_rank"] = gbest[f]["rank"]
     if rank == 0 and args.learned:
         line["learned_vs_uniform"] = learned_ab(args)
     if rank == 0 and args.cpu_baseline:
