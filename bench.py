@@ -155,6 +155,7 @@ def mapping_name(pop):
         return "warp per walker, shared-memory signature search"
     if pop["lanes"] == 1:
         sliced = ", bit-sliced slot search" if pop.get("slice_len") else ""
+        sliced += " (square factors compiled in)" if pop.get("square") else ""
         return f"thread per walker, {pop['slots_per_lane']} slots{sliced}"
     return f"{pop['lanes']} lanes x {pop['slots_per_lane']} slots"
 

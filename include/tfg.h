@@ -339,8 +339,11 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
  * slot capacity for one thread per walker; 0 for the warp-per-walker kernel),
  * and slice_len > 0 when the thread-per-walker kernel also keeps the slots
  * bit-sliced (one word per coefficient, bit k = slot k; formats whose factors
- * have at most slice_len coefficients), else 0.  Each output may be NULL. */
-int tfg_mapping(tfg_ctx *ctx, int32_t f, int32_t *lanes, int32_t *slots_per_lane, int32_t *slice_len);
+ * have at most slice_len coefficients), else 0; square = 1 when that kernel is
+ * the instantiation for three factors of exactly slice_len coefficients
+ * (offsets and masks compiled in), else 0.  Each output may be NULL. */
+int tfg_mapping(tfg_ctx *ctx, int32_t f, int32_t *lanes, int32_t *slots_per_lane, int32_t *slice_len,
+                int32_t *square);
 
 /* Release the context (host memory only; the workspace stays the caller's). */
 void tfg_destroy(tfg_ctx *ctx);

@@ -83,9 +83,15 @@ int cuda_fail(cudaError_t e, const char *what) {
     return TFG_ECUDA;
 }
 
+int max_factor_len(const tfg_format &f) { return std::max(f.m * f.n, std::max(f.n * f.p, f.p * f.m)); }
+int min_factor_len(const tfg_format &f) { return std::min(f.m * f.n, std::min(f.n * f.p, f.p * f.m)); }
+
 // The variant of the smallest capacity >= R for a mapping (G lanes per walker);
-// at equal capacity a bit-sliced variant (fl >= the longest factor, maxlen) wins.
-const tfg::WalkVariant *pick_variant(int mode, int bits, int tw, int G, int R, int maxlen) {
+// at equal capacity a bit-sliced variant (fl >= the longest factor) wins, and a
+// square one (every factor exactly fl) over that.
+const tfg::WalkVariant *pick_variant(int mode, int bits, int tw, int G, int R, const tfg_format &fmt) {
+    const int maxlen = max_factor_len(fmt), minlen = min_factor_len(fmt);
+    auto score = [](const tfg::WalkVariant &x) { return (x.fl ? 1 : 0) + (x.sq ? 1 : 0); };
     int cnt = 0;
     const tfg::WalkVariant *v = tfg::walk_variants(&cnt);
     const tfg::WalkVariant *best = nullptr;
@@ -93,24 +99,23 @@ const tfg::WalkVariant *pick_variant(int mode, int bits, int tw, int G, int R, i
         if (v[a].mode != mode || v[a].word_bits != bits || v[a].tw != tw || v[a].G != G) continue;
         if (v[a].capacity() < R) continue;
         if (v[a].fl && v[a].fl < maxlen) continue;
-        if (!best || v[a].S < best->S || (v[a].S == best->S && v[a].fl && !best->fl)) best = &v[a];
+        if (v[a].sq && (minlen != v[a].fl || maxlen != v[a].fl)) continue;
+        if (!best || v[a].S < best->S || (v[a].S == best->S && score(v[a]) > score(*best))) best = &v[a];
     }
     return best;
 }
 
-int max_factor_len(const tfg_format &f) { return std::max(f.m * f.n, std::max(f.n * f.p, f.p * f.m)); }
-
 // Default mapping: one thread per walker (shared-memory slots) when such a
 // variant exists for the rank; otherwise the fewest lanes per walker that keep
 // at most 4 slots per lane; otherwise 32 lanes.
-const tfg::WalkVariant *default_variant(int mode, int bits, int tw, int R, int maxlen) {
-    if (const tfg::WalkVariant *v = pick_variant(mode, bits, tw, 1, R, maxlen)) return v;
+const tfg::WalkVariant *default_variant(int mode, int bits, int tw, int R, const tfg_format &fmt) {
+    if (const tfg::WalkVariant *v = pick_variant(mode, bits, tw, 1, R, fmt)) return v;
     static const int order[4] = {4, 8, 16, 32};
     for (int G : order) {
-        const tfg::WalkVariant *v = pick_variant(mode, bits, tw, G, R, maxlen);
+        const tfg::WalkVariant *v = pick_variant(mode, bits, tw, G, R, fmt);
         if (v && v->S <= 4) return v;
     }
-    return pick_variant(mode, bits, tw, 32, R, maxlen);
+    return pick_variant(mode, bits, tw, 32, R, fmt);
 }
 
 }  // namespace
@@ -347,8 +352,8 @@ static int plan_segments(int32_t n_formats, const tfg_format *fmts, const int32_
         first += s.n;
         if (first > (int64_t)UINT32_MAX) { set_error("more than 2^32 walkers"); return TFG_EINVAL; }
         off = layout_segment(s, off);
-        s.var = prm.mapping ? pick_variant(s.fmt.mode, s.word_bits, s.tw, prm.mapping, s.R, max_factor_len(s.fmt))
-                            : default_variant(s.fmt.mode, s.word_bits, s.tw, s.R, max_factor_len(s.fmt));
+        s.var = prm.mapping ? pick_variant(s.fmt.mode, s.word_bits, s.tw, prm.mapping, s.R, s.fmt)
+                            : default_variant(s.fmt.mode, s.word_bits, s.tw, s.R, s.fmt);
         if (!s.var) { set_error("no compiled kernel variant for this format/rank/mapping"); return TFG_EINVAL; }
     }
     *bytes = off;
@@ -596,7 +601,7 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
         float best_ms = 1e30f;
         static const int lanes[5] = {1, 4, 8, 16, 32};
         for (int G : lanes) {
-            const tfg::WalkVariant *v = pick_variant(s.fmt.mode, s.word_bits, s.tw, G, s.R, max_factor_len(s.fmt));
+            const tfg::WalkVariant *v = pick_variant(s.fmt.mode, s.word_bits, s.tw, G, s.R, s.fmt);
             if (!v) continue;
             (void)all;
             const int b = v->block ? v->block : ctx->prm.block_threads;
@@ -647,11 +652,13 @@ int tfg_population(tfg_ctx *ctx, int32_t f, tfg_format *fmt, int32_t *r0, int32_
     return TFG_OK;
 }
 
-int tfg_mapping(tfg_ctx *ctx, int32_t f, int32_t *lanes, int32_t *slots_per_lane, int32_t *slice_len) {
+int tfg_mapping(tfg_ctx *ctx, int32_t f, int32_t *lanes, int32_t *slots_per_lane, int32_t *slice_len,
+                int32_t *square) {
     if (!ctx || f < 0 || f >= (int)ctx->segs.size()) { set_error("bad population index"); return TFG_EINVAL; }
     if (lanes) *lanes = ctx->segs[f].var->G;
     if (slots_per_lane) *slots_per_lane = ctx->segs[f].var->S;
     if (slice_len) *slice_len = ctx->segs[f].var->fl;
+    if (square) *square = ctx->segs[f].var->sq;
     return TFG_OK;
 }
 

@@ -53,6 +53,7 @@ struct WalkVariant {
     void (*prepare)();   // one-time kernel attribute set-up (may be null)
     int cap = 0;         // slot capacity when not given by G and S
     int fl = 0;          // > 0: formats whose factors have at most fl coefficients only (bit-sliced)
+    int sq = 0;          // 1: formats whose three factors have exactly fl coefficients only
     int capacity() const { return cap ? cap : (G == 1 ? S : G * S); }
 };
 

@@ -114,12 +114,15 @@ struct SlotBits {
 // slices hold w up to sign (its first non-zero coefficient made +1) and one
 // more word the sign bits, so that the sign changes of the normalisation
 // (Section 3.6) touch one word and a flip rewrites the slices of one factor.
-template <int MODE, class Wd, int RMAX, int BT, int FL = 0>
+// SQ: the three factors have exactly FL coefficients each (square formats
+// (k,k,k) with k*k = FL), so factor offsets and masks are compile-time constants.
+template <int MODE, class Wd, int RMAX, int BT, int FL = 0, bool SQ = false>
 struct SoloWalker {
     static constexpr bool ZT = (MODE == TFG_MODE_ZT);
     static constexpr int NWS = ZT ? 2 : 1;   // words per slot (TW = 1)
     static constexpr bool SL = FL > 0;
     static_assert(!SL || (RMAX <= 32 && sizeof(Wd) == 4), "slices hold 32 slots of 32-bit packed terms");
+    static_assert(!SQ || (SL && 3 * FL <= 32), "square factors: three of FL coefficients in one 32-bit word");
     static constexpr int NSL = 3 * FL;       // slices per sign
     // Z_2: the slices in registers; Z_T: (P, N) pairs in shared memory [slice][thread],
     // then the w sign word (row NSL, .x)
@@ -723,13 +726,23 @@ struct SoloWalker {
         policy = d.walk_policy;
         best_nnz = H->best_nnz;
         mk.load(d);
-        if constexpr (SL) {
+        if constexpr (SL && SQ) {
+            constexpr uint32_t lm = (1u << FL) - 1u;
+            mk.m[0][0] = (Wd)lm;
+            mk.m[1][0] = (Wd)(lm << FL);
+            mk.m[2][0] = (Wd)(lm << (2 * FL));
+            fb1 = FL;
+            fb2 = 2 * FL;
+            lm0 = lm1 = lm2 = lm;
+        } else if constexpr (SL) {
             fb1 = d.fbase[1];
             fb2 = d.fbase[2];
             const int l0 = d.m * d.n, l1 = d.n * d.p, l2 = d.p * d.m;
             lm0 = (1u << l0) - 1u;
             lm1 = (1u << l1) - 1u;
             lm2 = (1u << l2) - 1u;
+        }
+        if constexpr (SL) {
 #pragma unroll
             for (int q = 0; q < NSL + 1; ++q) {
                 if constexpr (ZT) ss[q * BT] = make_uint2(0u, 0u);
@@ -963,11 +976,11 @@ __host__ __device__ constexpr size_t solo_packed_bytes() {
     return (size_t)RMAX * (BT + 1) * ((MODE == TFG_MODE_ZT) ? 2 : 1) * sizeof(Wd);
 }
 
-template <int MODE, class Wd, int RMAX, int BT, int FL = 0>
+template <int MODE, class Wd, int RMAX, int BT, int FL = 0, bool SQ = false>
 __device__ __forceinline__ void walk_solo_body(const SegDesc &d, int32_t steps, unsigned char *smem_raw) {
     const int64_t w = (int64_t)blockIdx.x * BT + threadIdx.x;
     if (w >= d.n_walkers) return;   // no block-wide barrier is used
-    SoloWalker<MODE, Wd, RMAX, BT, FL> wk;
+    SoloWalker<MODE, Wd, RMAX, BT, FL, SQ> wk;
     constexpr int NWS = (MODE == TFG_MODE_ZT) ? 2 : 1;
     wk.sm = reinterpret_cast<Wd *>(smem_raw) + (size_t)threadIdx.x * NWS;
     if constexpr (FL > 0 && MODE == TFG_MODE_ZT)
@@ -997,16 +1010,16 @@ __global__ void __launch_bounds__(BT, 4) walk_solo_kernel_occ4(const SegDesc d, 
 #ifndef TFG_SLICED_Z2_MIN_BLOCKS
 #define TFG_SLICED_Z2_MIN_BLOCKS 4
 #endif
-template <int MODE, class Wd, int RMAX, int BT, int FL>
+template <int MODE, class Wd, int RMAX, int BT, int FL, bool SQ>
 __global__ void __launch_bounds__(BT, MODE == TFG_MODE_ZT ? TFG_SLICED_ZT_MIN_BLOCKS : TFG_SLICED_Z2_MIN_BLOCKS)
     walk_solo_kernel_sliced(const SegDesc d, const int32_t steps) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    walk_solo_body<MODE, Wd, RMAX, BT, FL>(d, steps, smem_raw);
+    walk_solo_body<MODE, Wd, RMAX, BT, FL, SQ>(d, steps, smem_raw);
 }
 
-template <int MODE, class Wd, int RMAX, int BT, int FL = 0>
+template <int MODE, class Wd, int RMAX, int BT, int FL = 0, bool SQ = false>
 constexpr auto solo_kernel() {
-    if constexpr (FL > 0) return &walk_solo_kernel_sliced<MODE, Wd, RMAX, BT, FL>;
+    if constexpr (FL > 0) return &walk_solo_kernel_sliced<MODE, Wd, RMAX, BT, FL, SQ>;
     else if constexpr (MODE == TFG_MODE_ZT && sizeof(Wd) == 4 && RMAX == 32) return &walk_solo_kernel_occ4<MODE, Wd, RMAX, BT>;
     else return &walk_solo_kernel<MODE, Wd, RMAX, BT>;
 }
@@ -1020,20 +1033,20 @@ constexpr size_t solo_smem_bytes() {
     else return packed;
 }
 
-template <int MODE, class Wd, int RMAX, int BT, int FL = 0>
+template <int MODE, class Wd, int RMAX, int BT, int FL = 0, bool SQ = false>
 void prepare_walk_solo() {
     static bool attr = [] {
-        cudaFuncSetAttribute(dev::solo_kernel<MODE, Wd, RMAX, BT, FL>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(dev::solo_kernel<MODE, Wd, RMAX, BT, FL, SQ>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)solo_smem_bytes<MODE, Wd, RMAX, BT, FL>());
         return true;
     }();
     (void)attr;
 }
 
-template <int MODE, class Wd, int RMAX, int BT, int FL = 0>
+template <int MODE, class Wd, int RMAX, int BT, int FL = 0, bool SQ = false>
 void launch_walk_solo(const SegDesc &d, int32_t steps, int grid, int /*block*/, cudaStream_t st) {
-    prepare_walk_solo<MODE, Wd, RMAX, BT, FL>();
-    dev::solo_kernel<MODE, Wd, RMAX, BT, FL>()<<<grid, BT, solo_smem_bytes<MODE, Wd, RMAX, BT, FL>(), st>>>(d, steps);
+    prepare_walk_solo<MODE, Wd, RMAX, BT, FL, SQ>();
+    dev::solo_kernel<MODE, Wd, RMAX, BT, FL, SQ>()<<<grid, BT, solo_smem_bytes<MODE, Wd, RMAX, BT, FL>(), st>>>(d, steps);
 }
 
 #define TFG_SOLO_VARIANT(MODE, WD, BITS, RMAX, BT) \
@@ -1041,10 +1054,10 @@ void launch_walk_solo(const SegDesc &d, int32_t steps, int grid, int /*block*/, 
                 reinterpret_cast<const void *>(dev::solo_kernel<MODE, WD, RMAX, BT>()), \
                 &prepare_walk_solo<MODE, WD, RMAX, BT>}
 
-// bit-sliced: formats whose factors have at most FL coefficients
-#define TFG_SOLO_SLICED_VARIANT(MODE, WD, BITS, RMAX, BT, FL) \
-    WalkVariant{MODE, BITS, 1, 1, RMAX, BT, &launch_walk_solo<MODE, WD, RMAX, BT, FL>, \
-                reinterpret_cast<const void *>(dev::solo_kernel<MODE, WD, RMAX, BT, FL>()), \
-                &prepare_walk_solo<MODE, WD, RMAX, BT, FL>, 0, FL}
+// bit-sliced: formats whose factors have at most FL coefficients (SQ: exactly FL each)
+#define TFG_SOLO_SLICED_VARIANT(MODE, WD, BITS, RMAX, BT, FL, SQ) \
+    WalkVariant{MODE, BITS, 1, 1, RMAX, BT, &launch_walk_solo<MODE, WD, RMAX, BT, FL, SQ>, \
+                reinterpret_cast<const void *>(dev::solo_kernel<MODE, WD, RMAX, BT, FL, SQ>()), \
+                &prepare_walk_solo<MODE, WD, RMAX, BT, FL, SQ>, 0, FL, SQ ? 1 : 0}
 
 }  // namespace tfg

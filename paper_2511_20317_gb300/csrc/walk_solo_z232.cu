@@ -12,7 +12,8 @@ const WalkVariant *walk_variants_solo_z232(int *n) {
         TFG_SOLO_VARIANT(TFG_MODE_Z2, uint32_t, 32, 16, 128),
         TFG_SOLO_VARIANT(TFG_MODE_Z2, uint32_t, 32, 24, 128),
         TFG_SOLO_VARIANT(TFG_MODE_Z2, uint32_t, 32, 32, 128),
-        TFG_SOLO_SLICED_VARIANT(TFG_MODE_Z2, uint32_t, 32, 32, TFG_SLICED_Z2_BLOCK, 9),
+        TFG_SOLO_SLICED_VARIANT(TFG_MODE_Z2, uint32_t, 32, 32, TFG_SLICED_Z2_BLOCK, 9, false),
+        TFG_SOLO_SLICED_VARIANT(TFG_MODE_Z2, uint32_t, 32, 32, TFG_SLICED_Z2_BLOCK, 9, true),
     };
     *n = (int)(sizeof(v) / sizeof(v[0]));
     return v;

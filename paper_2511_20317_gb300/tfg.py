@@ -133,7 +133,7 @@ def lib() -> ctypes.CDLL:
                 "tfg_checkpoint": (i32, [P, P, sz, ctypes.POINTER(sz)]),
                 "tfg_restore": (i32, [P, P, sz]),
                 "tfg_mapping": (i32, [P, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
-                                      ctypes.POINTER(ctypes.c_int32)]),
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
                 "tfg_destroy": (None, [P]),
                 "tfg_autotune": (i32, [P, i64, i64, P]),
                 "tfg_philox_device": (i32, [P, i32, u32, u32, P, P]),
@@ -462,11 +462,11 @@ class Walkers:
         fmt, r0, rmax, nw, first = tfg_format(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
         _check(lib().tfg_population(self.ctx, f, ctypes.byref(fmt), ctypes.byref(r0), ctypes.byref(rmax),
                                     ctypes.byref(nw), ctypes.byref(first)))
-        G, S, SL = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-        _check(lib().tfg_mapping(self.ctx, f, ctypes.byref(G), ctypes.byref(S), ctypes.byref(SL)))
+        G, S, SL, SQ = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().tfg_mapping(self.ctx, f, ctypes.byref(G), ctypes.byref(S), ctypes.byref(SL), ctypes.byref(SQ)))
         return {"fmt": (fmt.m, fmt.n, fmt.p), "mode": fmt.mode, "r0": r0.value, "r_max": rmax.value,
                 "walkers": nw.value, "first": first.value, "lanes": G.value, "slots_per_lane": S.value,
-                "slice_len": SL.value}
+                "slice_len": SL.value, "square": SQ.value}
 
     def tfg_autotune(self, trial_steps: int = 400, trial_walkers: int = 32768):
         lanes = (ctypes.c_int32 * self.n_formats)()

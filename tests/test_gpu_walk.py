@@ -72,6 +72,7 @@ def test_parity_small_all_mappings(fmt, L, steps, nw, lanes, mode):
     assert W.pop[0]["lanes"] == lanes
     # thread per walker: capacity 32 with factors of at most 9 coefficients is the bit-sliced kernel
     assert W.pop[0]["slice_len"] == (9 if lanes == 1 and fmt == (3, 3, 3) else 0)
+    assert W.pop[0]["square"] == (1 if lanes == 1 and fmt == (3, 3, 3) else 0)
     info, slots, best = W.read_walkers(0, nw)
     ref = oracle.Walkers(fmt, start, np.arange(nw), seed=seed, mode=mode, plateau_len=L).walk(steps, THREADS)
     assert (ref.info["plus"] > 0).any() and (ref.info["merges"] > 0).any()
@@ -92,7 +93,7 @@ def test_bit_sliced_kernel_uneven_factors(fmt, mode):
     nw, steps, L = 160, 3000, 150
     slack = 32 - start.shape[0]
     W = gpu_walkers(fmt, mode, start, nw, 21, steps, chunks=2, plateau_len=L, r_slack=slack, mapping=1)
-    assert W.pop[0]["slice_len"] == 9 and W.pop[0]["r_max"] == 32
+    assert W.pop[0]["slice_len"] == 9 and W.pop[0]["square"] == 0 and W.pop[0]["r_max"] == 32
     info, slots, best = W.read_walkers(0, nw)
     ref = oracle.Walkers(fmt, start, np.arange(nw), seed=21, mode=mode, plateau_len=L, r_slack=slack).walk(steps, THREADS)
     assert (ref.info["accepted"] > 0).all() and (ref.info["plus"] > 0).any()
