@@ -270,7 +270,7 @@ def run_ours(args):
     # integer ALU pipe: one warp instruction per 2 cycles per SM sub-partition (16 lanes/clk),
     # 4 sub-partitions x 152 SMs at the 2070 MHz maximum SM clock
     alu_peak = 152 * 4 * 16 * 2.07e9 / 1e12
-    traffic = recorded_traffic()
+    traffic = recorded_traffic() if args.workload == "333" else None   # the capture is of that workload
 
     # end to end through the public API with host buffers, per step:
     # init from the host start schemes, walk, verify, collect best to the host
