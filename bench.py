@@ -406,10 +406,15 @@ def run_reference(args):
         vals.append(cpu_baseline(args, pops, plateau, budget_s=max(3.0, 60.0 / (args.steps + args.warmup)))["value"])
     value = float(np.median(vals[args.warmup:])) if args.steps else cb["value"]
     cb["value"] = value
+    # one bench step of the workload (every walker, args.chunk steps), at the sampled rate
+    step_walker_steps = sum(p[3] for p in pops) * args.chunk
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "flips/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_walker_steps / value * 1e3,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "i8", "data": "synthetic",
-            "config": {"workload": "3x3x3 naive27 Z_T+Z_2 (bounded sample on host cores)"},
+            "config": {"workload": "3x3x3 naive27 Z_T+Z_2 (bounded sample on host cores)",
+                       "ms_per_step": "extrapolated from the sampled rate to one bench step "
+                                      f"({step_walker_steps} walker-steps)"},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "flips/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
