@@ -134,6 +134,7 @@ struct SoloWalker {
     // and the factors Y, Z the flip changes (Y | Z << 2), for the reduction filter
     uint32_t fmX, fmZ;
     int fYZ;
+    uint32_t fe1, fe3;   // Z_T: slots matching Y of the new term i / Z of the new term j (from the upkeep)
     using T = PTerm<Wd, 1, ZT>;
     using O = Ops<Wd, 1, ZT>;
     using M = Masks<Wd, 1>;
@@ -213,8 +214,9 @@ struct SoloWalker {
         }
         if constexpr (SL) sl_put(k, v);
     }
-    // store of a flipped term (factor f changed; see sl_put_flip)
-    __device__ __forceinline__ void st_flip(int k, const T &v, int f) {
+    // store of a flipped term (factor f changed; see sl_put_flip); Z_T slices: returns the
+    // slots whose factor f equals v's
+    __device__ __forceinline__ uint32_t st_flip(int k, const T &v, int f) {
         Wd *a = sm + (size_t)k * RS;
         if constexpr (ZT) {
             if constexpr (sizeof(Wd) == 4) *reinterpret_cast<uint2 *>(a) = make_uint2(v.p[0], v.n[0]);
@@ -222,7 +224,8 @@ struct SoloWalker {
         } else {
             a[0] = v.p[0];
         }
-        if constexpr (SL) sl_put_flip(k, v, f);
+        if constexpr (SL) return sl_put_flip(k, v, f);
+        else return 0u;
     }
 
     // ---- bit slices (FL > 0)
@@ -246,15 +249,21 @@ struct SoloWalker {
         return (xn & d & (0u - d)) != 0u;
     }
     // slices of factor f (f compile-time, or run-time through base) at slot k := (xp, xn);
-    // w (f = 2) up to sign, its sign bit in the sign word
-    __device__ __forceinline__ void sl_write(uint2 *base, uint32_t kb, uint32_t xp, uint32_t xn) const {
+    // w (f = 2) up to sign, its sign bit in the sign word.  Returns the slots whose
+    // factor f equals (xp, xn), from the words as they were (slot k's own bit aside,
+    // the same as after the write).
+    __device__ __forceinline__ uint32_t sl_write(uint2 *base, uint32_t kb, uint32_t xp, uint32_t xn) const {
+        uint32_t dd = 0;
 #pragma unroll
         for (int e = 0; e < FL; ++e) {
             uint2 w = base[e * BT];
-            w.x = (w.x & ~kb) | (bc(xp, e) & kb);
-            w.y = (w.y & ~kb) | (bc(xn, e) & kb);
+            const uint32_t bp = bc(xp, e), bn = bc(xn, e);
+            dd |= (w.x ^ bp) | (w.y ^ bn);
+            w.x = (w.x & ~kb) | (bp & kb);
+            w.y = (w.y & ~kb) | (bn & kb);
             base[e * BT] = w;
         }
+        return ~dd;
     }
     __device__ __forceinline__ void sl_sign(uint32_t kb, bool neg) const {
         uint2 *g = ss + NSL * BT;
@@ -289,7 +298,8 @@ struct SoloWalker {
     // slot k := term v that differs from the slot's previous term in factor f
     // (run-time) only, up to the sign changes of the normalisation (u and v
     // keep their own signs; w's sign is one bit).  Z_2: every slice.
-    __device__ __forceinline__ void sl_put_flip(int k, const T &v, int f) {
+    // Z_T returns the slots whose factor f equals v's (w up to sign), for the filter.
+    __device__ __forceinline__ uint32_t sl_put_flip(int k, const T &v, int f) {
         if constexpr (ZT) {
             const uint32_t kb = 1u << k;
             uint32_t xp = fx_rt((uint32_t)v.p[0], f), xn = fx_rt((uint32_t)v.n[0], f);
@@ -297,9 +307,10 @@ struct SoloWalker {
             const bool ng = lead_neg(wp, wn);
             sl_sign(kb, ng);
             if (f == 2 && ng) { const uint32_t t = xp; xp = xn; xn = t; }
-            sl_write(ss + f * FL * BT, kb, xp, xn);
+            return sl_write(ss + f * FL * BT, kb, xp, xn);
         } else {
             sl_put(k, v);
+            return 0u;
         }
     }
     // Slots (any of the 32) whose u / v / w equal term a's: w either sign (mw)
@@ -357,8 +368,9 @@ struct SoloWalker {
     // share a pair with each other: besides X that would need Y_i = 0, or Z_j equal to
     // 0 or to +-2 Z_i.
     __device__ __forceinline__ bool sl_pair_hit_flip(const T &a, int i, const T &b, int j) const {
-        const int Y = fYZ & 3, Z = fYZ >> 2;
-        const uint32_t e1 = sl_factor_match(a, Y), e2 = sl_factor_match(b, Y), e3 = sl_factor_match(b, Z);
+        const int Y = fYZ & 3;
+        (void)a;
+        const uint32_t e1 = fe1, e2 = sl_factor_match(b, Y), e3 = fe3;
         const uint32_t x = fmX, z = fmZ;
         const uint32_t live = (r >= 32 ? ~0u : ((1u << r) - 1u)) & ~(1u << i) & ~(1u << j);
         return (((x & z) | (e1 & (x | z)) | (e2 & (x | e3)) | (x & e3)) & live) != 0u;
@@ -817,8 +829,9 @@ struct SoloWalker {
         if (policy == 2) nnz += (zi ? 0u : nnz_of(ti2)) + (zj ? 0u : nnz_of(tj2)) - nnz_of(ti) - nnz_of(tj);
         O::canon(ti2, mk);
         O::canon(tj2, mk);
-        st_flip(i, ti2, Y);
-        st_flip(j, tj2, Z);
+        const uint32_t e1 = st_flip(i, ti2, Y), e3 = st_flip(j, tj2, Z);
+        if constexpr (SL && ZT) { fe1 = e1; fe3 = e3; }
+        else { (void)e1; (void)e3; }
         qlen = 0;
         if (zi || zj) {
             q_push(i);
