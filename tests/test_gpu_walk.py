@@ -216,6 +216,29 @@ def test_mixed_full_population_sampled():
     W.close()
 
 
+def test_large_formats_full_population_sampled():
+    """The large-format workload at its full size: (4,5,12), (5,6,10), (6,7,9) from the
+    meta-operator starts, 131072 walkers each, one forked graph launch per chunk (the
+    bench's configuration), 50000 steps; 4 walkers per format, spread over each
+    population, replayed by the oracle with their global walker ids."""
+    from paper_2511_20317_gb300 import starts
+    pops = starts.large_populations(131072)
+    L, steps, seed = 50_000, 50_000, 0
+    W = tfg.Walkers(pops, seed=seed, params=tfg.tfg_default_params(plateau_len=L, use_graph=2))
+    W.walk(steps // 2).walk(steps - steps // 2).sync()
+    for f, pop in enumerate(W.pop):
+        assert pop["slots_per_lane"] == 0, "warp-per-walker kernel expected"
+        take = np.linspace(0, pop["walkers"] - 1, 4).astype(int)
+        rows = [W.read_walkers(pop["first"] + int(w), 1) for w in take]
+        info = np.concatenate([x[0] for x in rows])
+        ids = pop["first"] + take
+        ref = oracle.Walkers(pop["fmt"], pops[f][2], ids, seed=seed, plateau_len=L).walk(steps, THREADS)
+        assert (ref.info["accepted"] > 0).all()
+        assert_parity(info, np.concatenate([x[1] for x in rows]), np.concatenate([x[2] for x in rows]), ref,
+                      range(len(take)), f"large full {pop['fmt']}")
+    W.close()
+
+
 def test_start_from_paper_scheme_and_edge_formats():
     """Start from the (2,2,3:11) example of Section 3.1.1; and the degenerate
     formats (1,1,1) (rank 1: no candidate ever) and (1,2,1)."""
