@@ -72,6 +72,41 @@ def test_window_learned_replay(fmt, nw, steps, L):
     assert_parity(W, ref, nw, f"window-learned {fmt}")
 
 
+@pytest.mark.parametrize("policy", [0, 1])
+def test_window_full_size_sampled(policy):
+    """The learned-proposal workload at its full size: (4,4,4) naive, 262144 walkers,
+    window steps with the uniform (0) or the learned (1, eps 0.05, a random network)
+    choice; 16 walkers spread over the population replayed by the oracle (the
+    learned ones from their logged window indices)."""
+    fmt, nw, steps, L = (4, 4, 4), 262144, 60, 50_000
+    start = naive_start(*fmt)
+    W = tfg.Walkers([(fmt, 0, start, nw)], seed=8, params=tfg.tfg_default_params(plateau_len=L))
+    if policy == 1:
+        p = mlp.Params.random(np.random.default_rng(5))
+        ch = W.walk_window(steps, policy=1, mlp_params=device_params(p), eps_thresh=int(0.05 * 2**32),
+                           record_choices=True).cpu().numpy()
+    else:
+        W.walk_window(steps, policy=0)
+    W.sync()
+    ids = np.linspace(0, nw - 1, 16).astype(int)
+    rows = [W.read_walkers(int(w), 1) for w in ids]
+    info = np.concatenate([x[0] for x in rows])
+    slots = np.concatenate([x[1] for x in rows])
+    best = np.concatenate([x[2] for x in rows])
+    ref = oracle.Walkers(fmt, start, ids, seed=8, plateau_len=L)
+    if policy == 1:
+        ref.walk_window(steps, policy=1, choices=np.ascontiguousarray(ch[:, ids].T), threads=THREADS)
+    else:
+        ref.walk_window(steps, threads=THREADS)
+    assert (ref.info["accepted"] > 0).any()
+    for a in range(ids.size):
+        for f in FIELDS:
+            assert info[f][a] == ref.info[f][a], f"walker {ids[a]}: {f} gpu={info[f][a]} oracle={ref.info[f][a]}"
+        r, br = ref.info["r"][a], ref.info["best_r"][a]
+        assert np.array_equal(slots[a, :r], ref.slots[a, :r]) and np.array_equal(best[a, :br], ref.best[a, :br])
+    W.close()
+
+
 @pytest.mark.parametrize("fmt", [(3, 3, 3), (4, 4, 4)])
 def test_window_features_scores_and_choice(fmt):
     """One learned step from a walked state: features and candidates equal the
