@@ -85,10 +85,10 @@ def invariants(fmt, scheme, mode):
             "rank_sums": [int(x) for x in sums]}
 
 
-def lift_population(W, f, max_tries: int = 256, max_nodes: int = 10**6):
+def lift_population(W, f, max_tries: int = 256, max_nodes: int = 10**6, stop_at_first: bool = False):
     """Z_2 -> Z_T sign lifting of the best schemes of the walkers at a Z_2
     population's lowest rank (up to max_tries of them): how many lift, and the
-    first ternary scheme found."""
+    first ternary scheme found (stop_at_first: stop there)."""
     pop = W.pop[f]
     info, _, _ = W.read_walkers(pop["first"], pop["walkers"], slots=False, best=False)
     low = int(info["best_r"].min())
@@ -104,6 +104,8 @@ def lift_population(W, f, max_tries: int = 256, max_nodes: int = 10**6):
         lifted += 1
         if first is None:
             first = zt
+            if stop_at_first:
+                break
     return low, len(cands), lifted, first
 
 
@@ -284,24 +286,32 @@ def device_resize_move(rng, W, formats, index, bests, block, next_block, p_resiz
 
 def explore(formats, walkers: int, cycles: int, steps_per_cycle: int, seed: int, plateau: int = 50_000,
             reseed_frac: float = 0.25, p_resize: float = 0.5, moves_per_cycle: int = 8, starts: dict | None = None,
-            r_slack: int = 3, quiet: bool = False, device_moves: int = 0, device_frac: float = 0.125):
+            r_slack: int = 3, quiet: bool = False, device_moves: int = 0, device_frac: float = 0.125,
+            lift_z2: bool = False):
     """Exploratory search over `formats` (Z_T, one population each, naive starts
     unless `starts` gives one).  Each cycle: a walk chunk; population sync (each
     format's best collected and verified); `moves_per_cycle` Resize moves of the
     best schemes on the host, whose prepared results re-seed a block of the
     result format's walkers when they beat its best; and `device_moves` Resize
     moves on the device (device_resize_move: blocks of device_frac of a
-    population, per walker).  Returns (per-population results, transfer log)."""
+    population, per walker).  lift_z2: a Z_2 population of every format walks
+    beside the Z_T ones, and each cycle a Z_2 best below the format's Z_T best is
+    lifted to Z_T signs (tfg_lift_signs) and re-seeds a block of the Z_T walkers
+    (the paper's Z_2 search followed by its ternary lifting).  Returns
+    (per-population results, transfer log)."""
     # one process per GPU (torch.distributed initialised): every rank runs its own
     # walkers of every format (global ids rank * len(formats) * walkers + ...), and the
     # population synchronisation takes each format's best over all ranks
     import torch.distributed as dist
     multi = dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1
     me = dist.get_rank() if multi else 0
-    id_base = me * len(formats) * walkers
+    id_base = me * len(formats) * walkers * (2 if lift_z2 else 1)
     rng = np.random.default_rng(seed + 7919 * me)
     starts = starts or {}
     pops = [(f, tfg.TFG_MODE_ZT, starts.get(f, naive_start(*f)), walkers) for f in formats]
+    if lift_z2:
+        pops += [(f, tfg.TFG_MODE_Z2, np.abs(starts.get(f, naive_start(*f))).astype(np.int8), walkers)
+                 for f in formats]
     W = tfg.Walkers(pops, seed=seed, params=tfg.tfg_default_params(plateau_len=plateau, r_slack=r_slack,
                                                                     walker_id_base=id_base))
 
@@ -315,7 +325,8 @@ def explore(formats, walkers: int, cycles: int, steps_per_cycle: int, seed: int,
             local = shard.sync_bests(local, {f: tfg.term_len(f) for f in formats},
                                      {f: W.pop[index[f]]["r_max"] for f in formats})
         return {f: local[f][2] for f in formats}
-    index = {f: a for a, f in enumerate(formats)}
+    index = {f: a for a, f in enumerate(formats)}             # the Z_T populations
+    z2_index = {f: len(formats) + a for a, f in enumerate(formats)} if lift_z2 else {}
     block = max(1, int(walkers * reseed_frac))
     next_block = {f: 0 for f in formats}
     next_dblock = {f: 0 for f in formats}
@@ -341,6 +352,24 @@ def explore(formats, walkers: int, cycles: int, steps_per_cycle: int, seed: int,
             next_block[f2] = (next_block[f2] + block) % max(1, walkers - block + 1)
             bests[f2] = prepared
             transfers.append({"cycle": cycle, "from": list(src), "to": list(f2), "op": op,
+                              "rank": int(prepared.shape[0])})
+            if not quiet:
+                print(json.dumps({"transfer": transfers[-1]}), flush=True)
+        for f, zf in z2_index.items():
+            low = W.stats(zf)[0]["min_best_r"]
+            if low >= bests[f].shape[0]:
+                continue
+            _, _, _, zt = lift_population(W, zf, max_tries=32, stop_at_first=True)
+            if zt is None:
+                continue
+            prepared = tfg.tfg_prepare(f, zt)
+            if prepared.shape[0] >= bests[f].shape[0] or prepared.shape[0] > W.pop[index[f]]["r_max"]:
+                continue
+            first = W.pop[index[f]]["first"] + next_block[f]
+            W.reseed(first, block, prepared)
+            next_block[f] = (next_block[f] + block) % max(1, walkers - block + 1)
+            bests[f] = prepared
+            transfers.append({"cycle": cycle, "from": list(f), "to": list(f), "op": "lift",
                               "rank": int(prepared.shape[0])})
             if not quiet:
                 print(json.dumps({"transfer": transfers[-1]}), flush=True)
@@ -383,6 +412,8 @@ def main():
     ap.add_argument("--p-expand", type=float, default=0.0, help="walk policy 1: expansion probability after a flip")
     ap.add_argument("--r-slack", type=int, default=3, help="slots per walker beyond the start rank")
     ap.add_argument("--explore", type=int, default=0, help="exploratory search: number of walk + resize cycles")
+    ap.add_argument("--lift-z2", action="store_true",
+                    help="exploratory search: Z_2 populations beside the Z_T ones, lifted to Z_T each cycle")
     ap.add_argument("--device-moves", type=int, default=0,
                     help="exploratory search: Resize moves per cycle on the device (blocks of walkers)")
     ap.add_argument("--quiet", action="store_true")
@@ -392,7 +423,7 @@ def main():
     if args.explore > 0:
         res, transfers = explore(EXPLORE_FORMATS, args.walkers or 16384, args.explore, int(args.steps), args.seed,
                                  plateau=args.plateau or 50_000, r_slack=args.r_slack, quiet=args.quiet,
-                                 device_moves=args.device_moves)
+                                 device_moves=args.device_moves, lift_z2=args.lift_z2)
         for r in res:
             print(json.dumps(r), flush=True)
         print(json.dumps({"transfers": len(transfers)}), flush=True)

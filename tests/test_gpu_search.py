@@ -90,3 +90,19 @@ def test_exploration_with_device_resize_moves():
     assert {t["op"][:4] for t in dev} & {"swap", "merg", "doub", "exte", "prod", "proj"}
     for r in res:
         assert r["best_scheme_verified_host"] and r["device_check_failures"] == 0
+
+
+def test_exploration_lifts_z2_schemes_into_ternary_populations():
+    """Z_2 populations walk beside the Z_T ones; a Z_2 best below the Z_T best of its
+    format is lifted to Z_T signs and re-seeds the Z_T walkers, whose final best
+    is then at most the lifted rank and satisfies Eq. (1) over the integers."""
+    formats = [(2, 2, 2), (3, 3, 3)]
+    res, transfers = search.explore(formats, walkers=4096, cycles=4, steps_per_cycle=25000, seed=3,
+                                    moves_per_cycle=0, lift_z2=True, quiet=True)
+    lifts = [t for t in transfers if t["op"] == "lift"]
+    assert any(tuple(t["to"]) == (3, 3, 3) for t in lifts)
+    by = {tuple(r["format"]): r for r in res}
+    low = min(t["rank"] for t in lifts if tuple(t["to"]) == (3, 3, 3))
+    assert by[(3, 3, 3)]["lowest_rank"] <= low < 27
+    for r in res:
+        assert r["best_scheme_verified_host"] and r["device_check_failures"] == 0
