@@ -412,6 +412,8 @@ def main():
     ap.add_argument("--p-expand", type=float, default=0.0, help="walk policy 1: expansion probability after a flip")
     ap.add_argument("--r-slack", type=int, default=3, help="slots per walker beyond the start rank")
     ap.add_argument("--explore", type=int, default=0, help="exploratory search: number of walk + resize cycles")
+    ap.add_argument("--formats", default=None,
+                    help="exploratory search: formats as m x n x p list, e.g. 2x2x2,3x3x3 (default: nine up to 4x4x4)")
     ap.add_argument("--lift-z2", action="store_true",
                     help="exploratory search: Z_2 populations beside the Z_T ones, lifted to Z_T each cycle")
     ap.add_argument("--device-moves", type=int, default=0,
@@ -421,7 +423,9 @@ def main():
     import torch
     torch.cuda.set_device(0)
     if args.explore > 0:
-        res, transfers = explore(EXPLORE_FORMATS, args.walkers or 16384, args.explore, int(args.steps), args.seed,
+        fmts = EXPLORE_FORMATS if not args.formats else \
+            [tuple(int(x) for x in f.split("x")) for f in args.formats.split(",")]
+        res, transfers = explore(fmts, args.walkers or 16384, args.explore, int(args.steps), args.seed,
                                  plateau=args.plateau or 50_000, r_slack=args.r_slack, quiet=args.quiet,
                                  device_moves=args.device_moves, lift_z2=args.lift_z2)
         for r in res:
