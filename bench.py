@@ -247,7 +247,14 @@ def run_ours(args):
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         t_max = float(tt.item())
     total_steps = walker_steps * world
-    value = total_steps / t_max
+    # the metric counts applied flips: steps whose flip passed the ternary check and was made
+    applied = sum(W.stats(f)[0]["accepted"] - st0_f[f]["accepted"] for f in range(W.n_formats))
+    if world > 1:
+        ta = torch.tensor([applied], dtype=torch.int64, device="cuda")
+        torch.distributed.all_reduce(ta)
+        applied = int(ta.item())
+    value = applied / t_max
+    steps_per_s = total_steps / t_max
 
     # roofline of the walk kernel: algorithmic integer ops per launch / launch time
     ops = 0.0
@@ -263,7 +270,7 @@ def run_ours(args):
             "lowest_rank": a1["min_best_r"], "mean_live_rank": round(mean_r, 2),
             "rank_hist": {int(k): int(v) for k, v in enumerate(W.stats(f)[1]) if v},
             "accepted_frac": round(acc / max(steps_f, 1), 4),
-            "reductions_per_1e9_flips": round((a1["reductions"] - a0["reductions"]) / max(steps_f, 1) * 1e9, 1),
+            "reductions_per_1e9_flips": round((a1["reductions"] - a0["reductions"]) / max(acc, 1) * 1e9, 1),
             "mapping": mapping_name(W.pop[f])}
     walk_s = sum(walk_ms) / 1e3
     achieved = ops / walk_s / 1e12          # Tops/s
@@ -272,13 +279,14 @@ def run_ours(args):
     alu_peak = 152 * 4 * 16 * 2.07e9 / 1e12
     traffic = recorded_traffic() if args.workload == "333" else None   # the capture is of that workload
 
-    # end to end through the public API with host buffers, per step:
-    # init from the host start schemes, walk, verify, collect best to the host
+    # end to end through the public API with host buffers, per step: init from the
+    # host start schemes (H2D), walk, verify, collect each population's best scheme
+    # to the host (D2H) and read the counters; applied flips / wall time
     e2e_steps = max(1, min(args.steps, 3))
     h2d = sum(np.asarray(p[2]).nbytes for p in pops)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    d2h = 0
+    d2h, e2e_applied = 0, 0
     for _ in range(e2e_steps):
         E = tfg.Walkers(pops, seed=args.seed + 1, params=params)
         E.walk(args.chunk)
@@ -286,16 +294,19 @@ def run_ours(args):
         for f in range(E.n_formats):
             sch, r, w = E.collect_best(f)
             d2h += sch.nbytes + 8
+        e2e_applied += E.stats()[0]["accepted"]
+        d2h += 8 * 11
         E.close()
         del E
     torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
-    e2e_val = total_steps / args.steps * e2e_steps / e2e_t
+    e2e_val = e2e_applied * world / e2e_t
 
     line = {
         "metric": METRIC,
         "value": value,
         "unit": "flips/s",
+        "walker_steps_per_s": steps_per_s,
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
@@ -308,7 +319,6 @@ def run_ours(args):
         "config": {"workload": workload_name(args, pops, plateau),
                    "walkers_per_gpu": per_rank, "steps_per_walker_per_step": args.chunk,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"walker shards x{world}"},
-        "accepted_flips_per_s": None,
         "modes": per_mode,
         "verified": {"device_checked_best_schemes": per_rank * args.steps, "failures": verify_failures,
                      "collected_best_ranks": best_ranks},
@@ -322,8 +332,6 @@ def run_ours(args):
         "clocks": clk,
         "wall_s": wall,
     }
-    sacc = sum(W.stats(f)[0]["accepted"] - st0_f[f]["accepted"] for f in range(W.n_formats))
-    line["accepted_flips_per_s"] = value * sacc / max(walker_steps, 1)
     if lanes is not None:
         line["config"]["autotuned_lanes_per_walker"] = lanes
     if world > 1:
@@ -344,7 +352,8 @@ def run_ours(args):
     if rank == 0 and args.learned:
         line["learned_vs_uniform"] = learned_ab(args)
     if rank == 0 and args.cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args, pops, plateau, budget_s=args.cpu_seconds)
+        cb = oracle_sample(args, pops, plateau)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -368,30 +377,39 @@ def learned_ab(args):
             "results": res, "seconds": time.perf_counter() - t0}
 
 
-def cpu_baseline(args, pops, plateau, budget_s=15.0):
+def oracle_sample(args, pops, plateau):
     """The oracle as it stands, on the host cores, on a bounded sample of the
-    workload: walkers 0, 256, 512, ... of each population, `n` steps each."""
+    bench workload: walkers 0, 256, 512, ... of each population (256 per
+    population at the default size), advanced exactly like the GPU walkers --
+    warmup + steps chunks of --cpu-chunk steps each (default: the bench's own
+    chunk), the timed chunks after the warm-up ones.  Returns the applied
+    flips per second of the timed chunks and the per-chunk times.  Both the GPU
+    arm's cpu_baseline and the reference arm run this same sample."""
     import oracle
     threads = len(os.sched_getaffinity(0))
-    total_steps, total_t = 0, 0.0
-    n_w = max(threads, 16)
-    steps = 2000
+    chunk = args.cpu_chunk or args.chunk
+    walkers = []
     for fmt, mode, start, nw in pops:
-        ids = np.arange(0, nw, max(1, nw // n_w))[:n_w]
-        W = oracle.Walkers(fmt, start, ids, seed=args.seed, mode=mode, plateau_len=plateau)
+        ids = np.arange(0, nw, max(1, nw // args.cpu_walkers))[:args.cpu_walkers]
+        walkers.append(oracle.Walkers(fmt, start, ids, seed=args.seed, mode=mode, plateau_len=plateau))
+    n_w = sum(w.walker_ids.size for w in walkers)
+    per_step, applied, steps_done = [], 0, 0
+    for k in range(args.warmup + args.steps):
+        acc0 = sum(int(w.info["accepted"].sum()) for w in walkers)
         t0 = time.perf_counter()
-        W.walk(steps, threads)
+        for w in walkers:
+            w.walk(chunk, threads)
         dt = time.perf_counter() - t0
-        # scale the sample so that the timed CPU work is roughly budget_s per population
-        reps = max(1, int(budget_s / len(pops) / max(dt, 1e-3)) - 1)
-        t1 = time.perf_counter()
-        W.walk(steps * reps, threads)
-        dt += time.perf_counter() - t1
-        total_steps += ids.size * steps * (reps + 1)
-        total_t += dt
-    return {"value": total_steps / total_t, "unit": "flips/s", "cores": threads, "kind": "oracle",
-            "sample": f"{n_w} walkers per population, the first steps of their trajectories, "
-                      f"{total_steps} walker-steps in {total_t:.1f} s"}
+        if k >= args.warmup:
+            per_step.append(dt)
+            applied += sum(int(w.info["accepted"].sum()) for w in walkers) - acc0
+            steps_done += n_w * chunk
+    t = sum(per_step)
+    return {"value": applied / t, "unit": "flips/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n_w} walkers ({args.cpu_walkers} per population, ids spread over it) advanced "
+                      f"{args.warmup} + {args.steps} chunks of {chunk} steps like the GPU walkers; "
+                      f"{applied} applied flips in {steps_done} walker-steps over {t:.1f} s timed",
+            "ms_per_step": t / max(1, len(per_step)) * 1e3, "walker_steps_per_s": steps_done / t}
 
 
 def run_reference(args):
@@ -399,23 +417,20 @@ def run_reference(args):
     if rank != 0:
         return
     pops, plateau = populations(args)
-    cb = cpu_baseline(args, pops, plateau, budget_s=max(5.0, 40.0 / max(1, args.steps + args.warmup)))
-    # steps: each bench step re-times the bounded sample
-    vals = []
-    for _ in range(args.warmup + args.steps):
-        vals.append(cpu_baseline(args, pops, plateau, budget_s=max(3.0, 60.0 / (args.steps + args.warmup)))["value"])
-    value = float(np.median(vals[args.warmup:])) if args.steps else cb["value"]
-    cb["value"] = value
-    # one bench step of the workload (every walker, args.chunk steps), at the sampled rate
+    cb = oracle_sample(args, pops, plateau)
+    value = cb["value"]
     step_walker_steps = sum(p[3] for p in pops) * args.chunk
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "flips/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_walker_steps / value * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["ms_per_step"],
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "i8", "data": "synthetic",
-            "config": {"workload": "3x3x3 naive27 Z_T+Z_2 (bounded sample on host cores)",
-                       "ms_per_step": "extrapolated from the sampled rate to one bench step "
-                                      f"({step_walker_steps} walker-steps)"},
-            "cpu_baseline": cb,
+            "config": {"workload": "333: 3x3x3 naive27 Z_T + Z_2, the oracle on a bounded sample of the "
+                                   "walkers on the host cores",
+                       "sample_walkers": args.cpu_walkers * len(pops),
+                       "steps_per_walker_per_step": args.cpu_chunk or args.chunk},
+            "walker_steps_per_s": cb["walker_steps_per_s"],
+            "full_step_extrapolated_ms": step_walker_steps / cb["walker_steps_per_s"] * 1e3,
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": value, "unit": "flips/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -432,7 +447,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--mapping", type=int, default=0)
     ap.add_argument("--graph", type=int, default=2, help="0 plain launches, 1 chained graph, 2 forked graph (default: the two populations run concurrently)")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-walkers", type=int, default=256, help="oracle sample: walkers per population")
+    ap.add_argument("--cpu-chunk", type=int, default=0, help="oracle sample: steps per chunk (0: --chunk)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-learned", dest="learned", action="store_false")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")

@@ -230,7 +230,10 @@ int tfg_init(int32_t n_formats, const tfg_format *fmts, const int32_t *ranks,
  * the next tfg_sync. */
 int tfg_walk(tfg_ctx *ctx, int64_t steps);
 
-/* Wait for the context stream; returns the first CUDA error seen, if any. */
+/* Wait for the context stream; returns the first CUDA error seen, if any,
+ * else TFG_ETIMEOUT when a bounded device wait of the context's work gave up
+ * since the last tfg_sync (the context's status word, set by the device, read
+ * here and cleared after reading; the context stays usable), else TFG_OK. */
 int tfg_sync(tfg_ctx *ctx);
 
 /* Best scheme of population `format_idx`: the walker with the lowest best rank
@@ -389,13 +392,26 @@ int tfg_mlp_train_step(void *d_state, void *d_params, const uint16_t *d_x, const
                        const float *d_weight, int64_t n, float lr, int32_t step, int32_t *d_err, void *cuda_stream);
 
 /* Window-mode walk (the step the learned proposal acts on).  Each step of a
- * walker considers a window of up to 128 try_flip candidates: starting at term
+ * walker considers a window of up to 256 try_flip candidates: starting at term
  * i0 = mulhi(x0, r), terms i0, i0+1, ... (mod r) append their candidates in
- * (factor, slot, rho) order until 128 are collected.  Each candidate gets 32
- * small-integer features (see the design doc of the repository: one-hot factor,
- * rho, sign, non-zero counts and ternary validity of the two sums, overlaps,
- * zero-sum flags, candidate count and window position of the term, r - best_r,
- * r, m, n, p, a constant 1).  policy 0 (uniform): candidate mulhi(x1, K);
+ * (factor, slot, rho) order until 256 are collected.  Candidate (X, j, s, rho)
+ * of term i flips Y_i' = Y_i + Y_j and Z_j' = Z_j - s Z_i, where (Y, Z) are the
+ * two factors after X in the order u, v, w, swapped when rho = 1.  Its 32
+ * features (bf16 values of small integers; nnz = number of non-zero
+ * coefficients):
+ *   f0..f2  one-hot X (u, v, w)        f3  rho            f4  1 when s = -1
+ *   f5  nnz(X_i)   f6  nnz(Y_i)   f7  nnz(Y_j)
+ *   f8  nnz(Y_i + Y_j) when that sum stays in Z_T, else 0;  f9  1 when it does
+ *   f10 nnz(Z_i)   f11 nnz(Z_j)
+ *   f12 nnz(Z_j - s Z_i) when in Z_T, else 0;  f13  1 when it is
+ *   f14 positions where Y_i and Y_j are both non-zero;  f15  the same for Z
+ *   f16 1 when Y_i + Y_j is valid and zero;  f17  1 when Z_j - s Z_i is
+ *   f18 the number of candidates of term i, at most 64
+ *   f19 r - best_r   f20 r   f21 m   f22 n   f23 p
+ *   f24 the position q of term i after i0 (i = i0 + q mod r), at most 64
+ *   f25..f30 0       f31 1
+ * Rows of a window past its K candidates are zero.  policy 0 (uniform):
+ * candidate mulhi(x1, K);
  * policy 1 (learned): with x3 < eps_thresh as policy 0, else the candidate of
  * highest MLP score (first on ties).  The chosen flip then goes through the
  * same validity test, reductions and bookkeeping as tfg_walk.
@@ -430,17 +446,30 @@ int tfg_walk_window(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_m
  * memory is reserved up front): the window features, candidate descriptors
  * and scores live in a 32 MiB array that the library itself defines as static
  * device memory, which every GPU that loads the library holds until the
- * process exits.  Contexts of more than 3639 walkers (the array's capacity at
- * 9220 bytes per walker) are rejected with TFG_EINVAL and a message.  The call
- * allocates nothing; the context's device must be current; the first call on a
- * device looks up the array's device address, so make that first call before
- * any stream capture.  All calls share the one array (it keeps the last
+ * process exits.  Contexts of more than 1820 walkers (the array's capacity at
+ * 18436 bytes per walker) are rejected with TFG_EINVAL and a message.  The call
+ * allocates nothing: tfg_init already looked up the array's device address on
+ * its device, which loads the library's module there and so reserves the
+ * 32 MiB at that point at the latest (under lazy module loading; at library
+ * load otherwise).  The context's device must be current (TFG_EINVAL
+ * otherwise).  All calls share the one array (it keeps the last
  * call's contents; every value a step reads is written by the same step), so
  * calls whose work overlaps on the GPU, such as two contexts on different
  * streams, race on it and must be serialised by the caller.  Results equal
  * tfg_walk_window's for the same context and arguments. */
 int tfg_walk_window_noalloc(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_mlp_params,
                             uint32_t eps_thresh, int32_t *d_choices, const tfg_log_spec *log);
+
+/* Test hook of the bounded device waits: the first tensor-core completion
+ * wait of every CTA of the scoring network (tfg_mlp_score and the learned
+ * window mode) polls at most `polls` times in later launches; a negative
+ * value restores the default of 2^22 polls, 0 makes that wait give up at
+ * once.  A CTA whose wait gave up skips its remaining tiles, waits (with the
+ * default limit) for its products in flight, releases its tensor memory and
+ * sets its error word: *d_err of tfg_mlp_score, or in window mode the
+ * context's status word, which the next tfg_sync returns as TFG_ETIMEOUT.
+ * Process-wide setting; it changes no result of a launch whose waits finish. */
+void tfg_test_set_wait_limit(int64_t polls);
 
 /* Philox4x32-10 of the device path, for tests: d_out[4k..4k+3] = Philox(d_ctr[4k..4k+3],
  * key), n counters; d_ctr and d_out are caller-owned device arrays of 4n words.

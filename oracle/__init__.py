@@ -94,7 +94,7 @@ def lib():
             L.orc_window_features.argtypes = [i32, i32, i32, i32, i32, P, i32, i32, P, P]
             L.orc_window_features.restype = i32
             L.orc_walk_window.argtypes = [i32, i32, i32, ctypes.POINTER(Params), i32, u64, i32, P, i64, i32,
-                                          i32, i32, P, P, P, P]
+                                          i32, i32, P, P, P, P, P, P, u32]
             L.orc_digest_init.argtypes = [u32]
             L.orc_digest_init.restype = u64
             L.orc_info_size.restype = i32
@@ -197,7 +197,7 @@ def apply_flip(fmt, scheme, i, X, j, s, rho, mode=MODE_ZT):
     return int(action), buf[: r_out.value].copy()
 
 
-WINDOW = 128
+WINDOW = 256   # candidates per window-mode step (up to 256 candidate pairs per step)
 
 
 def window_features(fmt, scheme, best_r, i0, W=WINDOW):
@@ -255,9 +255,12 @@ class Walkers:
         return self
 
     def walk_window(self, steps: int, policy: int = 0, choices=None, window: int = WINDOW,
-                    threads: int | None = None):
+                    threads: int | None = None, log_neg_thresh: int | None = None):
         """Window-mode steps: policy 0 uniform over the window, policy 1 replays
-        choices [n_walkers, steps] (window index per step, -1 = no candidate)."""
+        choices [n_walkers, steps] (window index per step, -1 = no candidate).
+        With log_neg_thresh given, the training-log records of these steps are
+        kept in self.log_label [n_walkers, steps] (-1: no record, else the label)
+        and self.log_feat [n_walkers, steps, 32] (uint8 features)."""
         if threads is None:
             threads = len(os.sched_getaffinity(0))
         m, n, p = self.fmt
@@ -265,10 +268,17 @@ class Walkers:
         if policy == 1:
             ch = np.ascontiguousarray(choices, dtype=np.int32)
             assert ch.shape == (self.walker_ids.size, steps)
+        lab = feat = None
+        if log_neg_thresh is not None:
+            lab = np.full((self.walker_ids.size, steps), -1, np.int8)
+            feat = np.zeros((self.walker_ids.size, steps, 32), np.uint8)
         lib().orc_walk_window(m, n, p, ctypes.byref(self.params), self.r_max, self.seed, self.walker_ids.size,
                               _ptr(self.walker_ids), int(steps), int(threads), int(window), int(policy),
                               _ptr(ch) if ch is not None else None, _ptr(self.slots), _ptr(self.best),
-                              _ptr(self.info))
+                              _ptr(self.info), _ptr(lab) if lab is not None else None,
+                              _ptr(feat) if feat is not None else None,
+                              int(log_neg_thresh or 0))
+        self.log_label, self.log_feat = lab, feat
         return self
 
     def scheme(self, w: int) -> np.ndarray:

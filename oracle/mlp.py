@@ -6,6 +6,7 @@ fixes: inputs, W1 and W2 are bf16 values, and the first hidden layer is
 rounded to bf16 before the second product (round to nearest, ties to even).
 Everything else is exact float64 here, so the device path differs only by
 FP32 accumulation order (and the rare bf16 rounding flip that causes).
+The optimiser of the training step, Adam, is written out as well (class Adam).
 """
 from __future__ import annotations
 
@@ -111,3 +112,28 @@ def split_vector(vec):
         out[name] = vec[o:o + k].reshape(shape) if shape else float(vec[o])
         o += k
     return out
+
+
+class Adam:
+    """Adam (Kingma & Ba, "Adam: A Method for Stochastic Optimization", ICLR 2015,
+    Algorithm 1) over a flat float64 parameter vector, written from its
+    definition: m <- b1 m + (1 - b1) g;  v <- b2 v + (1 - b2) g^2;
+    m_hat = m / (1 - b1^t);  v_hat = v / (1 - b2^t);
+    theta <- theta - lr m_hat / (sqrt(v_hat) + eps), with t counted from 1."""
+
+    def __init__(self, theta, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.theta = np.array(theta, dtype=np.float64)
+        self.m = np.zeros_like(self.theta)
+        self.v = np.zeros_like(self.theta)
+        self.beta1, self.beta2, self.eps = float(beta1), float(beta2), float(eps)
+        self.t = 0
+
+    def step(self, grad, lr):
+        g = np.asarray(grad, dtype=np.float64)
+        self.t += 1
+        self.m = self.beta1 * self.m + (1.0 - self.beta1) * g
+        self.v = self.beta2 * self.v + (1.0 - self.beta2) * g * g
+        m_hat = self.m / (1.0 - self.beta1 ** self.t)
+        v_hat = self.v / (1.0 - self.beta2 ** self.t)
+        self.theta = self.theta - lr * m_hat / (np.sqrt(v_hat) + self.eps)
+        return self.theta

@@ -753,31 +753,65 @@ static void window_features(const walker *wk, const wcand_t *c, float *f)
     f[31] = 1.f;
 }
 
+/* Training log of one window-mode step (the record the learned proposal is
+ * trained on): the chosen candidate's features, computed on the state before
+ * the flip, with label 1 when the step lowered the rank (the reductions
+ * counter advanced: a zero-term removal or a merge after the flip), else
+ * label 0; label-0 records are kept only when the first word of Philox
+ * sub-stream 256 of the step, (t_lo, t_hi, walker, 256), lies below
+ * neg_thresh.  *label_out = -1 when the step keeps no record (no candidate,
+ * or an unsampled label-0 step). */
+typedef struct {
+    int8_t *label;     /* [steps] per walker: -1, 0 or 1 */
+    uint8_t *feat;     /* [steps][32] per walker */
+    uint32_t neg_thresh;
+} wlog_t;
+
 /* One window-mode step.  policy 0: candidate mulhi(x1, K); otherwise the
  * candidate index is taken from *choice (a logged decision being replayed,
- * -1 when there was no candidate). */
-static void walk_step_window(walker *wk, wcand_t *wbuf, cand_t *tmp, int W, int policy, const int32_t *choice)
+ * -1 when there was no candidate).  lg (may be NULL) receives the step's
+ * training-log record at position `slot`. */
+static void walk_step_window(walker *wk, wcand_t *wbuf, cand_t *tmp, int W, int policy, const int32_t *choice,
+                             const wlog_t *lg, int64_t slot)
 {
     orc_info *in = wk->info;
     uint64_t t = (uint64_t)in->t;
     uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(t >> 32), wk->walker_id, 0u}, x[4];
     orc_philox4x32_10(ctr, wk->key, x);
     int r_before = in->r;
+    int64_t red_before = in->reductions;
     int i0 = (int)mulhi_range(x[0], (uint32_t)in->r);
     int K = build_window(wk, i0, W, wbuf, tmp);
     int action = ORC_NOCAND, X = 0, j = 0, s = 1, rho = 0, i = i0;
+    float f[ORC_FEATURES];
     if (K > 0) {
         int c = (policy == 0) ? (int)mulhi_range(x[1], (uint32_t)K) : *choice;
         if (c < 0 || c >= K) { in->debug_failures += 1; c = 0; }
         wcand_t w = wbuf[c];
         cand_t cc = {w.X, w.j, w.s, w.rho};
         i = w.i; X = w.X; j = w.j; s = w.s; rho = w.rho;
+        if (lg) window_features(wk, &w, f);
         action = apply_flip(wk, i, cc);
     } else {
         if (policy != 0 && *choice != -1) in->debug_failures += 1;
         in->nocand += 1;
     }
     finish_step(wk, x, r_before, action, X, rho, s, i, j);
+    if (lg) {
+        int label = -1;
+        if (K > 0) {
+            if (in->reductions > red_before) {
+                label = 1;
+            } else if (lg->neg_thresh) {
+                uint32_t c2[4] = {(uint32_t)t, (uint32_t)(t >> 32), wk->walker_id, 256u}, y[4];
+                orc_philox4x32_10(c2, wk->key, y);
+                if (y[0] < lg->neg_thresh) label = 0;
+            }
+        }
+        lg->label[slot] = (int8_t)label;
+        for (int k = 0; k < ORC_FEATURES; ++k)
+            lg->feat[(size_t)slot * ORC_FEATURES + k] = label >= 0 ? (uint8_t)f[k] : 0;
+    }
 }
 
 /* Window and features of a given state (rank r, best rank best_r) for i0:
@@ -866,6 +900,9 @@ typedef struct {
     int window;              /* 0: walk_step; > 0: window mode with this capacity */
     int policy;              /* window mode: 0 uniform, 1 replay choices */
     const int32_t *choices;  /* replay: [n_walkers][steps] */
+    int8_t *log_label;       /* window mode, optional: [n_walkers][steps] training-log labels */
+    uint8_t *log_feat;       /* [n_walkers][steps][32] */
+    uint32_t neg_thresh;
     int n_walkers;
     const uint32_t *walker_ids;
     int8_t *slots, *best;
@@ -889,9 +926,16 @@ static void run_walker(job_t *job, int w)
     cand_t *cbuf = (cand_t *)malloc(sizeof(cand_t) * (size_t)(6 * job->r_max + 6));
     if (job->window > 0) {
         wcand_t *wbuf = (wcand_t *)malloc(sizeof(wcand_t) * (size_t)job->window);
+        wlog_t lg;
+        if (job->log_label) {
+            lg.label = job->log_label + (size_t)w * job->steps;
+            lg.feat = job->log_feat + (size_t)w * job->steps * ORC_FEATURES;
+            lg.neg_thresh = job->neg_thresh;
+        }
         for (int64_t s = 0; s < job->steps; ++s)
             walk_step_window(&wk, wbuf, cbuf, job->window, job->policy,
-                             job->choices ? job->choices + (size_t)w * job->steps + s : NULL);
+                             job->choices ? job->choices + (size_t)w * job->steps + s : NULL,
+                             job->log_label ? &lg : NULL, s);
         free(wbuf);
     } else {
         for (int64_t s = 0; s < job->steps; ++s) walk_step(&wk, cbuf);
@@ -924,6 +968,7 @@ void orc_walk(int m, int n, int p, int mode, const orc_params *prm, int r_max, u
     job.n_walkers = n_walkers; job.walker_ids = walker_ids;
     job.slots = slots; job.best = best; job.info = info; job.next = 0;
     job.window = 0; job.policy = 0; job.choices = NULL;
+    job.log_label = NULL; job.log_feat = NULL; job.neg_thresh = 0;
     pthread_mutex_init(&job.lock, NULL);
     if (n_threads < 1) n_threads = 1;
     if (n_threads > n_walkers) n_threads = n_walkers > 0 ? n_walkers : 1;
@@ -935,10 +980,14 @@ void orc_walk(int m, int n, int p, int mode, const orc_params *prm, int r_max, u
 }
 
 /* Window mode: policy 0 picks uniformly over the window; policy 1 replays
- * choices [n_walkers][steps] (window index per step, -1 for no candidate). */
+ * choices [n_walkers][steps] (window index per step, -1 for no candidate).
+ * log_label / log_feat (both NULL, or [n_walkers][steps] and
+ * [n_walkers][steps][32]) receive each step's training-log record (see
+ * wlog_t) with label-0 records sampled below neg_thresh. */
 void orc_walk_window(int m, int n, int p, const orc_params *prm, int r_max, uint64_t seed, int n_walkers,
                      const uint32_t *walker_ids, int64_t steps, int n_threads, int window, int policy,
-                     const int32_t *choices, int8_t *slots, int8_t *best, orc_info *info)
+                     const int32_t *choices, int8_t *slots, int8_t *best, orc_info *info,
+                     int8_t *log_label, uint8_t *log_feat, uint32_t neg_thresh)
 {
     orc_fmt f = make_fmt(m, n, p, ORC_MODE_ZT);
     job_t job;
@@ -946,6 +995,7 @@ void orc_walk_window(int m, int n, int p, const orc_params *prm, int r_max, uint
     job.n_walkers = n_walkers; job.walker_ids = walker_ids;
     job.slots = slots; job.best = best; job.info = info; job.next = 0;
     job.window = window; job.policy = policy; job.choices = choices;
+    job.log_label = log_feat ? log_label : NULL; job.log_feat = log_feat; job.neg_thresh = neg_thresh;
     pthread_mutex_init(&job.lock, NULL);
     if (n_threads < 1) n_threads = 1;
     if (n_threads > n_walkers) n_threads = n_walkers > 0 ? n_walkers : 1;

@@ -29,6 +29,8 @@ struct Aux {
     int64_t sums[9];
     int32_t minmax[2];
     int64_t verify_failures;
+    int32_t status;          // 1: a bounded device wait gave up (read and cleared by tfg_sync)
+    int32_t status_pad;
     int64_t hist[kHistCap];
 };
 constexpr size_t kAuxBytes = (sizeof(Aux) + kAlign - 1) / kAlign * kAlign;
@@ -116,6 +118,32 @@ const tfg::WalkVariant *default_variant(int mode, int bits, int tw, int R, const
         if (v && v->S <= 4) return v;
     }
     return pick_variant(mode, bits, tw, 32, R, fmt);
+}
+
+// Window scratch of tfg_walk_window_noalloc, for callers that cannot call
+// cudaMalloc: a static device array of this translation unit.  Host code only
+// sees a host-side stand-in of the symbol, so its device address is looked up
+// per device with cudaGetSymbolAddress.  tfg_init does that lookup for its
+// device, which also loads this unit's module (and reserves the array) under
+// lazy module loading, so that tfg_walk_window_noalloc itself never causes a
+// device allocation.
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;   // 32 MiB, held by every GPU that loads the library
+__device__ __align__(256) unsigned char g_window_scratch[kNoAllocScratchBytes];
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+
+int window_scratch_address(int dev, void **out) {
+    if (dev < 0 || dev >= kMaxDevices) { set_error("device index beyond 64"); return TFG_EINVAL; }
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_window_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return TFG_OK;
 }
 
 }  // namespace
@@ -465,6 +493,13 @@ int tfg_init(int32_t n_formats, const tfg_format *fmts, const int32_t *ranks, co
     }
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "cudaGetDevice"); }
+    {
+        void *scratch = nullptr;   // load the static window scratch on this device now (see above)
+        rc = window_scratch_address(ctx->device, &scratch);
+        if (rc) { delete ctx; return rc; }
+    }
+    e = cudaMemsetAsync(&ctx->aux()->status, 0, sizeof(int32_t), ctx->stream);
+    if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "clear status"); }
     for (int f = 0; f < n_formats; ++f) {
         Segment &s = ctx->segs[f];
         s.first = (f == 0) ? 0 : ctx->segs[f - 1].first + ctx->segs[f - 1].n;
@@ -579,11 +614,18 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
     if (!ctx || trial_steps < 1 || trial_walkers < 1) { set_error("bad arguments"); return TFG_EINVAL; }
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "synchronize");
-    int cnt = 0;
-    const tfg::WalkVariant *all = tfg::walk_variants(&cnt);
-    cudaEvent_t t0, t1;
-    cudaEventCreate(&t0);
-    cudaEventCreate(&t1);
+    // timing events, released on every return path
+    struct Events {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Events() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    e = cudaEventCreate(&ev.a);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev.b);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune events");
+    cudaEvent_t t0 = ev.a, t1 = ev.b;
     for (size_t f = 0; f < ctx->segs.size(); ++f) {
         Segment &s = ctx->segs[f];
         if (s.n == 0) continue;
@@ -603,7 +645,6 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
         for (int G : lanes) {
             const tfg::WalkVariant *v = pick_variant(s.fmt.mode, s.word_bits, s.tw, G, s.R, s.fmt);
             if (!v) continue;
-            (void)all;
             const int b = v->block ? v->block : ctx->prm.block_threads;
             const int64_t grid = (nt * v->G + b - 1) / b;
             v->launch(d, (int32_t)std::min<int64_t>(trial_steps, 64), (int)grid, b, ctx->stream);   // warm-up
@@ -624,11 +665,25 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
         s.var = best;
         if (lanes_out) lanes_out[f] = best->G;
     }
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
     for (tfg_ctx::Graph &g : ctx->graphs) cudaGraphExecDestroy(g.exec);   // variants changed
     ctx->graphs.clear();
     return TFG_OK;
+}
+
+// The status word of the context: a device wait that gave up since the last
+// check sets it; it is read here and cleared only after it has been read.
+static int take_status(tfg_ctx *ctx) {
+    int32_t status = 0;
+    cudaError_t e = cudaMemcpyAsync(&status, &ctx->aux()->status, sizeof status, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "read status");
+    if (status == 0) return TFG_OK;
+    e = cudaMemsetAsync(&ctx->aux()->status, 0, sizeof(int32_t), ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clear status");
+    set_error("a bounded device wait gave up (tensor-core completion of the proposal network): the scores of "
+              "the window step it served are not valid");
+    return TFG_ETIMEOUT;
 }
 
 int tfg_sync(tfg_ctx *ctx) {
@@ -637,7 +692,7 @@ int tfg_sync(tfg_ctx *ctx) {
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "device error");
-    return TFG_OK;
+    return take_status(ctx);
 }
 
 int tfg_population(tfg_ctx *ctx, int32_t f, tfg_format *fmt, int32_t *r0, int32_t *r_max, int64_t *walkers,
@@ -1014,16 +1069,13 @@ int tfg_window_scratch_bytes(tfg_ctx *ctx, size_t *bytes) {
     return TFG_OK;
 }
 
-int tfg_walk_window(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_mlp_params, uint32_t eps_thresh,
-                    void *d_scratch, size_t scratch_bytes, int32_t *d_choices, const tfg_log_spec *log) {
-    if (!ctx || steps < 0 || (policy != 0 && policy != 1) || (policy == 1 && !d_mlp_params) || !d_scratch) {
+// Window mode applies to Z_T populations whose terms fit one word per sign and
+// whose slot capacity the apply kernel supports.
+static int check_window_ctx(const tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_mlp_params) {
+    if (!ctx || steps < 0 || (policy != 0 && policy != 1) || (policy == 1 && !d_mlp_params)) {
         set_error("bad arguments");
         return TFG_EINVAL;
     }
-    size_t need = 0;
-    tfg_window_scratch_bytes(ctx, &need);
-    if (scratch_bytes < need) { set_error("window scratch too small"); return TFG_ENOMEM; }
-    if ((uintptr_t)d_scratch % 16) { set_error("scratch must be 16-byte aligned"); return TFG_EINVAL; }
     if (ctx->prm.walk_policy != 0) { set_error("window mode needs walk_policy 0"); return TFG_EINVAL; }
     for (const Segment &s : ctx->segs) {
         if (s.fmt.mode != TFG_MODE_ZT || s.tw != 1 || s.R > 128 ||
@@ -1032,33 +1084,87 @@ int tfg_walk_window(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_m
             return TFG_EINVAL;
         }
     }
+    return TFG_OK;
+}
+
+// The window-mode steps on the context stream, with the scratch at `base`
+// (features, descriptors, scores, window sizes; tfg_window_scratch_bytes).
+// A tensor-core wait of the network that gives up sets the context's status
+// word, which tfg_sync reports as TFG_ETIMEOUT.
+static int window_steps(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_mlp_params, uint32_t eps_thresh,
+                        char *base, int32_t *d_choices, const tfg_log_spec *log) {
     const int W = tfg::window_cap();
     const int64_t N = ctx->total;
-    char *base = reinterpret_cast<char *>(d_scratch);
     auto *feat = reinterpret_cast<uint16_t *>(base);
     auto *desc = reinterpret_cast<uint32_t *>(base + (size_t)N * W * 64);
     auto *score = reinterpret_cast<float *>(base + (size_t)N * W * 68);
     auto *kwin = reinterpret_cast<int *>(base + (size_t)N * W * 72);
     tfg_log_spec lg{};
     if (log) lg = *log;
-    int32_t *err = reinterpret_cast<int32_t *>(&ctx->aux()->verify_failures);
-    cudaError_t e = cudaSuccess;
+    int32_t *status = &ctx->aux()->status;
     for (int64_t st = 0; st < steps; ++st) {
         for (const Segment &s : ctx->segs)
             tfg::launch_window(ctx->desc(s), feat + (size_t)s.first * W * 32, desc + (size_t)s.first * W,
                                kwin + s.first, ctx->stream);
-        if (policy == 1) tfg::launch_mlp_score(d_mlp_params, feat, N * W, score, err, ctx->stream);
+        if (policy == 1) tfg::launch_mlp_score(d_mlp_params, feat, N * W, score, status, ctx->stream);
         for (const Segment &s : ctx->segs) {
             int32_t *ch = d_choices ? d_choices + (size_t)st * N + s.first : nullptr;
             tfg::launch_window_apply(ctx->desc(s), desc + (size_t)s.first * W, kwin + s.first,
                                      score + (size_t)s.first * W, policy, eps_thresh,
                                      feat + (size_t)s.first * W * 32, ch, lg, ctx->stream);
         }
-        e = cudaGetLastError();
+        const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "window step launch");
     }
     return TFG_OK;
 }
+
+int tfg_walk_window(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_mlp_params, uint32_t eps_thresh,
+                    void *d_scratch, size_t scratch_bytes, int32_t *d_choices, const tfg_log_spec *log) {
+    int rc = check_window_ctx(ctx, steps, policy, d_mlp_params);
+    if (rc) return rc;
+    if (!d_scratch) { set_error("bad arguments: null scratch"); return TFG_EINVAL; }
+    size_t need = 0;
+    tfg_window_scratch_bytes(ctx, &need);
+    if (scratch_bytes < need) { set_error("window scratch too small"); return TFG_ENOMEM; }
+    if ((uintptr_t)d_scratch % 16) { set_error("scratch must be 16-byte aligned"); return TFG_EINVAL; }
+    return window_steps(ctx, steps, policy, d_mlp_params, eps_thresh, reinterpret_cast<char *>(d_scratch), d_choices,
+                        log);
+}
+
+// tfg_walk_window for callers that cannot call cudaMalloc: the scratch is the
+// library's static array g_window_scratch (see above), so the call allocates
+// nothing.  Every value a step reads from the scratch is written earlier in
+// the same step (features and window sizes by the window kernel, scores by
+// the network), so what an earlier call left there needs no clearing.
+int tfg_walk_window_noalloc(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_mlp_params,
+                            uint32_t eps_thresh, int32_t *d_choices, const tfg_log_spec *log) {
+    int rc = check_window_ctx(ctx, steps, policy, d_mlp_params);
+    if (rc) return rc;
+    size_t need = 0;
+    tfg_window_scratch_bytes(ctx, &need);
+    if (need > kNoAllocScratchBytes) {
+        set_error("tfg_walk_window_noalloc: " + std::to_string(ctx->total) + " walkers need " + std::to_string(need) +
+                  " scratch bytes, the static scratch holds " + std::to_string(kNoAllocScratchBytes) +
+                  " (at most " + std::to_string(kNoAllocScratchBytes / (window_row_bytes() + 4)) + " walkers)");
+        return TFG_EINVAL;
+    }
+    int dev = -1;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != ctx->device) {
+        set_error("tfg_walk_window_noalloc: device " + std::to_string(dev) + " is current, the context lives on device " +
+                  std::to_string(ctx->device) + "; make the context's device current");
+        return TFG_EINVAL;
+    }
+    void *scratch = nullptr;
+    rc = window_scratch_address(dev, &scratch);
+    if (rc) return rc;
+    return window_steps(ctx, steps, policy, d_mlp_params, eps_thresh, reinterpret_cast<char *>(scratch), d_choices,
+                        log);
+}
+
+void tfg_test_set_wait_limit(int64_t polls) { tfg::set_first_wait_limit(polls); }
 
 int tfg_philox_device(const uint32_t *d_ctr, int32_t n, uint32_t key_lo, uint32_t key_hi, uint32_t *d_out,
                       void *cuda_stream) {
@@ -1073,89 +1179,3 @@ int tfg_philox_device(const uint32_t *d_ctr, int32_t n, uint32_t key_lo, uint32_
 
 }  // extern "C"
 
-// ---------------------------------------------------------------------------
-// Window-mode walk with library-owned scratch, for callers that cannot call
-// cudaMalloc (e.g. code running inside another allocator's arena or a
-// runtime whose memory is fully reserved up front): the per-step window
-// scratch lives in this file's static device array instead of caller memory.
-// ---------------------------------------------------------------------------
-namespace {
-constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;   // 32 MiB, held by every GPU that loads the library
-__device__ __align__(256) unsigned char g_window_scratch[kNoAllocScratchBytes];
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-void *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_window_scratch on the current device (host code only
-// sees a host-side stand-in of the symbol); looked up once per device.
-int window_scratch_address(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) { set_error("device index beyond 64"); return TFG_EINVAL; }
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_window_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
-    return TFG_OK;
-}
-}  // namespace
-
-extern "C" int tfg_walk_window_noalloc(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_mlp_params,
-                                       uint32_t eps_thresh, int32_t *d_choices, const tfg_log_spec *log) {
-    if (!ctx || steps < 0 || (policy != 0 && policy != 1) || (policy == 1 && !d_mlp_params)) {
-        set_error("bad arguments");
-        return TFG_EINVAL;
-    }
-    size_t need = 0;
-    tfg_window_scratch_bytes(ctx, &need);
-    if (need > kNoAllocScratchBytes) {
-        set_error("tfg_walk_window_noalloc: " + std::to_string(ctx->total) + " walkers need " + std::to_string(need) +
-                  " scratch bytes, the static scratch holds " + std::to_string(kNoAllocScratchBytes) +
-                  " (at most " + std::to_string(kNoAllocScratchBytes / (window_row_bytes() + 4)) + " walkers)");
-        return TFG_EINVAL;
-    }
-    if (ctx->prm.walk_policy != 0) { set_error("window mode needs walk_policy 0"); return TFG_EINVAL; }
-    for (const Segment &s : ctx->segs) {
-        if (s.fmt.mode != TFG_MODE_ZT || s.tw != 1 || s.R > 128 ||
-            tfg::window_apply_capacity(s.word_bits, s.R) == 0) {
-            set_error("window mode needs Z_T populations with m*n+n*p+p*m <= 64 and r_max <= 88");
-            return TFG_EINVAL;
-        }
-    }
-    void *scratch = nullptr;
-    int rc = window_scratch_address(&scratch);
-    if (rc) return rc;
-    // Every row the step reads is written by the step itself (features and
-    // window sizes by the window kernel, scores by the network), so nothing
-    // left in the array by an earlier call needs clearing.
-    const int W = tfg::window_cap();
-    const int64_t N = ctx->total;
-    char *base = reinterpret_cast<char *>(scratch);
-    auto *feat = reinterpret_cast<uint16_t *>(base);
-    auto *desc = reinterpret_cast<uint32_t *>(base + (size_t)N * W * 64);
-    auto *score = reinterpret_cast<float *>(base + (size_t)N * W * 68);
-    auto *kwin = reinterpret_cast<int *>(base + (size_t)N * W * 72);
-    tfg_log_spec lg{};
-    if (log) lg = *log;
-    int32_t *err = reinterpret_cast<int32_t *>(&ctx->aux()->verify_failures);
-    for (int64_t st = 0; st < steps; ++st) {
-        for (const Segment &s : ctx->segs)
-            tfg::launch_window(ctx->desc(s), feat + (size_t)s.first * W * 32, desc + (size_t)s.first * W,
-                               kwin + s.first, ctx->stream);
-        if (policy == 1) tfg::launch_mlp_score(d_mlp_params, feat, N * W, score, err, ctx->stream);
-        for (const Segment &s : ctx->segs) {
-            int32_t *ch = d_choices ? d_choices + (size_t)st * N + s.first : nullptr;
-            tfg::launch_window_apply(ctx->desc(s), desc + (size_t)s.first * W, kwin + s.first,
-                                     score + (size_t)s.first * W, policy, eps_thresh,
-                                     feat + (size_t)s.first * W * 32, ch, lg, ctx->stream);
-        }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "window step launch");
-    }
-    return TFG_OK;
-}

@@ -41,7 +41,8 @@ __device__ __forceinline__ void store_row_bf16(uint8_t *base, int row, int col0,
 
 __global__ void __launch_bounds__(128, 1) mlp_score_kernel(const uint8_t *__restrict__ params,
                                                             const __nv_bfloat16 *__restrict__ x, int64_t n,
-                                                            float *__restrict__ out, int *__restrict__ err) {
+                                                            float *__restrict__ out, int *__restrict__ err,
+                                                            uint32_t first_limit) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
@@ -103,7 +104,8 @@ __global__ void __launch_bounds__(128, 1) mlp_score_kernel(const uint8_t *__rest
                              tc::make_desc(tc::smem_u32(sW1T) + kc * 256, 128, (kIn / 8) * 128), idesc, kc > 0);
             tc::mma_commit(mb);
         }
-        bool ok = tc::mbar_wait(mb, phase);
+        // the CTA's first completion wait takes first_limit polls (the test hook), later ones the default
+        bool ok = tc::mbar_wait(mb, phase, tile == blockIdx.x ? first_limit : tc::kWaitLimit);
         if (__syncthreads_or(!ok)) { if (tid == 0) timeout = 1; break; }
         phase ^= 1;
         tc::fence_after_sync();
@@ -159,7 +161,13 @@ __global__ void __launch_bounds__(128, 1) mlp_score_kernel(const uint8_t *__rest
     if (warp == 0) tc::tmem_dealloc(tmem, kHid);
 }
 
+uint32_t g_first_wait_limit = tc::kWaitLimit;
+
 }  // namespace
+
+void set_first_wait_limit(int64_t polls) {
+    g_first_wait_limit = (polls < 0 || polls > (int64_t)tc::kWaitLimit) ? tc::kWaitLimit : (uint32_t)polls;
+}
 
 size_t mlp_param_bytes() { return kParamBytes; }
 
@@ -176,7 +184,8 @@ int launch_mlp_score(const void *params, const void *x, int64_t n, float *out, i
     const int64_t tiles = (n + kTile - 1) / kTile;
     const int grid = (int)(tiles < 2LL * sms ? tiles : 2LL * sms);
     mlp_score_kernel<<<grid, 128, kScoreSmem, st>>>(reinterpret_cast<const uint8_t *>(params),
-                                                    reinterpret_cast<const __nv_bfloat16 *>(x), n, out, err);
+                                                    reinterpret_cast<const __nv_bfloat16 *>(x), n, out, err,
+                                                    g_first_wait_limit);
     return 0;
 }
 

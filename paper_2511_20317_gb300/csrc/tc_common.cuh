@@ -75,9 +75,10 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar_saddr, uint32_t count) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Bounded wait for the mbarrier phase `parity` to complete; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar_saddr, uint32_t parity) {
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+// Bounded wait for the mbarrier phase `parity` to complete: at most `limit`
+// polls; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar_saddr, uint32_t parity, uint32_t limit = kWaitLimit) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

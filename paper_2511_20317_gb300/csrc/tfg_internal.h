@@ -105,6 +105,7 @@ int launch_window_apply(const SegDesc &d, const uint32_t *desc, const int *kwin,
                         uint32_t eps, const void *feat, int32_t *choices, const WindowLog &log, cudaStream_t st);
 size_t mlp_param_bytes();
 int launch_mlp_score(const void *params, const void *x, int64_t n, float *out, int *err, cudaStream_t st);
+void set_first_wait_limit(int64_t polls);   // test hook of tfg_test_set_wait_limit
 int mlp_num_params();
 void launch_mlp_grad(const void *params, const void *x, const float *label, const float *weight, int64_t n,
                      float *grad, int *err, cudaStream_t st);

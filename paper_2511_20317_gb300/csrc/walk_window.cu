@@ -19,7 +19,7 @@
 namespace tfg {
 namespace dev {
 
-constexpr int kWin = 128;         // window capacity (= one tensor-core tile of rows)
+constexpr int kWin = 256;         // window capacity: up to 256 candidate pairs per step (two tensor-core tiles of rows)
 constexpr int kFeat = 32;
 constexpr int kWinMaxSlots = 128; // slots per walker supported by the window kernel
 

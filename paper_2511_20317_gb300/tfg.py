@@ -64,7 +64,7 @@ class tfg_log_spec(ctypes.Structure):
 
 LOG_ENTRY_DTYPE = np.dtype([("feat", np.uint16, 32), ("label", np.float32), ("walker_id", np.uint32),
                             ("step", np.uint32), ("pad", np.uint32)])
-WINDOW = 128
+WINDOW = 256
 
 WALKER_INFO_DTYPE = np.dtype([("r", np.int32), ("best_r", np.int32), ("r_max", np.int32), ("format", np.int32),
                               ("t", np.int64), ("plateau", np.int64), ("best_t", np.int64),
@@ -83,7 +83,8 @@ EXPORTED = ["tfg_default_params", "tfg_last_error", "tfg_verify", "tfg_additive_
             "tfg_checkpoint",
             "tfg_restore", "tfg_mapping", "tfg_autotune", "tfg_destroy", "tfg_philox_device", "tfg_mlp_param_bytes",
             "tfg_mlp_score", "tfg_mlp_grad", "tfg_mlp_train_state_bytes", "tfg_mlp_train_init",
-            "tfg_mlp_train_step", "tfg_window_scratch_bytes", "tfg_walk_window", "tfg_walk_window_noalloc"]
+            "tfg_mlp_train_step", "tfg_window_scratch_bytes", "tfg_walk_window", "tfg_walk_window_noalloc",
+            "tfg_test_set_wait_limit"]
 
 _lib = None
 _lock = threading.Lock()
@@ -147,6 +148,7 @@ def lib() -> ctypes.CDLL:
                 "tfg_mlp_train_state_bytes": (sz, []),
                 "tfg_mlp_train_init": (i32, [P, P, P]),
                 "tfg_mlp_train_step": (i32, [P, P, P, P, P, i64, ctypes.c_float, i32, P, P]),
+                "tfg_test_set_wait_limit": (None, [i64]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -355,6 +357,12 @@ def tfg_mlp_grad(params, x, label, weight, stream=None):
     if int(err.item()) != 0:
         raise TfgError(TFG_ETIMEOUT, "tensor-core completion wait gave up")
     return grad[:P], float(grad[P].item())
+
+
+def tfg_test_set_wait_limit(polls: int):
+    """Test hook: poll limit of the scoring network's first completion wait per CTA
+    (negative restores the default)."""
+    lib().tfg_test_set_wait_limit(int(polls))
 
 
 def tfg_mlp_train_state_bytes() -> int:
@@ -599,8 +607,8 @@ class Walkers:
     walk_window_noalloc = tfg_walk_window_noalloc
 
     def window_buffers(self):
-        """Views of the last window step's scratch: features (bf16 [N, 128, 32]),
-        descriptors (int32 [N, 128]), scores (float32 [N, 128]), window sizes (int32 [N])."""
+        """Views of the last window step's scratch: features (bf16 [N, W, 32]),
+        descriptors (int32 [N, W]), scores (float32 [N, W]), window sizes (int32 [N]); W = 256."""
         torch, N, W = self.torch, self.total, WINDOW
         b = self._wscratch
         feat = b[: N * W * 64].view(torch.bfloat16).view(N, W, 32)

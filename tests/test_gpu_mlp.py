@@ -99,3 +99,44 @@ def test_training_learns_a_separable_rule():
     assert loss1 < 0.5 * loss0, (loss0, loss1)
     acc = ((tfg.tfg_mlp_score(params, xs).cpu().numpy() > 0) == (label > 0)).mean()
     assert acc > 0.9, acc
+
+
+def test_adam_step_matches_reference_elementwise():
+    """Six device training steps against the float64 Adam of the reference fed
+    with the device's own gradient of each step: FP32 master weights, both
+    moments and the parameter blob (bf16 W1, W2 = the rounded master weights,
+    the rest the FP32 master values) element by element.  Bound: FP32 rounding
+    of each update (a few 2^-24 relative of the moment and update terms) per
+    step, accumulated over the steps."""
+    import torch
+    rng = np.random.default_rng(12)
+    p = mlp.Params.random(rng)
+    n = 128 * 40 + 9
+    x = rng.integers(0, 9, size=(n, mlp.IN)).astype(np.float32)
+    label = (rng.random(n) < 0.3).astype(np.float32)
+    weight = np.full(n, 1.0 / n, np.float32)
+    params = device_params(p)
+    xs, ls, ws = device_rows(x), torch.from_numpy(label).cuda(), torch.from_numpy(weight).cuda()
+    tr = tfg.MlpTrainer(params)
+    P = mlp.NUM_PARAMS
+    state = lambda k: tr.state[k * P:(k + 1) * P].cpu().numpy().astype(np.float64)
+    opt = mlp.Adam(state(0))
+    assert (opt.m == 0).all() and np.array_equal(state(1), np.zeros(P)) and np.array_equal(state(2), np.zeros(P))
+    lr, steps, gmax = 2e-3, 6, 0.0
+    for k in range(1, steps + 1):
+        tr.step(xs, ls, ws, lr)
+        g = state(3)                      # the gradient this step used
+        gmax = max(gmax, float(np.abs(g).max()))
+        opt.step(g, lr)
+    tol = 2.0 ** -21 * steps
+    assert (np.abs(state(1) - opt.m) <= tol * (np.abs(opt.m) + gmax * 1e-3)).all()
+    assert (np.abs(state(2) - opt.v) <= tol * (np.abs(opt.v) + gmax ** 2 * 1e-6)).all()
+    master = state(0)
+    assert (np.abs(master - opt.theta) <= tol * (np.abs(opt.theta) + lr)).all(), \
+        float(np.max(np.abs(master - opt.theta)))
+    # the blob: bf16 of the FP32 master for W1, W2; the FP32 master values for the rest
+    blob = params.cpu().numpy()
+    nw = mlp.IN * mlp.HID + mlp.HID * mlp.HID
+    m32 = tr.state[:P].cpu().numpy()
+    assert np.array_equal(blob[:2 * nw].view(np.uint16), mlp.bf16_bits(mlp.bf16_round(m32[:nw])))
+    assert np.array_equal(blob[2 * nw:2 * nw + 4 * (P - nw)].view(np.float32), m32[nw:])

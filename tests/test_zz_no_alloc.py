@@ -50,6 +50,41 @@ def test_noalloc_equals_caller_scratch_entry_point_two_calls():
     assert st["steps"] == 2 * steps * nw and st["reductions"] > 0
 
 
+def test_noalloc_calls_leave_free_device_memory_unchanged():
+    """After one warm-up call (which loads the kernels' modules), further calls
+    take no device memory: the free bytes the driver reports stay the same."""
+    import torch
+    fmt, nw = (3, 3, 3), 1000
+    start = naive_start(*fmt)
+    params = torch.from_numpy(np.frombuffer(mlp.Params.random(np.random.default_rng(8)).blob(),
+                                            dtype=np.uint8).copy()).cuda()
+    W = tfg.Walkers([(fmt, 0, start, nw)], seed=2, params=tfg.tfg_default_params(plateau_len=60))
+    ch = torch.full((4, nw), -2, dtype=torch.int32, device="cuda")
+    W.walk_window_noalloc(1, policy=1, mlp_params=params, eps_thresh=int(0.1 * 2**32))
+    W.sync()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        W.walk_window_noalloc(4, policy=1, mlp_params=params, eps_thresh=int(0.1 * 2**32), d_choices=ch)
+        W.sync()
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+    assert (ch >= -1).all()
+
+
+def test_noalloc_rejects_a_context_of_another_device():
+    import torch
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two devices")
+    fmt = (2, 2, 2)
+    with torch.cuda.device(1):
+        W = tfg.Walkers([(fmt, 0, naive_start(*fmt), 64)], seed=1)
+    with torch.cuda.device(0):
+        with pytest.raises(tfg.TfgError) as e:
+            W.walk_window_noalloc(1, policy=0)
+    assert e.value.code == tfg.TFG_EINVAL and "current" in str(e.value)
+
+
 def test_noalloc_rejects_contexts_beyond_the_static_capacity():
     fmt = (2, 2, 2)
     W = tfg.Walkers([(fmt, 0, naive_start(*fmt), 5000)], seed=1)
