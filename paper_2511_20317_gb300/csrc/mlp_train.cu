@@ -323,13 +323,16 @@ __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const uint8_t *__restr
 }
 
 // Adam on FP32 master weights; the BF16 / FP32 parameter blob is rewritten.
+// omb1 = 1 - beta1, omb2 = 1 - beta2 and the bias corrections bc1 = 1 - beta1^t,
+// bc2 = 1 - beta2^t come from the host, formed in double precision (1 - beta
+// formed from an FP32 beta would be off by up to 2^-24 / (1 - beta) relative).
 __global__ void adam_kernel(float *master, float *m1, float *m2, const float *grad, uint8_t *blob, float lr,
-                            float beta1, float beta2, float eps, float bc1, float bc2) {
+                            float beta1, float omb1, float beta2, float omb2, float eps, float bc1, float bc2) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= kNumParams) return;
     const float g = grad[e];
-    const float a = beta1 * m1[e] + (1.f - beta1) * g;
-    const float b = beta2 * m2[e] + (1.f - beta2) * g * g;
+    const float a = beta1 * m1[e] + omb1 * g;
+    const float b = beta2 * m2[e] + omb2 * g * g;
     m1[e] = a;
     m2[e] = b;
     const float p = master[e] - lr * (a / bc1) / (sqrtf(b / bc2) + eps);
@@ -374,11 +377,12 @@ void launch_mlp_grad(const void *params, const void *x, const float *label, cons
 
 void launch_adam(float *master, float *m1, float *m2, const float *grad, void *blob, float lr, int step,
                  cudaStream_t st) {
-    const float beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
-    float bc1 = 1.f, bc2 = 1.f;
-    for (int k = 0; k < step; ++k) { bc1 *= beta1; bc2 *= beta2; }
-    adam_kernel<<<(kNumParams + 255) / 256, 256, 0, st>>>(master, m1, m2, grad, reinterpret_cast<uint8_t *>(blob),
-                                                         lr, beta1, beta2, eps, 1.f - bc1, 1.f - bc2);
+    const double beta1 = 0.9, beta2 = 0.999, eps = 1e-8;
+    double p1 = 1.0, p2 = 1.0;
+    for (int k = 0; k < step; ++k) { p1 *= beta1; p2 *= beta2; }
+    adam_kernel<<<(kNumParams + 255) / 256, 256, 0, st>>>(
+        master, m1, m2, grad, reinterpret_cast<uint8_t *>(blob), lr, (float)beta1, (float)(1.0 - beta1),
+        (float)beta2, (float)(1.0 - beta2), (float)eps, (float)(1.0 - p1), (float)(1.0 - p2));
 }
 
 void launch_master_from_blob(const void *blob, float *master, float *m1, float *m2, cudaStream_t st) {
