@@ -279,27 +279,41 @@ def run_ours(args):
     alu_peak = 152 * 4 * 16 * 2.07e9 / 1e12
     traffic = recorded_traffic() if args.workload == "333" else None   # the capture is of that workload
 
-    # end to end through the public API with host buffers, per step: init from the
-    # host start schemes (H2D), walk, verify, collect each population's best scheme
-    # to the host (D2H) and read the counters; applied flips / wall time
+    # end to end through the public API with host buffers: the walkers' state lives
+    # in pinned host memory between steps, as for a caller that keeps it there.
+    # Per step: tfg_restore (H2D of the whole state), walk, verify every best
+    # scheme, collect each population's best scheme to the host, read the
+    # counters, tfg_checkpoint (D2H of the whole state).  The state continues
+    # the timed run's trajectories (a context created with the same arguments),
+    # so the step covers the same phase of the walk as the timed steps.
     e2e_steps = max(1, min(args.steps, 3))
-    h2d = sum(np.asarray(p[2]).nbytes for p in pops)
+    import ctypes as _ct
+    L_ = tfg.lib()
+    used = _ct.c_size_t()
+    tfg._check(L_.tfg_checkpoint(W.ctx, None, 0, _ct.byref(used)))
+    host_state = torch.empty(used.value, dtype=torch.uint8, pin_memory=True)
+    tfg._check(L_.tfg_checkpoint(W.ctx, _ct.c_void_p(host_state.data_ptr()), used.value, _ct.byref(used)))
+    E = tfg.Walkers(pops, seed=args.seed, params=params)
+    if lanes is not None:
+        E.autotune(trial_steps=300, trial_walkers=65536)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     d2h, e2e_applied = 0, 0
     for _ in range(e2e_steps):
-        E = tfg.Walkers(pops, seed=args.seed + 1, params=params)
+        tfg._check(L_.tfg_restore(E.ctx, _ct.c_void_p(host_state.data_ptr()), used.value))
+        a0 = E.stats()[0]["accepted"]
         E.walk(args.chunk)
         E.verify_all()
         for f in range(E.n_formats):
             sch, r, w = E.collect_best(f)
-            d2h += sch.nbytes + 8
-        e2e_applied += E.stats()[0]["accepted"]
-        d2h += 8 * 11
-        E.close()
-        del E
+            d2h += sch.nbytes + 12
+        e2e_applied += E.stats()[0]["accepted"] - a0
+        tfg._check(L_.tfg_checkpoint(E.ctx, _ct.c_void_p(host_state.data_ptr()), used.value, _ct.byref(used)))
+        d2h += used.value + 2 * 8 * 11
     torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
+    h2d = used.value
+    E.close()
     e2e_val = e2e_applied * world / e2e_t
 
     line = {
@@ -455,10 +469,25 @@ def main():
     ap.add_argument("--ab-walkers", type=int, default=8192)
     ap.add_argument("--ab-steps", type=int, default=2000)
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        spawn_ranks(args.gpus)
     if args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
+
+
+def spawn_ranks(n: int):
+    """--gpus N without an outside launcher: re-run this script as N ranks on
+    this node under torch.distributed.run (one process per GPU, rendezvous on
+    127.0.0.1) and exit with its status."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    sys.exit(subprocess.call(cmd))
 
 
 if __name__ == "__main__":

@@ -388,10 +388,19 @@ def explore(formats, walkers: int, cycles: int, steps_per_cycle: int, seed: int,
     results = []
     for f in formats:
         sch, r, w = W.collect_best(index[f])
-        results.append({"format": list(f), "lowest_rank": int(r), "best_walker": int(w),
+        results.append({"format": list(f), "mode": "Z_T", "lowest_rank": int(r), "best_walker": int(w),
                         "best_scheme_verified_host": bool(tfg.tfg_verify(f, sch)),
                         "additive_complexity": int(tfg.tfg_additive_complexity(f, sch)),
                         "isotropy_invariants": invariants(f, sch, tfg.TFG_MODE_ZT),
+                        "device_check_failures": int(fails)})
+    for f, zf in z2_index.items():
+        # the Z_2 populations: their own lowest rank and how many of the walkers at
+        # that rank lift to Z_T signs
+        sch, r, w = W.collect_best(zf)
+        low, tried, lifted, _ = lift_population(W, zf, max_tries=32)
+        results.append({"format": list(f), "mode": "Z_2", "lowest_rank": int(r), "best_walker": int(w),
+                        "best_scheme_verified_host": bool(tfg.tfg_verify(f, sch, tfg.TFG_MODE_Z2)),
+                        "lift": {"rank": int(low), "tried": int(tried), "lifted": int(lifted)},
                         "device_check_failures": int(fails)})
     W.close()
     return results, transfers

@@ -101,8 +101,12 @@ def test_exploration_lifts_z2_schemes_into_ternary_populations():
                                     moves_per_cycle=0, lift_z2=True, quiet=True)
     lifts = [t for t in transfers if t["op"] == "lift"]
     assert any(tuple(t["to"]) == (3, 3, 3) for t in lifts)
-    by = {tuple(r["format"]): r for r in res}
+    by = {(tuple(r["format"]), r["mode"]): r for r in res}
     low = min(t["rank"] for t in lifts if tuple(t["to"]) == (3, 3, 3))
-    assert by[(3, 3, 3)]["lowest_rank"] <= low < 27
+    assert by[((3, 3, 3), "Z_T")]["lowest_rank"] <= low < 27
+    # the Z_2 population is reported too: its lowest rank is at most the rank it lifted
+    z2 = by[((3, 3, 3), "Z_2")]
+    assert z2["lowest_rank"] <= low and z2["lift"]["rank"] == z2["lowest_rank"]
+    assert 1 <= z2["lift"]["tried"] and 0 <= z2["lift"]["lifted"] <= z2["lift"]["tried"]
     for r in res:
         assert r["best_scheme_verified_host"] and r["device_check_failures"] == 0

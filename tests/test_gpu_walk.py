@@ -239,6 +239,42 @@ def test_large_formats_full_population_sampled():
     W.close()
 
 
+def test_large_formats_million_step_prefix():
+    """The large-format trajectories over a 1e6-step prefix: 4 walkers per format
+    at the global ids they have in the full 131072-walker populations (the middle
+    of each population), in one context per format with walker_id_base set to
+    those ids (a trajectory depends only on seed, id and step, and the kernel
+    variant only on the format and capacity, so these are the full run's
+    trajectories), the three formats on their own streams; replayed by the oracle."""
+    import torch
+    from paper_2511_20317_gb300 import starts
+    pops = starts.large_populations(131072)
+    L, steps, seed, nw = 50_000, 1_000_000, 0, 4
+    ctxs, ids = [], []
+    for f, (fmt, mode, start, total) in enumerate(pops):
+        base = f * total + total // 2
+        st = torch.cuda.Stream()
+        W = tfg.Walkers([(fmt, mode, start, nw)], seed=seed, stream=st,
+                        params=tfg.tfg_default_params(plateau_len=L, walker_id_base=base))
+        assert W.pop[0]["slots_per_lane"] == 0, "warp-per-walker kernel expected"
+        ctxs.append(W)
+        ids.append(base + np.arange(nw))
+    for _ in range(steps // 100_000):
+        for W in ctxs:
+            W.walk(100_000)
+    for W in ctxs:
+        W.sync()
+    refs = [oracle.Walkers(p[0], p[2], i, seed=seed, plateau_len=L) for p, i in zip(pops, ids)]
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(len(refs)) as ex:   # all twelve walkers at once over the host cores
+        list(ex.map(lambda rf: rf.walk(steps, max(1, THREADS // len(refs))), refs))
+    for W, ref, (fmt, *_rest) in zip(ctxs, refs, pops):
+        info, slots, best = W.read_walkers(0, nw)
+        assert (ref.info["accepted"] > 0).all() and (info["t"] == steps).all()
+        assert_parity(info, slots, best, ref, range(nw), f"large 1e6 prefix {fmt}")
+        W.close()
+
+
 def test_start_from_paper_scheme_and_edge_formats():
     """Start from the (2,2,3:11) example of Section 3.1.1; and the degenerate
     formats (1,1,1) (rank 1: no candidate ever) and (1,2,1)."""

@@ -140,3 +140,24 @@ def test_two_rank_population_sync_and_counter_sums(tmp_path):
             assert np.array_equal(got[2:].reshape(br, -1), whole.best_scheme(bw))
     for r in range(world):
         assert np.array_equal(np.load(tmp_path / f"sums{r}.npy"), np.concatenate(want_counts))
+
+
+def test_bench_spawns_its_own_ranks_for_gpus_2():
+    """bench.py --gpus 2 without an outside launcher starts two ranks itself
+    (torch.distributed.run on 127.0.0.1); the reference arm runs on rank 0 and
+    prints one JSON line with n_gpus = 2, the other rank exits 0.  CPU only:
+    the reference arm uses gloo and no GPU."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", "2",
+                          "--steps", "1", "--warmup", "1", "--cpu-walkers", "2", "--cpu-chunk", "300"],
+                         capture_output=True, text=True, timeout=300, env=env, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    rec = json.loads(lines[0])
+    assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["value"] > 0
+    assert rec["ms_per_step"] > 0 and rec["e2e"]["value"] == rec["value"]
