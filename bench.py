@@ -375,17 +375,21 @@ def run_ours(args):
 
 
 def learned_ab(args):
-    """Reductions per 1e9 flips of the learned proposal against uniform choice over
-    the same candidate windows, at equal step budgets: train the network on the
-    device from window-uniform walks on the uniform workloads' formats, then run
-    both arms on the naive (4,4,4) and (3,4,5) schemes with seeds 0..2."""
+    """The learned proposal against uniform choice over the same candidate
+    windows (BASELINE config 5): the network is trained on the device from the
+    logged window-uniform walks of the uniform workloads' formats (seeds 100..),
+    then both arms run from the naive (4,4,4) and (3,4,5) schemes with 262144
+    walkers, plateau 5e4, evaluation seeds 1000..1004: the learned arm for
+    --ab-steps steps per walker, the uniform arm for as many steps (equal
+    budget) and for the learned arm's wall time (equal time)."""
     from paper_2511_20317_gb300 import learned
     t0 = time.perf_counter()
-    entries = learned.collect(walkers=4096, steps=2000)
+    entries = learned.collect(walkers=4096, steps=4000)
     params, info = learned.train(entries, epochs=30)
-    res = learned.ab_test(params, seeds=(0, 1, 2), walkers=args.ab_walkers, steps=args.ab_steps)
-    return {"workload": f"naive (4,4,4) and (3,4,5), Z_T, {args.ab_walkers} walkers x {args.ab_steps} window steps, "
-                        "3 seeds per arm, eps 0.05",
+    res = learned.ab_test(params, seeds=tuple(range(args.ab_seeds)), walkers=args.ab_walkers, steps=args.ab_steps)
+    return {"workload": f"naive (4,4,4) and (3,4,5), Z_T, {args.ab_walkers} walkers, {args.ab_steps} window steps "
+                        f"per walker (learned, and uniform at equal steps) and uniform at the learned arm's wall "
+                        f"time; plateau 5e4; {args.ab_seeds} evaluation seeds; eps 0.05; 256-candidate windows",
             "training": {"samples": info["samples"], "positives": info["positives"],
                          "loss_first": info["loss"][0], "loss_last": info["loss"][-1]},
             "results": res, "seconds": time.perf_counter() - t0}
@@ -466,8 +470,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-learned", dest="learned", action="store_false")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
-    ap.add_argument("--ab-walkers", type=int, default=8192)
-    ap.add_argument("--ab-steps", type=int, default=2000)
+    ap.add_argument("--ab-walkers", type=int, default=262144)
+    ap.add_argument("--ab-steps", type=int, default=1500)
+    ap.add_argument("--ab-seeds", type=int, default=5)
     args = ap.parse_args()
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         spawn_ranks(args.gpus)

@@ -410,14 +410,15 @@ int tfg_mlp_train_step(void *d_state, void *d_params, const uint16_t *d_x, const
  *   f19 r - best_r   f20 r   f21 m   f22 n   f23 p
  *   f24 the position q of term i after i0 (i = i0 + q mod r), at most 64
  *   f25..f30 0       f31 1
- * Rows of a window past its K candidates are zero.  policy 0 (uniform):
- * candidate mulhi(x1, K);
+ * (tfg_window_dump writes them; the learned step computes them in shared
+ * memory, on the tensor-core kernel, from the window's candidate list.)
+ * policy 0 (uniform): candidate mulhi(x1, K);
  * policy 1 (learned): with x3 < eps_thresh as policy 0, else the candidate of
  * highest MLP score (first on ties).  The chosen flip then goes through the
  * same validity test, reductions and bookkeeping as tfg_walk.
  * Populations must be Z_T with m*n + n*p + p*m <= 64 and r_max <= 88.
- * d_scratch: caller device memory of tfg_window_scratch_bytes (window
- * features, descriptors, scores).  d_choices (optional, device int32
+ * d_scratch: caller device memory of tfg_window_scratch_bytes (per walker
+ * the window's candidate descriptors, scores and size: 3076 bytes).  d_choices (optional, device int32
  * [steps][walkers]) receives the chosen window index of every step (-1: no
  * candidate).  log (optional): chosen features with label 1 when the step
  * lowered the rank (always kept) or 0 (kept when a Philox draw of sub-stream
@@ -437,17 +438,28 @@ typedef struct {
 } tfg_log_spec;
 
 int tfg_window_scratch_bytes(tfg_ctx *ctx, size_t *bytes);
+
+/* The window the next window-mode step of every walker would consider, without
+ * stepping (for inspection and tests).  d_desc (device, uint32 [walkers][256][2],
+ * 8-byte aligned): per window row the candidate descriptor i | X << 10 |
+ * j << 12 | (s < 0) << 22 | rho << 23 and the info word min(count of term i's
+ * candidates, 64) | min(q, 64) << 8; rows past the window are not written.
+ * d_kwin (device, int32 [walkers]): the window sizes K.  d_feat (optional,
+ * device bf16 [walkers][256][32], 16-byte aligned): the features listed
+ * above, rows past K zero.  Asynchronous on the context stream. */
+int tfg_window_dump(tfg_ctx *ctx, uint16_t *d_feat, uint32_t *d_desc, int32_t *d_kwin);
+
 int tfg_walk_window(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_mlp_params, uint32_t eps_thresh,
                     void *d_scratch, size_t scratch_bytes, int32_t *d_choices, const tfg_log_spec *log);
 
 /* tfg_walk_window without any caller scratch: the paper has no counterpart to
  * this entry point.  It is for callers that cannot call cudaMalloc (code that
  * runs inside another framework's memory arena, or a process whose device
- * memory is reserved up front): the window features, candidate descriptors
- * and scores live in a 32 MiB array that the library itself defines as static
+ * memory is reserved up front): the window's candidate descriptors, scores
+ * and sizes live in a 32 MiB array that the library itself defines as static
  * device memory, which every GPU that loads the library holds until the
- * process exits.  Contexts of more than 1820 walkers (the array's capacity at
- * 18436 bytes per walker) are rejected with TFG_EINVAL and a message.  The call
+ * process exits.  Contexts of more than 10908 walkers (the array's capacity at
+ * 3076 bytes per walker) are rejected with TFG_EINVAL and a message.  The call
  * allocates nothing: tfg_init already looked up the array's device address on
  * its device, which loads the library's module there and so reserves the
  * 32 MiB at that point at the latest (under lazy module loading; at library

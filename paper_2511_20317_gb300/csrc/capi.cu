@@ -1061,7 +1061,8 @@ int tfg_mlp_train_step(void *d_state, void *d_params, const uint16_t *d_x, const
     return TFG_OK;
 }
 
-static size_t window_row_bytes() { return (size_t)tfg::window_cap() * (32 * 2 + 4 + 4); }
+// per walker: W window rows of (descriptor, info) words and a score, then the window size
+static size_t window_row_bytes() { return (size_t)tfg::window_cap() * (8 + 4); }
 
 int tfg_window_scratch_bytes(tfg_ctx *ctx, size_t *bytes) {
     if (!ctx || !bytes) { set_error("bad arguments"); return TFG_EINVAL; }
@@ -1095,27 +1096,44 @@ static int window_steps(tfg_ctx *ctx, int64_t steps, int32_t policy, const void 
                         char *base, int32_t *d_choices, const tfg_log_spec *log) {
     const int W = tfg::window_cap();
     const int64_t N = ctx->total;
-    auto *feat = reinterpret_cast<uint16_t *>(base);
-    auto *desc = reinterpret_cast<uint32_t *>(base + (size_t)N * W * 64);
-    auto *score = reinterpret_cast<float *>(base + (size_t)N * W * 68);
-    auto *kwin = reinterpret_cast<int *>(base + (size_t)N * W * 72);
+    auto *desc = reinterpret_cast<uint2 *>(base);
+    auto *score = reinterpret_cast<float *>(base + (size_t)N * W * 8);
+    auto *kwin = reinterpret_cast<int *>(base + (size_t)N * W * 12);
     tfg_log_spec lg{};
     if (log) lg = *log;
     int32_t *status = &ctx->aux()->status;
     for (int64_t st = 0; st < steps; ++st) {
         for (const Segment &s : ctx->segs)
-            tfg::launch_window(ctx->desc(s), feat + (size_t)s.first * W * 32, desc + (size_t)s.first * W,
-                               kwin + s.first, ctx->stream);
-        if (policy == 1) tfg::launch_mlp_score(d_mlp_params, feat, N * W, score, status, ctx->stream);
+            tfg::launch_window(ctx->desc(s), nullptr, desc + (size_t)s.first * W, kwin + s.first, ctx->stream);
+        if (policy == 1)
+            for (const Segment &s : ctx->segs)
+                tfg::launch_window_score(ctx->desc(s), d_mlp_params, desc + (size_t)s.first * W, kwin + s.first,
+                                         score + (size_t)s.first * W, status, ctx->stream);
         for (const Segment &s : ctx->segs) {
             int32_t *ch = d_choices ? d_choices + (size_t)st * N + s.first : nullptr;
             tfg::launch_window_apply(ctx->desc(s), desc + (size_t)s.first * W, kwin + s.first,
-                                     score + (size_t)s.first * W, policy, eps_thresh,
-                                     feat + (size_t)s.first * W * 32, ch, lg, ctx->stream);
+                                     score + (size_t)s.first * W, policy, eps_thresh, ch, lg, ctx->stream);
         }
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "window step launch");
     }
+    return TFG_OK;
+}
+
+int tfg_window_dump(tfg_ctx *ctx, uint16_t *d_feat, uint32_t *d_desc, int32_t *d_kwin) {
+    int rc = check_window_ctx(ctx, 0, 0, nullptr);
+    if (rc) return rc;
+    if (!d_desc || !d_kwin) { set_error("bad arguments: null descriptor or window-size array"); return TFG_EINVAL; }
+    if ((d_feat && (uintptr_t)d_feat % 16) || (uintptr_t)d_desc % 8) {
+        set_error("features must be 16-byte aligned, descriptors 8-byte aligned");
+        return TFG_EINVAL;
+    }
+    const int W = tfg::window_cap();
+    for (const Segment &s : ctx->segs)
+        tfg::launch_window(ctx->desc(s), d_feat ? d_feat + (size_t)s.first * W * 32 : nullptr,
+                           reinterpret_cast<uint2 *>(d_desc) + (size_t)s.first * W, d_kwin + s.first, ctx->stream);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "window dump launch");
     return TFG_OK;
 }
 

@@ -3,17 +3,22 @@
 // kWin candidates: starting at term i0 = mulhi(x0, r), terms i0, i0+1, ...
 // (mod r) append their try_flip candidates in (factor, slot, rho) order until
 // the window is full.  Per step:
-//   1. window_kernel  (one warp per walker): window, candidate descriptors and
-//      32 integer features per candidate (bf16 rows for the network);
-//   2. the scoring MLP on the tensor cores (mlp_tc.cu) over all rows;
+//   1. window_kernel  (one warp per walker): the window as candidate
+//      descriptors (8 bytes per row; features only when asked for);
+//   2. learned policy: window_score_kernel, the tensor-core MLP (mlp_pipe.cuh)
+//      whose producer computes each row's 32 features from the descriptor and
+//      the walker's slots straight into the shared-memory A tile, so no
+//      feature row goes through device memory; it writes one score per row;
 //   3. window_apply_kernel (one thread per walker): policy choice (uniform
 //      over the window via x1, or epsilon-greedy argmax of the scores with
 //      epsilon decided by x3), then the flip, reductions and bookkeeping of
-//      the uniform walker; optional logging of the chosen features with the
-//      label "the step lowered the rank" for training.
+//      the uniform walker; optional logging of the chosen candidate's features
+//      (computed from the state before the flip) with the label "the step
+//      lowered the rank" for training.
 #include <cstdint>
 #include <cuda_bf16.h>
 
+#include "mlp_pipe.cuh"
 #include "walk_solo.cuh"
 
 namespace tfg {
@@ -78,16 +83,29 @@ __device__ __forceinline__ void cand_features(const PTerm<Wd, 1, true> &a, const
     f[31] = 1.f;
 }
 
+// Features of a candidate as 16 packed bf16x2 words (small integers: exact).
+template <class Wd>
+__device__ __forceinline__ void cand_features_bf16(const PTerm<Wd, 1, true> &a, const PTerm<Wd, 1, true> &b,
+                                                   const Masks<Wd, 1> &mk, uint32_t dc, uint32_t info, int r,
+                                                   int best_r, int m, int n, int p, uint32_t (&h)[kFeat / 2]) {
+    const int X = (int)((dc >> 10) & 3u), sneg = (int)((dc >> 22) & 1u), rho = (int)((dc >> 23) & 1u);
+    float f[kFeat];
+    cand_features<Wd>(a, b, mk, X, sneg, rho, (int)(info & 255u), (int)(info >> 8), r, best_r, m, n, p, f);
+#pragma unroll
+    for (int k = 0; k < kFeat / 2; ++k) h[k] = mlp::pack_bf16x2(f[2 * k], f[2 * k + 1]);
+}
+
 // One warp per walker.  Phase 1: eight terms i0 + g (g = lane / 4, then the
 // next eight while the window has room); the four lanes of a group scan
 // consecutive quarters of the slots for the term's try_flip candidates, and
 // every candidate's descriptor goes to its window position in shared memory
-// (order: term, then factor, then slot, then rho).  Phase 2: the lanes take
-// window rows l, l+32, ... and compute and store the feature rows (coalesced
-// 64-byte rows).
+// (order: term, then factor, then slot, then rho).  Phase 2: the lanes write
+// the window rows l, l+32, ... (descriptor and info words), and, when `feat`
+// is given, their feature rows (coalesced 64-byte rows; rows past the window
+// are zero).
 template <class Wd>
 __global__ void __launch_bounds__(128) window_kernel(const SegDesc d, __nv_bfloat16 *__restrict__ feat,
-                                                     uint32_t *__restrict__ desc, int *__restrict__ kwin) {
+                                                     uint2 *__restrict__ desc, int *__restrict__ kwin) {
     __shared__ __align__(16) Wd sp[4][kWinMaxSlots], sn[4][kWinMaxSlots];
     __shared__ uint32_t sdesc[4][kWin], sinfo[4][kWin];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -182,48 +200,126 @@ __global__ void __launch_bounds__(128) window_kernel(const SegDesc d, __nv_bfloa
     }
     const int K = carry < kWin ? carry : kWin;
     __syncwarp();
-    // ---- phase 2: feature rows (rows past the window are zero: scored, never chosen)
-    __nv_bfloat16 *fw = feat + (size_t)w * kWin * kFeat;
-    uint32_t *dw = desc + (size_t)w * kWin;
-    for (int row = lane; row < kWin; row += 32) {
-        uint4 *dst = reinterpret_cast<uint4 *>(fw + (size_t)row * kFeat);
-        if (row < K) {
-            const uint32_t dc = sdesc[warp][row], in = sinfo[warp][row];
-            const int i = (int)(dc & 1023u), X = (int)((dc >> 10) & 3u), j = (int)((dc >> 12) & 1023u);
-            const int sneg = (int)((dc >> 22) & 1u), rho = (int)((dc >> 23) & 1u);
-            T ti, tj;
-            ti.p[0] = sp[warp][i];
-            ti.n[0] = sn[warp][i];
-            tj.p[0] = sp[warp][j];
-            tj.n[0] = sn[warp][j];
-            float f[kFeat];
-            cand_features<Wd>(ti, tj, mk, X, sneg, rho, (int)(in & 255u), (int)(in >> 8), r, best_r, d.m, d.n, d.p, f);
+    // ---- phase 2: window rows (and feature rows when asked for)
+    uint2 *dw = desc + (size_t)w * kWin;
+    for (int row = lane; row < K; row += 32) dw[row] = make_uint2(sdesc[warp][row], sinfo[warp][row]);
+    if (feat) {
+        __nv_bfloat16 *fw = feat + (size_t)w * kWin * kFeat;
+        for (int row = lane; row < kWin; row += 32) {
+            uint4 *dst = reinterpret_cast<uint4 *>(fw + (size_t)row * kFeat);
+            if (row < K) {
+                const uint32_t dc = sdesc[warp][row], in = sinfo[warp][row];
+                const int i = (int)(dc & 1023u), j = (int)((dc >> 12) & 1023u);
+                T ti, tj;
+                ti.p[0] = sp[warp][i];
+                ti.n[0] = sn[warp][i];
+                tj.p[0] = sp[warp][j];
+                tj.n[0] = sn[warp][j];
+                uint32_t h[kFeat / 2];
+                cand_features_bf16<Wd>(ti, tj, mk, dc, in, r, best_r, d.m, d.n, d.p, h);
 #pragma unroll
-            for (int k = 0; k < kFeat / 8; ++k) {
-                uint32_t wv[4];
+                for (int k = 0; k < kFeat / 8; ++k) dst[k] = make_uint4(h[4 * k], h[4 * k + 1], h[4 * k + 2], h[4 * k + 3]);
+            } else {
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[8 * k + 2 * h], f[8 * k + 2 * h + 1]);
-                    wv[h] = *reinterpret_cast<const uint32_t *>(&b2);
-                }
-                dst[k] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+                for (int k = 0; k < kFeat / 8; ++k) dst[k] = make_uint4(0, 0, 0, 0);
             }
-            dw[row] = dc;
-        } else {
-#pragma unroll
-            for (int k = 0; k < kFeat / 8; ++k) dst[k] = make_uint4(0, 0, 0, 0);
         }
     }
     if (lane == 0) kwin[w] = K;
 }
 
+// Producer of the fused scoring kernel: tile t is half t & 1 (rows 0-127 or
+// 128-255) of walker t >> 1's window; thread q computes the features of row
+// 128 (t & 1) + q from its descriptor and the walker's two slots, straight
+// into the A tile.  A second half with no candidate is skipped; rows past the
+// window get zero features and no score.
+template <class Wd>
+struct WindowProducer {
+    const Wd *slots;
+    const tfg_walker_info *hdr;
+    int R, m, n, p;
+    const uint2 *desc;
+    const int *kwin;
+    float *score;
+    Masks<Wd, 1> mk;
+    // loaded by begin()
+    int64_t w;
+    int row, K, r, best_r;
+    uint2 dci;
+    PTerm<Wd, 1, true> ti, tj;
+    // latched by fill()
+    int64_t out_idx;
+    bool out_ok;
+    __device__ __forceinline__ bool begin(int64_t tile, int q) {
+        w = tile >> 1;
+        const int half = (int)(tile & 1);
+        row = half * kWin / 2 + q;
+        K = kwin[w];
+        if (half && K <= kWin / 2) return false;
+        if (row < K) {
+            dci = desc[(size_t)w * kWin + row];
+            const int i = (int)(dci.x & 1023u), j = (int)((dci.x >> 12) & 1023u);
+            const Wd *src = slots + (size_t)w * R * 2;
+            ti.p[0] = src[(size_t)i * 2];
+            ti.n[0] = src[(size_t)i * 2 + 1];
+            tj.p[0] = src[(size_t)j * 2];
+            tj.n[0] = src[(size_t)j * 2 + 1];
+            r = hdr[w].r;
+            best_r = hdr[w].best_r;
+        }
+        return true;
+    }
+    __device__ __forceinline__ void fill(uint8_t *sX, int q) {
+        uint32_t h[kFeat / 2];
+        if (row < K) {
+            cand_features_bf16<Wd>(ti, tj, mk, dci.x, dci.y, r, best_r, m, n, p, h);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kFeat / 2; ++k) h[k] = 0u;
+        }
+#pragma unroll
+        for (int c = 0; c < kFeat / 8; ++c)
+            mlp::st_row8(sX, q, 8 * c, mlp::kIn, make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]));
+        out_idx = w * kWin + row;
+        out_ok = row < K;
+    }
+    __device__ __forceinline__ void emit(float y, int) {
+        if (out_ok) score[out_idx] = y;
+    }
+};
+
+constexpr int kScoreWG = 4;
+
+template <class Wd>
+__global__ void __launch_bounds__(kScoreWG * 128, 1)
+    window_score_kernel(const SegDesc d, const uint8_t *__restrict__ params, const uint2 *__restrict__ desc,
+                        const int *__restrict__ kwin, float *__restrict__ score, int *__restrict__ err,
+                        uint32_t first_limit) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t mbar[kScoreWG];
+    __shared__ uint32_t tslot;
+    __shared__ int tflag;
+    WindowProducer<Wd> pr;
+    pr.slots = reinterpret_cast<const Wd *>(d.slots);
+    pr.hdr = d.hdr;
+    pr.R = d.R;
+    pr.m = d.m;
+    pr.n = d.n;
+    pr.p = d.p;
+    pr.desc = desc;
+    pr.kwin = kwin;
+    pr.score = score;
+    pr.mk.load(d);
+    mlp::run_tiles<kScoreWG>(params, pr, d.n_walkers * 2, err, first_limit, smem, mbar, &tslot, &tflag);
+}
+
 // One window-mode step per thread (walker), on the solo walker's state machine.
 template <class Wd, int RMAX, int BT>
-__global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const uint32_t *__restrict__ desc,
+__global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const uint2 *__restrict__ desc,
                                                           const int *__restrict__ kwin,
                                                           const float *__restrict__ score, int policy,
-                                                          uint32_t eps_thresh, const __nv_bfloat16 *__restrict__ feat,
-                                                          int32_t *__restrict__ choices, WindowLog log) {
+                                                          uint32_t eps_thresh, int32_t *__restrict__ choices,
+                                                          WindowLog log) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t w = (int64_t)blockIdx.x * BT + threadIdx.x;
     if (w >= d.n_walkers) return;
@@ -243,6 +339,7 @@ __global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const
     int action = kNoCand, X = 0, j = 0, rho = 0, sneg = 0, c = -1;
     int i = (int)__umulhi(x.x, (uint32_t)wk.r);
     bool need_check = false;
+    uint32_t lf[kFeat / 2];   // logged features of the chosen candidate (state before the flip)
     T ti2, tj2;
     ti2.p[0] = tj2.p[0] = 0;
     ti2.n[0] = tj2.n[0] = 0;
@@ -256,13 +353,15 @@ __global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const
             for (int k = 1; k < K; ++k)
                 if (sc[k] > best) { best = sc[k]; c = k; }
         }
-        const uint32_t dc = desc[(size_t)w * kWin + c];
+        const uint2 dci = desc[(size_t)w * kWin + c];
+        const uint32_t dc = dci.x;
         i = (int)(dc & 1023u);
         X = (int)((dc >> 10) & 3u);
         j = (int)((dc >> 12) & 1023u);
         sneg = (int)((dc >> 22) & 1u);
         rho = (int)((dc >> 23) & 1u);
         const T ti = wk.ld(i);
+        if (log.d_entries) cand_features_bf16<Wd>(ti, wk.ld(j), wk.mk, dc, dci.y, wk.r, wk.best_r, d.m, d.n, d.p, lf);
         wk.apply_candidate(ti, i, X, j, sneg, rho, action, need_check, ti2, tj2);
     } else {
         wk.c_noc += 1;
@@ -280,9 +379,9 @@ __global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const
             const unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(log.d_count), 1ull);
             if (slot < (unsigned long long)log.capacity) {
                 WindowLogEntry *e = reinterpret_cast<WindowLogEntry *>(log.d_entries) + slot;
-                const uint4 *fsrc = reinterpret_cast<const uint4 *>(feat + ((size_t)w * kWin + c) * kFeat);
 #pragma unroll
-                for (int k = 0; k < kFeat / 8; ++k) reinterpret_cast<uint4 *>(e->feat)[k] = fsrc[k];
+                for (int k = 0; k < kFeat / 8; ++k)
+                    reinterpret_cast<uint4 *>(e->feat)[k] = make_uint4(lf[4 * k], lf[4 * k + 1], lf[4 * k + 2], lf[4 * k + 3]);
                 e->label = positive ? 1.f : 0.f;
                 e->walker_id = wk.wid;
                 e->step = (uint32_t)t_step;
@@ -297,7 +396,7 @@ __global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const
 
 int window_cap() { return dev::kWin; }
 
-void launch_window(const SegDesc &d, void *feat, uint32_t *desc, int *kwin, cudaStream_t st) {
+void launch_window(const SegDesc &d, void *feat, uint2 *desc, int *kwin, cudaStream_t st) {
     const int64_t blocks = (d.n_walkers + 3) / 4;
     if (blocks <= 0) return;
     if (d.word_bits == 32)
@@ -308,9 +407,30 @@ void launch_window(const SegDesc &d, void *feat, uint32_t *desc, int *kwin, cuda
                                                                       desc, kwin);
 }
 
+template <class Wd>
+static void score_variant(const SegDesc &d, const void *params, const uint2 *desc, const int *kwin, float *score,
+                          int *err, cudaStream_t st) {
+    constexpr uint32_t smem = mlp::smem_bytes<dev::kScoreWG>();
+    static bool attr = [] {
+        cudaFuncSetAttribute(dev::window_score_kernel<Wd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return true;
+    }();
+    (void)attr;
+    const int grid = score_grid(d.n_walkers * 2, dev::kScoreWG);
+    dev::window_score_kernel<Wd><<<grid, dev::kScoreWG * 128, smem, st>>>(
+        d, reinterpret_cast<const uint8_t *>(params), desc, kwin, score, err, first_wait_limit());
+}
+
+void launch_window_score(const SegDesc &d, const void *params, const uint2 *desc, const int *kwin, float *score,
+                         int *err, cudaStream_t st) {
+    if (d.n_walkers <= 0) return;
+    if (d.word_bits == 32) score_variant<uint32_t>(d, params, desc, kwin, score, err, st);
+    else score_variant<uint64_t>(d, params, desc, kwin, score, err, st);
+}
+
 template <class Wd, int RMAX>
-static void apply_variant(const SegDesc &d, const uint32_t *desc, const int *kwin, const float *score, int policy,
-                          uint32_t eps, const void *feat, int32_t *choices, const WindowLog &log, cudaStream_t st) {
+static void apply_variant(const SegDesc &d, const uint2 *desc, const int *kwin, const float *score, int policy,
+                          uint32_t eps, int32_t *choices, const WindowLog &log, cudaStream_t st) {
     constexpr int BT = 128;
     constexpr size_t smem = solo_smem_bytes<TFG_MODE_ZT, Wd, RMAX, BT>();
     static bool attr = [] {
@@ -320,8 +440,8 @@ static void apply_variant(const SegDesc &d, const uint32_t *desc, const int *kwi
     }();
     (void)attr;
     const int64_t blocks = (d.n_walkers + BT - 1) / BT;
-    dev::window_apply_kernel<Wd, RMAX, BT><<<(unsigned)blocks, BT, smem, st>>>(
-        d, desc, kwin, score, policy, eps, reinterpret_cast<const __nv_bfloat16 *>(feat), choices, log);
+    dev::window_apply_kernel<Wd, RMAX, BT><<<(unsigned)blocks, BT, smem, st>>>(d, desc, kwin, score, policy, eps,
+                                                                              choices, log);
 }
 
 // Capacity of the apply kernel chosen for a population (0: not supported).
@@ -334,20 +454,20 @@ int window_apply_capacity(int word_bits, int R) {
     return 0;
 }
 
-int launch_window_apply(const SegDesc &d, const uint32_t *desc, const int *kwin, const float *score, int policy,
-                        uint32_t eps, const void *feat, int32_t *choices, const WindowLog &log, cudaStream_t st) {
+int launch_window_apply(const SegDesc &d, const uint2 *desc, const int *kwin, const float *score, int policy,
+                        uint32_t eps, int32_t *choices, const WindowLog &log, cudaStream_t st) {
     if (d.n_walkers <= 0) return 0;
     const int cap = window_apply_capacity(d.word_bits, d.R);
     if (d.word_bits == 32) {
-        if (cap == 12) apply_variant<uint32_t, 12>(d, desc, kwin, score, policy, eps, feat, choices, log, st);
-        else if (cap == 16) apply_variant<uint32_t, 16>(d, desc, kwin, score, policy, eps, feat, choices, log, st);
-        else if (cap == 32) apply_variant<uint32_t, 32>(d, desc, kwin, score, policy, eps, feat, choices, log, st);
+        if (cap == 12) apply_variant<uint32_t, 12>(d, desc, kwin, score, policy, eps, choices, log, st);
+        else if (cap == 16) apply_variant<uint32_t, 16>(d, desc, kwin, score, policy, eps, choices, log, st);
+        else if (cap == 32) apply_variant<uint32_t, 32>(d, desc, kwin, score, policy, eps, choices, log, st);
         else return -1;
     } else {
-        if (cap == 48) apply_variant<uint64_t, 48>(d, desc, kwin, score, policy, eps, feat, choices, log, st);
-        else if (cap == 64) apply_variant<uint64_t, 64>(d, desc, kwin, score, policy, eps, feat, choices, log, st);
-        else if (cap == 72) apply_variant<uint64_t, 72>(d, desc, kwin, score, policy, eps, feat, choices, log, st);
-        else if (cap == 88) apply_variant<uint64_t, 88>(d, desc, kwin, score, policy, eps, feat, choices, log, st);
+        if (cap == 48) apply_variant<uint64_t, 48>(d, desc, kwin, score, policy, eps, choices, log, st);
+        else if (cap == 64) apply_variant<uint64_t, 64>(d, desc, kwin, score, policy, eps, choices, log, st);
+        else if (cap == 72) apply_variant<uint64_t, 72>(d, desc, kwin, score, policy, eps, choices, log, st);
+        else if (cap == 88) apply_variant<uint64_t, 88>(d, desc, kwin, score, policy, eps, choices, log, st);
         else return -1;
     }
     return 0;

@@ -43,13 +43,15 @@ def _bf16_bits(a: np.ndarray) -> bytes:
     return r.tobytes()
 
 
-def collect(formats=TRAIN_FORMATS, walkers=4096, steps=2000, seed=100, neg_rate=0.01, plateau=500):
+def collect(formats=TRAIN_FORMATS, walkers=4096, steps=4000, seed=100, neg_rate=0.01, plateau=None):
     """Window-uniform walks with transition logging: every rank-lowering step
-    (label 1) and a neg_rate sample of the others (label 0)."""
+    (label 1) and a neg_rate sample of the others (label 0).  plateau None: the
+    configurations' plateau lengths (1e4 for (2,2,2), 5e4 for the others)."""
     entries = []
     for k, fmt in enumerate(formats):
+        L = plateau if plateau is not None else (10_000 if tuple(fmt) == (2, 2, 2) else 50_000)
         W = tfg.Walkers([(fmt, 0, naive_start(*fmt), walkers)], seed=seed + k,
-                        params=tfg.tfg_default_params(plateau_len=plateau))
+                        params=tfg.tfg_default_params(plateau_len=L))
         log = tfg.TransitionLog(walkers * steps // 20 + 100000, neg_thresh=int(neg_rate * 2**32))
         W.walk_window(steps, policy=0, log=log)
         e = log.read()
@@ -85,42 +87,93 @@ def train(entries, params=None, epochs=30, batch=8192, lr=2e-3, seed=0):
     return params, {"samples": n, "positives": pos, "negatives": neg, "loss": history}
 
 
-def evaluate(fmt, policy, params=None, walkers=16384, steps=3000, seed=0, eps=0.05, plateau=500):
-    """One arm of the A/B: window-mode walks from the naive scheme; returns
-    reductions per 1e9 steps, the lowest rank, every best scheme verified."""
+def evaluate(fmt, policy, params=None, walkers=262144, steps=1500, seed=0, eps=0.05, plateau=50_000,
+             seconds=None, chunk=100):
+    """One arm of the A/B: window-mode walks from the naive scheme for `steps`
+    steps per walker, or (seconds given) for as many whole chunks of steps as
+    fit in that wall time.  Returns the lowest rank, the final best-rank
+    histogram, the net rank descent (start rank - mean best rank), reductions
+    per 1e9 applied flips, steps/s; every walker's best scheme is verified."""
     import torch
-    W = tfg.Walkers([(fmt, 0, naive_start(*fmt), walkers)], seed=seed,
-                    params=tfg.tfg_default_params(plateau_len=plateau))
+    start = naive_start(*fmt)
+    W = tfg.Walkers([(fmt, 0, start, walkers)], seed=seed, params=tfg.tfg_default_params(plateau_len=plateau))
+    r0 = W.pop[0]["r0"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    W.walk_window(steps, policy=policy, mlp_params=params, eps_thresh=int(eps * 2**32))
-    W.sync()
+    done = 0
+    if seconds is None:
+        W.walk_window(steps, policy=policy, mlp_params=params, eps_thresh=int(eps * 2**32))
+        W.sync()
+        done = steps
+    else:
+        while time.perf_counter() - t0 < seconds:
+            W.walk_window(chunk, policy=policy, mlp_params=params, eps_thresh=int(eps * 2**32))
+            W.sync()
+            done += chunk
     dt = time.perf_counter() - t0
     st, hist = W.stats()
     fails = W.verify_all()
     scheme, rank, _ = W.collect_best(0)
     W.close()
-    return {"reductions_per_1e9": st["reductions"] / st["steps"] * 1e9, "lowest_rank": st["min_best_r"],
-            "steps_per_s": st["steps"] / dt, "verify_failures": fails, "accepted_frac": st["accepted"] / st["steps"],
+    ranks = np.arange(hist.size)
+    mean_best = float((hist * ranks).sum() / max(hist.sum(), 1))
+    return {"steps_per_walker": done, "seconds": dt, "lowest_rank": st["min_best_r"],
+            "mean_best_rank": mean_best, "net_descent": r0 - mean_best,
+            "reductions_per_1e9_applied": st["reductions"] / max(st["accepted"], 1) * 1e9,
+            "applied_frac": st["accepted"] / max(st["steps"], 1), "steps_per_s": st["steps"] / dt,
+            "verify_failures": fails, "collected_verified": bool(tfg.tfg_verify(fmt, scheme)),
             "rank_hist": {int(k): int(v) for k, v in enumerate(hist) if v}}
 
 
-def ab_test(params, formats=EVAL_FORMATS, seeds=(0, 1, 2, 3, 4), **kw):
+def _summary(runs, keys=("net_descent", "mean_best_rank", "lowest_rank", "reductions_per_1e9_applied",
+                          "steps_per_s", "steps_per_walker")):
+    out = {}
+    for k in keys:
+        v = np.array([r[k] for r in runs], dtype=np.float64)
+        ci = float(1.96 * v.std(ddof=1) / np.sqrt(v.size)) if v.size > 1 else None
+        out[k] = {"mean": float(v.mean()), "ci95": ci}
+    hist = {}
+    for r in runs:
+        for k, v in r["rank_hist"].items():
+            hist[k] = hist.get(k, 0) + v
+    out["rank_hist_all_seeds"] = {int(k): int(v) for k, v in sorted(hist.items())}
+    out["lowest_rank_any_seed"] = int(min(r["lowest_rank"] for r in runs))
+    out["verify_failures"] = int(sum(r["verify_failures"] for r in runs))
+    out["collected_verified"] = all(r["collected_verified"] for r in runs)
+    return out
+
+
+def _beats(a, b, key, higher_better=True):
+    """a beats b on key when their 95% intervals do not overlap in a's favour."""
+    ma, ca = a[key]["mean"], a[key]["ci95"] or 0.0
+    mb, cb = b[key]["mean"], b[key]["ci95"] or 0.0
+    return (ma - ca > mb + cb) if higher_better else (ma + ca < mb - cb)
+
+
+def ab_test(params, formats=EVAL_FORMATS, seeds=(0, 1, 2, 3, 4), walkers=262144, steps=1500, eps=0.05,
+            plateau=50_000):
+    """Learned against uniform over the same candidate windows: per format and
+    evaluation seed (disjoint from the training seeds), the learned arm for
+    `steps` steps per walker, the uniform arm for the same steps (equal step
+    budget) and for the learned arm's wall time (equal time).  Net measures:
+    rank descent and lowest rank with 95% intervals over the seeds."""
     out = {}
     for fmt in formats:
-        arms = {"uniform": [], "learned": []}
+        learned, uniform, uniform_t = [], [], []
         for s in seeds:
-            arms["uniform"].append(evaluate(fmt, 0, None, seed=1000 + s, **kw))
-            arms["learned"].append(evaluate(fmt, 1, params, seed=1000 + s, **kw))
-        res = {}
-        for arm, runs in arms.items():
-            v = np.array([r["reductions_per_1e9"] for r in runs])
-            res[arm] = {"reductions_per_1e9_mean": float(v.mean()),
-                        "ci95": float(1.96 * v.std(ddof=1) / np.sqrt(len(v))) if len(v) > 1 else None,
-                        "lowest_rank": int(min(r["lowest_rank"] for r in runs)),
-                        "steps_per_s": float(np.mean([r["steps_per_s"] for r in runs])),
-                        "verify_failures": int(sum(r["verify_failures"] for r in runs))}
-        res["gain"] = res["learned"]["reductions_per_1e9_mean"] / max(res["uniform"]["reductions_per_1e9_mean"], 1e-9)
+            sd = 1000 + s
+            l = evaluate(fmt, 1, params, walkers=walkers, steps=steps, seed=sd, eps=eps, plateau=plateau)
+            learned.append(l)
+            uniform.append(evaluate(fmt, 0, None, walkers=walkers, steps=steps, seed=sd, plateau=plateau))
+            uniform_t.append(evaluate(fmt, 0, None, walkers=walkers, seed=sd, plateau=plateau, seconds=l["seconds"]))
+        res = {"equal_steps": {"learned": _summary(learned), "uniform": _summary(uniform)},
+               "equal_time": {"learned": _summary(learned), "uniform": _summary(uniform_t)}}
+        eq, et = res["equal_steps"], res["equal_time"]
+        res["learned_beats_uniform"] = {
+            "net_descent_equal_steps": _beats(eq["learned"], eq["uniform"], "net_descent"),
+            "net_descent_equal_time": _beats(et["learned"], et["uniform"], "net_descent"),
+            "reductions_per_1e9_applied_equal_steps": _beats(eq["learned"], eq["uniform"],
+                                                             "reductions_per_1e9_applied")}
         out["x".join(map(str, fmt))] = res
     return out
 
@@ -128,10 +181,10 @@ def ab_test(params, formats=EVAL_FORMATS, seeds=(0, 1, 2, 3, 4), **kw):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--ab", action="store_true")
-    ap.add_argument("--walkers", type=int, default=16384)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--walkers", type=int, default=262144)
+    ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--collect-walkers", type=int, default=4096)
-    ap.add_argument("--collect-steps", type=int, default=2000)
+    ap.add_argument("--collect-steps", type=int, default=4000)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--seeds", type=int, default=5)
     args = ap.parse_args()

@@ -89,12 +89,23 @@ def mlp_grad(rows=1 << 18):
     return {"rows": rows, "ms": ms, "tflops": flops / ms / 1e9}
 
 
-def window(fmt=(4, 4, 4), walkers=16384):
-    W = tfg.Walkers([(fmt, 0, naive_start(*fmt), walkers)], seed=0, params=tfg.tfg_default_params(plateau_len=500))
-    W.walk_window(2, policy=0)
+def window(fmt=(4, 4, 4), walkers=16384, policy=0, steps=1):
+    """Window-mode steps: uniform (policy 0) or learned (1, a random network; its
+    scoring is the fused feature + MLP kernel over 2 x 128-row tiles per walker)."""
+    from .learned import init_params
+    params = init_params(0) if policy == 1 else None
+    W = tfg.Walkers([(fmt, 0, naive_start(*fmt), walkers)], seed=0, params=tfg.tfg_default_params(plateau_len=50_000))
+    W.walk_window(2, policy=policy, mlp_params=params)
     W.sync()
-    ms = _timed(lambda: W.walk_window(1, policy=0))
-    return {"walkers": walkers, "ms_per_window_step": ms}
+    ms = _timed(lambda: W.walk_window(steps, policy=policy, mlp_params=params))
+    out = {"walkers": walkers, "policy": policy, "ms_per_window_step": ms / steps,
+           "steps_per_s": walkers * steps / ms * 1e3}
+    if policy == 1:
+        _, _, kwin = W.window_buffers()
+        rows = int(kwin.sum().item())          # scored rows of the last step (tiles of 128 rows: more)
+        out["scored_rows_per_step"] = rows
+        out["score_tflops_per_step_upper"] = rows * 2 * (32 * 128 + 128 * 128 + 128) / (ms / steps) / 1e9
+    return out
 
 
 CASES = {
@@ -118,7 +129,9 @@ CASES = {
     "mlp_score_33m": lambda: mlp_score(rows=1 << 25),
     "mlp_grad": mlp_grad,
     "window_444": window,
-    "window_444_262k": lambda: window(walkers=262144),
+    "window_444_262k": lambda: window(walkers=262144, steps=20),
+    "window_444_learned": lambda: window(policy=1),
+    "window_444_learned_262k": lambda: window(walkers=262144, policy=1, steps=20),
 }
 
 

@@ -84,7 +84,7 @@ EXPORTED = ["tfg_default_params", "tfg_last_error", "tfg_verify", "tfg_additive_
             "tfg_restore", "tfg_mapping", "tfg_autotune", "tfg_destroy", "tfg_philox_device", "tfg_mlp_param_bytes",
             "tfg_mlp_score", "tfg_mlp_grad", "tfg_mlp_train_state_bytes", "tfg_mlp_train_init",
             "tfg_mlp_train_step", "tfg_window_scratch_bytes", "tfg_walk_window", "tfg_walk_window_noalloc",
-            "tfg_test_set_wait_limit"]
+            "tfg_test_set_wait_limit", "tfg_window_dump"]
 
 _lib = None
 _lock = threading.Lock()
@@ -149,6 +149,7 @@ def lib() -> ctypes.CDLL:
                 "tfg_mlp_train_init": (i32, [P, P, P]),
                 "tfg_mlp_train_step": (i32, [P, P, P, P, P, i64, ctypes.c_float, i32, P, P]),
                 "tfg_test_set_wait_limit": (None, [i64]),
+                "tfg_window_dump": (i32, [P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -607,15 +608,29 @@ class Walkers:
     walk_window_noalloc = tfg_walk_window_noalloc
 
     def window_buffers(self):
-        """Views of the last window step's scratch: features (bf16 [N, W, 32]),
-        descriptors (int32 [N, W]), scores (float32 [N, W]), window sizes (int32 [N]); W = 256."""
+        """Views of the last window step's scratch: window rows (int32 [N, W, 2]:
+        descriptor and info words), scores (float32 [N, W]), window sizes (int32 [N]); W = 256."""
         torch, N, W = self.torch, self.total, WINDOW
         b = self._wscratch
-        feat = b[: N * W * 64].view(torch.bfloat16).view(N, W, 32)
-        desc = b[N * W * 64: N * W * 68].view(torch.int32).view(N, W)
-        score = b[N * W * 68: N * W * 72].view(torch.float32).view(N, W)
-        kwin = b[N * W * 72: N * W * 72 + N * 4].view(torch.int32)
-        return feat, desc, score, kwin
+        desc = b[: N * W * 8].view(torch.int32).view(N, W, 2)
+        score = b[N * W * 8: N * W * 12].view(torch.float32).view(N, W)
+        kwin = b[N * W * 12: N * W * 12 + N * 4].view(torch.int32)
+        return desc, score, kwin
+
+    def tfg_window_dump(self, features: bool = True):
+        """The window of every walker's next window-mode step, without stepping:
+        (features bf16 [N, W, 32] or None, rows int32 [N, W, 2], sizes int32 [N])."""
+        torch, N, W = self.torch, self.total, WINDOW
+        feat = torch.zeros((N, W, 32), dtype=torch.bfloat16, device="cuda") if features else None
+        desc = torch.zeros((N, W, 2), dtype=torch.int32, device="cuda")
+        kwin = torch.zeros(N, dtype=torch.int32, device="cuda")
+        with torch.cuda.stream(self.stream):
+            _check(lib().tfg_window_dump(self.ctx, ctypes.c_void_p(feat.data_ptr()) if feat is not None else None,
+                                         ctypes.c_void_p(desc.data_ptr()), ctypes.c_void_p(kwin.data_ptr())))
+        self.sync()
+        return feat, desc, kwin
+
+    window_dump = tfg_window_dump
 
     def tfg_checkpoint(self) -> bytes:
         used = ctypes.c_size_t()

@@ -109,21 +109,24 @@ def test_window_full_size_sampled(policy):
 
 @pytest.mark.parametrize("fmt", [(3, 3, 3), (4, 4, 4)])
 def test_window_features_scores_and_choice(fmt):
-    """One learned step from a walked state: features and candidates equal the
-    oracle's; scores match the float64 network within the bf16 bound; exploit
-    steps pick a candidate whose reference score is the maximum up to that bound;
-    explore steps (x3 < eps) pick mulhi(x1, K)."""
+    """One learned step from a walked state: the window (candidate rows, their
+    info words and the features tfg_window_dump writes) equals the oracle's;
+    the scores the fused tensor-core kernel computes from the candidate rows
+    match the float64 network on the oracle's features within the bf16 bound;
+    exploit steps pick a candidate whose reference score is the maximum up to
+    that bound; explore steps (x3 < eps) pick mulhi(x1, K)."""
     nw, eps = 96, int(0.25 * 2**32)
     start = naive_start(*fmt)
     W = tfg.Walkers([(fmt, 0, start, nw)], seed=9, params=tfg.tfg_default_params(plateau_len=150))
     W.walk_window(300, policy=0)
     info0, slots0, _ = W.read_walkers(0, nw)
+    feat, rows, kwin = (b.cpu() for b in W.window_dump())
+    feat, rows, kwin = feat.float().numpy(), rows.numpy().view(np.uint32), kwin.numpy()
     p = mlp.Params.random(np.random.default_rng(4))
     ch = W.walk_window(1, policy=1, mlp_params=device_params(p), eps_thresh=eps, record_choices=True)
     ch = ch.cpu().numpy()[0]
-    feat, desc, score, kwin = (b.cpu() for b in W.window_buffers())
-    feat = feat.float().numpy()
-    desc, score, kwin = desc.numpy().view(np.uint32), score.numpy(), kwin.numpy()
+    rows2, score, kwin2 = (b.cpu().numpy() for b in W.window_buffers())
+    assert np.array_equal(kwin2, kwin)
     for w in range(nw):
         r, br, t, wid = int(info0["r"][w]), int(info0["best_r"][w]), int(info0["t"][w]), int(info0["walker_id"][w])
         x = oracle.philox4x32_10([t & 0xFFFFFFFF, t >> 32, wid, 0], [9, 0])
@@ -131,10 +134,12 @@ def test_window_features_scores_and_choice(fmt):
         f_ref, c_ref = oracle.window_features(fmt, slots0[w, :r], br, i0)
         K = f_ref.shape[0]
         assert kwin[w] == K
-        assert np.array_equal(feat[w, :K], f_ref)
-        d = desc[w, :K]
+        assert np.array_equal(feat[w, :K], f_ref) and not feat[w, K:].any()
+        d, info = rows[w, :K, 0], rows[w, :K, 1]
+        assert np.array_equal(rows2[w, :K].view(np.uint32), rows[w, :K])
         got = np.stack([d & 1023, (d >> 10) & 3, (d >> 12) & 1023, np.where((d >> 22) & 1, -1, 1), (d >> 23) & 1], 1)
         assert np.array_equal(got, c_ref)
+        assert np.array_equal(info & 255, f_ref[:, 18]) and np.array_equal(info >> 8, f_ref[:, 24])
         y, cache = mlp.forward(p, f_ref)
         path = np.abs(p.W2) @ np.abs(p.w3)
         bound = 2 * ((np.abs(cache[2]) * 2.0 ** -8) * path).max(axis=1) + 1e-5 * (1 + np.abs(y))
