@@ -87,7 +87,7 @@ def test_noalloc_rejects_a_context_of_another_device():
 
 def test_noalloc_rejects_contexts_beyond_the_static_capacity():
     fmt = (2, 2, 2)
-    W = tfg.Walkers([(fmt, 0, naive_start(*fmt), 5000)], seed=1)
+    W = tfg.Walkers([(fmt, 0, naive_start(*fmt), 20000)], seed=1)
     with pytest.raises(tfg.TfgError) as e:
         W.walk_window_noalloc(1, policy=0)
     assert e.value.code == tfg.TFG_EINVAL and "static scratch" in str(e.value)
