@@ -2,22 +2,31 @@
 // tensor cores, shared by the row-scoring kernel (features read from device
 // memory) and the fused window-scoring kernel (features computed in place).
 //
-// A CTA holds the weights once (W1^T and W2^T as K-major BF16 operands, b1,
-// b2, w3 in FP32) and runs NWG independent warpgroups.  Warpgroup g owns
+// A CTA holds the weights once (W1^T and W2^T as K-major BF16 operands, the
+// vectors in FP32) and runs NWG independent warpgroups.  Warpgroup g owns
 // TMEM columns [128 g, 128 g + 128) (its accumulator), an A tile X (128 rows
-// x 32 features) and an A tile H1 (128 rows x 128 hidden units) in shared
+// x 32 features) and an A tile H1 (128 rows x KH hidden inputs) in shared
 // memory, one mbarrier and one named barrier; its thread q owns tile row q,
 // which is TMEM lane 32 (warp % 4) + lane, so every tcgen05.ld of a thread
 // reads its own row.  Per tile:
-//   producer: row q -> X                      (the Prod object)
+//   producer: row q -> X                      (the Prod object, prefetched a tile ahead)
 //   MMA1  acc = X W1        (2 x K=16, one elected thread, commit -> mbarrier)
 //   epi1  H1 = bf16(relu(acc + b1))            (cvt.rn.relu.bf16x2: ReLU and rounding in one)
-//   MMA2  acc = H1 W2       (8 x K=16)
+//   MMA2  acc = H1 W2       (KH / 16 x K=16)
 //   epi2  y = b3 + sum_o w3[o] relu(acc[o] + b2[o])
 // The warpgroups of a CTA interleave on the tensor pipe: while one waits for
-// its products, the others run their epilogues.  The producer of a tile
-// prefetches the next tile's inputs before the products of the current one,
-// so their latency hides behind the pipeline.
+// its products, the others run their epilogues.  TMEM loads are issued one
+// 16-column chunk ahead of the arithmetic on the previous chunk.
+//
+// Bias folding (Prod::kFold, used where the producer controls the feature
+// rows): the constant-one input f31 is joined by f29 = f30 = 1 on every
+// real row, and W1^T's rows 29, 30, 31 hold s = W1[31] + b1 as three BF16
+// pieces (s = hi + mid + lo to FP32 precision), so MMA1 adds the bias; H1
+// gets 16 more columns (KH = 144): three of value one whose W2^T rows hold b2
+// as three BF16 pieces, the rest zero, so MMA2 adds b2.  The epilogues then
+// only apply ReLU (and the w3 dot product).  Features f29 and f30 are zero by
+// definition, so their W1 rows never contribute otherwise; rows past a window
+// (all features zero) get no bias, and their scores are not used.
 //
 // Every mbarrier wait is bounded; a warpgroup whose wait gives up records
 // the timeout, stops taking tiles, waits (bounded again) for its products in
@@ -41,16 +50,21 @@ constexpr uint32_t kParamW3 = kParamB2 + kHid * 4;
 constexpr uint32_t kParamB3 = kParamW3 + kHid * 4;
 constexpr uint32_t kParamBytes = kParamB3 + 16;
 
-// shared memory (dynamic part): weights, vectors, then per warpgroup X and H1
-constexpr uint32_t kSmW1T = 0;                              // B of MMA1: 128 (hidden) x 32 (input)
-constexpr uint32_t kSmW2T = kSmW1T + kHid * kIn * 2;        // B of MMA2: 128 (out) x 128 (hidden)
-constexpr uint32_t kSmVec = kSmW2T + kHid * kHid * 2;       // b1, b2, w3
-constexpr uint32_t kSmWG = kSmVec + 3 * kHid * 4;           // first warpgroup area
-constexpr uint32_t kSmX = 0;                                // per warpgroup: X 128 x 32
-constexpr uint32_t kSmH1 = kTile * kIn * 2;                 //                H1 128 x 128
-constexpr uint32_t kSmWGBytes = kSmH1 + kTile * kHid * 2;   // 40 KB
-template <int NWG>
-constexpr uint32_t smem_bytes() { return kSmWG + NWG * kSmWGBytes; }
+// Shared-memory layout (dynamic part): W1^T, W2^T, the vectors, then per
+// warpgroup X and H1.  KH = 128, or 144 with the folded b2.
+template <bool FOLD>
+struct Layout {
+    static constexpr int KH = FOLD ? kHid + 16 : kHid;
+    static constexpr uint32_t W1T = 0;                            // B of MMA1: 128 (hidden) x 32 (input)
+    static constexpr uint32_t W2T = W1T + kHid * kIn * 2;         // B of MMA2: 128 (out) x KH
+    static constexpr uint32_t Vec = W2T + kHid * KH * 2;          // b1, b2, w3 (w3 only when folded)
+    static constexpr uint32_t VecBytes = (FOLD ? 1 : 3) * kHid * 4;
+    static constexpr uint32_t WG = Vec + VecBytes;                // first warpgroup area
+    static constexpr uint32_t X = 0;                              // per warpgroup: X 128 x 32
+    static constexpr uint32_t H1 = kTile * kIn * 2;               //                H1 128 x KH
+    static constexpr uint32_t WGBytes = H1 + kTile * KH * 2;
+    static constexpr uint32_t bytes(int nwg) { return WG + nwg * WGBytes; }
+};
 template <int NWG>
 constexpr uint32_t tmem_cols() { return NWG <= 1 ? 128u : (NWG <= 2 ? 256u : 512u); }
 
@@ -84,22 +98,69 @@ __device__ __forceinline__ bool wg_any(int g, bool p) {
     return r != 0;
 }
 
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane, without
+// waiting: the registers are valid after the next tmem_wait().
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+// Wait for this thread's TMEM loads; the empty asm afterwards redefines the
+// registers of the chunk that is read next, so no use of them moves above the wait.
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                   "+r"(r[14]), "+r"(r[15]));
+}
+
+__device__ __forceinline__ __nv_bfloat16 bf(float v) { return __float2bfloat16_rn(v); }
+
 // Weights and vectors of the parameter blob into the CTA's shared memory.
+template <bool FOLD>
 __device__ __forceinline__ void load_weights(const uint8_t *__restrict__ params, uint8_t *smem, int tid, int nthr) {
+    using LY = Layout<FOLD>;
+    constexpr int KH = LY::KH;
     const __nv_bfloat16 *W1 = reinterpret_cast<const __nv_bfloat16 *>(params + kParamW1);
     const __nv_bfloat16 *W2 = reinterpret_cast<const __nv_bfloat16 *>(params + kParamW2);
-    uint8_t *sW1T = smem + kSmW1T, *sW2T = smem + kSmW2T;
+    const float *b1 = reinterpret_cast<const float *>(params + kParamB1);
+    const float *b2 = reinterpret_cast<const float *>(params + kParamB2);
+    uint8_t *sW1T = smem + LY::W1T, *sW2T = smem + LY::W2T;
     // B operands are K-major: row = output unit, K = input unit
     for (int e = tid; e < kIn * kHid; e += nthr) {
         const int i = e / kHid, h = e % kHid;
-        *reinterpret_cast<__nv_bfloat16 *>(sW1T + tc::kmajor_offset(h, i, kIn)) = W1[e];
+        __nv_bfloat16 v = W1[e];
+        if (FOLD && i >= 29) {
+            // rows 29..31: W1[31] + b1 in three bf16 pieces (inputs 29..31 are one)
+            const float s = __bfloat162float(W1[31 * kHid + h]) + b1[h];
+            const float hi = __bfloat162float(bf(s)), mid = __bfloat162float(bf(s - hi));
+            v = i == 31 ? bf(hi) : (i == 30 ? bf(mid) : bf(s - hi - mid));
+        }
+        *reinterpret_cast<__nv_bfloat16 *>(sW1T + tc::kmajor_offset(h, i, kIn)) = v;
     }
-    for (int e = tid; e < kHid * kHid; e += nthr) {
-        const int h = e / kHid, o = e % kHid;
-        *reinterpret_cast<__nv_bfloat16 *>(sW2T + tc::kmajor_offset(o, h, kHid)) = W2[e];
+    for (int e = tid; e < kHid * KH; e += nthr) {
+        const int o = e / KH, h = e % KH;
+        __nv_bfloat16 v;
+        if (h < kHid) {
+            v = W2[h * kHid + o];
+        } else {
+            // K rows 128..130: b2 in three bf16 pieces (H1 columns 128..130 are one), then zeros
+            const float s = b2[o];
+            const float hi = __bfloat162float(bf(s)), mid = __bfloat162float(bf(s - hi));
+            v = h == kHid ? bf(hi) : (h == kHid + 1 ? bf(mid) : (h == kHid + 2 ? bf(s - hi - mid) : bf(0.f)));
+        }
+        *reinterpret_cast<__nv_bfloat16 *>(sW2T + tc::kmajor_offset(o, h, KH)) = v;
     }
-    float *vec = reinterpret_cast<float *>(smem + kSmVec);
-    for (int e = tid; e < 3 * kHid; e += nthr) vec[e] = reinterpret_cast<const float *>(params + kParamB1)[e];
+    float *vec = reinterpret_cast<float *>(smem + LY::Vec);
+    if (FOLD) {
+        for (int e = tid; e < kHid; e += nthr) vec[e] = reinterpret_cast<const float *>(params + kParamW3)[e];
+    } else {
+        for (int e = tid; e < 3 * kHid; e += nthr) vec[e] = b1[e];   // b1, b2, w3 are consecutive in the blob
+    }
 }
 
 // Store 8 consecutive features (as 4 packed bf16x2 words) of row q into an A tile.
@@ -107,18 +168,30 @@ __device__ __forceinline__ void st_row8(uint8_t *tile, int q, int col0, int K, u
     *reinterpret_cast<uint4 *>(tile + tc::kmajor_offset(q, col0, K)) = v;
 }
 
-// The pipeline.  Prod (one object per thread) provides
-//   bool begin(int64_t tile, int q)   load tile `tile`'s input for row q (false: the tile is
-//                                     skipped; the answer must be the same for the 128 rows)
-//   void fill(uint8_t *sX, int q)     write row q of the tile loaded last into X
+// The pipeline.  Prod (one object per thread; static bool kFold) provides
+//   bool begin(int64_t tile, int q)   start loading tile `tile`'s input for row q (false: the
+//                                     tile is skipped; the answer is the same for the 128 rows)
+//   void mid(int q)                   second load phase of the tile begun last (may be empty)
+//   void fill(uint8_t *sX, int q)     write row q of the tile loaded last into X (kFold:
+//                                     features 29 and 30 one on every real row)
 //   void emit(float y, int q)         the score of row q of the tile last filled
-// and is called as begin(t), fill, begin(t + stride) (prefetch), ..., emit.
 template <int NWG, class Prod>
 __device__ __forceinline__ void run_tiles(const uint8_t *__restrict__ params, Prod &prod, int64_t ntiles,
                                           int *__restrict__ err, uint32_t first_limit, uint8_t *smem,
                                           uint64_t *mbar, uint32_t *tslot, int *timeout_flag) {
+    constexpr bool FOLD = Prod::kFold;
+    using LY = Layout<FOLD>;
+    constexpr int KH = LY::KH;
     const int tid = threadIdx.x, g = tid >> 7, q = tid & 127, warp = tid >> 5;
-    load_weights(params, smem, tid, NWG * 128);
+    load_weights<FOLD>(params, smem, tid, NWG * 128);
+    uint8_t *sX = smem + LY::WG + g * LY::WGBytes + LY::X;
+    uint8_t *sH1 = smem + LY::WG + g * LY::WGBytes + LY::H1;
+    if (FOLD) {
+        // the constant columns 128..143 of H1 (ones, then zeros), written once
+        const uint32_t one2 = 0x3F803F80u;
+        st_row8(sH1, q, kHid, KH, make_uint4(one2, 0x00003F80u, 0u, 0u));
+        st_row8(sH1, q, kHid + 8, KH, make_uint4(0u, 0u, 0u, 0u));
+    }
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), tmem_cols<NWG>());
     if (q == 0) tc::mbar_init(tc::smem_u32(&mbar[g]), 1);
     if (tid == 0) *timeout_flag = 0;
@@ -130,11 +203,10 @@ __device__ __forceinline__ void run_tiles(const uint8_t *__restrict__ params, Pr
     const uint32_t tacc = *tslot + (uint32_t)(g * 128);
     const uint32_t tlane = tacc + ((uint32_t)((warp & 3) * 32) << 16);
     const uint32_t mb = tc::smem_u32(&mbar[g]);
-    uint8_t *sX = smem + kSmWG + g * kSmWGBytes + kSmX;
-    uint8_t *sH1 = smem + kSmWG + g * kSmWGBytes + kSmH1;
     const uint32_t aX = tc::smem_u32(sX), aH1 = tc::smem_u32(sH1);
-    const uint32_t aW1 = tc::smem_u32(smem + kSmW1T), aW2 = tc::smem_u32(smem + kSmW2T);
-    const float *sB1 = reinterpret_cast<const float *>(smem + kSmVec), *sB2 = sB1 + kHid, *sW3 = sB2 + kHid;
+    const uint32_t aW1 = tc::smem_u32(smem + LY::W1T), aW2 = tc::smem_u32(smem + LY::W2T);
+    const float *vec = reinterpret_cast<const float *>(smem + LY::Vec);
+    const float *sB1 = vec, *sB2 = vec + kHid, *sW3 = FOLD ? vec : vec + 2 * kHid;
     const float b3 = *reinterpret_cast<const float *>(params + kParamB3);
     constexpr uint32_t idesc = tc::idesc_bf16_f32(kTile, kHid);
     uint32_t phase = 0;
@@ -142,16 +214,25 @@ __device__ __forceinline__ void run_tiles(const uint8_t *__restrict__ params, Pr
 
     const int64_t stride = (int64_t)gridDim.x * NWG;
     int64_t t = (int64_t)blockIdx.x * NWG + g;
-    bool live = t < ntiles && prod.begin(t, q);
+    bool live = false;
+    if (t < ntiles) {
+        live = prod.begin(t, q);
+        prod.mid(q);
+    }
     while (t < ntiles) {
         if (!live) {   // skipped tile (uniform over the warpgroup)
             t += stride;
-            live = t < ntiles && prod.begin(t, q);
+            if (t < ntiles) {
+                live = prod.begin(t, q);
+                prod.mid(q);
+            }
             continue;
         }
         prod.fill(sX, q);
         const int64_t tn = t + stride;
-        const bool live_next = tn < ntiles && prod.begin(tn, q);   // prefetch of the next tile
+        const bool has_next = tn < ntiles;
+        bool live_next = false;
+        if (has_next) live_next = prod.begin(tn, q);   // first load phase of the next tile
         tc::fence_async_smem();
         tc::fence_before_sync();
         wg_sync(g);
@@ -168,32 +249,41 @@ __device__ __forceinline__ void run_tiles(const uint8_t *__restrict__ params, Pr
         if (wg_any(g, !ok)) { timed_out = true; break; }
         phase ^= 1;
         tc::fence_after_sync();
-        // ---- epi1: h1 = bf16(relu(z1 + b1)) -> H1 (row q)
+        // ---- epi1: h1 = bf16(relu(z1 + b1)) -> H1 (row q), TMEM chunks of 16 one ahead
+        {
+            uint32_t ra[16], rb[16];
+            tmem_ld16_nowait(tlane, ra);
+            tmem_wait(ra);
 #pragma unroll
-        for (int c0 = 0; c0 < kHid; c0 += 32) {
-            float v[32];
-            tc::tmem_ld32(tlane + c0, v);
+            for (int c = 0; c < kHid / 16; ++c) {
+                uint32_t(&cur)[16] = (c & 1) ? rb : ra;
+                uint32_t(&nxt)[16] = (c & 1) ? ra : rb;
+                if (c + 1 < kHid / 16) tmem_ld16_nowait(tlane + 16 * (c + 1), nxt);
 #pragma unroll
-            for (int c = 0; c < 32; c += 8) {
-                const float4 ba = *reinterpret_cast<const float4 *>(sB1 + c0 + c);
-                const float4 bb = *reinterpret_cast<const float4 *>(sB1 + c0 + c + 4);
-                uint4 h;
-                h.x = pack_relu_bf16x2(v[c + 0] + ba.x, v[c + 1] + ba.y);
-                h.y = pack_relu_bf16x2(v[c + 2] + ba.z, v[c + 3] + ba.w);
-                h.z = pack_relu_bf16x2(v[c + 4] + bb.x, v[c + 5] + bb.y);
-                h.w = pack_relu_bf16x2(v[c + 6] + bb.z, v[c + 7] + bb.w);
-                st_row8(sH1, q, c0 + c, kHid, h);
+                for (int u = 0; u < 16; u += 8) {
+                    float f[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        f[k] = __uint_as_float(cur[u + k]);
+                        if (!FOLD) f[k] += sB1[16 * c + u + k];
+                    }
+                    st_row8(sH1, q, 16 * c + u, KH,
+                            make_uint4(pack_relu_bf16x2(f[0], f[1]), pack_relu_bf16x2(f[2], f[3]),
+                                       pack_relu_bf16x2(f[4], f[5]), pack_relu_bf16x2(f[6], f[7])));
+                }
+                if (c + 1 < kHid / 16) tmem_wait(nxt);
             }
         }
+        if (has_next) prod.mid(q);   // second load phase of the next tile
         tc::fence_async_smem();
         tc::fence_before_sync();
         wg_sync(g);
         tc::fence_after_sync();
         if (q == 0) {
 #pragma unroll
-            for (int kc = 0; kc < kHid / 16; ++kc)
-                tc::mma_bf16(tacc, tc::make_desc(aH1 + kc * 256, 128, (kHid / 8) * 128),
-                             tc::make_desc(aW2 + kc * 256, 128, (kHid / 8) * 128), idesc, kc > 0);
+            for (int kc = 0; kc < KH / 16; ++kc)
+                tc::mma_bf16(tacc, tc::make_desc(aH1 + kc * 256, 128, (KH / 8) * 128),
+                             tc::make_desc(aW2 + kc * 256, 128, (KH / 8) * 128), idesc, kc > 0);
             tc::mma_commit(mb);
         }
         ok = tc::mbar_wait(mb, phase);
@@ -201,22 +291,34 @@ __device__ __forceinline__ void run_tiles(const uint8_t *__restrict__ params, Pr
         phase ^= 1;
         tc::fence_after_sync();
         // ---- epi2: y = b3 + w3 . relu(z2 + b2)
-        float y0 = b3, y1 = 0.f;
+        float2 y2 = make_float2(b3, 0.f);
+        {
+            uint32_t ra[16], rb[16];
+            tmem_ld16_nowait(tlane, ra);
+            tmem_wait(ra);
 #pragma unroll
-        for (int c0 = 0; c0 < kHid; c0 += 32) {
-            float v[32];
-            tc::tmem_ld32(tlane + c0, v);
+            for (int c = 0; c < kHid / 16; ++c) {
+                uint32_t(&cur)[16] = (c & 1) ? rb : ra;
+                uint32_t(&nxt)[16] = (c & 1) ? ra : rb;
+                if (c + 1 < kHid / 16) tmem_ld16_nowait(tlane + 16 * (c + 1), nxt);
 #pragma unroll
-            for (int c = 0; c < 32; c += 4) {
-                const float4 b = *reinterpret_cast<const float4 *>(sB2 + c0 + c);
-                const float4 w = *reinterpret_cast<const float4 *>(sW3 + c0 + c);
-                y0 = fmaf(fmaxf(v[c + 0] + b.x, 0.f), w.x, y0);
-                y1 = fmaf(fmaxf(v[c + 1] + b.y, 0.f), w.y, y1);
-                y0 = fmaf(fmaxf(v[c + 2] + b.z, 0.f), w.z, y0);
-                y1 = fmaf(fmaxf(v[c + 3] + b.w, 0.f), w.w, y1);
+                for (int u = 0; u < 16; u += 4) {
+                    const float4 w = *reinterpret_cast<const float4 *>(sW3 + 16 * c + u);
+                    float z0 = __uint_as_float(cur[u]), z1 = __uint_as_float(cur[u + 1]);
+                    float z2 = __uint_as_float(cur[u + 2]), z3 = __uint_as_float(cur[u + 3]);
+                    if (!FOLD) {
+                        const float4 b = *reinterpret_cast<const float4 *>(sB2 + 16 * c + u);
+                        const float2 s01 = __fadd2_rn(make_float2(z0, z1), make_float2(b.x, b.y));
+                        const float2 s23 = __fadd2_rn(make_float2(z2, z3), make_float2(b.z, b.w));
+                        z0 = s01.x; z1 = s01.y; z2 = s23.x; z3 = s23.y;
+                    }
+                    y2 = __ffma2_rn(make_float2(fmaxf(z0, 0.f), fmaxf(z1, 0.f)), make_float2(w.x, w.y), y2);
+                    y2 = __ffma2_rn(make_float2(fmaxf(z2, 0.f), fmaxf(z3, 0.f)), make_float2(w.z, w.w), y2);
+                }
+                if (c + 1 < kHid / 16) tmem_wait(nxt);
             }
         }
-        prod.emit(y0 + y1, q);
+        prod.emit(y2.x + y2.y, q);
         // the next MMA1 overwrites the accumulator: order this thread's loads before it
         tc::fence_before_sync();
         t = tn;

@@ -19,6 +19,7 @@ constexpr int kWG = 4;
 
 // Rows of features from device memory (bf16 [n][32]); rows past n are zero.
 struct RowsProducer {
+    static constexpr bool kFold = false;   // arbitrary rows: the biases are added in the epilogues
     const __nv_bfloat16 *x;
     int64_t n;
     float *out;
@@ -35,6 +36,7 @@ struct RowsProducer {
         }
         return true;
     }
+    __device__ __forceinline__ void mid(int) {}
     __device__ __forceinline__ void fill(uint8_t *sX, int q) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) mlp::st_row8(sX, q, 8 * c, mlp::kIn, v[c]);
@@ -82,7 +84,7 @@ int score_grid(int64_t tiles, int wg) {
 
 int launch_mlp_score(const void *params, const void *x, int64_t n, float *out, int *err, cudaStream_t st) {
     if (n <= 0) return 0;
-    constexpr uint32_t smem = mlp::smem_bytes<kWG>();
+    constexpr uint32_t smem = mlp::Layout<false>::bytes(kWG);
     static bool attr = [] {
         cudaFuncSetAttribute(mlp_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         return true;

@@ -232,9 +232,14 @@ __global__ void __launch_bounds__(128) window_kernel(const SegDesc d, __nv_bfloa
 // 128-255) of walker t >> 1's window; thread q computes the features of row
 // 128 (t & 1) + q from its descriptor and the walker's two slots, straight
 // into the A tile.  A second half with no candidate is skipped; rows past the
-// window get zero features and no score.
+// window get zero features and no score.  Loads in two phases, so that no
+// load waits on another while the previous tile runs: begin() the window size,
+// the row's descriptor and the walker's rank (every row's descriptor word is
+// read; a row past the window holds a stale or undefined one, so its slot
+// indices are clamped), mid() the two slots the descriptor names.
 template <class Wd>
 struct WindowProducer {
+    static constexpr bool kFold = true;   // the producer writes features 29, 30 = 1: biases in the MMAs
     const Wd *slots;
     const tfg_walker_info *hdr;
     int R, m, n, p;
@@ -242,7 +247,7 @@ struct WindowProducer {
     const int *kwin;
     float *score;
     Masks<Wd, 1> mk;
-    // loaded by begin()
+    // loaded by begin() / mid()
     int64_t w;
     int row, K, r, best_r;
     uint2 dci;
@@ -255,24 +260,25 @@ struct WindowProducer {
         const int half = (int)(tile & 1);
         row = half * kWin / 2 + q;
         K = kwin[w];
-        if (half && K <= kWin / 2) return false;
-        if (row < K) {
-            dci = desc[(size_t)w * kWin + row];
-            const int i = (int)(dci.x & 1023u), j = (int)((dci.x >> 12) & 1023u);
-            const Wd *src = slots + (size_t)w * R * 2;
-            ti.p[0] = src[(size_t)i * 2];
-            ti.n[0] = src[(size_t)i * 2 + 1];
-            tj.p[0] = src[(size_t)j * 2];
-            tj.n[0] = src[(size_t)j * 2 + 1];
-            r = hdr[w].r;
-            best_r = hdr[w].best_r;
-        }
-        return true;
+        dci = desc[(size_t)w * kWin + row];
+        r = hdr[w].r;
+        best_r = hdr[w].best_r;
+        return !(half && K <= kWin / 2);
+    }
+    __device__ __forceinline__ void mid(int) {
+        const int i = min((int)(dci.x & 1023u), R - 1), j = min((int)((dci.x >> 12) & 1023u), R - 1);
+        const Wd *src = slots + (size_t)w * R * 2;
+        ti.p[0] = src[(size_t)i * 2];
+        ti.n[0] = src[(size_t)i * 2 + 1];
+        tj.p[0] = src[(size_t)j * 2];
+        tj.n[0] = src[(size_t)j * 2 + 1];
     }
     __device__ __forceinline__ void fill(uint8_t *sX, int q) {
         uint32_t h[kFeat / 2];
         if (row < K) {
             cand_features_bf16<Wd>(ti, tj, mk, dci.x, dci.y, r, best_r, m, n, p, h);
+            h[14] |= 0x3F800000u;   // feature 29 = 1 (bf16), the bias inputs of the folded MMA
+            h[15] |= 0x00003F80u;   // feature 30 = 1 (feature 31 is 1 already)
         } else {
 #pragma unroll
             for (int k = 0; k < kFeat / 2; ++k) h[k] = 0u;
@@ -410,7 +416,7 @@ void launch_window(const SegDesc &d, void *feat, uint2 *desc, int *kwin, cudaStr
 template <class Wd>
 static void score_variant(const SegDesc &d, const void *params, const uint2 *desc, const int *kwin, float *score,
                           int *err, cudaStream_t st) {
-    constexpr uint32_t smem = mlp::smem_bytes<dev::kScoreWG>();
+    constexpr uint32_t smem = mlp::Layout<true>::bytes(dev::kScoreWG);
     static bool attr = [] {
         cudaFuncSetAttribute(dev::window_score_kernel<Wd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         return true;
