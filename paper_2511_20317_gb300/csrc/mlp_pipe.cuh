@@ -169,9 +169,11 @@ __device__ __forceinline__ void st_row8(uint8_t *tile, int q, int col0, int K, u
 }
 
 // The pipeline.  Prod (one object per thread; static bool kFold) provides
-//   bool begin(int64_t tile, int q)   start loading tile `tile`'s input for row q (false: the
-//                                     tile is skipped; the answer is the same for the 128 rows)
+//   void begin(int64_t tile, int q)   start loading tile `tile`'s input for row q
 //   void mid(int q)                   second load phase of the tile begun last (may be empty)
+//   bool live()                       false: the tile begun last is skipped (the same answer for
+//                                     the 128 rows; asked only when the tile is due, so that its
+//                                     loads have landed)
 //   void fill(uint8_t *sX, int q)     write row q of the tile loaded last into X (kFold:
 //                                     features 29 and 30 one on every real row)
 //   void emit(float y, int q)         the score of row q of the tile last filled
@@ -214,16 +216,15 @@ __device__ __forceinline__ void run_tiles(const uint8_t *__restrict__ params, Pr
 
     const int64_t stride = (int64_t)gridDim.x * NWG;
     int64_t t = (int64_t)blockIdx.x * NWG + g;
-    bool live = false;
     if (t < ntiles) {
-        live = prod.begin(t, q);
+        prod.begin(t, q);
         prod.mid(q);
     }
     while (t < ntiles) {
-        if (!live) {   // skipped tile (uniform over the warpgroup)
+        if (!prod.live()) {   // skipped tile (uniform over the warpgroup)
             t += stride;
             if (t < ntiles) {
-                live = prod.begin(t, q);
+                prod.begin(t, q);
                 prod.mid(q);
             }
             continue;
@@ -231,8 +232,7 @@ __device__ __forceinline__ void run_tiles(const uint8_t *__restrict__ params, Pr
         prod.fill(sX, q);
         const int64_t tn = t + stride;
         const bool has_next = tn < ntiles;
-        bool live_next = false;
-        if (has_next) live_next = prod.begin(tn, q);   // first load phase of the next tile
+        if (has_next) prod.begin(tn, q);   // first load phase of the next tile
         tc::fence_async_smem();
         tc::fence_before_sync();
         wg_sync(g);
@@ -322,7 +322,6 @@ __device__ __forceinline__ void run_tiles(const uint8_t *__restrict__ params, Pr
         // the next MMA1 overwrites the accumulator: order this thread's loads before it
         tc::fence_before_sync();
         t = tn;
-        live = live_next;
     }
     if (timed_out) {
         // the awaited products may still be in flight: one more bounded wait before release

@@ -25,7 +25,8 @@ struct RowsProducer {
     float *out;
     uint4 v[4];
     int64_t row_loaded, row_filled;
-    __device__ __forceinline__ bool begin(int64_t tile, int q) {
+    __device__ __forceinline__ bool live() const { return true; }
+    __device__ __forceinline__ void begin(int64_t tile, int q) {
         row_loaded = tile * mlp::kTile + q;
 #pragma unroll
         for (int c = 0; c < 4; ++c) v[c] = make_uint4(0, 0, 0, 0);
@@ -34,7 +35,6 @@ struct RowsProducer {
 #pragma unroll
             for (int c = 0; c < 4; ++c) v[c] = src[c];
         }
-        return true;
     }
     __device__ __forceinline__ void mid(int) {}
     __device__ __forceinline__ void fill(uint8_t *sX, int q) {

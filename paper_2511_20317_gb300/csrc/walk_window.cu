@@ -236,7 +236,8 @@ __global__ void __launch_bounds__(128) window_kernel(const SegDesc d, __nv_bfloa
 // load waits on another while the previous tile runs: begin() the window size,
 // the row's descriptor and the walker's rank (every row's descriptor word is
 // read; a row past the window holds a stale or undefined one, so its slot
-// indices are clamped), mid() the two slots the descriptor names.
+// indices are clamped), mid() the two slots the descriptor names; the skip
+// decision (live) is taken when the tile is due.
 template <class Wd>
 struct WindowProducer {
     static constexpr bool kFold = true;   // the producer writes features 29, 30 = 1: biases in the MMAs
@@ -249,22 +250,22 @@ struct WindowProducer {
     Masks<Wd, 1> mk;
     // loaded by begin() / mid()
     int64_t w;
-    int row, K, r, best_r;
+    int row, half, K, r, best_r;
     uint2 dci;
     PTerm<Wd, 1, true> ti, tj;
     // latched by fill()
     int64_t out_idx;
     bool out_ok;
-    __device__ __forceinline__ bool begin(int64_t tile, int q) {
+    __device__ __forceinline__ void begin(int64_t tile, int q) {
         w = tile >> 1;
-        const int half = (int)(tile & 1);
+        half = (int)(tile & 1);
         row = half * kWin / 2 + q;
         K = kwin[w];
         dci = desc[(size_t)w * kWin + row];
         r = hdr[w].r;
         best_r = hdr[w].best_r;
-        return !(half && K <= kWin / 2);
     }
+    __device__ __forceinline__ bool live() const { return !(half && K <= kWin / 2); }
     __device__ __forceinline__ void mid(int) {
         const int i = min((int)(dci.x & 1023u), R - 1), j = min((int)((dci.x >> 12) & 1023u), R - 1);
         const Wd *src = slots + (size_t)w * R * 2;
