@@ -237,32 +237,6 @@ struct SoloWalker {
     __device__ __forceinline__ static uint32_t bc(uint32_t y, int e) {
         return (uint32_t)((int32_t)(y << (31 - e)) >> 31);
     }
-    // The broadcasts bc(x, e) of every coefficient bit e < FL of one factor value.
-    // With TFG_SLICE_PRMT, bits 0-3 and 4-7 are first moved to the sign bits of the
-    // four bytes of a word by one multiply each (bit k lands on bit 8k + 7 - 32 (k / 4);
-    // the four shifted copies of the nibble never overlap, so the product has no
-    // carries), and each broadcast is one byte permute that replicates a byte's sign
-    // bit; bit 8 keeps the two shifts.
-#ifndef TFG_SLICE_PRMT
-#define TFG_SLICE_PRMT 1
-#endif
-    struct Bcast {
-        uint32_t x, s0, s1;
-        __device__ __forceinline__ explicit Bcast(uint32_t v) : x(v), s0(0u), s1(0u) {
-            if (TFG_SLICE_PRMT) {
-                s0 = (v & 0xFu) * 0x10204080u;
-                s1 = (v & 0xF0u) * 0x01020408u;
-            }
-        }
-        __device__ __forceinline__ uint32_t operator()(int e) const {
-            if (TFG_SLICE_PRMT && e < 8) {
-                uint32_t r;
-                asm("prmt.b32 %0, %1, 0, %2;" : "=r"(r) : "r"(e < 4 ? s0 : s1), "r"(0x8888u + 0x1111u * (uint32_t)(e & 3)));
-                return r;
-            }
-            return bc(x, e);
-        }
-    };
     // factor f (run-time) of packed word x, in the low bits
     __device__ __forceinline__ uint32_t fx_rt(uint32_t x, int f) const {
         const int sh = f == 0 ? 0 : (f == 1 ? fb1 : fb2);
@@ -280,11 +254,10 @@ struct SoloWalker {
     // the same as after the write).
     __device__ __forceinline__ uint32_t sl_write(uint2 *base, uint32_t kb, uint32_t xp, uint32_t xn) const {
         uint32_t dd = 0;
-        const Bcast Bp(xp), Bn(xn);
 #pragma unroll
         for (int e = 0; e < FL; ++e) {
             uint2 w = base[e * BT];
-            const uint32_t bp = Bp(e), bn = Bn(e);
+            const uint32_t bp = bc(xp, e), bn = bc(xn, e);
             dd |= (w.x ^ bp) | (w.y ^ bn);
             w.x = (w.x & ~kb) | (bp & kb);
             w.y = (w.y & ~kb) | (bn & kb);
@@ -313,11 +286,11 @@ struct SoloWalker {
         } else {
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                const Bcast Bp(fx((uint32_t)v.p[0], f));
+                const uint32_t xp = fx((uint32_t)v.p[0], f);
 #pragma unroll
                 for (int e = 0; e < FL; ++e) {
                     const int q = f * FL + e;
-                    S[q] = (S[q] & ~kb) | (Bp(e) & kb);
+                    S[q] = (S[q] & ~kb) | (bc(xp, e) & kb);
                 }
             }
         }
@@ -354,16 +327,15 @@ struct SoloWalker {
                 wneg = lead_neg(xp, xn);
                 if (wneg) { const uint32_t t = xp; xp = xn; xn = t; }
             }
-            const Bcast Bp(xp), Bn(xn);
 #pragma unroll
             for (int e = 0; e < FL; ++e) {
                 const int q = f * FL + e;
                 uint32_t dd;
                 if constexpr (ZT) {
                     const uint2 w = ss[q * BT];
-                    dd = (w.x ^ Bp(e)) | (w.y ^ Bn(e));
+                    dd = (w.x ^ bc(xp, e)) | (w.y ^ bc(xn, e));
                 } else {
-                    dd = S[q] ^ Bp(e);
+                    dd = S[q] ^ bc(xp, e);
                 }
                 if (f == 0) du |= dd;
                 else if (f == 1) dv |= dd;
@@ -382,11 +354,10 @@ struct SoloWalker {
         if (f == 2 && lead_neg(xp, xn)) { const uint32_t t = xp; xp = xn; xn = t; }
         const uint2 *base = ss + f * FL * BT;
         uint32_t dd = 0;
-        const Bcast Bp(xp), Bn(xn);
 #pragma unroll
         for (int e = 0; e < FL; ++e) {
             const uint2 w = base[e * BT];
-            dd |= (w.x ^ Bp(e)) | (w.y ^ Bn(e));
+            dd |= (w.x ^ bc(xp, e)) | (w.y ^ bc(xn, e));
         }
         return ~dd;
     }
