@@ -156,8 +156,8 @@ def mapping_name(pop):
     if pop["lanes"] == 1:
         sliced = ", bit-sliced slot search" if pop.get("slice_len") else ""
         sliced += " (square factors compiled in)" if pop.get("square") else ""
-        return f"thread per walker, {pop['slots_per_lane']} slots{sliced}"
-    return f"{pop['lanes']} lanes x {pop['slots_per_lane']} slots"
+        return f"thread per walker, {pop['slots_per_lane']} slots{sliced}, {pop['block_threads']} walkers per block"
+    return f"{pop['lanes']} lanes x {pop['slots_per_lane']} slots, {pop['block_threads']} threads per block"
 
 
 def dist_setup(args):

@@ -68,7 +68,10 @@ typedef struct {
     int32_t plus_enabled;     /* 1: plus transitions on plateaus (default), 0: never */
     int32_t r_slack;          /* slots per walker = prepared start rank + r_slack (default 3, >= 1) */
     int32_t mapping;          /* lanes per walker G in {4,8,16,32}; 0 = autotune (default) */
-    int32_t block_threads;    /* CUDA block size, multiple of 32, at most 256 (default 256) */
+    int32_t block_threads;    /* CUDA block size, multiple of 32, at most 256 (default 256), of the
+                                 lane-group kernels; a thread-per-walker kernel takes it as its
+                                 walkers per block when a variant with that block size is compiled
+                                 for its capacity (else its compiled default; see tfg_launch_shape) */
     uint32_t walker_id_base;  /* global id of this context's first walker (sharding across GPUs) */
     int32_t use_graph;        /* tfg_walk launches one captured CUDA graph of all populations' kernels:
                                  1 chained (default), 2 forked onto one stream per population
@@ -331,12 +334,21 @@ int tfg_checkpoint(tfg_ctx *ctx, void *buf, size_t cap, size_t *used);
 int tfg_restore(tfg_ctx *ctx, const void *buf, size_t size);
 
 /* Autotuner: for every population, time each compiled kernel variant that fits
- * it (one thread per walker; 4, 8, 16 or 32 lanes per walker) for trial_steps
- * steps on its first min(walkers, trial_walkers) walkers, keep the fastest, and
- * restore those walkers' state bit for bit (host copies; no device memory is
- * allocated).  lanes_out[f] (optional) receives the chosen lanes per walker.
- * Synchronous. */
+ * it -- every mapping (one thread per walker; 4, 8, 16 or 32 lanes per walker)
+ * and, for each, every walkers-per-block choice (the block sizes compiled for
+ * the thread-per-walker kernel of that capacity, whose shared memory per block
+ * depends on it; 128 or 256 threads for the lane-group kernels) -- for
+ * trial_steps steps on its first min(walkers, trial_walkers) walkers, keep the
+ * fastest, and restore those walkers' state bit for bit (host copies; no device
+ * memory is allocated).  The choice changes no trajectory.  lanes_out[f]
+ * (optional) receives the chosen lanes per walker; tfg_launch_shape reports
+ * the whole launch shape.  Synchronous. */
 int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32_t *lanes_out);
+
+/* Launch shape of population f's walk kernel: lanes per walker, threads per
+ * block (walkers per block = block_threads / lanes) and blocks.  Any output may
+ * be NULL. */
+int tfg_launch_shape(tfg_ctx *ctx, int32_t f, int32_t *lanes, int32_t *block_threads, int64_t *grid);
 
 /* Mapping chosen for population f: lanes per walker G, slots per lane S (the
  * slot capacity for one thread per walker; 0 for the warp-per-walker kernel),

@@ -42,6 +42,7 @@ struct Segment {
     int64_t n = 0, first = 0;
     size_t off_hdr = 0, off_slots = 0, off_best = 0, off_start = 0;
     const tfg::WalkVariant *var = nullptr;
+    int block = 0;   // threads per block for variants whose block size the caller chooses (0: default)
     std::vector<int8_t> start_rows;
 };
 
@@ -105,6 +106,22 @@ const tfg::WalkVariant *pick_variant(int mode, int bits, int tw, int G, int R, c
         if (!best || v[a].S < best->S || (v[a].S == best->S && score(v[a]) > score(*best))) best = &v[a];
     }
     return best;
+}
+
+// The variant compiled for the same mapping and capacity as v with `block`
+// threads per block, if any (else v): how tfg_params.block_threads selects the
+// walkers per block of a thread-per-walker kernel.
+const tfg::WalkVariant *with_block(const tfg::WalkVariant *v, int block) {
+    if (!v || !v->block || v->block == block) return v;
+    int cnt = 0;
+    const tfg::WalkVariant *all = tfg::walk_variants(&cnt);
+    for (int a = 0; a < cnt; ++a) {
+        const tfg::WalkVariant &x = all[a];
+        if (x.mode == v->mode && x.word_bits == v->word_bits && x.tw == v->tw && x.G == v->G &&
+            x.capacity() == v->capacity() && x.fl == v->fl && x.sq == v->sq && x.block == block)
+            return &x;
+    }
+    return v;
 }
 
 // Default mapping: one thread per walker (shared-memory slots) when such a
@@ -382,6 +399,7 @@ static int plan_segments(int32_t n_formats, const tfg_format *fmts, const int32_
         off = layout_segment(s, off);
         s.var = prm.mapping ? pick_variant(s.fmt.mode, s.word_bits, s.tw, prm.mapping, s.R, s.fmt)
                             : default_variant(s.fmt.mode, s.word_bits, s.tw, s.R, s.fmt);
+        s.var = with_block(s.var, prm.block_threads);
         if (!s.var) { set_error("no compiled kernel variant for this format/rank/mapping"); return TFG_EINVAL; }
     }
     *bytes = off;
@@ -522,8 +540,12 @@ int tfg_init(int32_t n_formats, const tfg_format *fmts, const int32_t *ranks, co
     return TFG_OK;
 }
 
+static int block_of(const tfg_ctx *ctx, const Segment &s) {
+    return s.var->block ? s.var->block : (s.block ? s.block : ctx->prm.block_threads);
+}
+
 static void launch_segment(tfg_ctx *ctx, const Segment &s, int32_t steps, cudaStream_t st) {
-    const int b = s.var->block ? s.var->block : ctx->prm.block_threads;
+    const int b = block_of(ctx, s);
     const int64_t threads = s.n * s.var->G;
     const int64_t grid = (threads + b - 1) / b;
     s.var->launch(ctx->desc(s), steps, (int)grid, b, st);
@@ -626,6 +648,8 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
     if (e == cudaSuccess) e = cudaEventCreate(&ev.b);
     if (e != cudaSuccess) return cuda_fail(e, "autotune events");
     cudaEvent_t t0 = ev.a, t1 = ev.b;
+    int nvar = 0;
+    const tfg::WalkVariant *all = tfg::walk_variants(&nvar);
     for (size_t f = 0; f < ctx->segs.size(); ++f) {
         Segment &s = ctx->segs[f];
         if (s.n == 0) continue;
@@ -640,22 +664,35 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
         tfg::SegDesc d = ctx->desc(s);
         d.n_walkers = nt;
         const tfg::WalkVariant *best = s.var;
+        int best_block = s.block;
         float best_ms = 1e30f;
+        // every mapping (lanes per walker), and for each every compiled block size of its
+        // kernel (walkers per block: compiled into thread-per-walker kernels, whose shared
+        // memory per block depends on it; 128 or 256 threads for the lane-group kernels)
         static const int lanes[5] = {1, 4, 8, 16, 32};
         for (int G : lanes) {
-            const tfg::WalkVariant *v = pick_variant(s.fmt.mode, s.word_bits, s.tw, G, s.R, s.fmt);
-            if (!v) continue;
-            const int b = v->block ? v->block : ctx->prm.block_threads;
-            const int64_t grid = (nt * v->G + b - 1) / b;
-            v->launch(d, (int32_t)std::min<int64_t>(trial_steps, 64), (int)grid, b, ctx->stream);   // warm-up
-            cudaEventRecord(t0, ctx->stream);
-            v->launch(d, (int32_t)trial_steps, (int)grid, b, ctx->stream);
-            cudaEventRecord(t1, ctx->stream);
-            e = cudaEventSynchronize(t1);
-            if (e != cudaSuccess) return cuda_fail(e, "autotune trial");
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, t0, t1);
-            if (ms < best_ms) { best_ms = ms; best = v; }
+            const tfg::WalkVariant *base = pick_variant(s.fmt.mode, s.word_bits, s.tw, G, s.R, s.fmt);
+            if (!base) continue;
+            for (int a = 0; a < nvar; ++a) {
+                const tfg::WalkVariant &v = all[a];
+                if (v.mode != base->mode || v.word_bits != base->word_bits || v.tw != base->tw || v.G != base->G ||
+                    v.capacity() != base->capacity() || v.fl != base->fl || v.sq != base->sq)
+                    continue;
+                static const int free_blocks[2] = {128, 256};
+                for (int k = 0; k < (v.block ? 1 : 2); ++k) {
+                    const int b = v.block ? v.block : free_blocks[k];
+                    const int64_t grid = (nt * v.G + b - 1) / b;
+                    v.launch(d, (int32_t)std::min<int64_t>(trial_steps, 64), (int)grid, b, ctx->stream);   // warm-up
+                    cudaEventRecord(t0, ctx->stream);
+                    v.launch(d, (int32_t)trial_steps, (int)grid, b, ctx->stream);
+                    cudaEventRecord(t1, ctx->stream);
+                    e = cudaEventSynchronize(t1);
+                    if (e != cudaSuccess) return cuda_fail(e, "autotune trial");
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, t0, t1);
+                    if (ms < best_ms) { best_ms = ms; best = &v; best_block = v.block ? 0 : b; }
+                }
+            }
         }
         // restore the trial walkers bit for bit
         e = cudaMemcpy(ctx->ws + s.off_hdr, hdr.data(), hdr.size(), cudaMemcpyHostToDevice);
@@ -663,10 +700,21 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
         if (e == cudaSuccess) e = cudaMemcpy(ctx->ws + s.off_best, be.data(), be.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e, "autotune restore");
         s.var = best;
+        s.block = best_block;
         if (lanes_out) lanes_out[f] = best->G;
     }
     for (tfg_ctx::Graph &g : ctx->graphs) cudaGraphExecDestroy(g.exec);   // variants changed
     ctx->graphs.clear();
+    return TFG_OK;
+}
+
+int tfg_launch_shape(tfg_ctx *ctx, int32_t f, int32_t *lanes, int32_t *block_threads, int64_t *grid) {
+    if (!ctx || f < 0 || f >= (int)ctx->segs.size()) { set_error("bad population index"); return TFG_EINVAL; }
+    const Segment &s = ctx->segs[f];
+    const int b = block_of(ctx, s);
+    if (lanes) *lanes = s.var->G;
+    if (block_threads) *block_threads = b;
+    if (grid) *grid = (s.n * s.var->G + b - 1) / b;
     return TFG_OK;
 }
 

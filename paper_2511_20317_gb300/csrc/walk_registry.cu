@@ -12,6 +12,7 @@ const WalkVariant *walk_variants_solo_zt32(int *n);
 const WalkVariant *walk_variants_solo_z232(int *n);
 const WalkVariant *walk_variants_solo_zt64(int *n);
 const WalkVariant *walk_variants_solo_z264(int *n);
+const WalkVariant *walk_variants_solo_zt64_alt(int *n);
 
 const WalkVariant *walk_variants(int *count) {
     static std::vector<WalkVariant> all = [] {
@@ -25,6 +26,7 @@ const WalkVariant *walk_variants(int *count) {
             walk_variants_solo_z232,
             walk_variants_solo_zt64,
             walk_variants_solo_z264,
+            walk_variants_solo_zt64_alt,   // after the defaults: pick_variant takes the first match
         };
         for (auto part : parts) {
             int n = 0;

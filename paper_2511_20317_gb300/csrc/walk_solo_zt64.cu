@@ -31,4 +31,5 @@ const WalkVariant *walk_variants_solo_zt64(int *n) {
     *n = (int)(sizeof(v) / sizeof(v[0]));
     return v;
 }
+
 }  // namespace tfg

@@ -84,7 +84,7 @@ EXPORTED = ["tfg_default_params", "tfg_last_error", "tfg_verify", "tfg_additive_
             "tfg_restore", "tfg_mapping", "tfg_autotune", "tfg_destroy", "tfg_philox_device", "tfg_mlp_param_bytes",
             "tfg_mlp_score", "tfg_mlp_grad", "tfg_mlp_train_state_bytes", "tfg_mlp_train_init",
             "tfg_mlp_train_step", "tfg_window_scratch_bytes", "tfg_walk_window", "tfg_walk_window_noalloc",
-            "tfg_test_set_wait_limit", "tfg_window_dump"]
+            "tfg_test_set_wait_limit", "tfg_window_dump", "tfg_launch_shape"]
 
 _lib = None
 _lock = threading.Lock()
@@ -150,6 +150,8 @@ def lib() -> ctypes.CDLL:
                 "tfg_mlp_train_step": (i32, [P, P, P, P, P, i64, ctypes.c_float, i32, P, P]),
                 "tfg_test_set_wait_limit": (None, [i64]),
                 "tfg_window_dump": (i32, [P, P, P, P]),
+                "tfg_launch_shape": (i32, [P, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int64)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -473,9 +475,11 @@ class Walkers:
                                     ctypes.byref(nw), ctypes.byref(first)))
         G, S, SL, SQ = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _check(lib().tfg_mapping(self.ctx, f, ctypes.byref(G), ctypes.byref(S), ctypes.byref(SL), ctypes.byref(SQ)))
+        BT, GR = ctypes.c_int32(), ctypes.c_int64()
+        _check(lib().tfg_launch_shape(self.ctx, f, None, ctypes.byref(BT), ctypes.byref(GR)))
         return {"fmt": (fmt.m, fmt.n, fmt.p), "mode": fmt.mode, "r0": r0.value, "r_max": rmax.value,
                 "walkers": nw.value, "first": first.value, "lanes": G.value, "slots_per_lane": S.value,
-                "slice_len": SL.value, "square": SQ.value}
+                "slice_len": SL.value, "square": SQ.value, "block_threads": BT.value, "grid": GR.value}
 
     def tfg_autotune(self, trial_steps: int = 400, trial_walkers: int = 32768):
         lanes = (ctypes.c_int32 * self.n_formats)()

@@ -216,6 +216,24 @@ def test_mixed_full_population_sampled():
     W.close()
 
 
+@pytest.mark.parametrize("fmt,block", [((2, 4, 5), 96), ((3, 4, 5), 128), ((4, 4, 4), 128), ((4, 4, 5), 160)])
+def test_walkers_per_block_choices_are_bit_exact(fmt, block):
+    """The other compiled walkers-per-block choices of the thread-per-walker
+    kernels (selected through tfg_params.block_threads; the autotuner times them
+    all): capacities 48, 64, 72 and 88 at 96, 128, 128 and 160 threads per block."""
+    start = naive_start(*fmt)
+    nw, steps, L = 700, 1500, 300
+    W = gpu_walkers(fmt, 0, start, nw, 31, steps, chunks=2, plateau_len=L, block_threads=block)
+    assert W.pop[0]["lanes"] == 1 and W.pop[0]["block_threads"] == block
+    assert W.pop[0]["grid"] == (nw + block - 1) // block
+    info, slots, best = W.read_walkers(0, nw)
+    ref = oracle.Walkers(fmt, start, np.arange(nw), seed=31, plateau_len=L).walk(steps, THREADS)
+    assert (ref.info["accepted"] > 0).all() and (ref.info["plus"] > 0).any()
+    assert_parity(info, slots, best, ref, range(nw), f"{fmt} block {block}")
+    assert W.verify_all() == 0
+    W.close()
+
+
 def test_large_formats_full_population_sampled():
     """The large-format workload at its full size: (4,5,12), (5,6,10), (6,7,9) from the
     meta-operator starts, 131072 walkers each, one forked graph launch per chunk (the
