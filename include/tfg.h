@@ -426,13 +426,11 @@ int tfg_mlp_train_step(void *d_state, void *d_params, const uint16_t *d_x, const
  * memory, on the tensor-core kernel, from the window's candidate list.)
  * policy 0 (uniform): candidate mulhi(x1, K);
  * policy 1 (learned): with x3 < eps_thresh as policy 0, else the candidate of
- * highest MLP score (first on ties; scores compared by their order-preserving
- * integer images, so -0 ranks below +0).  The chosen flip then goes through the
+ * highest MLP score (first on ties).  The chosen flip then goes through the
  * same validity test, reductions and bookkeeping as tfg_walk.
  * Populations must be Z_T with m*n + n*p + p*m <= 64 and r_max <= 88.
  * d_scratch: caller device memory of tfg_window_scratch_bytes (per walker
- * the window's candidate descriptors, scores, size and greedy choice: 3084
- * bytes).  d_choices (optional, device int32
+ * the window's candidate descriptors, scores and size: 3076 bytes).  d_choices (optional, device int32
  * [steps][walkers]) receives the chosen window index of every step (-1: no
  * candidate).  log (optional): chosen features with label 1 when the step
  * lowered the rank (always kept) or 0 (kept when a Philox draw of sub-stream
@@ -469,11 +467,11 @@ int tfg_walk_window(tfg_ctx *ctx, int64_t steps, int32_t policy, const void *d_m
 /* tfg_walk_window without any caller scratch: the paper has no counterpart to
  * this entry point.  It is for callers that cannot call cudaMalloc (code that
  * runs inside another framework's memory arena, or a process whose device
- * memory is reserved up front): the window's candidate descriptors, scores,
- * sizes and greedy choices live in a 32 MiB array that the library itself defines as static
+ * memory is reserved up front): the window's candidate descriptors, scores
+ * and sizes live in a 32 MiB array that the library itself defines as static
  * device memory, which every GPU that loads the library holds until the
- * process exits.  Contexts of more than 10880 walkers (the array's capacity at
- * 3084 bytes per walker) are rejected with TFG_EINVAL and a message.  The call
+ * process exits.  Contexts of more than 10908 walkers (the array's capacity at
+ * 3076 bytes per walker) are rejected with TFG_EINVAL and a message.  The call
  * allocates nothing: tfg_init already looked up the array's device address on
  * its device, which loads the library's module there and so reserves the
  * 32 MiB at that point at the latest (under lazy module loading; at library

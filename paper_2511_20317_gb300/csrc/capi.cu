@@ -1109,14 +1109,12 @@ int tfg_mlp_train_step(void *d_state, void *d_params, const uint16_t *d_x, const
     return TFG_OK;
 }
 
-// per walker: W window rows of (descriptor, info) words and W scores; then the window sizes
-// and the argmax keys of the scores (tfg_window_scratch_bytes)
-static size_t window_row_bytes() { return (size_t)tfg::window_cap() * (8 + 4) + 8; }
+// per walker: W window rows of (descriptor, info) words and a score, then the window size
+static size_t window_row_bytes() { return (size_t)tfg::window_cap() * (8 + 4); }
 
 int tfg_window_scratch_bytes(tfg_ctx *ctx, size_t *bytes) {
     if (!ctx || !bytes) { set_error("bad arguments"); return TFG_EINVAL; }
-    const size_t N = (size_t)ctx->total, W = (size_t)tfg::window_cap();
-    *bytes = align_up(N * W * 12 + (N * 4 + 7) / 8 * 8 + N * 8);   // rows, scores, window sizes, argmax keys
+    *bytes = align_up((size_t)ctx->total * window_row_bytes() + (size_t)ctx->total * 4);
     return TFG_OK;
 }
 
@@ -1149,22 +1147,20 @@ static int window_steps(tfg_ctx *ctx, int64_t steps, int32_t policy, const void 
     auto *desc = reinterpret_cast<uint2 *>(base);
     auto *score = reinterpret_cast<float *>(base + (size_t)N * W * 8);
     auto *kwin = reinterpret_cast<int *>(base + (size_t)N * W * 12);
-    auto *keys = reinterpret_cast<unsigned long long *>(base + (size_t)N * W * 12 + ((size_t)N * 4 + 7) / 8 * 8);
     tfg_log_spec lg{};
     if (log) lg = *log;
     int32_t *status = &ctx->aux()->status;
     for (int64_t st = 0; st < steps; ++st) {
         for (const Segment &s : ctx->segs)
-            tfg::launch_window(ctx->desc(s), nullptr, desc + (size_t)s.first * W, kwin + s.first,
-                               policy == 1 ? keys + s.first : nullptr, ctx->stream);
+            tfg::launch_window(ctx->desc(s), nullptr, desc + (size_t)s.first * W, kwin + s.first, ctx->stream);
         if (policy == 1)
             for (const Segment &s : ctx->segs)
                 tfg::launch_window_score(ctx->desc(s), d_mlp_params, desc + (size_t)s.first * W, kwin + s.first,
-                                         score + (size_t)s.first * W, keys + s.first, status, ctx->stream);
+                                         score + (size_t)s.first * W, status, ctx->stream);
         for (const Segment &s : ctx->segs) {
             int32_t *ch = d_choices ? d_choices + (size_t)st * N + s.first : nullptr;
-            tfg::launch_window_apply(ctx->desc(s), desc + (size_t)s.first * W, kwin + s.first, keys + s.first,
-                                     policy, eps_thresh, ch, lg, ctx->stream);
+            tfg::launch_window_apply(ctx->desc(s), desc + (size_t)s.first * W, kwin + s.first,
+                                     score + (size_t)s.first * W, policy, eps_thresh, ch, lg, ctx->stream);
         }
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "window step launch");
@@ -1183,8 +1179,7 @@ int tfg_window_dump(tfg_ctx *ctx, uint16_t *d_feat, uint32_t *d_desc, int32_t *d
     const int W = tfg::window_cap();
     for (const Segment &s : ctx->segs)
         tfg::launch_window(ctx->desc(s), d_feat ? d_feat + (size_t)s.first * W * 32 : nullptr,
-                           reinterpret_cast<uint2 *>(d_desc) + (size_t)s.first * W, d_kwin + s.first, nullptr,
-                           ctx->stream);
+                           reinterpret_cast<uint2 *>(d_desc) + (size_t)s.first * W, d_kwin + s.first, ctx->stream);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "window dump launch");
     return TFG_OK;

@@ -103,13 +103,11 @@ int window_apply_capacity(int word_bits, int R);
 // Window mode (walk_window.cu).  desc[w][k] = (descriptor, info) of window row k of
 // walker w: descriptor i | X << 10 | j << 12 | (s < 0) << 22 | rho << 23, info = the term's
 // candidate count (at most 64) | its position after i0 (at most 64) << 8.
-// best_key[w]: the scoring kernel's running argmax of walker w's window (zeroed by the window kernel).
-void launch_window(const SegDesc &d, void *feat /*nullable*/, uint2 *desc, int *kwin,
-                   unsigned long long *best_key /*nullable*/, cudaStream_t st);
+void launch_window(const SegDesc &d, void *feat /*nullable*/, uint2 *desc, int *kwin, cudaStream_t st);
 void launch_window_score(const SegDesc &d, const void *params, const uint2 *desc, const int *kwin, float *score,
-                         unsigned long long *best_key, int *err, cudaStream_t st);
-int launch_window_apply(const SegDesc &d, const uint2 *desc, const int *kwin, const unsigned long long *best_key,
-                        int policy, uint32_t eps, int32_t *choices, const WindowLog &log, cudaStream_t st);
+                         int *err, cudaStream_t st);
+int launch_window_apply(const SegDesc &d, const uint2 *desc, const int *kwin, const float *score, int policy,
+                        uint32_t eps, int32_t *choices, const WindowLog &log, cudaStream_t st);
 size_t mlp_param_bytes();
 int launch_mlp_score(const void *params, const void *x, int64_t n, float *out, int *err, cudaStream_t st);
 void set_first_wait_limit(int64_t polls);   // test hook of tfg_test_set_wait_limit

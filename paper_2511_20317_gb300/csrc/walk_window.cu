@@ -39,12 +39,6 @@ __device__ __forceinline__ int popc_w(Wd v) {
     else return __popcll(v);
 }
 
-// Exact float of a small non-negative integer (n < 2^23) without the
-// conversion pipe: 2^23 + n is a float with n in its mantissa.
-__device__ __forceinline__ float small_int_float(int n) {
-    return __uint_as_float(0x4B000000u + (uint32_t)n) - 8388608.0f;
-}
-
 // Features of candidate (X, j, sign, rho) of term a = slot i (b = slot j).
 template <class Wd>
 __device__ __forceinline__ void cand_features(const PTerm<Wd, 1, true> &a, const PTerm<Wd, 1, true> &b,
@@ -62,37 +56,31 @@ __device__ __forceinline__ void cand_features(const PTerm<Wd, 1, true> &a, const
     const Wd zp = sneg ? a.p[0] : a.n[0], zn = sneg ? a.n[0] : a.p[0];
     const bool vz = (((b.p[0] & zp) | (b.n[0] & zn)) & MZ) == Wd(0);
     const Wd szd = (((b.p[0] | zp) & ~(b.n[0] | zn)) | ((b.n[0] | zn) & ~(b.p[0] | zp))) & MZ;
-    int v[kFeat];
 #pragma unroll
-    for (int k = 0; k < kFeat; ++k) v[k] = 0;
-    v[0] = X == 0;
-    v[1] = X == 1;
-    v[2] = X == 2;
-    v[3] = rho;
-    v[4] = sneg;
-    v[5] = popc_w<Wd>(ad & MX);
-    v[6] = popc_w<Wd>(ad & MY);
-    v[7] = popc_w<Wd>(bd & MY);
-    v[8] = vy ? popc_w<Wd>(syd) : 0;
-    v[9] = vy;
-    v[10] = popc_w<Wd>(ad & MZ);
-    v[11] = popc_w<Wd>(bd & MZ);
-    v[12] = vz ? popc_w<Wd>(szd) : 0;
-    v[13] = vz;
-    v[14] = popc_w<Wd>(ad & bd & MY);
-    v[15] = popc_w<Wd>(ad & bd & MZ);
-    v[16] = vy && syd == Wd(0);
-    v[17] = vz && szd == Wd(0);
-    v[18] = k_i < 64 ? k_i : 64;
-    v[19] = r - best_r;
-    v[20] = r;
-    v[21] = m;
-    v[22] = n;
-    v[23] = p;
-    v[24] = q < 64 ? q : 64;
-    v[31] = 1;
-#pragma unroll
-    for (int k = 0; k < kFeat; ++k) f[k] = small_int_float(v[k]);
+    for (int k = 0; k < kFeat; ++k) f[k] = (k == X) ? 1.f : 0.f;   // one-hot X in f[0..2]
+    f[3] = (float)rho;
+    f[4] = (float)sneg;
+    f[5] = (float)popc_w<Wd>(ad & MX);
+    f[6] = (float)popc_w<Wd>(ad & MY);
+    f[7] = (float)popc_w<Wd>(bd & MY);
+    f[8] = vy ? (float)popc_w<Wd>(syd) : 0.f;
+    f[9] = vy ? 1.f : 0.f;
+    f[10] = (float)popc_w<Wd>(ad & MZ);
+    f[11] = (float)popc_w<Wd>(bd & MZ);
+    f[12] = vz ? (float)popc_w<Wd>(szd) : 0.f;
+    f[13] = vz ? 1.f : 0.f;
+    f[14] = (float)popc_w<Wd>(ad & bd & MY);
+    f[15] = (float)popc_w<Wd>(ad & bd & MZ);
+    f[16] = (vy && syd == Wd(0)) ? 1.f : 0.f;
+    f[17] = (vz && szd == Wd(0)) ? 1.f : 0.f;
+    f[18] = (float)(k_i < 64 ? k_i : 64);
+    f[19] = (float)(r - best_r);
+    f[20] = (float)r;
+    f[21] = (float)m;
+    f[22] = (float)n;
+    f[23] = (float)p;
+    f[24] = (float)(q < 64 ? q : 64);
+    f[31] = 1.f;
 }
 
 // Features of a candidate as 16 packed bf16x2 words (small integers: exact).
@@ -117,8 +105,7 @@ __device__ __forceinline__ void cand_features_bf16(const PTerm<Wd, 1, true> &a, 
 // are zero).
 template <class Wd>
 __global__ void __launch_bounds__(128) window_kernel(const SegDesc d, __nv_bfloat16 *__restrict__ feat,
-                                                     uint2 *__restrict__ desc, int *__restrict__ kwin,
-                                                     unsigned long long *__restrict__ best_key) {
+                                                     uint2 *__restrict__ desc, int *__restrict__ kwin) {
     __shared__ __align__(16) Wd sp[4][kWinMaxSlots], sn[4][kWinMaxSlots];
     __shared__ uint32_t sdesc[4][kWin], sinfo[4][kWin];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -238,10 +225,7 @@ __global__ void __launch_bounds__(128) window_kernel(const SegDesc d, __nv_bfloa
             }
         }
     }
-    if (lane == 0) {
-        kwin[w] = K;
-        if (best_key) best_key[w] = 0ull;
-    }
+    if (lane == 0) kwin[w] = K;
 }
 
 // Producer of the fused scoring kernel: tile t is half t & 1 (rows 0-127 or
@@ -263,7 +247,6 @@ struct WindowProducer {
     const uint2 *desc;
     const int *kwin;
     float *score;
-    unsigned long long *best_key;
     Masks<Wd, 1> mk;
     // loaded by begin() / mid()
     int64_t w;
@@ -271,8 +254,7 @@ struct WindowProducer {
     uint2 dci;
     PTerm<Wd, 1, true> ti, tj;
     // latched by fill()
-    int64_t out_idx, out_w;
-    int out_row;
+    int64_t out_idx;
     bool out_ok;
     __device__ __forceinline__ void begin(int64_t tile, int q) {
         w = tile >> 1;
@@ -306,29 +288,10 @@ struct WindowProducer {
         for (int c = 0; c < kFeat / 8; ++c)
             mlp::st_row8(sX, q, 8 * c, mlp::kIn, make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]));
         out_idx = w * kWin + row;
-        out_w = w;
-        out_row = row;
         out_ok = row < K;
     }
-    // The score, and the walker's running argmax: key = (order-preserving bits of
-    // the score) << 32 | (2^32 - 1 - row), maximised over the warp's rows and then
-    // with one 64-bit atomicMax per warp, so the highest score wins and, among
-    // equal scores, the lowest row (the first maximum).  Rows past the window
-    // carry key 0, below every real row's key.
     __device__ __forceinline__ void emit(float y, int) {
-        unsigned long long key = 0ull;
-        if (out_ok) {
-            score[out_idx] = y;
-            const uint32_t u = __float_as_uint(y);
-            const uint32_t ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-            key = ((unsigned long long)ord << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)out_row);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
-            key = other > key ? other : key;
-        }
-        if ((threadIdx.x & 31) == 0 && key) atomicMax(best_key + out_w, key);
+        if (out_ok) score[out_idx] = y;
     }
 };
 
@@ -337,8 +300,8 @@ constexpr int kScoreWG = 4;
 template <class Wd>
 __global__ void __launch_bounds__(kScoreWG * 128, 1)
     window_score_kernel(const SegDesc d, const uint8_t *__restrict__ params, const uint2 *__restrict__ desc,
-                        const int *__restrict__ kwin, float *__restrict__ score,
-                        unsigned long long *__restrict__ best_key, int *__restrict__ err, uint32_t first_limit) {
+                        const int *__restrict__ kwin, float *__restrict__ score, int *__restrict__ err,
+                        uint32_t first_limit) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar[kScoreWG];
     __shared__ uint32_t tslot;
@@ -353,7 +316,6 @@ __global__ void __launch_bounds__(kScoreWG * 128, 1)
     pr.desc = desc;
     pr.kwin = kwin;
     pr.score = score;
-    pr.best_key = best_key;
     pr.mk.load(d);
     mlp::run_tiles<kScoreWG>(params, pr, d.n_walkers * 2, err, first_limit, smem, mbar, &tslot, &tflag);
 }
@@ -362,7 +324,7 @@ __global__ void __launch_bounds__(kScoreWG * 128, 1)
 template <class Wd, int RMAX, int BT>
 __global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const uint2 *__restrict__ desc,
                                                           const int *__restrict__ kwin,
-                                                          const unsigned long long *__restrict__ best_key, int policy,
+                                                          const float *__restrict__ score, int policy,
                                                           uint32_t eps_thresh, int32_t *__restrict__ choices,
                                                           WindowLog log) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -392,10 +354,11 @@ __global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const
         if (policy == 0 || x.w < eps_thresh) {
             c = (int)__umulhi(x.y, (uint32_t)K);
         } else {
-            // the scoring kernel's argmax (key 0: no row was scored, e.g. after a timeout)
-            const unsigned long long key = best_key[w];
-            const int row = (int)(0xFFFFFFFFu - (uint32_t)key);
-            c = key && row < K ? row : 0;
+            const float *sc = score + (size_t)w * kWin;
+            c = 0;
+            float best = sc[0];
+            for (int k = 1; k < K; ++k)
+                if (sc[k] > best) { best = sc[k]; c = k; }
         }
         const uint2 dci = desc[(size_t)w * kWin + c];
         const uint32_t dc = dci.x;
@@ -440,21 +403,20 @@ __global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const
 
 int window_cap() { return dev::kWin; }
 
-void launch_window(const SegDesc &d, void *feat, uint2 *desc, int *kwin, unsigned long long *best_key,
-                   cudaStream_t st) {
+void launch_window(const SegDesc &d, void *feat, uint2 *desc, int *kwin, cudaStream_t st) {
     const int64_t blocks = (d.n_walkers + 3) / 4;
     if (blocks <= 0) return;
     if (d.word_bits == 32)
         dev::window_kernel<uint32_t><<<(unsigned)blocks, 128, 0, st>>>(d, reinterpret_cast<__nv_bfloat16 *>(feat),
-                                                                      desc, kwin, best_key);
+                                                                      desc, kwin);
     else
         dev::window_kernel<uint64_t><<<(unsigned)blocks, 128, 0, st>>>(d, reinterpret_cast<__nv_bfloat16 *>(feat),
-                                                                      desc, kwin, best_key);
+                                                                      desc, kwin);
 }
 
 template <class Wd>
 static void score_variant(const SegDesc &d, const void *params, const uint2 *desc, const int *kwin, float *score,
-                          unsigned long long *best_key, int *err, cudaStream_t st) {
+                          int *err, cudaStream_t st) {
     constexpr uint32_t smem = mlp::Layout<true>::bytes(dev::kScoreWG);
     static bool attr = [] {
         cudaFuncSetAttribute(dev::window_score_kernel<Wd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -463,19 +425,19 @@ static void score_variant(const SegDesc &d, const void *params, const uint2 *des
     (void)attr;
     const int grid = score_grid(d.n_walkers * 2, dev::kScoreWG);
     dev::window_score_kernel<Wd><<<grid, dev::kScoreWG * 128, smem, st>>>(
-        d, reinterpret_cast<const uint8_t *>(params), desc, kwin, score, best_key, err, first_wait_limit());
+        d, reinterpret_cast<const uint8_t *>(params), desc, kwin, score, err, first_wait_limit());
 }
 
 void launch_window_score(const SegDesc &d, const void *params, const uint2 *desc, const int *kwin, float *score,
-                         unsigned long long *best_key, int *err, cudaStream_t st) {
+                         int *err, cudaStream_t st) {
     if (d.n_walkers <= 0) return;
-    if (d.word_bits == 32) score_variant<uint32_t>(d, params, desc, kwin, score, best_key, err, st);
-    else score_variant<uint64_t>(d, params, desc, kwin, score, best_key, err, st);
+    if (d.word_bits == 32) score_variant<uint32_t>(d, params, desc, kwin, score, err, st);
+    else score_variant<uint64_t>(d, params, desc, kwin, score, err, st);
 }
 
 template <class Wd, int RMAX>
-static void apply_variant(const SegDesc &d, const uint2 *desc, const int *kwin, const unsigned long long *best_key,
-                          int policy, uint32_t eps, int32_t *choices, const WindowLog &log, cudaStream_t st) {
+static void apply_variant(const SegDesc &d, const uint2 *desc, const int *kwin, const float *score, int policy,
+                          uint32_t eps, int32_t *choices, const WindowLog &log, cudaStream_t st) {
     constexpr int BT = 128;
     constexpr size_t smem = solo_smem_bytes<TFG_MODE_ZT, Wd, RMAX, BT>();
     static bool attr = [] {
@@ -485,7 +447,7 @@ static void apply_variant(const SegDesc &d, const uint2 *desc, const int *kwin, 
     }();
     (void)attr;
     const int64_t blocks = (d.n_walkers + BT - 1) / BT;
-    dev::window_apply_kernel<Wd, RMAX, BT><<<(unsigned)blocks, BT, smem, st>>>(d, desc, kwin, best_key, policy, eps,
+    dev::window_apply_kernel<Wd, RMAX, BT><<<(unsigned)blocks, BT, smem, st>>>(d, desc, kwin, score, policy, eps,
                                                                               choices, log);
 }
 
@@ -499,20 +461,20 @@ int window_apply_capacity(int word_bits, int R) {
     return 0;
 }
 
-int launch_window_apply(const SegDesc &d, const uint2 *desc, const int *kwin, const unsigned long long *best_key,
-                        int policy, uint32_t eps, int32_t *choices, const WindowLog &log, cudaStream_t st) {
+int launch_window_apply(const SegDesc &d, const uint2 *desc, const int *kwin, const float *score, int policy,
+                        uint32_t eps, int32_t *choices, const WindowLog &log, cudaStream_t st) {
     if (d.n_walkers <= 0) return 0;
     const int cap = window_apply_capacity(d.word_bits, d.R);
     if (d.word_bits == 32) {
-        if (cap == 12) apply_variant<uint32_t, 12>(d, desc, kwin, best_key, policy, eps, choices, log, st);
-        else if (cap == 16) apply_variant<uint32_t, 16>(d, desc, kwin, best_key, policy, eps, choices, log, st);
-        else if (cap == 32) apply_variant<uint32_t, 32>(d, desc, kwin, best_key, policy, eps, choices, log, st);
+        if (cap == 12) apply_variant<uint32_t, 12>(d, desc, kwin, score, policy, eps, choices, log, st);
+        else if (cap == 16) apply_variant<uint32_t, 16>(d, desc, kwin, score, policy, eps, choices, log, st);
+        else if (cap == 32) apply_variant<uint32_t, 32>(d, desc, kwin, score, policy, eps, choices, log, st);
         else return -1;
     } else {
-        if (cap == 48) apply_variant<uint64_t, 48>(d, desc, kwin, best_key, policy, eps, choices, log, st);
-        else if (cap == 64) apply_variant<uint64_t, 64>(d, desc, kwin, best_key, policy, eps, choices, log, st);
-        else if (cap == 72) apply_variant<uint64_t, 72>(d, desc, kwin, best_key, policy, eps, choices, log, st);
-        else if (cap == 88) apply_variant<uint64_t, 88>(d, desc, kwin, best_key, policy, eps, choices, log, st);
+        if (cap == 48) apply_variant<uint64_t, 48>(d, desc, kwin, score, policy, eps, choices, log, st);
+        else if (cap == 64) apply_variant<uint64_t, 64>(d, desc, kwin, score, policy, eps, choices, log, st);
+        else if (cap == 72) apply_variant<uint64_t, 72>(d, desc, kwin, score, policy, eps, choices, log, st);
+        else if (cap == 88) apply_variant<uint64_t, 88>(d, desc, kwin, score, policy, eps, choices, log, st);
         else return -1;
     }
     return 0;
