@@ -333,16 +333,19 @@ int tfg_population(tfg_ctx *ctx, int32_t f, tfg_format *fmt, int32_t *r0, int32_
 int tfg_checkpoint(tfg_ctx *ctx, void *buf, size_t cap, size_t *used);
 int tfg_restore(tfg_ctx *ctx, const void *buf, size_t size);
 
-/* Autotuner: for every population, time each compiled kernel variant that fits
- * it -- every mapping (one thread per walker; 4, 8, 16 or 32 lanes per walker)
- * and, for each, every walkers-per-block choice (the block sizes compiled for
- * the thread-per-walker kernel of that capacity, whose shared memory per block
- * depends on it; 128 or 256 threads for the lane-group kernels) -- for
- * trial_steps steps on its first min(walkers, trial_walkers) walkers, keep the
- * fastest, and restore those walkers' state bit for bit (host copies; no device
- * memory is allocated).  The choice changes no trajectory.  lanes_out[f]
- * (optional) receives the chosen lanes per walker; tfg_launch_shape reports
- * the whole launch shape.  Synchronous. */
+/* Autotuner: the candidates of a population are its compiled kernel variants
+ * -- every mapping (one thread per walker; 4, 8, 16 or 32 lanes per walker) and,
+ * for each, every walkers-per-block choice (the block sizes compiled for the
+ * thread-per-walker kernel of that capacity, whose shared memory per block
+ * depends on it; 128 or 256 threads for the lane-group kernels).  Population
+ * by population, each candidate is timed for trial_steps steps on the first
+ * min(walkers, trial_walkers) walkers of every population, all populations
+ * launched as tfg_walk launches them (concurrently for use_graph 2) with the
+ * others at their current choice; a candidate replaces the current choice
+ * when it is more than 1% faster.  The trial walkers' state is restored bit for
+ * bit afterwards (host copies; no device memory is allocated); the choice
+ * changes no trajectory.  lanes_out[f] (optional) receives the chosen lanes
+ * per walker; tfg_launch_shape reports the whole launch shape.  Synchronous. */
 int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32_t *lanes_out);
 
 /* Launch shape of population f's walk kernel: lanes per walker, threads per

@@ -551,14 +551,8 @@ static void launch_segment(tfg_ctx *ctx, const Segment &s, int32_t steps, cudaSt
     s.var->launch(ctx->desc(s), steps, (int)grid, b, st);
 }
 
-// Capture (once per step count) a graph of every population's walk kernel:
-// chained on one stream (use_graph 1), or forked into one stream per
-// population and joined (use_graph 2).
-// The capture origin is a private stream (the caller's stream may be the
-// legacy default stream, which cannot be captured).
-static int walk_graph(tfg_ctx *ctx, int32_t steps, cudaGraphExec_t *out) {
-    for (const tfg_ctx::Graph &g : ctx->graphs)
-        if (g.steps == steps) { *out = g.exec; return TFG_OK; }
+// Streams and events of the forked launch: [0] the origin, [1 + f] population f.
+static int ensure_fork_resources(tfg_ctx *ctx) {
     const size_t P = ctx->segs.size();
     cudaError_t e = cudaSuccess;
     while (ctx->fork_streams.size() < P + 1 && e == cudaSuccess) {
@@ -571,7 +565,22 @@ static int walk_graph(tfg_ctx *ctx, int32_t steps, cudaGraphExec_t *out) {
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e == cudaSuccess) ctx->fork_events.push_back(ev);
     }
-    if (e != cudaSuccess) return cuda_fail(e, "graph streams");
+    if (e != cudaSuccess) return cuda_fail(e, "fork streams");
+    return TFG_OK;
+}
+
+// Capture (once per step count) a graph of every population's walk kernel:
+// chained on one stream (use_graph 1), or forked into one stream per
+// population and joined (use_graph 2).
+// The capture origin is a private stream (the caller's stream may be the
+// legacy default stream, which cannot be captured).
+static int walk_graph(tfg_ctx *ctx, int32_t steps, cudaGraphExec_t *out) {
+    for (const tfg_ctx::Graph &g : ctx->graphs)
+        if (g.steps == steps) { *out = g.exec; return TFG_OK; }
+    const size_t P = ctx->segs.size();
+    int rc = ensure_fork_resources(ctx);
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
     for (const Segment &s : ctx->segs)
         if (s.var->prepare) s.var->prepare();   // kernel attributes are set outside the capture
     cudaStream_t origin = ctx->fork_streams[0];
@@ -636,6 +645,8 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
     if (!ctx || trial_steps < 1 || trial_walkers < 1) { set_error("bad arguments"); return TFG_EINVAL; }
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    int rc = ensure_fork_resources(ctx);
+    if (rc) return rc;
     // timing events, released on every return path
     struct Events {
         cudaEvent_t a = nullptr, b = nullptr;
@@ -647,29 +658,35 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
     e = cudaEventCreate(&ev.a);
     if (e == cudaSuccess) e = cudaEventCreate(&ev.b);
     if (e != cudaSuccess) return cuda_fail(e, "autotune events");
-    cudaEvent_t t0 = ev.a, t1 = ev.b;
+    const size_t P = ctx->segs.size();
     int nvar = 0;
     const tfg::WalkVariant *all = tfg::walk_variants(&nvar);
-    for (size_t f = 0; f < ctx->segs.size(); ++f) {
+
+    // the trial walkers (the first min(walkers, trial_walkers) of each population), saved on the host
+    struct Saved { std::vector<char> hdr, sl, be; int64_t nt = 0; size_t per = 0; };
+    std::vector<Saved> saved(P);
+    for (size_t f = 0; f < P; ++f) {
         Segment &s = ctx->segs[f];
-        if (s.n == 0) continue;
-        const int64_t nt = std::min<int64_t>(s.n, trial_walkers);
-        const size_t per = (size_t)s.R * s.nws * (s.word_bits / 8);
-        // save the trial walkers' records and schemes
-        std::vector<char> hdr(sizeof(tfg_walker_info) * nt), sl(per * nt), be(per * nt);
-        e = cudaMemcpy(hdr.data(), ctx->ws + s.off_hdr, hdr.size(), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess) e = cudaMemcpy(sl.data(), ctx->ws + s.off_slots, sl.size(), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess) e = cudaMemcpy(be.data(), ctx->ws + s.off_best, be.size(), cudaMemcpyDeviceToHost);
+        Saved &sv = saved[f];
+        sv.nt = std::min<int64_t>(s.n, trial_walkers);
+        sv.per = (size_t)s.R * s.nws * (s.word_bits / 8);
+        sv.hdr.resize(sizeof(tfg_walker_info) * sv.nt);
+        sv.sl.resize(sv.per * sv.nt);
+        sv.be.resize(sv.per * sv.nt);
+        e = cudaMemcpy(sv.hdr.data(), ctx->ws + s.off_hdr, sv.hdr.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(sv.sl.data(), ctx->ws + s.off_slots, sv.sl.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(sv.be.data(), ctx->ws + s.off_best, sv.be.size(), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "autotune save");
-        tfg::SegDesc d = ctx->desc(s);
-        d.n_walkers = nt;
-        const tfg::WalkVariant *best = s.var;
-        int best_block = s.block;
-        float best_ms = 1e30f;
-        // every mapping (lanes per walker), and for each every compiled block size of its
-        // kernel (walkers per block: compiled into thread-per-walker kernels, whose shared
-        // memory per block depends on it; 128 or 256 threads for the lane-group kernels)
-        static const int lanes[5] = {1, 4, 8, 16, 32};
+    }
+    // candidates of every population: every mapping (lanes per walker) at its smallest
+    // capacity, and for each every walkers-per-block choice (the block sizes compiled for a
+    // thread-per-walker kernel of that capacity, whose shared memory per block depends on it;
+    // 128 or 256 threads for the lane-group kernels)
+    struct Choice { const tfg::WalkVariant *var; int block; };
+    std::vector<std::vector<Choice>> cand(P);
+    static const int lanes[5] = {1, 4, 8, 16, 32};
+    for (size_t f = 0; f < P; ++f) {
+        const Segment &s = ctx->segs[f];
         for (int G : lanes) {
             const tfg::WalkVariant *base = pick_variant(s.fmt.mode, s.word_bits, s.tw, G, s.R, s.fmt);
             if (!base) continue;
@@ -678,30 +695,76 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
                 if (v.mode != base->mode || v.word_bits != base->word_bits || v.tw != base->tw || v.G != base->G ||
                     v.capacity() != base->capacity() || v.fl != base->fl || v.sq != base->sq)
                     continue;
-                static const int free_blocks[2] = {128, 256};
-                for (int k = 0; k < (v.block ? 1 : 2); ++k) {
-                    const int b = v.block ? v.block : free_blocks[k];
-                    const int64_t grid = (nt * v.G + b - 1) / b;
-                    v.launch(d, (int32_t)std::min<int64_t>(trial_steps, 64), (int)grid, b, ctx->stream);   // warm-up
-                    cudaEventRecord(t0, ctx->stream);
-                    v.launch(d, (int32_t)trial_steps, (int)grid, b, ctx->stream);
-                    cudaEventRecord(t1, ctx->stream);
-                    e = cudaEventSynchronize(t1);
-                    if (e != cudaSuccess) return cuda_fail(e, "autotune trial");
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, t0, t1);
-                    if (ms < best_ms) { best_ms = ms; best = &v; best_block = v.block ? 0 : b; }
-                }
+                if (v.block) cand[f].push_back({&v, 0});
+                else { cand[f].push_back({&v, 128}); cand[f].push_back({&v, 256}); }
             }
         }
-        // restore the trial walkers bit for bit
-        e = cudaMemcpy(ctx->ws + s.off_hdr, hdr.data(), hdr.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(ctx->ws + s.off_slots, sl.data(), sl.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(ctx->ws + s.off_best, be.data(), be.size(), cudaMemcpyHostToDevice);
+    }
+    // One timed trial: every population's current choice for `steps` steps on its trial
+    // walkers, launched as tfg_walk launches them (concurrently on one stream per
+    // population for use_graph 2, else one after another): milliseconds, or < 0 on error.
+    cudaStream_t origin = ctx->fork_streams[0];
+    auto trial = [&](int32_t steps) -> float {
+        cudaEventRecord(ev.a, origin);
+        for (size_t f = 0; f < P; ++f) {
+            const Segment &s = ctx->segs[f];
+            if (saved[f].nt == 0) continue;
+            tfg::SegDesc d = ctx->desc(s);
+            d.n_walkers = saved[f].nt;
+            const int b = block_of(ctx, s);
+            const int64_t grid = (saved[f].nt * s.var->G + b - 1) / b;
+            cudaStream_t st = origin;
+            if (ctx->prm.use_graph == 2) {
+                st = ctx->fork_streams[1 + f];
+                cudaStreamWaitEvent(st, ev.a, 0);
+            }
+            s.var->launch(d, steps, (int)grid, b, st);
+            if (ctx->prm.use_graph == 2) {
+                cudaEventRecord(ctx->fork_events[f], st);
+                cudaStreamWaitEvent(origin, ctx->fork_events[f], 0);
+            }
+        }
+        cudaEventRecord(ev.b, origin);
+        if (cudaEventSynchronize(ev.b) != cudaSuccess || cudaGetLastError() != cudaSuccess) return -1.f;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev.a, ev.b);
+        return ms;
+    };
+    // coordinate descent: population by population, every candidate timed with the other
+    // populations at their current choice; a candidate replaces the current choice only
+    // when it is more than 1% faster
+    for (size_t f = 0; f < P; ++f) {
+        Segment &s = ctx->segs[f];
+        if (s.n == 0 || cand[f].empty()) continue;
+        const Choice cur{s.var, s.block};
+        float base_ms = -1.f;
+        if (trial((int32_t)std::min<int64_t>(trial_steps, 64)) < 0.f || (base_ms = trial((int32_t)trial_steps)) < 0.f)
+            return cuda_fail(cudaGetLastError(), "autotune trial");
+        Choice best = cur;
+        float best_ms = base_ms;
+        for (const Choice &c : cand[f]) {
+            if (c.var == cur.var && c.block == cur.block) continue;
+            s.var = c.var;
+            s.block = c.block;
+            float ms = trial((int32_t)std::min<int64_t>(trial_steps, 64));   // warm-up (first launch of a kernel)
+            if (ms >= 0.f) ms = trial((int32_t)trial_steps);
+            if (ms < 0.f) { s.var = cur.var; s.block = cur.block; return cuda_fail(cudaGetLastError(), "autotune trial"); }
+            if (ms < best_ms) { best_ms = ms; best = c; }
+        }
+        if (!(best_ms < 0.99f * base_ms)) best = cur;
+        s.var = best.var;
+        s.block = best.block;
+        if (lanes_out) lanes_out[f] = best.var->G;
+    }
+    // restore the trial walkers bit for bit
+    for (size_t f = 0; f < P; ++f) {
+        Segment &s = ctx->segs[f];
+        Saved &sv = saved[f];
+        if (lanes_out && (s.n == 0 || cand[f].empty())) lanes_out[f] = s.var->G;
+        e = cudaMemcpy(ctx->ws + s.off_hdr, sv.hdr.data(), sv.hdr.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(ctx->ws + s.off_slots, sv.sl.data(), sv.sl.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(ctx->ws + s.off_best, sv.be.data(), sv.be.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e, "autotune restore");
-        s.var = best;
-        s.block = best_block;
-        if (lanes_out) lanes_out[f] = best->G;
     }
     for (tfg_ctx::Graph &g : ctx->graphs) cudaGraphExecDestroy(g.exec);   // variants changed
     ctx->graphs.clear();
