@@ -645,8 +645,6 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
     if (!ctx || trial_steps < 1 || trial_walkers < 1) { set_error("bad arguments"); return TFG_EINVAL; }
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "synchronize");
-    int rc = ensure_fork_resources(ctx);
-    if (rc) return rc;
     // timing events, released on every return path
     struct Events {
         cudaEvent_t a = nullptr, b = nullptr;
@@ -700,31 +698,19 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
             }
         }
     }
-    // One timed trial: every population's current choice for `steps` steps on its trial
-    // walkers, launched as tfg_walk launches them (concurrently on one stream per
-    // population for use_graph 2, else one after another): milliseconds, or < 0 on error.
-    cudaStream_t origin = ctx->fork_streams[0];
+    // One timed trial: `steps` steps of the trial walkers through tfg_walk itself (the
+    // graph rebuilt for the current choices), so a trial is timed in the launch shape the
+    // walk uses: milliseconds, or < 0 on error.  The populations are cut to their trial
+    // walkers meanwhile.
+    std::vector<int64_t> full_n(P);
+    for (size_t f = 0; f < P; ++f) { full_n[f] = ctx->segs[f].n; ctx->segs[f].n = saved[f].nt; }
+    auto restore_n = [&] { for (size_t f = 0; f < P; ++f) ctx->segs[f].n = full_n[f]; };
     auto trial = [&](int32_t steps) -> float {
-        cudaEventRecord(ev.a, origin);
-        for (size_t f = 0; f < P; ++f) {
-            const Segment &s = ctx->segs[f];
-            if (saved[f].nt == 0) continue;
-            tfg::SegDesc d = ctx->desc(s);
-            d.n_walkers = saved[f].nt;
-            const int b = block_of(ctx, s);
-            const int64_t grid = (saved[f].nt * s.var->G + b - 1) / b;
-            cudaStream_t st = origin;
-            if (ctx->prm.use_graph == 2) {
-                st = ctx->fork_streams[1 + f];
-                cudaStreamWaitEvent(st, ev.a, 0);
-            }
-            s.var->launch(d, steps, (int)grid, b, st);
-            if (ctx->prm.use_graph == 2) {
-                cudaEventRecord(ctx->fork_events[f], st);
-                cudaStreamWaitEvent(origin, ctx->fork_events[f], 0);
-            }
-        }
-        cudaEventRecord(ev.b, origin);
+        for (tfg_ctx::Graph &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+        ctx->graphs.clear();
+        cudaEventRecord(ev.a, ctx->stream);
+        if (tfg_walk(ctx, steps) != TFG_OK) return -1.f;
+        cudaEventRecord(ev.b, ctx->stream);
         if (cudaEventSynchronize(ev.b) != cudaSuccess || cudaGetLastError() != cudaSuccess) return -1.f;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev.a, ev.b);
@@ -735,11 +721,13 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
     // when it is more than 1% faster
     for (size_t f = 0; f < P; ++f) {
         Segment &s = ctx->segs[f];
-        if (s.n == 0 || cand[f].empty()) continue;
+        if (full_n[f] == 0 || cand[f].empty()) continue;
         const Choice cur{s.var, s.block};
         float base_ms = -1.f;
-        if (trial((int32_t)std::min<int64_t>(trial_steps, 64)) < 0.f || (base_ms = trial((int32_t)trial_steps)) < 0.f)
+        if (trial((int32_t)std::min<int64_t>(trial_steps, 64)) < 0.f || (base_ms = trial((int32_t)trial_steps)) < 0.f) {
+            restore_n();
             return cuda_fail(cudaGetLastError(), "autotune trial");
+        }
         Choice best = cur;
         float best_ms = base_ms;
         for (const Choice &c : cand[f]) {
@@ -748,7 +736,12 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
             s.block = c.block;
             float ms = trial((int32_t)std::min<int64_t>(trial_steps, 64));   // warm-up (first launch of a kernel)
             if (ms >= 0.f) ms = trial((int32_t)trial_steps);
-            if (ms < 0.f) { s.var = cur.var; s.block = cur.block; return cuda_fail(cudaGetLastError(), "autotune trial"); }
+            if (ms < 0.f) {
+                s.var = cur.var;
+                s.block = cur.block;
+                restore_n();
+                return cuda_fail(cudaGetLastError(), "autotune trial");
+            }
             if (ms < best_ms) { best_ms = ms; best = c; }
         }
         if (!(best_ms < 0.99f * base_ms)) best = cur;
@@ -756,6 +749,7 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
         s.block = best.block;
         if (lanes_out) lanes_out[f] = best.var->G;
     }
+    restore_n();
     // restore the trial walkers bit for bit
     for (size_t f = 0; f < P; ++f) {
         Segment &s = ctx->segs[f];
