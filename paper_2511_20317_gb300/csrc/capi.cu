@@ -698,6 +698,20 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
             }
         }
     }
+    // Put the trial walkers back into their saved state (before every timed trial, so
+    // that every candidate is timed from the same point of the walk: the cost of a step
+    // changes along a trajectory).
+    auto restore_state = [&]() -> cudaError_t {
+        cudaError_t r = cudaSuccess;
+        for (size_t f = 0; f < P && r == cudaSuccess; ++f) {
+            const Segment &s = ctx->segs[f];
+            const Saved &sv = saved[f];
+            r = cudaMemcpy(ctx->ws + s.off_hdr, sv.hdr.data(), sv.hdr.size(), cudaMemcpyHostToDevice);
+            if (r == cudaSuccess) r = cudaMemcpy(ctx->ws + s.off_slots, sv.sl.data(), sv.sl.size(), cudaMemcpyHostToDevice);
+            if (r == cudaSuccess) r = cudaMemcpy(ctx->ws + s.off_best, sv.be.data(), sv.be.size(), cudaMemcpyHostToDevice);
+        }
+        return r;
+    };
     // One timed trial: `steps` steps of the trial walkers through tfg_walk itself (the
     // graph rebuilt for the current choices), so a trial is timed in the launch shape the
     // walk uses: milliseconds, or < 0 on error.  The populations are cut to their trial
@@ -724,7 +738,8 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
         if (full_n[f] == 0 || cand[f].empty()) continue;
         const Choice cur{s.var, s.block};
         float base_ms = -1.f;
-        if (trial((int32_t)std::min<int64_t>(trial_steps, 64)) < 0.f || (base_ms = trial((int32_t)trial_steps)) < 0.f) {
+        if (trial((int32_t)std::min<int64_t>(trial_steps, 64)) < 0.f || restore_state() != cudaSuccess ||
+            (base_ms = trial((int32_t)trial_steps)) < 0.f) {
             restore_n();
             return cuda_fail(cudaGetLastError(), "autotune trial");
         }
@@ -735,6 +750,7 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
             s.var = c.var;
             s.block = c.block;
             float ms = trial((int32_t)std::min<int64_t>(trial_steps, 64));   // warm-up (first launch of a kernel)
+            if (ms >= 0.f && restore_state() != cudaSuccess) ms = -1.f;
             if (ms >= 0.f) ms = trial((int32_t)trial_steps);
             if (ms < 0.f) {
                 s.var = cur.var;
@@ -751,15 +767,10 @@ int tfg_autotune(tfg_ctx *ctx, int64_t trial_steps, int64_t trial_walkers, int32
     }
     restore_n();
     // restore the trial walkers bit for bit
-    for (size_t f = 0; f < P; ++f) {
-        Segment &s = ctx->segs[f];
-        Saved &sv = saved[f];
-        if (lanes_out && (s.n == 0 || cand[f].empty())) lanes_out[f] = s.var->G;
-        e = cudaMemcpy(ctx->ws + s.off_hdr, sv.hdr.data(), sv.hdr.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(ctx->ws + s.off_slots, sv.sl.data(), sv.sl.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(ctx->ws + s.off_best, sv.be.data(), sv.be.size(), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return cuda_fail(e, "autotune restore");
-    }
+    for (size_t f = 0; f < P; ++f)
+        if (lanes_out && (ctx->segs[f].n == 0 || cand[f].empty())) lanes_out[f] = ctx->segs[f].var->G;
+    e = restore_state();
+    if (e != cudaSuccess) return cuda_fail(e, "autotune restore");
     for (tfg_ctx::Graph &g : ctx->graphs) cudaGraphExecDestroy(g.exec);   // variants changed
     ctx->graphs.clear();
     return TFG_OK;
