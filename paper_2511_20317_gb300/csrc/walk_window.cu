@@ -438,7 +438,9 @@ void launch_window_score(const SegDesc &d, const void *params, const uint2 *desc
 template <class Wd, int RMAX>
 static void apply_variant(const SegDesc &d, const uint2 *desc, const int *kwin, const float *score, int policy,
                           uint32_t eps, int32_t *choices, const WindowLog &log, cudaStream_t st) {
-    constexpr int BT = 128;
+    // walkers per block as for the walk kernels: at 64-bit capacities 64 and 72 a 64-thread
+    // block's slots (capacity x 65 x 16 bytes) let three blocks share an SM instead of one
+    constexpr int BT = (sizeof(Wd) == 8 && (RMAX == 64 || RMAX == 72)) ? 64 : 128;
     constexpr size_t smem = solo_smem_bytes<TFG_MODE_ZT, Wd, RMAX, BT>();
     static bool attr = [] {
         cudaFuncSetAttribute(dev::window_apply_kernel<Wd, RMAX, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
