@@ -42,9 +42,10 @@ C_FLIP = {0: 18, 1: 2}
 C_PHILOX = 100
 
 
-def algorithmic_ops(mode, steps, accepted, rejected, mean_r, word_mult=1):
+def algorithmic_ops(mode, steps, accepted, rejected, mean_r, word_mult=1, philox=True):
     cs = C_SEARCH[mode] * (mean_r - 1)
-    return word_mult * (steps * (cs + C_PHILOX) + (accepted + rejected) * C_FLIP[mode] + accepted * 2 * cs)
+    return word_mult * (steps * (cs + (C_PHILOX if philox else 0)) + (accepted + rejected) * C_FLIP[mode] +
+                        accepted * 2 * cs)
 
 
 def kernel_hash() -> str:
@@ -257,7 +258,7 @@ def run_ours(args):
     steps_per_s = total_steps / t_max
 
     # roofline of the walk kernel: algorithmic integer ops per launch / launch time
-    ops = 0.0
+    ops, ops_nophilox = 0.0, 0.0
     per_mode = {}
     for f, (fmt, mode, _, nw) in enumerate(pops):
         a0, a1 = st0_f[f], W.stats(f)[0]
@@ -266,6 +267,7 @@ def run_ours(args):
         steps_f = a1["steps"] - a0["steps"]
         acc, rej = a1["accepted"] - a0["accepted"], a1["rejected"] - a0["rejected"]
         ops += algorithmic_ops(mode, steps_f, acc, rej, mean_r)
+        ops_nophilox += algorithmic_ops(mode, steps_f, acc, rej, mean_r, philox=False)
         per_mode[f"{'ZT' if mode == 0 else 'Z2'} {fmt[0]}x{fmt[1]}x{fmt[2]}"] = {
             "lowest_rank": a1["min_best_r"], "mean_live_rank": round(mean_r, 2),
             "rank_hist": {int(k): int(v) for k, v in enumerate(W.stats(f)[1]) if v},
@@ -338,6 +340,7 @@ def run_ours(args):
                      "collected_best_ranks": best_ranks},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
+                     "frac_excluding_philox": ops_nophilox / walk_s / 1e12 / alu_peak,
                      "kernel": "walk kernels of the step (" + "; ".join(p["mapping"] for p in per_mode.values()) + ")",
                      "walk_ms_per_step": sum(walk_ms) / len(walk_ms)},
         "e2e": {"value": e2e_val, "unit": "flips/s", "h2d_bytes_per_step": h2d,
