@@ -43,8 +43,9 @@ def assert_parity(W, ref, n, label):
         assert np.array_equal(best[w, :br], ref.best[w, :br]), f"{label} walker {w} best"
 
 
+# window capacities of the apply kernel: 12 (32-bit words), 32, 64, 72 and 88 (64-bit words)
 CASES = [((2, 2, 2), 300, 3000, 200), ((3, 3, 3), 160, 1500, 300), ((3, 4, 5), 70, 400, 100),
-         ((4, 4, 4), 70, 400, 100)]
+         ((4, 4, 4), 70, 400, 100), ((4, 4, 5), 40, 300, 100)]
 
 
 @pytest.mark.parametrize("fmt,nw,steps,L", CASES)
