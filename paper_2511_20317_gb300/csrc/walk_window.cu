@@ -95,33 +95,11 @@ __device__ __forceinline__ void cand_features_bf16(const PTerm<Wd, 1, true> &a, 
     for (int k = 0; k < kFeat / 2; ++k) h[k] = mlp::pack_bf16x2(f[2 * k], f[2 * k + 1]);
 }
 
-// 32-bit signature of a factor (its +1 and -1 coefficient masks): equal factors
-// have equal signatures; a signature match is confirmed on the words.
-__device__ __forceinline__ uint32_t factor_sig(uint64_t p, uint64_t n) {
-    const uint64_t x = (p * 0x9E3779B97F4A7C15ull) ^ ((n + 0x632BE59BD9B4E019ull) * 0xC2B2AE3D27D4EB4Full);
-    return (uint32_t)(x >> 32) ^ (uint32_t)x;
-}
-
-// Signatures of a term: u, v, w up to sign (w with its first non-zero made +1),
-// and w's sign (1 when its first non-zero coefficient is -1).
-template <class Wd>
-__device__ __forceinline__ uint4 term_sigs(const PTerm<Wd, 1, true> &t, const Masks<Wd, 1> &mk) {
-    const uint64_t p = (uint64_t)t.p[0], n = (uint64_t)t.n[0];
-    const uint64_t mu = (uint64_t)mk.m[0][0], mv = (uint64_t)mk.m[1][0], mw = (uint64_t)mk.m[2][0];
-    uint64_t pw = p & mw, nw = n & mw;
-    const uint64_t dw = pw | nw;
-    const bool neg = (nw & dw & (0ull - dw)) != 0ull;
-    if (neg) { const uint64_t t2 = pw; pw = nw; nw = t2; }
-    return make_uint4(factor_sig(p & mu, n & mu), factor_sig(p & mv, n & mv), factor_sig(pw, nw), neg ? 1u : 0u);
-}
-
 // One warp per walker.  Phase 1: eight terms i0 + g (g = lane / 4, then the
 // next eight while the window has room); the four lanes of a group scan
-// consecutive quarters of the slots for the term's try_flip candidates --
-// comparing the slots' factor signatures (computed once per step) and
-// confirming every signature match on the words, so the candidates are exactly
-// those of the word comparison -- and every candidate's descriptor goes to its
-// window position in shared memory (order: term, then factor, then slot, then rho).  Phase 2: the lanes write
+// consecutive quarters of the slots for the term's try_flip candidates, and
+// every candidate's descriptor goes to its window position in shared memory
+// (order: term, then factor, then slot, then rho).  Phase 2: the lanes write
 // the window rows l, l+32, ... (descriptor and info words), and, when `feat`
 // is given, their feature rows (coalesced 64-byte rows; rows past the window
 // are zero).
@@ -129,7 +107,6 @@ template <class Wd>
 __global__ void __launch_bounds__(128) window_kernel(const SegDesc d, __nv_bfloat16 *__restrict__ feat,
                                                      uint2 *__restrict__ desc, int *__restrict__ kwin) {
     __shared__ __align__(16) Wd sp[4][kWinMaxSlots], sn[4][kWinMaxSlots];
-    __shared__ __align__(16) uint4 ssig[4][kWinMaxSlots];
     __shared__ uint32_t sdesc[4][kWin], sinfo[4][kWin];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * 4 + warp;
@@ -144,10 +121,8 @@ __global__ void __launch_bounds__(128) window_kernel(const SegDesc d, __nv_bfloa
     const int i0 = (int)__umulhi(x.x, (uint32_t)r);
     const Wd *src = reinterpret_cast<const Wd *>(d.slots) + (size_t)w * d.R * 2;
     for (int k = lane; k < r; k += 32) {
-        T t;
-        t.p[0] = sp[warp][k] = src[(size_t)k * 2];
-        t.n[0] = sn[warp][k] = src[(size_t)k * 2 + 1];
-        ssig[warp][k] = term_sigs<Wd>(t, mk);
+        sp[warp][k] = src[(size_t)k * 2];
+        sn[warp][k] = src[(size_t)k * 2 + 1];
     }
     __syncwarp();
     // ---- phase 1: candidate descriptors in window order
@@ -162,13 +137,11 @@ __global__ void __launch_bounds__(128) window_kernel(const SegDesc d, __nv_bfloa
         T ti;
         ti.p[0] = sp[warp][i];
         ti.n[0] = sn[warp][i];
-        const uint4 si = ssig[warp][i];
         // bit (j - jb): slot j of this lane's quarter is a candidate of factor u / v / w (w negated)
         uint32_t bu = 0, bv = 0, bw = 0, bn = 0;
         if (has) {
             for (int j = jb; j < je; ++j) {
-                const uint4 sj = ssig[warp][j];
-                if (j == i || (sj.x != si.x && sj.y != si.y && sj.z != si.z)) continue;
+                if (j == i) continue;
                 T c;
                 c.p[0] = sp[warp][j];
                 c.n[0] = sn[warp][j];
@@ -373,9 +346,7 @@ __global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const
     int action = kNoCand, X = 0, j = 0, rho = 0, sneg = 0, c = -1;
     int i = (int)__umulhi(x.x, (uint32_t)wk.r);
     bool need_check = false;
-    T li, lj;                  // logging: the chosen candidate's two terms before the flip
-    uint2 ldci = make_uint2(0u, 0u);
-    const int r0 = wk.r, best0 = wk.best_r;
+    uint32_t lf[kFeat / 2];   // logged features of the chosen candidate (state before the flip)
     T ti2, tj2;
     ti2.p[0] = tj2.p[0] = 0;
     ti2.n[0] = tj2.n[0] = 0;
@@ -397,11 +368,7 @@ __global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const
         sneg = (int)((dc >> 22) & 1u);
         rho = (int)((dc >> 23) & 1u);
         const T ti = wk.ld(i);
-        if (log.d_entries) {
-            li = ti;
-            lj = wk.ld(j);
-            ldci = dci;
-        }
+        if (log.d_entries) cand_features_bf16<Wd>(ti, wk.ld(j), wk.mk, dc, dci.y, wk.r, wk.best_r, d.m, d.n, d.p, lf);
         wk.apply_candidate(ti, i, X, j, sneg, rho, action, need_check, ti2, tj2);
     } else {
         wk.c_noc += 1;
@@ -419,8 +386,6 @@ __global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const
             const unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(log.d_count), 1ull);
             if (slot < (unsigned long long)log.capacity) {
                 WindowLogEntry *e = reinterpret_cast<WindowLogEntry *>(log.d_entries) + slot;
-                uint32_t lf[kFeat / 2];   // the chosen candidate's features, on the state before the flip
-                cand_features_bf16<Wd>(li, lj, wk.mk, ldci.x, ldci.y, r0, best0, d.m, d.n, d.p, lf);
 #pragma unroll
                 for (int k = 0; k < kFeat / 8; ++k)
                     reinterpret_cast<uint4 *>(e->feat)[k] = make_uint4(lf[4 * k], lf[4 * k + 1], lf[4 * k + 2], lf[4 * k + 3]);
