@@ -379,7 +379,8 @@ def run_ours(args):
 
 def learned_ab(args):
     """The learned proposal against uniform choice over the same candidate
-    windows (BASELINE config 5): the network is trained on the device from the
+    windows (the learned-proposal workload: (4,4,4) and (3,4,5), 262144 walkers,
+    equal step budgets): the network is trained on the device from the
     logged window-uniform walks of the uniform workloads' formats (seeds 100..),
     then both arms run from the naive (4,4,4) and (3,4,5) schemes with 262144
     walkers, plateau 5e4, evaluation seeds 1000..1004: the learned arm for

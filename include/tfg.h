@@ -366,7 +366,7 @@ int tfg_mapping(tfg_ctx *ctx, int32_t f, int32_t *lanes, int32_t *slots_per_lane
 /* Release the context (host memory only; the workspace stays the caller's). */
 void tfg_destroy(tfg_ctx *ctx);
 
-/* ---- learned flip proposal (BASELINE configs[4]; not in the paper) -------- */
+/* ---- learned flip proposal (not in the paper) ------------------------------ */
 
 /* Scoring MLP 32 -> 128 -> 128 -> 1 with ReLU, BF16 weights and inputs, FP32
  * accumulation, run on the tensor cores (tcgen05).  Parameter blob layout
