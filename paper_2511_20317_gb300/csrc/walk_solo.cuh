@@ -116,13 +116,18 @@ struct SlotBits {
 // (Section 3.6) touch one word and a flip rewrites the slices of one factor.
 // SQ: the three factors have exactly FL coefficients each (square formats
 // (k,k,k) with k*k = FL), so factor offsets and masks are compile-time constants.
-template <int MODE, class Wd, int RMAX, int BT, int FL = 0, bool SQ = false>
+// GM: the slots stay in the walker's device-memory array (slot k at sm[k * NWS],
+// sm the walker's own slots) instead of shared-memory rows -- for kernels that run
+// one step per launch, where staging every slot costs more than it saves; a load
+// past the walker's R slots (the unrolled scans run to RMAX) gives an empty term.
+template <int MODE, class Wd, int RMAX, int BT, int FL = 0, bool SQ = false, bool GM = false>
 struct SoloWalker {
     static constexpr bool ZT = (MODE == TFG_MODE_ZT);
     static constexpr int NWS = ZT ? 2 : 1;   // words per slot (TW = 1)
     static constexpr bool SL = FL > 0;
     static_assert(!SL || (RMAX <= 32 && sizeof(Wd) == 4), "slices hold 32 slots of 32-bit packed terms");
     static_assert(!SQ || (SL && 3 * FL <= 32), "square factors: three of FL coefficients in one 32-bit word");
+    static_assert(!GM || !SL, "device-memory slots: no bit slices");
     static constexpr int NSL = 3 * FL;       // slices per sign
     // Z_2: the slices in registers; Z_T: (P, N) pairs in shared memory [slice][thread],
     // then the w sign word (row NSL, .x)
@@ -142,14 +147,14 @@ struct SoloWalker {
     // Shared-memory rows hold one slot of every thread of the block; a row is
     // padded by one element so that walking one thread's column across the
     // lanes of a warp (cooperative filter and snapshot) spreads over the banks.
-    static constexpr int RS = (BT + 1) * NWS;   // words per row
+    static constexpr int RS = GM ? NWS : (BT + 1) * NWS;   // words per row (per slot with GM)
     // walkers per round of the cooperative reduction filter (interleaved scans
     // on small capacities)
 #ifndef TFG_SOLO_ROUND_WALKERS
 #define TFG_SOLO_ROUND_WALKERS 2
 #endif
     static constexpr int kRoundWalkers = RMAX <= 32 ? TFG_SOLO_ROUND_WALKERS : 1;
-    Wd *sm;      // this thread's column: slot k at sm[k * RS]
+    Wd *sm;      // this thread's column: slot k at sm[k * RS] (GM: the walker's slots in device memory)
     M mk;
     int r, best_r, R;
     int64_t t, plateau, best_t;
@@ -169,9 +174,15 @@ struct SoloWalker {
         else return __popc(x);
     }
 
-    __device__ __forceinline__ static T ld_from(const Wd *col, int k) {
+    __device__ __forceinline__ T ld_from(const Wd *col, int k) const {
         const Wd *a = col + (size_t)k * RS;
         T v;
+        if constexpr (GM) {
+            if (k >= R) {
+                v.p[0] = v.n[0] = Wd(0);
+                return v;
+            }
+        }
         if constexpr (ZT) {
             if constexpr (sizeof(Wd) == 4) {
                 const uint2 q = *reinterpret_cast<const uint2 *>(a);
@@ -190,6 +201,12 @@ struct SoloWalker {
         const Wd *a = sm + (size_t)k * RS;
 
         T v;
+        if constexpr (GM) {
+            if (k >= R) {
+                v.p[0] = v.n[0] = Wd(0);
+                return v;
+            }
+        }
         if constexpr (ZT) {
             if constexpr (sizeof(Wd) == 4) {
                 const uint2 q = *reinterpret_cast<const uint2 *>(a);
@@ -548,6 +565,7 @@ struct SoloWalker {
         }
         unsigned pend = __ballot_sync(wmask, need);
         if (__popc(pend) * 4 > RMAX * 3) return need && pair_hit2(ti2, i, tj2, j);
+        if constexpr (GM) __syncwarp(wmask);   // other lanes' device-memory slot writes visible
         bool mine = false;
         const int packed = i | (j << 10) | (r << 20);
         if constexpr (kRoundWalkers > 1) {
@@ -564,11 +582,13 @@ struct SoloWalker {
                 T A[WR], B[WR];
                 int pk[WR];
                 bool h[WR];
+                const Wd *colq[WR];
 #pragma unroll
                 for (int q = 0; q < WR; ++q) {
                     A[q] = shfl_term(wmask, ti2, a[q]);
                     B[q] = shfl_term(wmask, tj2, a[q]);
                     pk[q] = __shfl_sync(wmask, packed, a[q]);
+                    colq[q] = col_of(wmask, a[q], lane);
                     h[q] = false;
                 }
                 if (nl == 32) {
@@ -576,13 +596,13 @@ struct SoloWalker {
                     for (int kk = 0; kk < (RMAX + 31) / 32; ++kk) {
                         const int k = lane + 32 * kk;
 #pragma unroll
-                        for (int q = 0; q < WR; ++q) h[q] |= slot_shares_pair(sm + (a[q] - lane) * NWS, k, pk[q], A[q], B[q]);
+                        for (int q = 0; q < WR; ++q) h[q] |= slot_shares_pair(colq[q], k, pk[q], A[q], B[q]);
                     }
                 } else {
 #pragma unroll 1
                     for (int k = lane; k < RMAX; k += nl) {
 #pragma unroll
-                        for (int q = 0; q < WR; ++q) h[q] |= slot_shares_pair(sm + (a[q] - lane) * NWS, k, pk[q], A[q], B[q]);
+                        for (int q = 0; q < WR; ++q) h[q] |= slot_shares_pair(colq[q], k, pk[q], A[q], B[q]);
                     }
                 }
 #pragma unroll
@@ -599,7 +619,7 @@ struct SoloWalker {
                 pend &= pend - 1;
                 const T A = shfl_term(wmask, ti2, a), B = shfl_term(wmask, tj2, a);
                 const int pa = __shfl_sync(wmask, packed, a);
-                const Wd *col = sm + (a - lane) * NWS;   // walker a's column
+                const Wd *col = col_of(wmask, a, lane);   // walker a's slots
                 const int ra = pa >> 20;
                 const int ia = pa & 1023, ja = (pa >> 10) & 1023;
                 bool hit = false;
@@ -620,6 +640,14 @@ struct SoloWalker {
             }
         }
         return mine;
+    }
+    // Slots of walker a (a lane of this warp): its column of the shared-memory rows,
+    // or (GM) its device-memory slots, whose address lane a holds.  Warp-converged.
+    __device__ __forceinline__ const Wd *col_of(unsigned wmask, int a, int lane) const {
+        if constexpr (GM)
+            return reinterpret_cast<const Wd *>(__shfl_sync(wmask, reinterpret_cast<unsigned long long>(sm), a));
+        else
+            return sm + (a - lane) * NWS;
     }
     __device__ __forceinline__ static T shfl_term(unsigned wmask, const T &v, int src) {
         T o;
@@ -647,13 +675,14 @@ struct SoloWalker {
     // requesting walker's column to its best buffer (coalesced stores).
     __device__ __forceinline__ void coop_snapshot(unsigned wmask, int lane, int nl, bool want, Wd *bestp) const {
         unsigned pend = __ballot_sync(wmask, want);
+        if constexpr (GM) __syncwarp(wmask);
 #pragma unroll 1
         while (pend) {
             const int a = __ffs(pend) - 1;
             pend &= pend - 1;
             const int ra = __shfl_sync(wmask, r, a);
             Wd *dst = reinterpret_cast<Wd *>(__shfl_sync(wmask, reinterpret_cast<unsigned long long>(bestp), a));
-            const Wd *col = sm + (a - lane) * NWS;
+            const Wd *col = col_of(wmask, a, lane);
 #pragma unroll 1
             for (int k = lane; k < ra; k += nl) {
                 const T v = ld_from(col, k);
@@ -763,6 +792,16 @@ struct SoloWalker {
         }
         c_acc = c_rej = c_noc = c_drp = c_mrg = c_pls = c_red = 0;
         qlen = 0; q0 = q1 = q2 = 0;
+        if constexpr (!GM) load_slots(d, w);
+        nnz = 0;
+        if (policy == 2) {
+#pragma unroll
+            for (int k = 0; k < RMAX; ++k)
+                if (k < r) nnz += nnz_of(ld(k));
+        }
+    }
+
+    __device__ __forceinline__ void load_slots(const SegDesc &d, int64_t w) {
         const Wd *src = reinterpret_cast<const Wd *>(d.slots) + (size_t)w * R * NWS;
         auto load_slot = [&](int k) {
             T v;
@@ -778,22 +817,18 @@ struct SoloWalker {
 #pragma unroll
             for (int k = 0; k < RMAX; ++k) load_slot(k);
         }
-        nnz = 0;
-        if (policy == 2) {
-#pragma unroll
-            for (int k = 0; k < RMAX; ++k)
-                if (k < r) nnz += nnz_of(ld(k));
-        }
     }
 
     __device__ __forceinline__ void store(const SegDesc &d, int64_t w) {
-        Wd *dst = reinterpret_cast<Wd *>(d.slots) + (size_t)w * R * NWS;
+        if constexpr (!GM) {   // GM: the slots were written in place
+            Wd *dst = reinterpret_cast<Wd *>(d.slots) + (size_t)w * R * NWS;
 #pragma unroll
-        for (int k = 0; k < RMAX; ++k) {
-            if (k < R) {
-                const T v = ld(k);
-                dst[(size_t)k * NWS] = v.p[0];
-                if constexpr (ZT) dst[(size_t)k * NWS + 1] = v.n[0];
+            for (int k = 0; k < RMAX; ++k) {
+                if (k < R) {
+                    const T v = ld(k);
+                    dst[(size_t)k * NWS] = v.p[0];
+                    if constexpr (ZT) dst[(size_t)k * NWS + 1] = v.n[0];
+                }
             }
         }
         tfg_walker_info *H = d.hdr + w;

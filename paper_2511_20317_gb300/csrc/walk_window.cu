@@ -9,9 +9,10 @@
 //      whose producer computes each row's 32 features from the descriptor and
 //      the walker's slots straight into the shared-memory A tile, so no
 //      feature row goes through device memory; it writes one score per row;
-//   3. window_apply_kernel (one thread per walker): policy choice (uniform
-//      over the window via x1, or epsilon-greedy argmax of the scores with
-//      epsilon decided by x3), then the flip, reductions and bookkeeping of
+//   3. window_apply_kernel (one thread per walker, working on its slots in
+//      place in device memory): policy choice (uniform over the window via
+//      x1, or epsilon-greedy argmax of the scores with epsilon decided by
+//      x3), then the flip, reductions and bookkeeping of
 //      the uniform walker; optional logging of the chosen candidate's features
 //      (computed from the state before the flip) with the label "the step
 //      lowered the rank" for training.
@@ -327,13 +328,15 @@ __global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const
                                                           const float *__restrict__ score, int policy,
                                                           uint32_t eps_thresh, int32_t *__restrict__ choices,
                                                           WindowLog log) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t w = (int64_t)blockIdx.x * BT + threadIdx.x;
     if (w >= d.n_walkers) return;
-    using SW = SoloWalker<TFG_MODE_ZT, Wd, RMAX, BT>;
+    // one step per launch: the walker works on its slots in place in device memory
+    // (staging them through shared memory cost more than the step: 255 registers,
+    // 3.5 warps per SM)
+    using SW = SoloWalker<TFG_MODE_ZT, Wd, RMAX, BT, 0, false, true>;
     using T = typename SW::T;
     SW wk;
-    wk.sm = reinterpret_cast<Wd *>(smem_raw) + (size_t)threadIdx.x * 2;
+    wk.sm = reinterpret_cast<Wd *>(d.slots) + (size_t)w * d.R * 2;
     wk.load(d, w);
     Wd *bestp = reinterpret_cast<Wd *>(d.best) + (size_t)w * d.R * 2;
     const unsigned wmask = __activemask();
@@ -438,19 +441,10 @@ void launch_window_score(const SegDesc &d, const void *params, const uint2 *desc
 template <class Wd, int RMAX>
 static void apply_variant(const SegDesc &d, const uint2 *desc, const int *kwin, const float *score, int policy,
                           uint32_t eps, int32_t *choices, const WindowLog &log, cudaStream_t st) {
-    // walkers per block as for the walk kernels: at 64-bit capacities 64 and 72 a 64-thread
-    // block's slots (capacity x 65 x 16 bytes) let three blocks share an SM instead of one
-    constexpr int BT = (sizeof(Wd) == 8 && (RMAX == 64 || RMAX == 72)) ? 64 : 128;
-    constexpr size_t smem = solo_smem_bytes<TFG_MODE_ZT, Wd, RMAX, BT>();
-    static bool attr = [] {
-        cudaFuncSetAttribute(dev::window_apply_kernel<Wd, RMAX, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        return true;
-    }();
-    (void)attr;
+    constexpr int BT = 128;
     const int64_t blocks = (d.n_walkers + BT - 1) / BT;
-    dev::window_apply_kernel<Wd, RMAX, BT><<<(unsigned)blocks, BT, smem, st>>>(d, desc, kwin, score, policy, eps,
-                                                                              choices, log);
+    dev::window_apply_kernel<Wd, RMAX, BT><<<(unsigned)blocks, BT, 0, st>>>(d, desc, kwin, score, policy, eps,
+                                                                           choices, log);
 }
 
 // Capacity of the apply kernel chosen for a population (0: not supported).
