@@ -438,7 +438,18 @@ int tfg_mlp_train_step(void *d_state, void *d_params, const uint16_t *d_x, const
  * candidate).  log (optional): chosen features with label 1 when the step
  * lowered the rank (always kept) or 0 (kept when a Philox draw of sub-stream
  * 256 is below neg_thresh), appended at d_count (device int64, caller-zeroed)
- * up to capacity entries. */
+ * up to capacity entries.  With horizon H > 1 each walker keeps a ring of the
+ * features of its last H chosen candidates; a step that lowers the rank
+ * appends (label 1, each with its own step) every ring entry chosen at steps
+ * t - H + 1 .. t since the walker's previous such step, in step order, and
+ * empties the ring; label-0 entries are this step's alone, as for H = 1 (a
+ * step logged with label 0 can later be logged again with label 1).  The
+ * ring persists across calls in caller memory: d_ring (device bf16
+ * [walkers][H][32], 16-byte aligned) and d_ring_step (device uint32
+ * [walkers][H], the step of each entry, 0xFFFFFFFF = empty, which the caller
+ * writes into every word before the first call); walkers = all of the
+ * context's, in its walker order.  The window of steps is taken on the low
+ * 32 bits of the step counter. */
 typedef struct {
     uint16_t feat[32];  /* bf16 features of the chosen candidate */
     float label;        /* 1: the step lowered the rank */
@@ -450,6 +461,9 @@ typedef struct {
     int64_t capacity;
     int64_t *d_count;
     uint32_t neg_thresh;
+    int32_t horizon;        /* H: 0 or 1 = this step's features only; 2..64 = the ring */
+    uint16_t *d_ring;       /* H > 1 */
+    uint32_t *d_ring_step;  /* H > 1 */
 } tfg_log_spec;
 
 int tfg_window_scratch_bytes(tfg_ctx *ctx, size_t *bytes);

@@ -260,7 +260,9 @@ class Walkers:
         choices [n_walkers, steps] (window index per step, -1 = no candidate).
         With log_neg_thresh given, the training-log records of these steps are
         kept in self.log_label [n_walkers, steps] (-1: no record, else the label)
-        and self.log_feat [n_walkers, steps, 32] (uint8 features)."""
+        and self.log_feat [n_walkers, steps, 32] (uint8 features of the chosen
+        candidate of every step that had one, recorded or not; self.log_chosen
+        marks those steps: feature 31 is one on every candidate)."""
         if threads is None:
             threads = len(os.sched_getaffinity(0))
         m, n, p = self.fmt
@@ -279,6 +281,7 @@ class Walkers:
                               _ptr(feat) if feat is not None else None,
                               int(log_neg_thresh or 0))
         self.log_label, self.log_feat = lab, feat
+        self.log_chosen = None if feat is None else feat[:, :, 31] == 1
         return self
 
     def scheme(self, w: int) -> np.ndarray:
@@ -286,6 +289,36 @@ class Walkers:
 
     def best_scheme(self, w: int) -> np.ndarray:
         return self.best[w, : self.info["best_r"][w]].copy()
+
+
+def horizon_log(label, feat, chosen, walker_ids, H):
+    """Training log with an H-step horizon, from one window walk's per-step
+    records (label [walkers, steps]: 1 when the step lowered the rank, 0 for a
+    sampled label-0 step, -1 otherwise; feat [walkers, steps, 32]; chosen
+    [walkers, steps]: the step had a candidate).  Per walker, in step order: a
+    step t that lowered the rank contributes label-1 entries for the chosen
+    steps s with t - H < s <= t and s after the walker's previous rank-lowering
+    step; a sampled label-0 step contributes itself with label 0.  H = 1 is the
+    plain log.  Returns (walker_id, step, label, feat) sorted by walker id,
+    step, label."""
+    out_w, out_s, out_l, out_f = [], [], [], []
+    nw, steps = label.shape
+    for w in range(nw):
+        last = -1
+        for t in range(steps):
+            if label[w, t] == 1:
+                for s in range(max(t - H + 1, last + 1), t + 1):
+                    if chosen[w, s]:
+                        out_w.append(walker_ids[w]); out_s.append(s); out_l.append(1.0); out_f.append(feat[w, s])
+                last = t
+            elif label[w, t] == 0:
+                out_w.append(walker_ids[w]); out_s.append(t); out_l.append(0.0); out_f.append(feat[w, t])
+    wid = np.array(out_w, np.int64)
+    st = np.array(out_s, np.int64)
+    lab = np.array(out_l, np.float32)
+    f = np.array(out_f, np.uint8).reshape(-1, 32)
+    o = np.lexsort((lab, st, wid))
+    return wid[o], st[o], lab[o], f[o]
 
 
 # ---------------------------------------------------------------------------------------------

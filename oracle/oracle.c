@@ -760,7 +760,8 @@ static void window_features(const walker *wk, const wcand_t *c, float *f)
  * label 0; label-0 records are kept only when the first word of Philox
  * sub-stream 256 of the step, (t_lo, t_hi, walker, 256), lies below
  * neg_thresh.  *label_out = -1 when the step keeps no record (no candidate,
- * or an unsampled label-0 step). */
+ * or an unsampled label-0 step).  The features are stored for every step
+ * with a candidate, recorded or not (the horizon log draws on them). */
 typedef struct {
     int8_t *label;     /* [steps] per walker: -1, 0 or 1 */
     uint8_t *feat;     /* [steps][32] per walker */
@@ -810,7 +811,7 @@ static void walk_step_window(walker *wk, wcand_t *wbuf, cand_t *tmp, int W, int 
         }
         lg->label[slot] = (int8_t)label;
         for (int k = 0; k < ORC_FEATURES; ++k)
-            lg->feat[(size_t)slot * ORC_FEATURES + k] = label >= 0 ? (uint8_t)f[k] : 0;
+            lg->feat[(size_t)slot * ORC_FEATURES + k] = K > 0 ? (uint8_t)f[k] : 0;
     }
 }
 

@@ -1217,6 +1217,16 @@ static int window_steps(tfg_ctx *ctx, int64_t steps, int32_t policy, const void 
     auto *kwin = reinterpret_cast<int *>(base + (size_t)N * W * 12);
     tfg_log_spec lg{};
     if (log) lg = *log;
+    if (lg.d_entries && lg.horizon > 1) {
+        if (lg.horizon > 64 || !lg.d_ring || !lg.d_ring_step || (uintptr_t)lg.d_ring % 16 ||
+            (uintptr_t)lg.d_ring_step % 4) {
+            set_error("log horizon: 2..64 with a 16-byte aligned ring and its step words");
+            return TFG_EINVAL;
+        }
+    } else {
+        lg.horizon = 1;
+    }
+    const int H = lg.horizon;
     int32_t *status = &ctx->aux()->status;
     for (int64_t st = 0; st < steps; ++st) {
         for (const Segment &s : ctx->segs)
@@ -1227,8 +1237,13 @@ static int window_steps(tfg_ctx *ctx, int64_t steps, int32_t policy, const void 
                                          score + (size_t)s.first * W, status, ctx->stream);
         for (const Segment &s : ctx->segs) {
             int32_t *ch = d_choices ? d_choices + (size_t)st * N + s.first : nullptr;
+            tfg_log_spec ls = lg;   // the segment's walkers' rings
+            if (H > 1) {
+                ls.d_ring = lg.d_ring + (size_t)s.first * H * 32;
+                ls.d_ring_step = lg.d_ring_step + (size_t)s.first * H;
+            }
             tfg::launch_window_apply(ctx->desc(s), desc + (size_t)s.first * W, kwin + s.first,
-                                     score + (size_t)s.first * W, policy, eps_thresh, ch, lg, ctx->stream);
+                                     score + (size_t)s.first * W, policy, eps_thresh, ch, ls, ctx->stream);
         }
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "window step launch");

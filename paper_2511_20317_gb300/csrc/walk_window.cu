@@ -321,6 +321,20 @@ __global__ void __launch_bounds__(kScoreWG * 128, 1)
     mlp::run_tiles<kScoreWG>(params, pr, d.n_walkers * 2, err, first_limit, smem, mbar, &tslot, &tflag);
 }
 
+// Log entry `slot` := (features, label, walker id, step).
+__device__ __forceinline__ void write_log_entry(const WindowLog &log, unsigned long long slot,
+                                                const uint32_t (&f)[kFeat / 2], float label, uint32_t wid,
+                                                uint32_t step) {
+    WindowLogEntry *e = reinterpret_cast<WindowLogEntry *>(log.d_entries) + slot;
+#pragma unroll
+    for (int k = 0; k < kFeat / 8; ++k)
+        reinterpret_cast<uint4 *>(e->feat)[k] = make_uint4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+    e->label = label;
+    e->walker_id = wid;
+    e->step = step;
+    e->pad = 0;
+}
+
 // One window-mode step per thread (walker), on the solo walker's state machine.
 template <class Wd, int RMAX, int BT>
 __global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const uint2 *__restrict__ desc,
@@ -380,23 +394,51 @@ __global__ void __launch_bounds__(BT) window_apply_kernel(const SegDesc d, const
     if (choices) choices[w] = c;
     if (log.d_entries && c >= 0) {
         const bool positive = wk.c_red > 0;   // the flip's reductions lowered the rank this step
-        bool keep = positive;
+        const int H = log.horizon > 1 ? log.horizon : 1;
+        bool keep0 = false;
         if (!positive && log.neg_thresh) {
             const U4 y = philox10((uint32_t)t_step, (uint32_t)(t_step >> 32), wk.wid, 0x100u, wk.key0, wk.key1);
-            keep = y.x < log.neg_thresh;
+            keep0 = y.x < log.neg_thresh;
         }
+        if (H > 1) {
+            // this step's features into ring slot t mod H; a rank-lowering step appends the
+            // entries of steps t-H+1 .. t still in the ring (step order) and empties it
+            uint4 *ring = reinterpret_cast<uint4 *>(log.d_ring) + (size_t)w * H * (kFeat / 8);
+            uint32_t *rs = log.d_ring_step + (size_t)w * H;
+            const int kt = (int)(t_step % H);
+#pragma unroll
+            for (int k = 0; k < kFeat / 8; ++k)
+                ring[kt * (kFeat / 8) + k] = make_uint4(lf[4 * k], lf[4 * k + 1], lf[4 * k + 2], lf[4 * k + 3]);
+            rs[kt] = (uint32_t)t_step;
+            if (positive) {
+                int n = 0;
+                for (int dd = 0; dd < H && dd <= t_step; ++dd)
+                    n += rs[(int)((t_step - dd) % H)] == (uint32_t)(t_step - dd);
+                unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(log.d_count),
+                                                    (unsigned long long)n);
+                for (int dd = H - 1; dd >= 0; --dd) {
+                    if (dd > t_step) continue;
+                    const int k = (int)((t_step - dd) % H);
+                    if (rs[k] != (uint32_t)(t_step - dd)) continue;
+                    if (slot < (unsigned long long)log.capacity) {
+                        uint32_t e16[kFeat / 2];
+#pragma unroll
+                        for (int q = 0; q < kFeat / 8; ++q) {
+                            const uint4 v = ring[k * (kFeat / 8) + q];
+                            e16[4 * q] = v.x; e16[4 * q + 1] = v.y; e16[4 * q + 2] = v.z; e16[4 * q + 3] = v.w;
+                        }
+                        write_log_entry(log, slot, e16, 1.f, wk.wid, (uint32_t)(t_step - dd));
+                    }
+                    ++slot;
+                }
+                for (int k = 0; k < H; ++k) rs[k] = 0xFFFFFFFFu;
+            }
+        }
+        const bool keep = (H == 1 && positive) || keep0;
         if (keep) {
             const unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(log.d_count), 1ull);
-            if (slot < (unsigned long long)log.capacity) {
-                WindowLogEntry *e = reinterpret_cast<WindowLogEntry *>(log.d_entries) + slot;
-#pragma unroll
-                for (int k = 0; k < kFeat / 8; ++k)
-                    reinterpret_cast<uint4 *>(e->feat)[k] = make_uint4(lf[4 * k], lf[4 * k + 1], lf[4 * k + 2], lf[4 * k + 3]);
-                e->label = positive ? 1.f : 0.f;
-                e->walker_id = wk.wid;
-                e->step = (uint32_t)t_step;
-                e->pad = 0;
-            }
+            if (slot < (unsigned long long)log.capacity) write_log_entry(log, slot, lf, positive ? 1.f : 0.f, wk.wid,
+                                                                         (uint32_t)t_step);
         }
     }
     wk.store(d, w);

@@ -43,16 +43,18 @@ def _bf16_bits(a: np.ndarray) -> bytes:
     return r.tobytes()
 
 
-def collect(formats=TRAIN_FORMATS, walkers=4096, steps=4000, seed=100, neg_rate=0.01, plateau=None):
-    """Window-uniform walks with transition logging: every rank-lowering step
-    (label 1) and a neg_rate sample of the others (label 0).  plateau None: the
-    configurations' plateau lengths (1e4 for (2,2,2), 5e4 for the others)."""
+def collect(formats=TRAIN_FORMATS, walkers=4096, steps=4000, seed=100, neg_rate=0.01, plateau=None, horizon=1):
+    """Window-uniform walks with transition logging: the chosen candidates of
+    the last `horizon` steps before every rank-lowering step (label 1; horizon
+    1: that step's alone) and a neg_rate sample of the others (label 0).
+    plateau None: the configurations' plateau lengths (1e4 for (2,2,2), 5e4
+    for the others)."""
     entries = []
     for k, fmt in enumerate(formats):
         L = plateau if plateau is not None else (10_000 if tuple(fmt) == (2, 2, 2) else 50_000)
         W = tfg.Walkers([(fmt, 0, naive_start(*fmt), walkers)], seed=seed + k,
                         params=tfg.tfg_default_params(plateau_len=L))
-        log = tfg.TransitionLog(walkers * steps // 20 + 100000, neg_thresh=int(neg_rate * 2**32))
+        log = tfg.TransitionLog(walkers * steps // 20 + 100000, neg_thresh=int(neg_rate * 2**32), horizon=horizon)
         W.walk_window(steps, policy=0, log=log)
         e = log.read()
         entries.append(e)
@@ -187,11 +189,12 @@ def main():
     ap.add_argument("--collect-steps", type=int, default=4000)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--seeds", type=int, default=5)
+    ap.add_argument("--horizon", type=int, default=1, help="label-1 horizon of the training log (steps)")
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
-    e = collect(walkers=args.collect_walkers, steps=args.collect_steps)
+    e = collect(walkers=args.collect_walkers, steps=args.collect_steps, horizon=args.horizon)
     t1 = time.perf_counter()
     params, info = train(e, epochs=args.epochs)
     t2 = time.perf_counter()

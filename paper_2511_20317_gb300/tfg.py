@@ -59,7 +59,8 @@ class tfg_stats(ctypes.Structure):
 
 class tfg_log_spec(ctypes.Structure):
     _fields_ = [("d_entries", ctypes.c_void_p), ("capacity", ctypes.c_int64), ("d_count", ctypes.c_void_p),
-                ("neg_thresh", ctypes.c_uint32)]
+                ("neg_thresh", ctypes.c_uint32), ("horizon", ctypes.c_int32), ("d_ring", ctypes.c_void_p),
+                ("d_ring_step", ctypes.c_void_p)]
 
 
 LOG_ENTRY_DTYPE = np.dtype([("feat", np.uint16, 32), ("label", np.float32), ("walker_id", np.uint32),
@@ -375,12 +376,25 @@ def tfg_mlp_train_state_bytes() -> int:
 class TransitionLog:
     """Device buffers for window-mode logging (entries, count), read back as numpy."""
 
-    def __init__(self, capacity: int, neg_thresh: int = 0):
+    def __init__(self, capacity: int, neg_thresh: int = 0, horizon: int = 1):
         import torch
         self.capacity = int(capacity)
         self.neg_thresh = int(neg_thresh)
+        self.horizon = int(horizon)
         self.entries = torch.zeros(self.capacity * LOG_ENTRY_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
         self.count = torch.zeros(1, dtype=torch.int64, device="cuda")
+        self.ring = self.ring_step = None   # horizon > 1: per-walker rings, made at the first walk
+
+    def spec(self, walkers: int) -> "tfg_log_spec":
+        import torch
+        ring = step = None
+        if self.horizon > 1:
+            if self.ring is None or self.ring_step.numel() != walkers * self.horizon:
+                self.ring = torch.zeros(walkers * self.horizon * 32, dtype=torch.int16, device="cuda")
+                self.ring_step = torch.full((walkers * self.horizon,), -1, dtype=torch.int32, device="cuda")
+            ring, step = self.ring.data_ptr(), self.ring_step.data_ptr()
+        return tfg_log_spec(self.entries.data_ptr(), self.capacity, self.count.data_ptr(), self.neg_thresh,
+                            self.horizon, ring, step)
 
     def read(self) -> np.ndarray:
         n = min(int(self.count.item()), self.capacity)
@@ -587,7 +601,7 @@ class Walkers:
             choices = torch.full((steps, self.total), -2, dtype=torch.int32, device="cuda")
         spec = None
         if log is not None:
-            spec = tfg_log_spec(log.entries.data_ptr(), log.capacity, log.count.data_ptr(), log.neg_thresh)
+            spec = log.spec(self.total)
         _check(lib().tfg_walk_window(self.ctx, int(steps), int(policy),
                                      ctypes.c_void_p(mlp_params.data_ptr()) if mlp_params is not None else None,
                                      ctypes.c_uint32(eps_thresh), ctypes.c_void_p(self._wscratch.data_ptr()),

@@ -181,3 +181,41 @@ def test_transition_log_equals_the_oracle_log():
     assert np.array_equal(e["feat"], want_feat)
     assert int((e["label"] == 1).sum()) == st["reductions"]
     assert (e["label"] == 0).sum() > 0
+
+
+@pytest.mark.parametrize("H", [2, 8])
+def test_transition_log_with_horizon_equals_the_oracle_log(H):
+    """H-step horizon: every rank-lowering step logs the chosen candidates of
+    its last H steps (since the previous rank-lowering step) with label 1.  The
+    device walks in two calls, so the per-walker rings carry over between them;
+    the oracle's log comes from one walk of all the steps."""
+    fmt, nw, steps, L = (3, 3, 3), 256, 700, 200
+    neg = int(0.02 * 2**32)
+    start = naive_start(*fmt)
+    W = tfg.Walkers([(fmt, 0, start, nw)], seed=3, params=tfg.tfg_default_params(plateau_len=L))
+    log = tfg.TransitionLog(nw * steps, neg_thresh=neg, horizon=H)
+    W.walk_window(300, policy=0, log=log)
+    W.walk_window(steps - 300, policy=0, log=log)
+    W.sync()
+    st, _ = W.stats()
+    assert int(log.count.item()) <= log.capacity
+    e = log.read()
+    e = e[np.lexsort((e["label"], e["step"], e["walker_id"]))]
+    ref = oracle.Walkers(fmt, start, np.arange(nw), seed=3, plateau_len=L).walk_window(
+        steps, threads=THREADS, log_neg_thresh=neg)
+    wid, stp, lab, feat = oracle.horizon_log(ref.log_label, ref.log_feat, ref.log_chosen, np.arange(nw), H)
+    assert e.size == wid.size, (e.size, wid.size)
+    assert np.array_equal(e["walker_id"], wid.astype(np.uint32))
+    assert np.array_equal(e["step"], stp.astype(np.uint32))
+    assert np.array_equal(e["label"], lab)
+    assert np.array_equal(e["feat"], mlp.bf16_bits(feat.astype(np.float32)))
+    assert (e["label"] == 1).sum() > st["reductions"]       # the horizon adds the steps before each reduction
+
+
+def test_transition_log_horizon_out_of_range_is_rejected():
+    fmt = (2, 2, 2)
+    W = tfg.Walkers([(fmt, 0, naive_start(*fmt), 8)], seed=1)
+    with pytest.raises(tfg.TfgError):
+        W.walk_window(1, policy=0, log=tfg.TransitionLog(64, horizon=65))
+    W.walk_window(1, policy=0, log=tfg.TransitionLog(64, horizon=64))
+    W.sync()

@@ -195,6 +195,56 @@ def test_training_log_is_the_rank_lowering_steps_and_a_philox_sample(fmt, seed):
     assert np.array_equal(whole.info["digest"], step_by_step.info["digest"])
 
 
+def test_horizon_log_by_hand():
+    """One walker, nine steps, H = 3: rank-lowering steps 3, 6, 8; sampled
+    label-0 steps 1 and 7; step 5 had no candidate.  Step 3 logs the chosen
+    steps 1..3, step 6 the chosen steps 4..6 after step 3 (5 had none: 4, 6),
+    step 8 the steps 7..8 after 6 (its window 6..8 starts at the previous
+    rank-lowering step); steps 1 and 7 also appear with label 0."""
+    label = np.array([[-1, 0, -1, 1, -1, -1, 1, 0, 1]], np.int8)
+    chosen = np.array([[1, 1, 1, 1, 1, 0, 1, 1, 1]], bool)
+    feat = np.zeros((1, 9, 32), np.uint8)
+    feat[0, :, 0] = np.arange(9) + 10          # a per-step marker
+    wid, st, lab, f = oracle.horizon_log(label, feat, chosen, np.array([42]), 3)
+    want = [(1, 0.0), (1, 1.0), (2, 1.0), (3, 1.0), (4, 1.0), (6, 1.0), (7, 0.0), (7, 1.0), (8, 1.0)]
+    assert list(zip(st.tolist(), lab.tolist())) == want
+    assert (wid == 42).all() and np.array_equal(f[:, 0], st + 10)
+
+
+@pytest.mark.parametrize("H", [1, 4, 10_000])
+def test_horizon_log_on_an_oracle_walk(H):
+    """H = 1 is the plain log (the records of label >= 0); any H keeps the
+    label-0 records; with H beyond the walk every chosen step up to the last
+    rank-lowering step appears once with label 1; label-1 entries never
+    exceed H per rank-lowering step."""
+    fmt, nw, steps = (3, 3, 3), 8, 400
+    start = naive_start(*fmt)
+    ids = np.arange(nw) * 5
+    o = oracle.Walkers(fmt, start, ids, seed=9, plateau_len=60).walk_window(steps, threads=2,
+                                                                            log_neg_thresh=int(0.05 * 2**32))
+    wid, st, lab, f = oracle.horizon_log(o.log_label, o.log_feat, o.log_chosen, ids, H)
+    zw, zt = np.nonzero(o.log_label == 0)
+    assert np.array_equal(np.sort(ids[zw] * steps + zt), np.sort(wid[lab == 0] * steps + st[lab == 0]))
+    n_low = int((o.log_label == 1).sum())
+    assert n_low > 0
+    assert (lab == 1).sum() <= H * n_low
+    for k in np.nonzero(lab == 1)[0]:
+        w = int(np.nonzero(ids == wid[k])[0][0])
+        assert o.log_chosen[w, st[k]]
+        assert np.array_equal(f[k], o.log_feat[w, st[k]])
+    if H == 1:
+        ow, ot = np.nonzero(o.log_label == 1)
+        assert np.array_equal(ids[ow] * steps + ot, wid[lab == 1] * steps + st[lab == 1])
+    if H >= steps:
+        for w in range(nw):
+            low = np.nonzero(o.log_label[w] == 1)[0]
+            if low.size == 0:
+                assert not (wid[lab == 1] == ids[w]).any()
+                continue
+            want = np.nonzero(o.log_chosen[w, : low[-1] + 1])[0]
+            assert np.array_equal(st[(lab == 1) & (wid == ids[w])], want)
+
+
 def test_adam_first_step_and_constant_gradient_closed_forms():
     """t = 1: m_hat = g, v_hat = g^2, so the update is -lr g / (|g| + eps); with a
     constant gradient the bias corrections keep m_hat = g and v_hat = g^2 on
