@@ -381,22 +381,23 @@ def learned_ab(args):
     """The learned proposal against uniform choice over the same candidate
     windows (the learned-proposal workload: (4,4,4) and (3,4,5), 262144 walkers,
     equal step budgets): the network is trained on the device from the
-    logged window-uniform walks of the uniform workloads' formats (seeds 100..;
-    label 1 on the chosen candidates of the --ab-horizon steps up to each
-    rank-lowering step),
+    logged window-uniform walks of the uniform workloads' formats (4096
+    walkers x --ab-collect-steps steps each, seeds 100..; label 1 on the
+    chosen candidates of the --ab-horizon steps up to each rank-lowering step),
     then both arms run from the naive (4,4,4) and (3,4,5) schemes with 262144
     walkers, plateau 5e4, evaluation seeds 1000..1004: the learned arm for
     --ab-steps steps per walker, the uniform arm for as many steps (equal
     budget) and for the learned arm's wall time (equal time)."""
     from paper_2511_20317_gb300 import learned
     t0 = time.perf_counter()
-    entries = learned.collect(walkers=4096, steps=4000, horizon=args.ab_horizon)
+    entries = learned.collect(walkers=4096, steps=args.ab_collect_steps, horizon=args.ab_horizon)
     params, info = learned.train(entries, epochs=30)
     res = learned.ab_test(params, seeds=tuple(range(args.ab_seeds)), walkers=args.ab_walkers, steps=args.ab_steps)
     return {"workload": f"naive (4,4,4) and (3,4,5), Z_T, {args.ab_walkers} walkers, {args.ab_steps} window steps "
                         f"per walker (learned, and uniform at equal steps) and uniform at the learned arm's wall "
                         f"time; plateau 5e4; {args.ab_seeds} evaluation seeds; eps 0.05; 256-candidate windows",
-            "training": {"label_horizon_steps": args.ab_horizon, "samples": info["samples"],
+            "training": {"label_horizon_steps": args.ab_horizon, "collect_steps": args.ab_collect_steps,
+                         "samples": info["samples"],
                          "positives": info["positives"],
                          "loss_first": info["loss"][0], "loss_last": info["loss"][-1]},
             "results": res, "seconds": time.perf_counter() - t0}
@@ -480,7 +481,8 @@ def main():
     ap.add_argument("--ab-walkers", type=int, default=262144)
     ap.add_argument("--ab-steps", type=int, default=1500)
     ap.add_argument("--ab-seeds", type=int, default=5)
-    ap.add_argument("--ab-horizon", type=int, default=8, help="label-1 horizon of the training log (steps)")
+    ap.add_argument("--ab-horizon", type=int, default=16, help="label-1 horizon of the training log (steps)")
+    ap.add_argument("--ab-collect-steps", type=int, default=16000, help="window steps of the logged training walks")
     args = ap.parse_args()
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         spawn_ranks(args.gpus)

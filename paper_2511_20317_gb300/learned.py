@@ -153,17 +153,18 @@ def _beats(a, b, key, higher_better=True):
 
 
 def ab_test(params, formats=EVAL_FORMATS, seeds=(0, 1, 2, 3, 4), walkers=262144, steps=1500, eps=0.05,
-            plateau=50_000):
+            plateau=50_000, seed_base=1000):
     """Learned against uniform over the same candidate windows: per format and
     evaluation seed (disjoint from the training seeds), the learned arm for
     `steps` steps per walker, the uniform arm for the same steps (equal step
     budget) and for the learned arm's wall time (equal time).  Net measures:
-    rank descent and lowest rank with 95% intervals over the seeds."""
+    rank descent and lowest rank with 95% intervals over the seeds.  The
+    evaluation walks use seeds seed_base + s."""
     out = {}
     for fmt in formats:
         learned, uniform, uniform_t = [], [], []
         for s in seeds:
-            sd = 1000 + s
+            sd = seed_base + s
             l = evaluate(fmt, 1, params, walkers=walkers, steps=steps, seed=sd, eps=eps, plateau=plateau)
             learned.append(l)
             uniform.append(evaluate(fmt, 0, None, walkers=walkers, steps=steps, seed=sd, plateau=plateau))
@@ -190,6 +191,7 @@ def main():
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--seeds", type=int, default=5)
     ap.add_argument("--horizon", type=int, default=1, help="label-1 horizon of the training log (steps)")
+    ap.add_argument("--eval-seed-base", type=int, default=1000)
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
@@ -198,7 +200,8 @@ def main():
     t1 = time.perf_counter()
     params, info = train(e, epochs=args.epochs)
     t2 = time.perf_counter()
-    res = ab_test(params, seeds=tuple(range(args.seeds)), walkers=args.walkers, steps=args.steps)
+    res = ab_test(params, seeds=tuple(range(args.seeds)), walkers=args.walkers, steps=args.steps,
+                  seed_base=args.eval_seed_base)
     t3 = time.perf_counter()
     print(json.dumps({"train": {k: v for k, v in info.items() if k != "loss"}, "loss_first_last":
                       [info["loss"][0], info["loss"][-1]], "ab": res,
