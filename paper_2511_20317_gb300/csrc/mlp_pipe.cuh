@@ -15,8 +15,10 @@
 //   MMA2  acc = H1 W2       (KH / 16 x K=16)
 //   epi2  y = b3 + sum_o w3[o] relu(acc[o] + b2[o])
 // The warpgroups of a CTA interleave on the tensor pipe: while one waits for
-// its products, the others run their epilogues.  TMEM loads are issued one
-// 16-column chunk ahead of the arithmetic on the previous chunk.
+// its products, the others run their epilogues; a warpgroup itself writes
+// the next tile's X while its MMA2 runs (X's only reader, MMA1, is done), so
+// the next MMA1 follows epi2 at once.  TMEM loads are issued one 16-column
+// chunk ahead of the arithmetic on the previous chunk.
 //
 // Bias folding (Prod::kFold, used where the producer controls the feature
 // rows): the constant-one input f31 is joined by f29 = f30 = 1 on every
@@ -174,9 +176,10 @@ __device__ __forceinline__ void st_row8(uint8_t *tile, int q, int col0, int K, u
 //   bool live()                       false: the tile begun last is skipped (the same answer for
 //                                     the 128 rows; asked only when the tile is due, so that its
 //                                     loads have landed)
-//   void fill(uint8_t *sX, int q)     write row q of the tile loaded last into X (kFold:
-//                                     features 29 and 30 one on every real row)
-//   void emit(float y, int q)         the score of row q of the tile last filled
+//   int64_t fill(uint8_t *sX, int q)  write row q of the tile loaded last into X (kFold:
+//                                     features 29 and 30 one on every real row); returns
+//                                     the row's output index (-1: no output)
+//   void emit(float y, int64_t o)     the score y of the row whose fill returned o
 template <int NWG, class Prod>
 __device__ __forceinline__ void run_tiles(const uint8_t *__restrict__ params, Prod &prod, int64_t ntiles,
                                           int *__restrict__ err, uint32_t first_limit, uint8_t *smem,
@@ -216,23 +219,22 @@ __device__ __forceinline__ void run_tiles(const uint8_t *__restrict__ params, Pr
 
     const int64_t stride = (int64_t)gridDim.x * NWG;
     int64_t t = (int64_t)blockIdx.x * NWG + g;
+    // the first live tile, its features in X
     if (t < ntiles) {
         prod.begin(t, q);
         prod.mid(q);
     }
-    while (t < ntiles) {
-        if (!prod.live()) {   // skipped tile (uniform over the warpgroup)
-            t += stride;
-            if (t < ntiles) {
-                prod.begin(t, q);
-                prod.mid(q);
-            }
-            continue;
+    while (t < ntiles && !prod.live()) {   // skipped tile (uniform over the warpgroup)
+        t += stride;
+        if (t < ntiles) {
+            prod.begin(t, q);
+            prod.mid(q);
         }
-        prod.fill(sX, q);
-        const int64_t tn = t + stride;
-        const bool has_next = tn < ntiles;
-        if (has_next) prod.begin(tn, q);   // first load phase of the next tile
+    }
+    int64_t out_cur = t < ntiles ? prod.fill(sX, q) : -1;
+    while (t < ntiles) {
+        int64_t tn = t + stride;
+        if (tn < ntiles) prod.begin(tn, q);   // first load phase of the next tile
         tc::fence_async_smem();
         tc::fence_before_sync();
         wg_sync(g);
@@ -274,7 +276,7 @@ __device__ __forceinline__ void run_tiles(const uint8_t *__restrict__ params, Pr
                 if (c + 1 < kHid / 16) tmem_wait(nxt);
             }
         }
-        if (has_next) prod.mid(q);   // second load phase of the next tile
+        if (tn < ntiles) prod.mid(q);   // second load phase of the next tile
         tc::fence_async_smem();
         tc::fence_before_sync();
         wg_sync(g);
@@ -286,6 +288,15 @@ __device__ __forceinline__ void run_tiles(const uint8_t *__restrict__ params, Pr
                              tc::make_desc(aW2 + kc * 256, 128, (KH / 8) * 128), idesc, kc > 0);
             tc::mma_commit(mb);
         }
+        // while MMA2 runs: the next live tile's features into X (MMA1, its only reader, is done)
+        while (tn < ntiles && !prod.live()) {
+            tn += stride;
+            if (tn < ntiles) {
+                prod.begin(tn, q);
+                prod.mid(q);
+            }
+        }
+        const int64_t out_next = tn < ntiles ? prod.fill(sX, q) : -1;
         ok = tc::mbar_wait(mb, phase);
         if (wg_any(g, !ok)) { timed_out = true; break; }
         phase ^= 1;
@@ -318,9 +329,10 @@ __device__ __forceinline__ void run_tiles(const uint8_t *__restrict__ params, Pr
                 if (c + 1 < kHid / 16) tmem_wait(nxt);
             }
         }
-        prod.emit(y2.x + y2.y, q);
+        prod.emit(y2.x + y2.y, out_cur);
         // the next MMA1 overwrites the accumulator: order this thread's loads before it
         tc::fence_before_sync();
+        out_cur = out_next;
         t = tn;
     }
     if (timed_out) {

@@ -24,7 +24,7 @@ struct RowsProducer {
     int64_t n;
     float *out;
     uint4 v[4];
-    int64_t row_loaded, row_filled;
+    int64_t row_loaded;
     __device__ __forceinline__ bool live() const { return true; }
     __device__ __forceinline__ void begin(int64_t tile, int q) {
         row_loaded = tile * mlp::kTile + q;
@@ -37,13 +37,13 @@ struct RowsProducer {
         }
     }
     __device__ __forceinline__ void mid(int) {}
-    __device__ __forceinline__ void fill(uint8_t *sX, int q) {
+    __device__ __forceinline__ int64_t fill(uint8_t *sX, int q) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) mlp::st_row8(sX, q, 8 * c, mlp::kIn, v[c]);
-        row_filled = row_loaded;
+        return row_loaded < n ? row_loaded : -1;
     }
-    __device__ __forceinline__ void emit(float y, int) {
-        if (row_filled < n) out[row_filled] = y;
+    __device__ __forceinline__ void emit(float y, int64_t o) {
+        if (o >= 0) out[o] = y;
     }
 };
 

@@ -254,9 +254,6 @@ struct WindowProducer {
     int row, half, K, r, best_r;
     uint2 dci;
     PTerm<Wd, 1, true> ti, tj;
-    // latched by fill()
-    int64_t out_idx;
-    bool out_ok;
     __device__ __forceinline__ void begin(int64_t tile, int q) {
         w = tile >> 1;
         half = (int)(tile & 1);
@@ -275,7 +272,7 @@ struct WindowProducer {
         tj.p[0] = src[(size_t)j * 2];
         tj.n[0] = src[(size_t)j * 2 + 1];
     }
-    __device__ __forceinline__ void fill(uint8_t *sX, int q) {
+    __device__ __forceinline__ int64_t fill(uint8_t *sX, int q) {
         uint32_t h[kFeat / 2];
         if (row < K) {
             cand_features_bf16<Wd>(ti, tj, mk, dci.x, dci.y, r, best_r, m, n, p, h);
@@ -288,11 +285,10 @@ struct WindowProducer {
 #pragma unroll
         for (int c = 0; c < kFeat / 8; ++c)
             mlp::st_row8(sX, q, 8 * c, mlp::kIn, make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]));
-        out_idx = w * kWin + row;
-        out_ok = row < K;
+        return row < K ? w * kWin + row : -1;
     }
-    __device__ __forceinline__ void emit(float y, int) {
-        if (out_ok) score[out_idx] = y;
+    __device__ __forceinline__ void emit(float y, int64_t o) {
+        if (o >= 0) score[o] = y;
     }
 };
 
