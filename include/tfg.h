@@ -429,7 +429,8 @@ int tfg_mlp_train_step(void *d_state, void *d_params, const uint16_t *d_x, const
  * memory, on the tensor-core kernel, from the window's candidate list.)
  * policy 0 (uniform): candidate mulhi(x1, K);
  * policy 1 (learned): with x3 < eps_thresh as policy 0, else the candidate of
- * highest MLP score (first on ties).  The chosen flip then goes through the
+ * highest MLP score (first on ties); d_mlp_params is the parameter blob of
+ * tfg_mlp_score (device, 16-byte aligned, TFG_EINVAL otherwise).  The chosen flip then goes through the
  * same validity test, reductions and bookkeeping as tfg_walk.
  * Populations must be Z_T with m*n + n*p + p*m <= 64 and r_max <= 88.
  * d_scratch: caller device memory of tfg_window_scratch_bytes (per walker

@@ -1193,6 +1193,7 @@ static int check_window_ctx(const tfg_ctx *ctx, int64_t steps, int32_t policy, c
         set_error("bad arguments");
         return TFG_EINVAL;
     }
+    if (policy == 1 && (uintptr_t)d_mlp_params % 16) { set_error("network parameters must be 16-byte aligned"); return TFG_EINVAL; }
     if (ctx->prm.walk_policy != 0) { set_error("window mode needs walk_policy 0"); return TFG_EINVAL; }
     for (const Segment &s : ctx->segs) {
         if (s.fmt.mode != TFG_MODE_ZT || s.tw != 1 || s.R > 128 ||
