@@ -371,6 +371,9 @@ def run_ours(args):
     if rank == 0 and args.cpu_baseline:
         cb = oracle_sample(args, pops, plateau)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        # the roofline's op count (counters and the live rank at the end) against the
+        # oracle's exact per-step count, on the oracle's sample of the same walkers
+        line["roofline"]["ops_estimate_over_oracle_count"] = cb["ops_estimate"] / max(cb["ops_exact"], 1.0)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -421,6 +424,9 @@ def oracle_sample(args, pops, plateau):
     n_w = sum(w.walker_ids.size for w in walkers)
     per_step, applied, steps_done = [], 0, 0
     for k in range(args.warmup + args.steps):
+        if k == args.warmup:   # counters at the start of the timed chunks
+            c0 = [{f: int(w.info[f].astype(np.int64).sum()) for f in ("ops", "t", "accepted", "rejected")}
+                  for w in walkers]
         acc0 = sum(int(w.info["accepted"].sum()) for w in walkers)
         t0 = time.perf_counter()
         for w in walkers:
@@ -431,7 +437,17 @@ def oracle_sample(args, pops, plateau):
             applied += sum(int(w.info["accepted"].sum()) for w in walkers) - acc0
             steps_done += n_w * chunk
     t = sum(per_step)
+    # the oracle's exact algorithmic op count of the timed chunks, and the estimate the
+    # GPU arm's roofline makes from the same kind of inputs (counters, the live rank
+    # at the end) for the same walkers
+    exact = estimate = 0.0
+    for w, c, (fmt, mode, _, _) in zip(walkers, c0, pops):
+        exact += float(w.info["ops"].astype(np.int64).sum() - c["ops"])
+        estimate += algorithmic_ops(mode, float(w.info["t"].astype(np.int64).sum() - c["t"]),
+                                    float(w.info["accepted"].sum() - c["accepted"]),
+                                    float(w.info["rejected"].sum() - c["rejected"]), float(w.info["r"].mean()))
     return {"value": applied / t, "unit": "flips/s", "cores": threads, "kind": "oracle",
+            "ops_exact": exact, "ops_estimate": estimate,
             "sample": f"{n_w} walkers ({args.cpu_walkers} per population, ids spread over it) advanced "
                       f"{args.warmup} + {args.steps} chunks of {chunk} steps like the GPU walkers; "
                       f"{applied} applied flips in {steps_done} walker-steps over {t:.1f} s timed",

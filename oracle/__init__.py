@@ -63,7 +63,7 @@ INFO_DTYPE = np.dtype([("r", np.int32), ("best_r", np.int32), ("r_max", np.int32
                        ("digest", np.uint64),
                        ("accepted", np.int64), ("rejected", np.int64), ("nocand", np.int64),
                        ("drops", np.int64), ("merges", np.int64), ("plus", np.int64),
-                       ("reductions", np.int64), ("debug_failures", np.int64)])
+                       ("reductions", np.int64), ("debug_failures", np.int64), ("ops", np.int64)])
 
 
 def lib():

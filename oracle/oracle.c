@@ -221,6 +221,7 @@ typedef struct {
     uint64_t digest;
     int64_t accepted, rejected, nocand, drops, merges, plus, reductions;
     int64_t debug_failures;
+    int64_t ops;             /* algorithmic word operations of the uniform steps (walk_step_ops) */
 } orc_info;
 
 typedef struct {
@@ -657,6 +658,26 @@ static void finish_step(walker *wk, const uint32_t *x, int r_before, int action,
 }
 
 /* One step of the walk (Algorithm 1, with the plateau or the p_expand expansion policy). */
+/* Algorithmic word operations of one uniform step, the count the roofline of
+ * the walk is taken against: the Philox draw (10 rounds of 10 operations);
+ * the try_flip comparison of term i with the r - 1 other live slots (Z_T 8
+ * word tests per slot: u and v exact, two words each, w exact or negated,
+ * four; Z_2 3); when a candidate was drawn, the two new factors (Z_T 18:
+ * validity 3 + result 6 each; Z_2 2 XOR); after an accepted flip, the
+ * reduction check of both modified terms against the other slots.  Word
+ * counts are per machine word of a sign: one word for terms of at most 64
+ * coefficients, three (factor-aligned) when every factor fits 64, else six.
+ * r is the rank when the step began. */
+static int64_t walk_step_ops(const orc_fmt *F, int r, int action)
+{
+    const int64_t words = F->LT <= 64 ? 1 : ((F->len[0] <= 64 && F->len[1] <= 64 && F->len[2] <= 64) ? 3 : 6);
+    const int64_t search = (F->mode == ORC_MODE_ZT ? 8 : 3) * (int64_t)(r - 1);
+    int64_t ops = 100 + search;
+    if (action != ORC_NOCAND) ops += F->mode == ORC_MODE_ZT ? 18 : 2;
+    if (action == ORC_ACCEPT) ops += 2 * search;
+    return words * ops;
+}
+
 static void walk_step(walker *wk, cand_t *cbuf)
 {
     orc_info *in = wk->info;
@@ -675,6 +696,7 @@ static void walk_step(walker *wk, cand_t *cbuf)
     } else {
         in->nocand += 1;
     }
+    in->ops += walk_step_ops(wk->f, r_before, action);
     finish_step(wk, x, r_before, action, X, rho, s, i, j);
 }
 
