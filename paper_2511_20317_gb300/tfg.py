@@ -374,7 +374,9 @@ def tfg_mlp_train_state_bytes() -> int:
 
 
 class TransitionLog:
-    """Device buffers for window-mode logging (entries, count), read back as numpy."""
+    """Device buffers for window-mode logging (entries, count), read back as numpy.
+    With horizon > 1 it also holds the walkers' rings of recent chosen
+    candidates, which carry over between calls: use one log per context."""
 
     def __init__(self, capacity: int, neg_thresh: int = 0, horizon: int = 1):
         import torch
