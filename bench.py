@@ -373,7 +373,9 @@ def run_ours(args):
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         # the roofline's op count (counters and the live rank at the end) against the
         # oracle's exact per-step count, on the oracle's sample of the same walkers
-        line["roofline"]["ops_estimate_over_oracle_count"] = cb["ops_estimate"] / max(cb["ops_exact"], 1.0)
+        ratio = cb["ops_estimate"] / max(cb["ops_exact"], 1.0)
+        line["roofline"]["ops_estimate_over_oracle_count"] = ratio
+        line["roofline"]["frac_at_oracle_count"] = line["roofline"]["frac"] / ratio
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
