@@ -394,11 +394,16 @@ int tfg_mlp_score(const void *d_params, const uint16_t *d_x, int64_t n, float *d
  * tfg_mlp_grad: d_grad (device f32 [P + 1], overwritten) receives the gradient
  * and, at [P], the loss.  Asynchronous; *d_err set to 1 if a tensor-core
  * completion wait gave up.
+ * The gradient's per-CTA sums are added by atomics, so its low bits may vary
+ * from run to run.
  * tfg_mlp_train_state_bytes / tfg_mlp_train_init: optimizer state (FP32 master
- * weights, Adam moments, gradient) in caller device memory, initialised from
+ * weights, Adam moments, gradient, and one gradient row per CTA of the
+ * training step's gradient launch) in caller device memory, initialised from
  * the parameter blob.
  * tfg_mlp_train_step: one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step
- * counted from 1) on the samples; rewrites d_params (bf16 W1, W2, f32 rest). */
+ * counted from 1) on the samples; rewrites d_params (bf16 W1, W2, f32 rest).
+ * Its gradient adds the per-CTA rows in CTA order: the same inputs give the
+ * same bits on every run (on a GPU of the same SM count). */
 int tfg_mlp_grad(const void *d_params, const uint16_t *d_x, const float *d_label, const float *d_weight, int64_t n,
                  float *d_grad, int32_t *d_err, void *cuda_stream);
 size_t tfg_mlp_train_state_bytes(void);

@@ -1136,7 +1136,12 @@ int tfg_mlp_score(const void *d_params, const uint16_t *d_x, int64_t n, float *d
     return TFG_OK;
 }
 
-size_t tfg_mlp_train_state_bytes(void) { return (size_t)(4 * tfg::mlp_num_params() + 4) * sizeof(float); }
+// optimizer state: master weights, Adam moments (P each), the gradient (P + 1, then padding to 4 floats),
+// then the per-CTA gradient rows of the deterministic gradient launch
+static size_t train_partial_offset() { return (size_t)4 * tfg::mlp_num_params() + 4; }
+size_t tfg_mlp_train_state_bytes(void) {
+    return (train_partial_offset() + (size_t)tfg::grad_partial_rows() * (tfg::mlp_num_params() + 1)) * sizeof(float);
+}
 
 int tfg_mlp_grad(const void *d_params, const uint16_t *d_x, const float *d_label, const float *d_weight, int64_t n,
                  float *d_grad, int32_t *d_err, void *cuda_stream) {
@@ -1169,9 +1174,16 @@ int tfg_mlp_train_step(void *d_state, void *d_params, const uint16_t *d_x, const
     if (!d_state || !d_params || step < 1) { set_error("bad arguments (step counts from 1)"); return TFG_EINVAL; }
     const int P = tfg::mlp_num_params();
     float *s = reinterpret_cast<float *>(d_state);
-    int rc = tfg_mlp_grad(d_params, d_x, d_label, d_weight, n, s + 3 * P, d_err, cuda_stream);
-    if (rc) return rc;
-    tfg::launch_adam(s, s + P, s + 2 * P, s + 3 * P, d_params, lr, step, reinterpret_cast<cudaStream_t>(cuda_stream));
+    if (n < 0 || !d_err || (n > 0 && (!d_x || !d_label || !d_weight))) { set_error("bad arguments"); return TFG_EINVAL; }
+    if (((uintptr_t)d_x % 16) != 0) { set_error("features must be 16-byte aligned"); return TFG_EINVAL; }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    if (n == 0) {
+        cudaError_t e = cudaMemsetAsync(s + 3 * P, 0, sizeof(float) * (P + 1), st);
+        if (e != cudaSuccess) return cuda_fail(e, "memset");
+    }
+    // the gradient from per-CTA rows added in CTA order: the same bits on every run
+    tfg::launch_mlp_grad(d_params, d_x, d_label, d_weight, n, s + 3 * P, d_err, st, s + train_partial_offset());
+    tfg::launch_adam(s, s + P, s + 2 * P, s + 3 * P, d_params, lr, step, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "adam launch");
     return TFG_OK;

@@ -30,6 +30,7 @@ constexpr int kVW1 = 0, kVW2 = kIn * kHid, kVB1 = kVW2 + kHid * kHid, kVB2 = kVB
               kVB3 = kVW3 + kHid;
 
 // shared memory regions (bytes)
+constexpr int kGradPartialRows = 256;          // CTAs of a deterministic (partial-row) gradient launch, at most
 constexpr uint32_t kSX = 0;                    // A  (s, i)   K = 32
 constexpr uint32_t kSXT = kSX + 8192;          // B  (i, s)   K = 128
 constexpr uint32_t kSW1T = kSXT + 8192;        // B  (h, i)   K = 32
@@ -39,8 +40,8 @@ constexpr uint32_t kSH1 = kSW2 + 32768;        // A  (s, h)   K = 128
 constexpr uint32_t kSH1T = kSH1 + 32768;       // B  (h, s)   K = 128
 constexpr uint32_t kSD2 = kSH1T + 32768;       // A  (s, o) = dZ2, then (h, s) = dZ1^T
 constexpr uint32_t kSD2T = kSD2 + 32768;       // A  (o, s)   K = 128
-constexpr uint32_t kSVec = kSD2T + 32768;      // b1, b2, w3, then sums gb1, gb2, gw3, gb3, loss
-constexpr uint32_t kTrainSmem = kSVec + (6 * kHid + 4) * 4;
+constexpr uint32_t kSVec = kSD2T + 32768;      // b1, b2, w3, then per-warp sums gb1, gb2, gw3 [4][128], gb3, loss [4][2]
+constexpr uint32_t kTrainSmem = kSVec + (3 * kHid + 3 * 4 * kHid + 8) * 4;
 
 constexpr uint32_t kTmemCols = 512;   // [0,128) layer/ dH1 accumulator, [128,256) dW2^T, [256,288) dW1^T
 
@@ -78,11 +79,17 @@ __device__ __forceinline__ void sync_all() {
     tc::fence_after_sync();
 }
 
+// Gradient sums: every warp keeps its own column sums (its lanes own the
+// columns, so no atomics), added in warp order at the end; the CTA's totals go
+// to grad by atomics (tfg_mlp_grad), or, with `partial`, to the CTA's own row
+// partial[blockIdx.x][P + 1], which grad_reduce_kernel adds up in CTA order:
+// the training step's gradient is then the same bits on every run.
 __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const uint8_t *__restrict__ params,
                                                            const __nv_bfloat16 *__restrict__ x,
                                                            const float *__restrict__ label,
                                                            const float *__restrict__ weight, int64_t n,
-                                                           float *__restrict__ grad, int *__restrict__ err) {
+                                                           float *__restrict__ grad, float *__restrict__ partial,
+                                                           int *__restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
@@ -91,7 +98,8 @@ __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const uint8_t *__restr
     uint8_t *sX = smem + kSX, *sXT = smem + kSXT, *sW1T = smem + kSW1T, *sW2T = smem + kSW2T, *sW2 = smem + kSW2;
     uint8_t *sH1 = smem + kSH1, *sH1T = smem + kSH1T, *sD2 = smem + kSD2, *sD2T = smem + kSD2T;
     float *sB1 = reinterpret_cast<float *>(smem + kSVec), *sB2 = sB1 + kHid, *sW3 = sB2 + kHid;
-    float *gB1 = sW3 + kHid, *gB2 = gB1 + kHid, *gW3 = gB2 + kHid, *gScal = gW3 + kHid;   // gScal: gb3, loss
+    // per-warp sums [4][128] and scalars [4][2] (gb3, loss)
+    float *gB1 = sW3 + kHid, *gB2 = gB1 + 4 * kHid, *gW3 = gB2 + 4 * kHid, *gScal = gW3 + 4 * kHid;
 
     const __nv_bfloat16 *W1 = reinterpret_cast<const __nv_bfloat16 *>(params + kPW1);
     const __nv_bfloat16 *W2 = reinterpret_cast<const __nv_bfloat16 *>(params + kPW2);
@@ -108,9 +116,9 @@ __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const uint8_t *__restr
         sB1[e] = reinterpret_cast<const float *>(params + kPB1)[e];
         sB2[e] = reinterpret_cast<const float *>(params + kPB2)[e];
         sW3[e] = reinterpret_cast<const float *>(params + kPW3)[e];
-        gB1[e] = gB2[e] = gW3[e] = 0.f;
     }
-    if (tid < 2) gScal[tid] = 0.f;
+    for (int e = tid; e < 4 * kHid; e += blockDim.x) gB1[e] = gB2[e] = gW3[e] = 0.f;
+    if (tid < 8) gScal[tid] = 0.f;
     const float b3 = *reinterpret_cast<const float *>(params + kPB3);
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tslot), kTmemCols);
     if (tid == 0) {
@@ -238,8 +246,8 @@ __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const uint8_t *__restr
             }
             const float s_w3 = warp_colsum32(gw, lane);
             const float s_b2 = warp_colsum32(gb, lane);
-            atomicAdd(&gW3[c0 + lane], s_w3);
-            atomicAdd(&gB2[c0 + lane], s_b2);
+            gW3[warp * kHid + c0 + lane] += s_w3;
+            gB2[warp * kHid + c0 + lane] += s_b2;
         }
         sync_all();
         if (tid == 0) {
@@ -265,7 +273,7 @@ __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const uint8_t *__restr
 #pragma unroll
             for (int q = 0; q < 32; ++q) st_bf16(sD2, tc::kmajor_offset(c0 + q, tid, kTile), v[q]);
             const float s_b1 = warp_colsum32(v, lane);
-            atomicAdd(&gB1[c0 + lane], s_b1);
+            gB1[warp * kHid + c0 + lane] += s_b1;
         }
         sync_all();
         if (tid == 0) {
@@ -285,35 +293,56 @@ __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const uint8_t *__restr
         if (tid == 0) atomicExch(err, 1);
     } else if (!first) {
         // ---- flush: dW2[h][o] (TMEM lane o, column h), dW1[i][h] (lane h, column i), vectors
+        float *pp = partial ? partial + (size_t)blockIdx.x * (kNumParams + 1) : nullptr;
 #pragma unroll
         for (int c0 = 0; c0 < kHid; c0 += 32) {
             float v[32];
             tc::tmem_ld32(tDW2 + lane_base + c0, v);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) atomicAdd(&grad[kVW2 + (c0 + q) * kHid + tid], v[q]);
+            for (int q = 0; q < 32; ++q) {
+                const int e = kVW2 + (c0 + q) * kHid + tid;
+                if (pp) pp[e] = v[q];
+                else atomicAdd(&grad[e], v[q]);
+            }
         }
         {
             float v[32];
             tc::tmem_ld32(tDW1 + lane_base, v);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) atomicAdd(&grad[kVW1 + q * kHid + tid], v[q]);
+            for (int q = 0; q < 32; ++q) {
+                const int e = kVW1 + q * kHid + tid;
+                if (pp) pp[e] = v[q];
+                else atomicAdd(&grad[e], v[q]);
+            }
         }
-        // scalar sums: warp reduce then one atomic per warp
+        // scalar sums: warp reduce (a fixed butterfly), one slot per warp
         for (int o = 16; o > 0; o >>= 1) {
             my_gb3 += __shfl_xor_sync(0xffffffffu, my_gb3, o);
             my_loss += __shfl_xor_sync(0xffffffffu, my_loss, o);
         }
         if (lane == 0) {
-            atomicAdd(&gScal[0], my_gb3);
-            atomicAdd(&gScal[1], my_loss);
+            gScal[2 * warp] = my_gb3;
+            gScal[2 * warp + 1] = my_loss;
         }
         __syncthreads();
-        atomicAdd(&grad[kVB1 + tid], gB1[tid]);
-        atomicAdd(&grad[kVB2 + tid], gB2[tid]);
-        atomicAdd(&grad[kVW3 + tid], gW3[tid]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {   // b1, b2, w3: the four warps' sums in warp order
+            const float *gv = gB1 + k * 4 * kHid;
+            const float v = ((gv[tid] + gv[kHid + tid]) + gv[2 * kHid + tid]) + gv[3 * kHid + tid];
+            const int e = (k == 0 ? kVB1 : (k == 1 ? kVB2 : kVW3)) + tid;
+            if (pp) pp[e] = v;
+            else atomicAdd(&grad[e], v);
+        }
         if (tid == 0) {
-            atomicAdd(&grad[kVB3], gScal[0]);
-            atomicAdd(&grad[kNumParams], gScal[1]);   // loss follows the gradient vector
+            const float sb3 = ((gScal[0] + gScal[2]) + gScal[4]) + gScal[6];
+            const float sl = ((gScal[1] + gScal[3]) + gScal[5]) + gScal[7];
+            if (pp) {
+                pp[kVB3] = sb3;
+                pp[kNumParams] = sl;   // loss follows the gradient vector
+            } else {
+                atomicAdd(&grad[kVB3], sb3);
+                atomicAdd(&grad[kNumParams], sl);
+            }
         }
     }
     tc::fence_before_sync();
@@ -357,8 +386,19 @@ __global__ void master_from_blob_kernel(const uint8_t *blob, float *master, floa
 
 int mlp_num_params() { return kNumParams; }
 
+// grad[e] = sum over b < parts of partial[b][e], in order of b
+__global__ void grad_reduce_kernel(const float *__restrict__ partial, int parts, float *__restrict__ grad) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e > kNumParams) return;
+    float s = 0.f;
+    for (int b = 0; b < parts; ++b) s += partial[(size_t)b * (kNumParams + 1) + e];
+    grad[e] = s;
+}
+
+int grad_partial_rows() { return kGradPartialRows; }
+
 void launch_mlp_grad(const void *params, const void *x, const float *label, const float *weight, int64_t n,
-                     float *grad, int *err, cudaStream_t st) {
+                     float *grad, int *err, cudaStream_t st, float *partial) {
     if (n <= 0) return;
     static bool attr = [] {
         cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
@@ -369,10 +409,12 @@ void launch_mlp_grad(const void *params, const void *x, const float *label, cons
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t tiles = (n + kTile - 1) / kTile;
-    const int grid = (int)(tiles < sms ? tiles : sms);
+    int grid = (int)(tiles < sms ? tiles : sms);
+    if (partial && grid > kGradPartialRows) grid = kGradPartialRows;
     mlp_grad_kernel<<<grid, 128, kTrainSmem, st>>>(reinterpret_cast<const uint8_t *>(params),
                                                    reinterpret_cast<const __nv_bfloat16 *>(x), label, weight, n,
-                                                   grad, err);
+                                                   grad, partial, err);
+    if (partial) grad_reduce_kernel<<<(kNumParams + 1 + 255) / 256, 256, 0, st>>>(partial, grid, grad);
 }
 
 void launch_adam(float *master, float *m1, float *m2, const float *grad, void *blob, float lr, int step,

@@ -114,8 +114,11 @@ void set_first_wait_limit(int64_t polls);   // test hook of tfg_test_set_wait_li
 uint32_t first_wait_limit();                 // the current limit (polls) of a CTA's first completion wait
 int score_grid(int64_t tiles, int warpgroups);   // CTAs of a tile-pipeline launch (at most one per SM)
 int mlp_num_params();
+// partial (optional, [grad_partial_rows()][P + 1]): per-CTA rows added in CTA order (deterministic);
+// null: CTA totals added to grad by atomics (grad zeroed by the caller)
 void launch_mlp_grad(const void *params, const void *x, const float *label, const float *weight, int64_t n,
-                     float *grad, int *err, cudaStream_t st);
+                     float *grad, int *err, cudaStream_t st, float *partial = nullptr);
+int grad_partial_rows();
 void launch_adam(float *master, float *m1, float *m2, const float *grad, void *blob, float lr, int step,
                  cudaStream_t st);
 void launch_master_from_blob(const void *blob, float *master, float *m1, float *m2, cudaStream_t st);

@@ -66,6 +66,7 @@ class tfg_log_spec(ctypes.Structure):
 LOG_ENTRY_DTYPE = np.dtype([("feat", np.uint16, 32), ("label", np.float32), ("walker_id", np.uint32),
                             ("step", np.uint32), ("pad", np.uint32)])
 WINDOW = 256
+MLP_NUM_PARAMS = 32 * 128 + 128 * 128 + 3 * 128 + 1   # W1, W2, b1, b2, w3, b3 of the proposal network
 
 WALKER_INFO_DTYPE = np.dtype([("r", np.int32), ("best_r", np.int32), ("r_max", np.int32), ("format", np.int32),
                               ("t", np.int64), ("plateau", np.int64), ("best_t", np.int64),
@@ -352,7 +353,7 @@ def _vp(t):
 def tfg_mlp_grad(params, x, label, weight, stream=None):
     """Gradient (float32 [P]) and loss of the weighted logistic loss on (x, label, weight)."""
     import torch
-    P = (tfg_mlp_train_state_bytes() // 4 - 4) // 4
+    P = MLP_NUM_PARAMS
     grad = torch.empty(P + 1, dtype=torch.float32, device=x.device)
     err = torch.zeros(1, dtype=torch.int32, device=x.device)
     st = stream if stream is not None else torch.cuda.current_stream()
@@ -424,8 +425,8 @@ class MlpTrainer:
     step = tfg_mlp_train_step
 
     def loss(self) -> float:
-        P = self.state.numel() // 4 - 1
-        return float(self.state[3 * P + P].item())
+        P = MLP_NUM_PARAMS
+        return float(self.state[3 * P + P].item())   # the loss follows the gradient
 
 
 # ---------------------------------------------------------------------------------------------

@@ -140,3 +140,37 @@ def test_adam_step_matches_reference_elementwise():
     m32 = tr.state[:P].cpu().numpy()
     assert np.array_equal(blob[:2 * nw].view(np.uint16), mlp.bf16_bits(mlp.bf16_round(m32[:nw])))
     assert np.array_equal(blob[2 * nw:2 * nw + 4 * (P - nw)].view(np.float32), m32[nw:])
+
+
+def test_training_steps_are_bit_reproducible():
+    """The training step adds the per-CTA gradient rows in CTA order (no
+    floating-point atomics): two trainers started from the same parameters on
+    the same batches end with the same bits, and their gradients equal the
+    atomic-sum gradient of tfg_mlp_grad to rounding."""
+    import torch
+    rng = np.random.default_rng(5)
+    p = mlp.Params.random(rng, scale=0.5)
+    n = 128 * 300 + 17                      # more tiles than SMs, a ragged last tile
+    x = rng.integers(0, 9, size=(n, mlp.IN)).astype(np.float32)
+    label = (rng.random(n) < 0.3).astype(np.float32)
+    weight = np.full(n, 1.0 / n, np.float32)
+    xs, ls, ws = device_rows(x), torch.from_numpy(label).cuda(), torch.from_numpy(weight).cuda()
+    blobs, states = [], []
+    for _ in range(2):
+        params = device_params(p)
+        tr = tfg.MlpTrainer(params)
+        for _ in range(5):
+            tr.step(xs, ls, ws, 3e-3)
+        torch.cuda.synchronize()
+        blobs.append(params.cpu().numpy())
+        states.append(tr.state[: 4 * tfg.MLP_NUM_PARAMS + 1].cpu().numpy())
+    assert np.array_equal(blobs[0], blobs[1])
+    assert np.array_equal(states[0].view(np.uint32), states[1].view(np.uint32))
+    # the ordered gradient against the atomic-sum gradient at the same parameters
+    params = device_params(p)
+    tr = tfg.MlpTrainer(params)
+    tr.step(xs, ls, ws, 0.0)                 # lr 0: the parameters stay, the gradient is kept
+    g_det = tr.state[3 * tfg.MLP_NUM_PARAMS: 4 * tfg.MLP_NUM_PARAMS].cpu().numpy().astype(np.float64)
+    g_atom, _ = tfg.tfg_mlp_grad(params, xs, ls, ws)
+    g_atom = g_atom.cpu().numpy().astype(np.float64)
+    assert np.allclose(g_det, g_atom, rtol=1e-4, atol=1e-7 * np.abs(g_atom).max())
