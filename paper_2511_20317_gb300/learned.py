@@ -56,10 +56,16 @@ def collect(formats=TRAIN_FORMATS, walkers=4096, steps=4000, seed=100, neg_rate=
                         params=tfg.tfg_default_params(plateau_len=L))
         log = tfg.TransitionLog(walkers * steps // 20 + 100000, neg_thresh=int(neg_rate * 2**32), horizon=horizon)
         W.walk_window(steps, policy=0, log=log)
-        e = log.read()
-        entries.append(e)
+        entries.append(canonical_order(log.read()))
         W.close()
     return np.concatenate(entries)
+
+
+def canonical_order(entries):
+    """Log entries sorted by walker, step and label: the device appends them in
+    arrival order, which differs from run to run, and the training batches are
+    drawn from positions in this array."""
+    return entries[np.lexsort((entries["label"], entries["step"], entries["walker_id"]))]
 
 
 def train(entries, params=None, epochs=30, batch=8192, lr=2e-3, seed=0):
