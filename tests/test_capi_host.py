@@ -60,7 +60,8 @@ def test_error_codes():
     with pytest.raises(tfg.TfgError) as e:
         tfg.tfg_prepare((12, 12, 1), np.zeros((1, 144 + 12 + 12), np.int8))   # a factor of 144 > 128 entries
     assert e.value.code == tfg.TFG_EINVAL
-    assert not tfg.tfg_verify(fmt, s, mode=tfg.TFG_MODE_Z2) or True  # Strassen is also valid mod 2
+    assert tfg.tfg_verify(fmt, np.abs(s), mode=tfg.TFG_MODE_Z2)    # Strassen reduced mod 2 is a Z_2 scheme
+    assert not tfg.tfg_verify(fmt, s, mode=tfg.TFG_MODE_Z2)        # -1 is not a Z_2 coefficient
     with pytest.raises(tfg.TfgError) as e:
         tfg.tfg_project(fmt, s, 0, 5)
     assert e.value.code == tfg.TFG_EINVAL
